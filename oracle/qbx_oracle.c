@@ -1,0 +1,659 @@
+/*
+ * qbx_oracle.c -- plain, slow, FP64 CPU oracle for quadrature by expansion
+ * (QBX) applied to 2D Helmholtz layer potentials.
+ *
+ * TEST INFRASTRUCTURE ONLY.  The GPU library is checked against this file.
+ * Only the test suite, the smoke check and the benchmark's CPU-baseline leg
+ * may build, load or call it.  It shares no code, header, table or constant
+ * generator with the CUDA library, and it includes nothing from it.
+ *
+ * Method: Kloeckner, Barnett, Greengard, O'Neil, "Quadrature by Expansion: a
+ * new method for the evaluation of layer potentials" (arXiv:1207.4461).
+ *   Green's function       G(x,x') = (i/4) H0(k|x-x'|), Im k >= 0   (Sec. 1, eq. helmholtz-ker)
+ *   layer potentials       S sigma, D mu                           (Sec. 1, eqs. kernelint, kernelintd)
+ *   centres                c_j = x_j -/+ (h_m/2) n_j                (Sec. 3.3, step 4a)
+ *   S coefficients         Graf's addition theorem                 (Sec. 2, eqs. graf-coefficient, graf-addition)
+ *   D coefficients         normal derivative at the source         (Sec. 3.2, eq. graf-coefficient-dlp)
+ *   evaluation             local (Bessel) expansion                (Sec. 2, eq. local-exp; Sec. 3.3 step 4c)
+ *   target gradient        derivative of the local expansion       (Sec. 3.2)
+ *   jumps / PV / averaging                                          (Sec. 3.2, eqs. dlpjump, dlp-twosided)
+ *   source oversampling    interpolate density to a finer grid      (Sec. 3.4.2)
+ *   far targets            plain smooth quadrature                 (Sec. 1, Sec. 2)
+ *
+ * Phase convention (a reading of Sec. 2, eqs. graf-coefficient / local-exp):
+ *   alpha_l = (i/4) sum_s w_s sigma_s H_l(k rho_s) e^{-i l theta_s},
+ *   u(x)    = sum_{l=-p..p} alpha_l J_l(k rho) e^{+i l theta},
+ * where (rho_s, theta_s), (rho, theta) are polar coordinates of x_s - c and
+ * x - c.  The paper writes the same sum with l -> -l; since
+ * H_{-l} = (-1)^l H_l and J_{-l} = (-1)^l J_l, alpha^paper_{-l} = (-1)^l alpha_l
+ * and the potential is identical.
+ *
+ * Sums over sources run in source-index order.  OpenMP parallelises over
+ * centres / targets only, so results are bitwise independent of the number
+ * of threads.
+ */
+#include <complex.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef double complex cplx;
+
+#define ORC_PI 3.14159265358979323846264338327950288
+#define ORC_EULER_GAMMA 0.57721566490153286060651209008240243
+
+enum { OP_S = 0, OP_D = 1, OP_GRAD_S = 2 };
+enum { SIDE_INT = 0, SIDE_EXT = 1, SIDE_TWO = 2 };
+enum { LIMIT_ONE_SIDED = 0, LIMIT_PV = 1 };
+enum { WHAT_VALUE = 0, WHAT_GRAD = 1 };
+
+/* ------------------------------------------------------------------------- */
+/* Gauss-Legendre rule on [-1,1]: Newton's method on P_q, evaluated by the    */
+/* three-term recurrence (n+1)P_{n+1} = (2n+1) x P_n - n P_{n-1}.             */
+/* Starting guess cos(pi (i - 1/4)/(q + 1/2)).  Nodes ascending.              */
+/* w_i = 2 / ((1 - x_i^2) P_q'(x_i)^2).                                       */
+/* ------------------------------------------------------------------------- */
+static void legendre_eval(int q, double x, double *pq, double *dpq)
+{
+    double p0 = 1.0, p1 = x;
+    if (q == 0) { *pq = 1.0; *dpq = 0.0; return; }
+    for (int n = 1; n < q; ++n) {
+        double p2 = ((2.0 * n + 1.0) * x * p1 - n * p0) / (n + 1.0);
+        p0 = p1;
+        p1 = p2;
+    }
+    *pq = p1;
+    /* P_q'(x) = q (x P_q - P_{q-1}) / (x^2 - 1) */
+    *dpq = q * (x * p1 - p0) / (x * x - 1.0);
+}
+
+int orc_gauss_legendre(int q, double *nodes, double *weights)
+{
+    if (q < 1) return 1;
+    for (int i = 1; i <= q; ++i) {
+        double x = cos(ORC_PI * (i - 0.25) / (q + 0.5));
+        double pq, dpq;
+        for (int it = 0; it < 100; ++it) {
+            legendre_eval(q, x, &pq, &dpq);
+            double dx = pq / dpq;
+            x -= dx;
+            if (fabs(dx) < 1e-16) break;
+        }
+        legendre_eval(q, x, &pq, &dpq);
+        /* i = 1 is the largest node; store ascending */
+        nodes[q - i] = x;
+        weights[q - i] = 2.0 / ((1.0 - x * x) * dpq * dpq);
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Bessel and Hankel functions of the first kind, integer order, complex z   */
+/* with Im z >= 0, z != 0.                                                     */
+/*   |z| <  1e-3 : ascending series (DLMF 10.2.2, 10.8.1)                      */
+/*   |z| <= 25   : J_n by Miller's backward recurrence, normalised with        */
+/*                 J_0 + 2 sum_k J_2k = 1 (generating function, DLMF 10.12.4   */
+/*                 at t = 1); Y_0, Y_1 by Neumann series (DLMF 10.23.?, A&S   */
+/*                 9.1.88 and its derivative)                                  */
+/*   |z| >  25   : Hankel's asymptotic expansion (DLMF 10.17.5), truncated     */
+/*                 at the smallest term                                        */
+/* ------------------------------------------------------------------------- */
+#define ORC_MAXN 1024
+
+/* digamma at positive integers: psi(1) = -gamma, psi(m+1) = psi(m) + 1/m */
+static double psi_int(int m)
+{
+    double s = -ORC_EULER_GAMMA;
+    for (int j = 1; j < m; ++j) s += 1.0 / j;
+    return s;
+}
+
+static void jy01_series(cplx z, cplx *j0, cplx *j1, cplx *y0, cplx *y1)
+{
+    cplx t = -z * z / 4.0;
+    cplx lg = clog(z / 2.0);
+    cplx sj0 = 0, sj1 = 0, sy0 = 0, sy1 = 0;
+    cplx tk = 1.0;             /* t^k */
+    double fk = 1.0, fk1 = 1.0; /* k!, (k+1)! */
+    for (int k = 0; k < 40; ++k) {
+        if (k > 0) { fk *= k; fk1 *= (k + 1); }
+        cplx a0 = tk / (fk * fk);
+        cplx a1 = tk / (fk * fk1);
+        sj0 += a0;
+        sj1 += a1;
+        sy0 += psi_int(k + 1) * a0;
+        sy1 += (psi_int(k + 1) + psi_int(k + 2)) * a1;
+        if (cabs(a0) < 1e-20 * cabs(sj0) && k > 2) break;
+        tk *= t;
+    }
+    *j0 = sj0;
+    *j1 = (z / 2.0) * sj1;
+    *y0 = (2.0 / ORC_PI) * lg * (*j0) - (2.0 / ORC_PI) * sy0;
+    *y1 = -(2.0 / ORC_PI) / z + (2.0 / ORC_PI) * lg * (*j1) - (z / (2.0 * ORC_PI)) * sy1;
+}
+
+/* Miller: fills f[0..N] with J_0..J_N(z), N = returned start index (even). */
+static int miller_j(cplx z, int nmax, cplx *f)
+{
+    double az = cabs(z);
+    int N = nmax + 2 * (int)ceil(az) + 30;
+    if (N & 1) ++N;
+    if (N > ORC_MAXN - 2) N = ORC_MAXN - 2;
+    f[N + 1] = 0.0;
+    f[N] = 1e-30;
+    for (int n = N; n >= 1; --n) {
+        f[n - 1] = (2.0 * n / z) * f[n] - f[n + 1];
+        if (cabs(f[n - 1]) > 1e250) {           /* rescale to avoid overflow */
+            for (int m = n - 1; m <= N + 1; ++m) f[m] *= 1e-250;
+        }
+    }
+    cplx norm = f[0];
+    for (int m = 2; m <= N; m += 2) norm += 2.0 * f[m];
+    for (int m = 0; m <= N; ++m) f[m] /= norm;
+    return N;
+}
+
+static void jy01_miller(cplx z, cplx *j0, cplx *j1, cplx *y0, cplx *y1)
+{
+    cplx f[ORC_MAXN];
+    int N = miller_j(z, 2, f);
+    cplx lg = clog(z / 2.0) + ORC_EULER_GAMMA;
+    cplx s0 = 0, s1 = 0;
+    for (int k = 1; 2 * k + 1 <= N; ++k) {
+        double sg = (k & 1) ? -1.0 : 1.0;     /* (-1)^k */
+        s0 += sg * f[2 * k] / (double)k;
+        s1 += sg * (f[2 * k - 1] - f[2 * k + 1]) / (2.0 * k);
+    }
+    *j0 = f[0];
+    *j1 = f[1];
+    *y0 = (2.0 / ORC_PI) * lg * f[0] - (4.0 / ORC_PI) * s0;
+    *y1 = -(2.0 / ORC_PI) * f[0] / z + (2.0 / ORC_PI) * lg * f[1] + (4.0 / ORC_PI) * s1;
+}
+
+/* DLMF 10.17.5: H_nu(z) ~ sqrt(2/(pi z)) e^{i w} sum_k i^k a_k(nu) / z^k,
+ * w = z - nu pi/2 - pi/4, a_k(nu) = prod_{j=1..k} (4 nu^2 - (2j-1)^2) / (k! 8^k). */
+static cplx hankel_asymptotic(cplx z, int nu)
+{
+    double mu = 4.0 * nu * nu;
+    cplx sum = 1.0, term = 1.0;
+    double prev = 1.0;
+    for (int k = 1; k < 200; ++k) {
+        double a = (mu - (2.0 * k - 1.0) * (2.0 * k - 1.0)) / (8.0 * k);
+        cplx next = term * (I * a / z);
+        double mag = cabs(next);
+        if (mag >= prev) break;                 /* smallest term reached */
+        term = next;
+        sum += term;
+        prev = mag;
+        if (mag < 1e-18 * cabs(sum)) break;
+    }
+    cplx w = z - nu * ORC_PI / 2.0 - ORC_PI / 4.0;
+    return csqrt(2.0 / (ORC_PI * z)) * cexp(I * w) * sum;
+}
+
+void orc_hankel01(cplx z, cplx *h0, cplx *h1)
+{
+    double az = cabs(z);
+    if (az > 25.0) {
+        *h0 = hankel_asymptotic(z, 0);
+        *h1 = hankel_asymptotic(z, 1);
+        return;
+    }
+    cplx j0, j1, y0, y1;
+    if (az < 1e-3) jy01_series(z, &j0, &j1, &y0, &y1);
+    else jy01_miller(z, &j0, &j1, &y0, &y1);
+    *h0 = j0 + I * y0;
+    *h1 = j1 + I * y1;
+}
+
+/* H_0..H_n by the upward recurrence H_{l+1} = (2l/z) H_l - H_{l-1}. */
+void orc_hankel_seq(cplx z, int n, cplx *h)
+{
+    cplx h0, h1;
+    orc_hankel01(z, &h0, &h1);
+    h[0] = h0;
+    if (n >= 1) h[1] = h1;
+    for (int l = 1; l < n; ++l) h[l + 1] = (2.0 * l / z) * h[l] - h[l - 1];
+}
+
+/* J_0..J_n: ascending series J_l = sum_m (-1)^m (z/2)^{2m+l} / (m! (m+l)!) for
+ * |z| <= 4 (DLMF 10.2.2), otherwise Miller's algorithm. */
+void orc_besselj_seq(cplx z, int n, cplx *j)
+{
+    if (cabs(z) <= 4.0) {
+        cplx hz = z / 2.0, t = -hz * hz;
+        cplx hzl = 1.0;      /* (z/2)^l / l! */
+        for (int l = 0; l <= n; ++l) {
+            if (l > 0) hzl *= hz / (double)l;
+            cplx term = hzl, sum = hzl;
+            for (int m = 1; m < 200; ++m) {
+                term *= t / ((double)m * (double)(m + l));
+                sum += term;
+                if (cabs(term) < 1e-20 * cabs(sum)) break;
+            }
+            j[l] = sum;
+        }
+        return;
+    }
+    cplx f[ORC_MAXN];
+    miller_j(z, n, f);
+    for (int l = 0; l <= n; ++l) j[l] = f[l];
+}
+
+/* Convenience for testing: H0, H1 at an array of points. */
+void orc_hankel01_array(int n, const double *zin, double *h0out, double *h1out)
+{
+    for (int i = 0; i < n; ++i) {
+        cplx z = zin[2 * i] + I * zin[2 * i + 1];
+        cplx a, b;
+        orc_hankel01(z, &a, &b);
+        h0out[2 * i] = creal(a); h0out[2 * i + 1] = cimag(a);
+        h1out[2 * i] = creal(b); h1out[2 * i + 1] = cimag(b);
+    }
+}
+
+void orc_hankel_seq_array(int n, const double *zin, int nmax, double *hout)
+{
+    cplx h[ORC_MAXN];
+    for (int i = 0; i < n; ++i) {
+        cplx z = zin[2 * i] + I * zin[2 * i + 1];
+        orc_hankel_seq(z, nmax, h);
+        for (int l = 0; l <= nmax; ++l) {
+            hout[2 * (i * (nmax + 1) + l)] = creal(h[l]);
+            hout[2 * (i * (nmax + 1) + l) + 1] = cimag(h[l]);
+        }
+    }
+}
+
+void orc_besselj_seq_array(int n, const double *zin, int nmax, double *jout)
+{
+    cplx j[ORC_MAXN];
+    for (int i = 0; i < n; ++i) {
+        cplx z = zin[2 * i] + I * zin[2 * i + 1];
+        orc_besselj_seq(z, nmax, j);
+        for (int l = 0; l <= nmax; ++l) {
+            jout[2 * (i * (nmax + 1) + l)] = creal(j[l]);
+            jout[2 * (i * (nmax + 1) + l) + 1] = cimag(j[l]);
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Geometry (Sec. 3.3, "informal description"; Sec. 4.1 discretisation).     */
+/* Panel m spans [t_m, t_{m+1}] of the curve parameter.  The caller samples   */
+/* gamma and gamma' at the q-node Gauss-Legendre points of every panel.       */
+/*   n = (gamma'_y, -gamma'_x)/|gamma'|   outward for a counter-clockwise      */
+/*        curve (Sec. 3.2: n = (t_2, -t_1))                                   */
+/*   w = w^GL (t_{m+1}-t_m)/2 |gamma'|    arc-length quadrature weight         */
+/*   h_m = sum of the panel's source weights (arc length of the panel)        */
+/*   r_m = r_factor h_m (Sec. 3.3 step 3: r_m = h_m/2)                         */
+/*   c   = x - r_m n (interior side), x + r_m n (exterior side)  (step 4a)    */
+/*   ratio = min_s |x_s - c| / r_m  (Graf validity, eq. x-c-closest)          */
+/* Centre arrays have length 2*n_tgt: interior centres first, then exterior.  */
+/* ------------------------------------------------------------------------- */
+int orc_geometry(int M, int q_tgt, int q_src, const double *t_edges,
+                 const double *gam_tgt, const double *dgam_tgt,
+                 const double *gam_src, const double *dgam_src,
+                 double r_factor,
+                 double *src_x, double *src_y, double *src_nx, double *src_ny, double *src_w,
+                 double *tgt_x, double *tgt_y, double *tgt_nx, double *tgt_ny, double *tgt_w,
+                 double *panel_h,
+                 double *ctr_x, double *ctr_y, double *ctr_r, double *ctr_ratio)
+{
+    double xt[ORC_MAXN], wt[ORC_MAXN], xs[ORC_MAXN], ws[ORC_MAXN];
+    if (q_tgt < 1 || q_src < 1 || q_tgt > ORC_MAXN || q_src > ORC_MAXN) return 1;
+    orc_gauss_legendre(q_tgt, xt, wt);
+    orc_gauss_legendre(q_src, xs, ws);
+    int n_tgt = M * q_tgt, n_src = M * q_src;
+    for (int m = 0; m < M; ++m) {
+        double half = 0.5 * (t_edges[m + 1] - t_edges[m]);
+        double h = 0.0;
+        for (int j = 0; j < q_src; ++j) {
+            int s = m * q_src + j;
+            double dx = dgam_src[2 * s], dy = dgam_src[2 * s + 1];
+            double sp = sqrt(dx * dx + dy * dy);
+            src_x[s] = gam_src[2 * s];
+            src_y[s] = gam_src[2 * s + 1];
+            src_nx[s] = dy / sp;
+            src_ny[s] = -dx / sp;
+            src_w[s] = ws[j] * half * sp;
+            h += src_w[s];
+        }
+        panel_h[m] = h;
+        for (int i = 0; i < q_tgt; ++i) {
+            int t = m * q_tgt + i;
+            double dx = dgam_tgt[2 * t], dy = dgam_tgt[2 * t + 1];
+            double sp = sqrt(dx * dx + dy * dy);
+            tgt_x[t] = gam_tgt[2 * t];
+            tgt_y[t] = gam_tgt[2 * t + 1];
+            tgt_nx[t] = dy / sp;
+            tgt_ny[t] = -dx / sp;
+            tgt_w[t] = wt[i] * half * sp;
+            double r = r_factor * h;
+            ctr_x[t] = tgt_x[t] - r * tgt_nx[t];
+            ctr_y[t] = tgt_y[t] - r * tgt_ny[t];
+            ctr_r[t] = r;
+            ctr_x[n_tgt + t] = tgt_x[t] + r * tgt_nx[t];
+            ctr_y[n_tgt + t] = tgt_y[t] + r * tgt_ny[t];
+            ctr_r[n_tgt + t] = r;
+        }
+    }
+    #pragma omp parallel for schedule(static)
+    for (int c = 0; c < 2 * n_tgt; ++c) {
+        double best = INFINITY;
+        for (int s = 0; s < n_src; ++s) {
+            double d = hypot(src_x[s] - ctr_x[c], src_y[s] - ctr_y[c]);
+            if (d < best) best = d;
+        }
+        ctr_ratio[c] = best / ctr_r[c];
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Source oversampling (Sec. 3.4.2): per panel, interpolate the density from  */
+/* the q_tgt target nodes to the q_src source nodes with the barycentric      */
+/* Lagrange formula (second form; Berrut & Trefethen, SIAM Review 2004), then */
+/* multiply by the source weights: wdens_s = w_s sigma(x_s).                  */
+/* Densities are [n][nrhs] complex, row-major.                                */
+/* ------------------------------------------------------------------------- */
+int orc_upsample(int M, int q_tgt, int q_src, int nrhs, const double *src_w,
+                 const cplx *dens_tgt, cplx *wdens_src)
+{
+    double xt[ORC_MAXN], wt[ORC_MAXN], xs[ORC_MAXN], ws[ORC_MAXN], lam[ORC_MAXN];
+    if (q_tgt < 1 || q_src < 1 || q_tgt > ORC_MAXN || q_src > ORC_MAXN) return 1;
+    orc_gauss_legendre(q_tgt, xt, wt);
+    orc_gauss_legendre(q_src, xs, ws);
+    for (int i = 0; i < q_tgt; ++i) {
+        double pr = 1.0;
+        for (int k = 0; k < q_tgt; ++k) if (k != i) pr *= (xt[i] - xt[k]);
+        lam[i] = 1.0 / pr;
+    }
+    for (int m = 0; m < M; ++m) {
+        for (int j = 0; j < q_src; ++j) {
+            int s = m * q_src + j;
+            int exact = -1;
+            for (int i = 0; i < q_tgt; ++i) if (xs[j] == xt[i]) exact = i;
+            for (int r = 0; r < nrhs; ++r) {
+                cplx val;
+                if (exact >= 0) {
+                    val = dens_tgt[(m * q_tgt + exact) * nrhs + r];
+                } else {
+                    cplx num = 0.0;
+                    double den = 0.0;
+                    for (int i = 0; i < q_tgt; ++i) {
+                        double c = lam[i] / (xs[j] - xt[i]);
+                        num += c * dens_tgt[(m * q_tgt + i) * nrhs + r];
+                        den += c;
+                    }
+                    val = num / den;
+                }
+                wdens_src[s * nrhs + r] = src_w[s] * val;
+            }
+        }
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Expansion coefficients (Sec. 3.3 step 4b), literal double loop.            */
+/*   S: alpha_l   = (i/4) sum_s wdens_s H_l(k rho_s) e^{-i l theta_s}          */
+/*      (Sec. 2, eq. graf-coefficient with l -> -l)                            */
+/*   D: alpha^D_l = (i/4) sum_s wdens_s  n_s . grad_{x_s} [H_l(k rho_s) e^{-i l theta_s}] */
+/*      (Sec. 3.2, eq. graf-coefficient-dlp).  With F_m(y) = H_m(k|y|) e^{i m arg y}, */
+/*      H_l e^{-i l theta} = (-1)^l F_{-l}, and (DLMF 10.6.2 in polar form)     */
+/*      n . grad F_m = (k/2) [ nu F_{m-1} - conj(nu) F_{m+1} ],  nu = n_x + i n_y. */
+/* alpha is [n_ctr][2p+1][nrhs], index l + p.                                  */
+/* ------------------------------------------------------------------------- */
+static cplx F_m(int m, const cplx *H, double theta)
+{
+    int am = m < 0 ? -m : m;
+    cplx h = H[am];
+    if (m < 0 && (am & 1)) h = -h;           /* H_{-m} = (-1)^m H_m */
+    return h * cexp(I * (double)m * theta);
+}
+
+int orc_form_locals(int kind, int n_ctr, const double *ctr_x, const double *ctr_y,
+                    int n_src, const double *src_x, const double *src_y,
+                    const double *src_nx, const double *src_ny,
+                    const cplx *wdens, int nrhs, double kre, double kim, int p,
+                    cplx *alpha)
+{
+    cplx k = kre + I * kim;
+    if (p < 0 || p + 2 >= ORC_MAXN) return 1;
+    int nl = 2 * p + 1;
+    #pragma omp parallel for schedule(dynamic, 4)
+    for (int c = 0; c < n_ctr; ++c) {
+        cplx H[ORC_MAXN];
+        cplx *a = alpha + (size_t)c * nl * nrhs;
+        for (int i = 0; i < nl * nrhs; ++i) a[i] = 0.0;
+        for (int s = 0; s < n_src; ++s) {
+            double dx = src_x[s] - ctr_x[c], dy = src_y[s] - ctr_y[c];
+            double rho = hypot(dx, dy);
+            double theta = atan2(dy, dx);
+            orc_hankel_seq(k * rho, p + 1, H);
+            cplx nu = src_nx[s] + I * src_ny[s];
+            for (int l = -p; l <= p; ++l) {
+                cplx kern;
+                if (kind == OP_D) {
+                    double sg = (l & 1) ? -1.0 : 1.0;   /* (-1)^l */
+                    kern = sg * (k / 2.0) * (nu * F_m(-l - 1, H, theta) - conj(nu) * F_m(-l + 1, H, theta));
+                } else {
+                    int al = l < 0 ? -l : l;
+                    cplx hl = H[al];
+                    if (l < 0 && (al & 1)) hl = -hl;
+                    kern = hl * cexp(-I * (double)l * theta);
+                }
+                for (int r = 0; r < nrhs; ++r)
+                    a[(l + p) * nrhs + r] += (I / 4.0) * wdens[(size_t)s * nrhs + r] * kern;
+            }
+        }
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Evaluation of the local expansion (Sec. 2 eq. local-exp, Sec. 3.3 step 4c) */
+/*   u = sum_{l=-p..p} alpha_l J_l(k rho) e^{i l theta}                        */
+/* and its target gradient (Sec. 3.2: differentiate the expansion), through    */
+/*   (d_x + i d_y)[J_l e^{i l th}] = -k J_{l+1} e^{i(l+1)th}                   */
+/*   (d_x - i d_y)[J_l e^{i l th}] =  k J_{l-1} e^{i(l-1)th}   (DLMF 10.6.2)   */
+/* so d_x u = (U+ + U-)/2, d_y u = (U+ - U-)/(2i).                             */
+/* Target e is evaluated from centre ectr[e]; out is [n_eval][nrhs] (VALUE) or */
+/* [n_eval][2][nrhs] (GRAD: d_x then d_y).                                     */
+/* ------------------------------------------------------------------------- */
+static cplx J_signed(int l, const cplx *J)
+{
+    int al = l < 0 ? -l : l;
+    cplx j = J[al];
+    if (l < 0 && (al & 1)) j = -j;           /* J_{-l} = (-1)^l J_l */
+    return j;
+}
+
+int orc_eval_locals(int n_eval, const double *ex, const double *ey, const int *ectr,
+                    const double *ctr_x, const double *ctr_y,
+                    const cplx *alpha, int nrhs, double kre, double kim, int p,
+                    int what, cplx *out)
+{
+    cplx k = kre + I * kim;
+    int nl = 2 * p + 1;
+    if (p < 0 || p + 2 >= ORC_MAXN) return 1;
+    #pragma omp parallel for schedule(static)
+    for (int e = 0; e < n_eval; ++e) {
+        cplx J[ORC_MAXN];
+        int c = ectr[e];
+        double dx = ex[e] - ctr_x[c], dy = ey[e] - ctr_y[c];
+        double rho = hypot(dx, dy), theta = atan2(dy, dx);
+        orc_besselj_seq(k * rho, p + 1, J);
+        const cplx *a = alpha + (size_t)c * nl * nrhs;
+        for (int r = 0; r < nrhs; ++r) {
+            if (what == WHAT_GRAD) {
+                cplx up = 0.0, um = 0.0;
+                for (int l = -p; l <= p; ++l) {
+                    cplx al = a[(l + p) * nrhs + r];
+                    up += al * (-k) * J_signed(l + 1, J) * cexp(I * (double)(l + 1) * theta);
+                    um += al * k * J_signed(l - 1, J) * cexp(I * (double)(l - 1) * theta);
+                }
+                out[((size_t)e * 2 + 0) * nrhs + r] = (up + um) / 2.0;
+                out[((size_t)e * 2 + 1) * nrhs + r] = (up - um) / (2.0 * I);
+            } else {
+                cplx u = 0.0;
+                for (int l = -p; l <= p; ++l)
+                    u += a[(l + p) * nrhs + r] * J_signed(l, J) * cexp(I * (double)l * theta);
+                out[(size_t)e * nrhs + r] = u;
+            }
+        }
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Full on-surface apply, Sec. 3.3: upsample, coefficients at every centre of  */
+/* the requested side(s), evaluation at the centre's own target, and the jump */
+/* step 5 (Sec. 3.2):                                                          */
+/*   S:      continuous, no correction                                         */
+/*   D:      PV = lim_{+-} D mu  -/+ mu/2            (eq. dlpjump)             */
+/*   grad S: PV = lim_{+-} grad S sigma +/- n sigma/2                          */
+/*   two-sided: PV = (lim_+ + lim_-)/2                (eq. dlp-twosided)        */
+/* (+ = exterior side, - = interior side).  Output [n_tgt][nrhs] for S and D,  */
+/* [n_tgt][2][nrhs] for grad S.  If sel != NULL only the n_sel targets sel[i]  */
+/* are computed and output row i belongs to target sel[i].                      */
+/* ------------------------------------------------------------------------- */
+int orc_apply(int op, int side, int limit, double kre, double kim, int p,
+              int M, int q_tgt, int q_src,
+              const double *src_x, const double *src_y, const double *src_nx,
+              const double *src_ny, const double *src_w,
+              const double *tgt_x, const double *tgt_y, const double *tgt_nx,
+              const double *tgt_ny,
+              const double *ctr_x, const double *ctr_y,
+              const cplx *dens_tgt, int nrhs, int n_sel, const int *sel, cplx *out)
+{
+    int n_tgt = M * q_tgt, n_src = M * q_src, nl = 2 * p + 1;
+    int ncomp = (op == OP_GRAD_S) ? 2 : 1;
+    if (n_sel <= 0 || !sel) n_sel = n_tgt, sel = NULL;
+    cplx *wd = malloc(sizeof(cplx) * (size_t)n_src * nrhs);
+    cplx *alpha = malloc(sizeof(cplx) * (size_t)n_sel * nl * nrhs);
+    cplx *val = malloc(sizeof(cplx) * (size_t)n_sel * ncomp * nrhs);
+    int *ectr = malloc(sizeof(int) * (size_t)n_sel);
+    double *cx = malloc(sizeof(double) * (size_t)n_sel), *cy = malloc(sizeof(double) * (size_t)n_sel);
+    double *ex = malloc(sizeof(double) * (size_t)n_sel), *ey = malloc(sizeof(double) * (size_t)n_sel);
+    if (!wd || !alpha || !val || !ectr || !cx || !cy || !ex || !ey) {
+        free(wd); free(alpha); free(val); free(ectr); free(cx); free(cy); free(ex); free(ey);
+        return 2;
+    }
+    orc_upsample(M, q_tgt, q_src, nrhs, src_w, dens_tgt, wd);
+    for (size_t i = 0; i < (size_t)n_sel * ncomp * nrhs; ++i) out[i] = 0.0;
+    int s0 = (side == SIDE_TWO) ? SIDE_INT : side;
+    int s1 = (side == SIDE_TWO) ? SIDE_EXT : side;
+    for (int sd = s0; sd <= s1; ++sd) {
+        for (int i = 0; i < n_sel; ++i) {
+            int t = sel ? sel[i] : i;
+            cx[i] = ctr_x[(size_t)sd * n_tgt + t];
+            cy[i] = ctr_y[(size_t)sd * n_tgt + t];
+            ex[i] = tgt_x[t];
+            ey[i] = tgt_y[t];
+            ectr[i] = i;
+        }
+        orc_form_locals(op == OP_D ? OP_D : OP_S, n_sel, cx, cy, n_src, src_x, src_y,
+                        src_nx, src_ny, wd, nrhs, kre, kim, p, alpha);
+        orc_eval_locals(n_sel, ex, ey, ectr, cx, cy, alpha, nrhs, kre, kim, p,
+                        op == OP_GRAD_S ? WHAT_GRAD : WHAT_VALUE, val);
+        double sgn = (sd == SIDE_EXT) ? 1.0 : -1.0;    /* +1 exterior, -1 interior */
+        for (int i = 0; i < n_sel; ++i) {
+            int t = sel ? sel[i] : i;
+            for (int r = 0; r < nrhs; ++r) {
+                cplx dens = dens_tgt[(size_t)t * nrhs + r];
+                if (op == OP_GRAD_S) {
+                    cplx gx = val[((size_t)i * 2 + 0) * nrhs + r];
+                    cplx gy = val[((size_t)i * 2 + 1) * nrhs + r];
+                    if (side != SIDE_TWO && limit == LIMIT_PV) {
+                        gx += sgn * 0.5 * tgt_nx[t] * dens;
+                        gy += sgn * 0.5 * tgt_ny[t] * dens;
+                    }
+                    if (side == SIDE_TWO) { gx *= 0.5; gy *= 0.5; }
+                    out[((size_t)i * 2 + 0) * nrhs + r] += gx;
+                    out[((size_t)i * 2 + 1) * nrhs + r] += gy;
+                } else {
+                    cplx u = val[(size_t)i * nrhs + r];
+                    if (op == OP_D && side != SIDE_TWO && limit == LIMIT_PV) u -= sgn * 0.5 * dens;
+                    if (side == SIDE_TWO) u *= 0.5;
+                    out[(size_t)i * nrhs + r] += u;
+                }
+            }
+        }
+    }
+    free(wd); free(alpha); free(val); free(ectr); free(cx); free(cy); free(ex); free(ey);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Far targets: the plain smooth quadrature rule (Sec. 1; Sec. 2 "high-       */
+/* accuracy region").  With d = |x - x_s|:                                     */
+/*   S      = (i/4) sum_s wdens_s H0(k d)                                      */
+/*   D      = (i/4) sum_s wdens_s n_s . grad_{x_s} H0(k|x - x_s|)              */
+/*          = (i k/4) sum_s wdens_s H1(k d) ((x - x_s) . n_s) / d              */
+/*   grad S = (i/4) sum_s wdens_s grad_x H0(k d) = -(i k/4) sum_s wdens_s H1(k d) (x - x_s)/d */
+/* Output [n][nrhs] or [n][2][nrhs].                                           */
+/* ------------------------------------------------------------------------- */
+int orc_far(int op, int n_far, const double *xy, int n_src,
+            const double *src_x, const double *src_y, const double *src_nx, const double *src_ny,
+            const cplx *wdens, int nrhs, double kre, double kim, cplx *out)
+{
+    cplx k = kre + I * kim;
+    #pragma omp parallel for schedule(static)
+    for (int e = 0; e < n_far; ++e) {
+        int ncomp = (op == OP_GRAD_S) ? 2 : 1;
+        for (int i = 0; i < ncomp * nrhs; ++i) out[(size_t)e * ncomp * nrhs + i] = 0.0;
+        for (int s = 0; s < n_src; ++s) {
+            double rx = xy[2 * e] - src_x[s], ry = xy[2 * e + 1] - src_y[s];
+            double d = hypot(rx, ry);
+            cplx h0, h1;
+            orc_hankel01(k * d, &h0, &h1);
+            for (int r = 0; r < nrhs; ++r) {
+                cplx wdv = wdens[(size_t)s * nrhs + r];
+                if (op == OP_S) {
+                    out[(size_t)e * nrhs + r] += (I / 4.0) * wdv * h0;
+                } else if (op == OP_D) {
+                    out[(size_t)e * nrhs + r] += (I * k / 4.0) * wdv * h1 * (rx * src_nx[s] + ry * src_ny[s]) / d;
+                } else {
+                    out[((size_t)e * 2 + 0) * nrhs + r] += -(I * k / 4.0) * wdv * h1 * rx / d;
+                    out[((size_t)e * 2 + 1) * nrhs + r] += -(I * k / 4.0) * wdv * h1 * ry / d;
+                }
+            }
+        }
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Which centre serves an off-surface point (Sec. 2: a point inside a disk    */
+/* uses that disk's expansion; otherwise it is in the high-accuracy region of */
+/* the smooth rule).  Reading: among centres [c0, c1) with |x - c| <= r_c,     */
+/* pick the smallest |x - c|/r_c, ties to the lowest index; -1 if none.        */
+/* ------------------------------------------------------------------------- */
+int orc_assign_centres(int n, const double *xy, int c0, int c1,
+                       const double *ctr_x, const double *ctr_y, const double *ctr_r,
+                       int *out)
+{
+    #pragma omp parallel for schedule(static)
+    for (int e = 0; e < n; ++e) {
+        int best = -1;
+        double bestq = INFINITY;
+        for (int c = c0; c < c1; ++c) {
+            double q = hypot(xy[2 * e] - ctr_x[c], xy[2 * e + 1] - ctr_y[c]) / ctr_r[c];
+            if (q <= 1.0 && q < bestq) { bestq = q; best = c; }
+        }
+        out[e] = best;
+    }
+    return 0;
+}
+
+int orc_num_threads(void)
+{
+#ifdef _OPENMP
+    extern int omp_get_max_threads(void);
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

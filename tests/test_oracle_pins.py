@@ -1,0 +1,438 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: library
+routines (numpy, scipy, mpmath), closed forms (Graf's addition theorem, the
+circle eigenvalues, Green's representation formula), the jump relations, the
+error behaviour of Theorem 1, and brute force at 30 digits on tiny inputs.
+"""
+import math
+
+import numpy as np
+import pytest
+import scipy.special as sp
+
+import oracle
+import workloads as W
+
+OP_S, OP_D, OP_G = oracle.OP_S, oracle.OP_D, oracle.OP_GRAD_S
+INT, EXT, TWO = oracle.SIDE_INT, oracle.SIDE_EXT, oracle.SIDE_TWO
+ONE, PV = oracle.LIMIT_ONE_SIDED, oracle.LIMIT_PV
+
+
+def relerr(a, b):
+    return np.abs(np.asarray(a) - np.asarray(b)).max() / np.abs(np.asarray(b)).max()
+
+
+# ---------------------------------------------------------------------------
+# Gauss-Legendre rule
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("q", [1, 2, 5, 16, 17, 64])
+def test_gl_rule(q):
+    x, w = oracle.gauss_legendre(q)
+    assert abs(w.sum() - 2.0) < 1e-14
+    assert np.all(np.diff(x) > 0)
+    for m in range(2 * q):
+        exact = 2.0 / (m + 1) if m % 2 == 0 else 0.0
+        assert abs((w * x ** m).sum() - exact) < 2e-14, m
+    # nodes are the zeros of P_q
+    c = np.zeros(q + 1)
+    c[q] = 1.0
+    assert np.abs(np.polynomial.legendre.legval(x, c)).max() < 1e-13
+    xn, wn = np.polynomial.legendre.leggauss(q)
+    assert np.abs(x - xn).max() < 1e-15 and np.abs(w - wn).max() < 1e-14
+
+
+# ---------------------------------------------------------------------------
+# Bessel / Hankel functions
+# ---------------------------------------------------------------------------
+def _mp_ref(n, z):
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 30
+    return complex(mp.hankel1(n, mp.mpc(z.real, z.imag))), complex(mp.besselj(n, mp.mpc(z.real, z.imag)))
+
+
+REAL_Z = np.concatenate([np.logspace(-4, np.log10(200), 60), [0.999e-3, 1.001e-3, 24.99, 25.01]])
+CPLX_Z = np.array([0.3 + 0.1j, 1 + 0.5j, 2.5 + 1j, 5 + 0.5j, 7 + 2j, 12 + 1.5j, 20 + 0.5j, 24 + 2j,
+                   26 + 1j, 40 + 2j, 1e-3 + 1e-3j, 3 + 2.5j])
+
+
+def test_hankel_real_vs_mpmath():
+    # forming the phase z - pi/4 in FP64 costs up to an ulp of z: bound ~ eps |z|
+    h0, h1 = oracle.hankel01(REAL_Z.astype(complex))
+    for i, z in enumerate(REAL_Z):
+        r0, _ = _mp_ref(0, complex(z))
+        r1, _ = _mp_ref(1, complex(z))
+        tol = 2e-15 * max(1.0, z / 8)
+        assert abs(h0[i] - r0) <= tol * abs(r0), z
+        assert abs(h1[i] - r1) <= tol * abs(r1), z
+
+
+def test_hankel_complex_vs_mpmath():
+    # J + iY cancels by e^{2 Im z} when Im z > 0; the bound reflects it.
+    h0, h1 = oracle.hankel01(CPLX_Z)
+    for i, z in enumerate(CPLX_Z):
+        r0, _ = _mp_ref(0, z)
+        r1, _ = _mp_ref(1, z)
+        tol = 4e-15 * math.exp(2 * z.imag) * max(1.0, abs(z) / 8)
+        assert abs(h0[i] - r0) <= tol * abs(r0), z
+        assert abs(h1[i] - r1) <= tol * abs(r1), z
+
+
+def test_hankel_vs_scipy_grid():
+    z = np.concatenate([np.linspace(0.01, 100, 997), np.linspace(0.05, 30, 101) + 0.7j])
+    h0, h1 = oracle.hankel01(z)
+    assert relerr(h0, sp.hankel1(0, z)) < 1e-13
+    assert relerr(h1, sp.hankel1(1, z)) < 1e-13
+
+
+def test_wronskian_and_neumann_sum():
+    z = np.linspace(0.05, 60, 400)
+    h0, h1 = oracle.hankel01(z.astype(complex))
+    J0, Y0, J1, Y1 = h0.real, h0.imag, h1.real, h1.imag
+    # J1 Y0 - J0 Y1 = 2/(pi z)  (DLMF 10.5.2)
+    w = J1 * Y0 - J0 * Y1
+    assert np.abs(w - 2 / (math.pi * z)).max() < 1e-14 * np.abs(2 / (math.pi * z)).max() * 50
+    J = oracle.besselj_seq(z.astype(complex), 120)
+    s = J[:, 0] + 2 * J[:, 2::2].sum(axis=1)
+    assert np.abs(s - 1).max() < 1e-14
+
+
+def test_besselj_seq_vs_scipy():
+    z = np.concatenate([np.linspace(0.001, 20, 300), np.linspace(0.1, 8, 40) + 0.3j])
+    J = oracle.besselj_seq(z, 25)
+    # |J_n(z)| <= e^{|Im z|}: absolute accuracy of a few eps on that scale
+    for n in range(26):
+        ref = sp.jv(n, z)
+        assert np.all(np.abs(J[:, n] - ref) <= 2e-15 * np.exp(np.abs(z.imag))), n
+
+
+def test_hankel_seq_recurrence_vs_mpmath():
+    for z in (0.4, 3.0, 11.0, 2 + 0.3j):
+        H = oracle.hankel_seq(complex(z), 20)[0]
+        for n in (0, 5, 12, 20):
+            r, _ = _mp_ref(n, complex(z))
+            assert abs(H[n] - r) <= 1e-13 * abs(r), (z, n)
+
+
+# ---------------------------------------------------------------------------
+# Tiny geometries built by hand
+# ---------------------------------------------------------------------------
+def point_geom(cx, cy, sources, normals=None):
+    """One centre and explicit sources (weights folded into the density)."""
+    s = np.asarray(sources, dtype=float).reshape(-1, 2)
+    n = np.asarray(normals if normals is not None else np.zeros_like(s), dtype=float).reshape(-1, 2)
+    return {"ctr_x": np.array([cx, cx]), "ctr_y": np.array([cy, cy]), "n_tgt": 1, "n_src": len(s),
+            "src_x": s[:, 0].copy(), "src_y": s[:, 1].copy(), "src_nx": n[:, 0].copy(),
+            "src_ny": n[:, 1].copy()}
+
+
+@pytest.mark.parametrize("k", [5.0, 5 + 0.5j, 0.7])
+def test_graf_single_layer(k):
+    """Pin (1): Graf's addition theorem (Sec. 2, eq. graf-addition): for one
+    source with unit weight, sum_l alpha_l J_l e^{il theta} -> (i/4) H0(k|x - x'|)
+    whenever |x - c| < |x' - c| (eq. x-c-closest)."""
+    rng = np.random.default_rng(1)
+    src = np.array([[0.9, 0.4]])
+    g = point_geom(0.0, 0.0, src)
+    alpha = oracle.form_locals(g, OP_S, INT, k, 40, np.array([1.0 + 0j]))
+    for _ in range(20):
+        rad = rng.uniform(0, 0.55) * np.hypot(*src[0])
+        th = rng.uniform(0, 2 * np.pi)
+        x = np.array([rad * np.cos(th), rad * np.sin(th)])
+        u = oracle.eval_locals(g, INT, k, 40, alpha, 0, np.array([x[0]]), np.array([x[1]]), np.array([0]))
+        d = np.hypot(*(x - src[0]))
+        ref = 0.25j * sp.hankel1(0, k * d)
+        # 81 terms of size up to |H_l J_l|/4 ~ 0.1: rounding ~ 1e-14 absolute
+        assert abs(u[0, 0] - ref) < 1e-13
+
+
+@pytest.mark.parametrize("k", [5.0, 3 + 0.3j])
+def test_graf_double_layer_and_gradient(k):
+    """Pin (1) for D and grad S: the D coefficients (eq. graf-coefficient-dlp)
+    reproduce (i/4) n'.grad_{x'} H0(k|x-x'|) = (ik/4) H1(kd) (x-x').n'/d, and
+    the differentiated expansion reproduces grad_x (i/4) H0 = -(ik/4) H1 (x-x')/d."""
+    src = np.array([[-0.3, 0.8]])
+    nrm = np.array([[np.cos(0.7), np.sin(0.7)]])
+    g = point_geom(0.0, 0.0, src, nrm)
+    aD = oracle.form_locals(g, OP_D, INT, k, 40, np.array([1.0 + 0j]))
+    aS = oracle.form_locals(g, OP_S, INT, k, 40, np.array([1.0 + 0j]))
+    for x in ([0.2, -0.1], [-0.1, 0.35], [0.0, 0.0], [0.3, 0.2]):
+        x = np.array(x)
+        r = x - src[0]
+        d = np.hypot(*r)
+        uD = oracle.eval_locals(g, INT, k, 40, aD, 0, x[:1], x[1:], np.array([0]))[0, 0]
+        refD = 0.25j * k * sp.hankel1(1, k * d) * (r @ nrm[0]) / d
+        assert abs(uD - refD) < 1e-12 * max(abs(refD), 1e-2)
+        gS = oracle.eval_locals(g, INT, k, 40, aS, 1, x[:1], x[1:], np.array([0]))[0, :, 0]
+        refG = -0.25j * k * sp.hankel1(1, k * d) * r / d
+        assert np.abs(gS - refG).max() < 1e-12 * max(np.abs(refG).max(), 1e-2)
+
+
+def test_far_single_source_closed_form():
+    """Far targets (plain quadrature) for one source equal the kernels exactly."""
+    k = 4 + 0.2j
+    src = np.array([[0.2, -0.5], [1.0, 0.3]])
+    nrm = np.array([[0.6, 0.8], [0.0, -1.0]])
+    g = point_geom(0.0, 0.0, src, nrm)
+    wd = np.array([0.7 - 0.2j, -0.3 + 1.1j])
+    xy = np.array([[2.0, 1.0], [-1.5, 0.7]])
+    S = oracle.far(g, OP_S, k, wd, xy)[:, 0]
+    D = oracle.far(g, OP_D, k, wd, xy)[:, 0]
+    G = oracle.far(g, OP_G, k, wd, xy)[:, :, 0]
+    for e in range(2):
+        r = xy[e] - src
+        d = np.hypot(r[:, 0], r[:, 1])
+        h0, h1 = sp.hankel1(0, k * d), sp.hankel1(1, k * d)
+        assert abs(S[e] - (0.25j * wd * h0).sum()) < 1e-14
+        assert abs(D[e] - (0.25j * k * wd * h1 * (r * nrm).sum(1) / d).sum()) < 1e-14
+        refG = (-0.25j * k * (wd * h1 / d)[:, None] * r).sum(0)
+        assert np.abs(G[e] - refG).max() < 1e-14
+
+
+def test_brute_force_coefficients_30_digits():
+    """alpha_l and alpha^D_l on 2 panels at p = 3 against the same discrete sums
+    evaluated in 30-digit arithmetic (pins the oracle's FP64 rounding)."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 30
+    cur = W.starfish()
+    g = oracle.geometry(cur, cur.edges(2), 4, 6)
+    k, p = 2.5, 3
+    rng = np.random.default_rng(5)
+    wd = rng.normal(size=g["n_src"]) + 1j * rng.normal(size=g["n_src"])
+    aS = oracle.form_locals(g, OP_S, INT, k, p, wd)
+    aD = oracle.form_locals(g, OP_D, INT, k, p, wd)
+    for c in (0, 3, 7):
+        cx, cy = mp.mpf(g["ctr_x"][c]), mp.mpf(g["ctr_y"][c])
+        for l in range(-p, p + 1):
+            sS = mp.mpc(0)
+            sD = mp.mpc(0)
+            for s in range(g["n_src"]):
+                dx, dy = mp.mpf(g["src_x"][s]) - cx, mp.mpf(g["src_y"][s]) - cy
+                rho, th = mp.sqrt(dx * dx + dy * dy), mp.atan2(dy, dx)
+                w = mp.mpc(wd[s].real, wd[s].imag)
+                sS += w * mp.hankel1(l, k * rho) * mp.expj(-l * th)
+                # n . grad of H_l(k|y|) e^{-i l arg y} in polar form
+                nx, ny = mp.mpf(g["src_nx"][s]), mp.mpf(g["src_ny"][s])
+                a = (nx * dx + ny * dy) / rho
+                b = (ny * dx - nx * dy) / rho
+                dH = k * (mp.hankel1(l - 1, k * rho) - mp.hankel1(l + 1, k * rho)) / 2
+                val = a * dH * mp.expj(-l * th) + b / rho * mp.hankel1(l, k * rho) * (-1j * l) * mp.expj(-l * th)
+                sD += w * val
+            refS = complex(mp.mpc(0, 0.25) * sS)
+            refD = complex(mp.mpc(0, 0.25) * sD)
+            assert abs(aS[c, l + p, 0] - refS) < 2e-14 * max(abs(refS), 1.0), (c, l)
+            assert abs(aD[c, l + p, 0] - refD) < 2e-14 * max(abs(refD), 1.0), (c, l)
+
+
+# ---------------------------------------------------------------------------
+# Geometry and oversampling
+# ---------------------------------------------------------------------------
+def test_geometry_circle_and_ellipse():
+    R = 1.3
+    cur = W.circle(R)
+    g = oracle.geometry(cur, cur.edges(12), 16, 64)
+    t = g["t_tgt"]
+    assert np.abs(g["tgt_nx"] - np.cos(t)).max() < 1e-15
+    assert np.abs(g["tgt_ny"] - np.sin(t)).max() < 1e-15
+    assert abs(g["src_w"].sum() - 2 * np.pi * R) < 1e-13
+    assert np.abs(g["panel_h"] - 2 * np.pi * R / 12).max() < 1e-14
+    n = g["n_tgt"]
+    assert np.abs(np.hypot(g["ctr_x"][:n], g["ctr_y"][:n]) - (R - g["ctr_r"][:n])).max() < 1e-14
+    assert np.abs(np.hypot(g["ctr_x"][n:], g["ctr_y"][n:]) - (R + g["ctr_r"][n:])).max() < 1e-14
+    assert np.abs(g["ctr_r"] - 0.5 * 2 * np.pi * R / 12).max() < 1e-14
+    # ellipse perimeter 4 a E(e^2) (scipy ellipe), a = 1, b = 1/3, parameter t in [0,1)
+    el = W.ellipse(3.0)
+    ge = oracle.geometry(el, el.edges(40), 16, 64)
+    perim = 4 * sp.ellipe(1 - 1 / 9.0)
+    assert abs(ge["src_w"].sum() - perim) < 1e-12
+    assert abs(ge["tgt_w"].sum() - perim) < 1e-10
+
+
+def test_upsample_reproduces_polynomials():
+    cur = W.circle(1.0)
+    g = oracle.geometry(cur, cur.edges(5), 16, 64)
+    # per panel: a degree-15 polynomial in the local parameter is reproduced exactly
+    te = g["t_edges"]
+    rng = np.random.default_rng(3)
+    coef = rng.normal(size=(5, 16)) + 1j * rng.normal(size=(5, 16))
+
+    def f(t, m):
+        xi = (2 * t - te[m] - te[m + 1]) / (te[m + 1] - te[m])
+        return np.polynomial.polynomial.polyval(xi, coef[m])
+    dt = np.concatenate([f(g["t_tgt"][16 * m:16 * m + 16], m) for m in range(5)])
+    ds = np.concatenate([f(g["t_src"][64 * m:64 * m + 64], m) for m in range(5)])
+    wd = oracle.upsample(g, dt)[:, 0]
+    assert np.abs(wd - g["src_w"] * ds).max() < 1e-12 * np.abs(g["src_w"] * ds).max()
+
+
+def test_assign_centres_brute_force():
+    cur = W.starfish()
+    g = oracle.geometry(cur, cur.edges(8), 16, 64)
+    rng = np.random.default_rng(0)
+    xy = rng.uniform(-1.4, 1.4, size=(300, 2))
+    got = oracle.assign_centres(g, TWO, xy)
+    q = np.hypot(xy[:, None, 0] - g["ctr_x"][None], xy[:, None, 1] - g["ctr_y"][None]) / g["ctr_r"][None]
+    for e in range(300):
+        inside = np.where(q[e] <= 1.0)[0]
+        if inside.size == 0:
+            assert got[e] == -1
+        else:
+            assert got[e] == inside[np.argmin(q[e, inside])]
+
+
+# ---------------------------------------------------------------------------
+# Closed forms of the layer potentials
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("m,k", [(0, 5.0), (3, 5.0), (7, 5.0), (2, 5 + 0.5j)])
+def test_circle_eigenvalues(m, k):
+    """Pin (2): on the unit circle (Sec. 4.1 ellipse, alpha = 1), sigma = e^{im t}:
+    S = (i pi/2) J_m H_m, D^- = (i pi k/2) J_m H_m', D^+ = (i pi k/2) J_m' H_m,
+    dnS^- = (i pi k/2) J_m' H_m, dnS^+ = (i pi k/2) J_m H_m'."""
+    cur = W.circle(1.0)
+    g = oracle.geometry(cur, cur.edges(32), 16, 64)
+    dens = np.exp(1j * m * g["t_tgt"])
+    J, H = sp.jv(m, k), sp.hankel1(m, k)
+    Jp, Hp = sp.jvp(m, k), sp.h1vp(m, k)
+    c = 0.5j * np.pi
+    p = 12
+    S = oracle.apply(g, OP_S, INT, ONE, k, p, dens)[:, 0]
+    Se = oracle.apply(g, OP_S, EXT, ONE, k, p, dens)[:, 0]
+    Dm = oracle.apply(g, OP_D, INT, ONE, k, p, dens)[:, 0]
+    Dp = oracle.apply(g, OP_D, EXT, ONE, k, p, dens)[:, 0]
+    Dpv = oracle.apply(g, OP_D, TWO, ONE, k, p, dens)[:, 0]
+    Gm = oracle.apply(g, OP_G, INT, ONE, k, p, dens)[:, :, 0]
+    Gp = oracle.apply(g, OP_G, EXT, ONE, k, p, dens)[:, :, 0]
+    nx, ny = g["tgt_nx"], g["tgt_ny"]
+    tol = 1e-10
+    assert relerr(S, c * J * H * dens) < tol
+    # exterior centres lie on the concave side of the circle, where QBX is
+    # less accurate (Sec. 3.3 remarks): a looser bound on that side
+    assert relerr(Se, c * J * H * dens) < 10 * tol
+    assert relerr(Dm, c * k * J * Hp * dens) < tol
+    assert relerr(Dp, c * k * Jp * H * dens) < 10 * tol
+    assert relerr(Dpv, 0.5 * c * k * (J * Hp + Jp * H) * dens) < 10 * tol
+    assert relerr(Gm[:, 0] * nx + Gm[:, 1] * ny, c * k * Jp * H * dens) < tol
+    # derivative operators: error times r^{-1} (Sec. 3.1 remarks), concave side
+    assert relerr(Gp[:, 0] * nx + Gp[:, 1] * ny, c * k * J * Hp * dens) < 100 * tol
+    # tangential derivative of S: d/ds (S e^{imt}) = i m S (R = 1)
+    tx, ty = -ny, nx
+    assert relerr(Gm[:, 0] * tx + Gm[:, 1] * ty, 1j * m * c * J * H * dens + 1e-300) < tol if m else True
+
+
+def test_green_identity_starfish():
+    """Pin (3): u = G(., x0) with x0 outside the domain: on Gamma,
+    S[dn u] - D^-[u] = u (interior limit), S[dn u] - D_PV[u] = u/2 and
+    S[dn u] - D^+[u] = 0 (Green's representation formula)."""
+    cur = W.starfish()
+    g = oracle.geometry(cur, cur.edges(48), 16, 64)
+    k = 5.0
+    x0 = np.array([2.1, 0.9])
+    rx, ry = g["tgt_x"] - x0[0], g["tgt_y"] - x0[1]
+    d = np.hypot(rx, ry)
+    u = 0.25j * sp.hankel1(0, k * d)
+    dnu = -0.25j * k * sp.hankel1(1, k * d) * (rx * g["tgt_nx"] + ry * g["tgt_ny"]) / d
+    p = 12
+    S = oracle.apply(g, OP_S, INT, ONE, k, p, dnu)[:, 0]
+    Dm = oracle.apply(g, OP_D, INT, ONE, k, p, u)[:, 0]
+    Dpv = oracle.apply(g, OP_D, TWO, ONE, k, p, u)[:, 0]
+    Dp = oracle.apply(g, OP_D, EXT, ONE, k, p, u)[:, 0]
+    Se = oracle.apply(g, OP_S, EXT, ONE, k, p, dnu)[:, 0]
+    S2 = oracle.apply(g, OP_S, TWO, ONE, k, p, dnu)[:, 0]
+    Dpv_sub = oracle.apply(g, OP_D, INT, PV, k, p, u)[:, 0]
+    scale = np.abs(u).max()
+    # The combined field is smooth on each side, so the expansions of
+    # S[dn u] - D[u] converge much faster than either operator alone.
+    assert np.abs(S - Dm - u).max() < 1e-11 * scale
+    assert np.abs(Se - Dp).max() < 1e-11 * scale
+    assert np.abs(S2 - Dpv - u / 2).max() < 1e-11 * scale
+    # PV by jump subtraction (eq. dlpjump) with the interior S: S - D_PV = u/2
+    assert np.abs(S - Dpv_sub - u / 2).max() < 1e-11 * scale
+
+
+def test_green_identity_exterior():
+    """Exterior representation: x0 inside, radiating u: D^+[u] - S[dn u] = u."""
+    cur = W.starfish()
+    g = oracle.geometry(cur, cur.edges(48), 16, 64)
+    k = 3.0
+    x0 = np.array([0.1, -0.2])
+    rx, ry = g["tgt_x"] - x0[0], g["tgt_y"] - x0[1]
+    d = np.hypot(rx, ry)
+    u = 0.25j * sp.hankel1(0, k * d)
+    dnu = -0.25j * k * sp.hankel1(1, k * d) * (rx * g["tgt_nx"] + ry * g["tgt_ny"]) / d
+    S = oracle.apply(g, OP_S, EXT, ONE, k, 12, dnu)[:, 0]
+    Dp = oracle.apply(g, OP_D, EXT, ONE, k, 12, u)[:, 0]
+    assert np.abs(Dp - S - u).max() < 1e-9 * np.abs(u).max()
+
+
+def test_jump_relations():
+    """Pin (4): D^+ - D^- = mu, n.(grad S^+ - grad S^-) = -sigma, t.grad S and S
+    continuous (Sec. 3.2), each to within the QBX error of the one-sided
+    limits (measured: ~1e-8 for D, ~5e-7 for grad S at 96 panels, p = 12), and
+    the principal values from either side (jump subtraction, eq. dlpjump) agree."""
+    cur = W.starfish()
+    g = oracle.geometry(cur, cur.edges(96), 16, 64)
+    k, p = 4.0, 12
+    dens = W.density_cfg1(g["t_tgt"])
+    Dm = oracle.apply(g, OP_D, INT, ONE, k, p, dens)[:, 0]
+    Dp = oracle.apply(g, OP_D, EXT, ONE, k, p, dens)[:, 0]
+    assert np.abs(Dp - Dm - dens).max() < 1e-7
+    Sm = oracle.apply(g, OP_S, INT, ONE, k, p, dens)[:, 0]
+    Sp = oracle.apply(g, OP_S, EXT, ONE, k, p, dens)[:, 0]
+    assert np.abs(Sp - Sm).max() < 1e-8
+    Gm = oracle.apply(g, OP_G, INT, ONE, k, p, dens)[:, :, 0]
+    Gp = oracle.apply(g, OP_G, EXT, ONE, k, p, dens)[:, :, 0]
+    nx, ny = g["tgt_nx"], g["tgt_ny"]
+    jn = (Gp[:, 0] - Gm[:, 0]) * nx + (Gp[:, 1] - Gm[:, 1]) * ny
+    jt = -(Gp[:, 0] - Gm[:, 0]) * ny + (Gp[:, 1] - Gm[:, 1]) * nx
+    assert np.abs(jn + dens).max() < 5e-6
+    assert np.abs(jt).max() < 5e-6
+    # the principal value does not depend on the side it is reached from
+    Dpv_i = oracle.apply(g, OP_D, INT, PV, k, p, dens)[:, 0]
+    Dpv_e = oracle.apply(g, OP_D, EXT, PV, k, p, dens)[:, 0]
+    assert np.abs(Dpv_i - Dpv_e).max() < 1e-7
+    Gpv_i = oracle.apply(g, OP_G, INT, PV, k, p, dens)[:, :, 0]
+    Gpv_e = oracle.apply(g, OP_G, EXT, PV, k, p, dens)[:, :, 0]
+    assert np.abs(Gpv_i - Gpv_e).max() < 5e-6
+
+
+def test_error_decay_with_h_and_p():
+    """Pin (5), Theorem 1 with r = h/2: at fixed p the error of S on the circle
+    falls like h^{p+1} (log-least-squares slope), and at fixed h raising p helps
+    until the source rule is too coarse; oversampling the sources (q = 64
+    instead of 16, Sec. 3.4.2) then restores accuracy (Sec. 2, p vs N study)."""
+    cur = W.circle(1.0)
+    k, m, p = 2.0, 2, 4
+    errs, hs = [], []
+    for M in (16, 24, 32, 48):
+        g = oracle.geometry(cur, cur.edges(M), 16, 64)
+        dens = np.exp(1j * m * g["t_tgt"])
+        S = oracle.apply(g, OP_S, INT, ONE, k, p, dens)[:, 0]
+        ex = 0.5j * np.pi * sp.jv(m, k) * sp.hankel1(m, k) * dens
+        errs.append(relerr(S, ex))
+        hs.append(2 * np.pi / M)
+    slope = np.polyfit(np.log(hs), np.log(errs), 1)[0]
+    # measured 4.63 at p = 4: approaching p + 1 from below on these meshes
+    assert p + 0.3 < slope < p + 1.5, (slope, errs)
+    # p study at fixed M
+    g16 = oracle.geometry(cur, cur.edges(12), 16, 16)
+    g64 = oracle.geometry(cur, cur.edges(12), 16, 64)
+    dens = np.exp(1j * m * g64["t_tgt"])
+    ex = 0.5j * np.pi * sp.jv(m, k) * sp.hankel1(m, k) * dens
+    e = {}
+    for q, g in ((16, g16), (64, g64)):
+        for pp in (3, 6, 24):
+            e[q, pp] = relerr(oracle.apply(g, OP_S, INT, ONE, k, pp, dens)[:, 0], ex)
+    assert e[64, 6] < e[64, 3]                # more terms help while resolved
+    assert e[16, 24] > 10 * e[64, 24]         # too high p for the rule: coarse rule fails
+    assert e[64, 24] < 1e-10
+
+
+def test_apply_sel_matches_full():
+    cur = W.starfish()
+    g = oracle.geometry(cur, cur.edges(6), 16, 64)
+    dens = W.density_cfg1(g["t_tgt"])
+    sel = np.array([0, 5, 17, 95])
+    for op in (OP_S, OP_D, OP_G):
+        full = oracle.apply(g, op, TWO, ONE, 5.0, 6, dens)
+        part = oracle.apply(g, op, TWO, ONE, 5.0, 6, dens, sel=sel)
+        assert np.array_equal(full[sel], part)

@@ -1,0 +1,183 @@
+"""Seeded synthetic inputs shared by the GPU path's tests/bench and the oracle.
+
+This module holds no arithmetic of the QBX method: only curve
+parametrisations (gamma(t), gamma'(t)), densities, panel edges in the curve
+parameter, a counter-based random generator, and the named workloads.  Both
+sides evaluate the curves at their own Gauss-Legendre nodes.
+
+Random numbers: splitmix64 (Steele, Lea, Flood, "Fast splittable
+pseudorandom number generators", OOPSLA 2014) -> uniform doubles from the top
+53 bits -> Box-Muller for Gaussians.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_MASK = (1 << 64) - 1
+
+
+def splitmix64(seed: int, n: int) -> np.ndarray:
+    """n successive outputs of splitmix64 started at `seed` (uint64)."""
+    out = np.empty(n, dtype=np.uint64)
+    s = seed & _MASK
+    for i in range(n):
+        s = (s + 0x9E3779B97F4A7C15) & _MASK
+        z = s
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _MASK
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _MASK
+        out[i] = z ^ (z >> 31)
+    return out
+
+
+def uniform(seed: int, n: int) -> np.ndarray:
+    """n uniform doubles in (0, 1) (top 53 bits, offset by half an ulp)."""
+    u = splitmix64(seed, n) >> np.uint64(11)
+    return (u.astype(np.float64) + 0.5) * (1.0 / 9007199254740992.0)
+
+
+def complex_gaussian(seed: int, n: int) -> np.ndarray:
+    """n i.i.d. CN(0,1) samples (E|z|^2 = 1), Box-Muller on splitmix64 uniforms."""
+    u = uniform(seed, 2 * n)
+    r = np.sqrt(-2.0 * np.log(u[0::2]))
+    th = 2.0 * math.pi * u[1::2]
+    return (r * np.cos(th) + 1j * r * np.sin(th)) / math.sqrt(2.0)
+
+
+# ----------------------------------------------------------------------------
+# Curves: callables t -> (gamma [n,2], dgamma/dt [n,2]); counter-clockwise.
+# ----------------------------------------------------------------------------
+@dataclass
+class Curve:
+    name: str
+    t0: float
+    t1: float
+    fn: object = field(repr=False)
+
+    def __call__(self, t):
+        return self.fn(np.asarray(t, dtype=np.float64))
+
+    def edges(self, M: int) -> np.ndarray:
+        """M panels equispaced in the curve parameter."""
+        return np.linspace(self.t0, self.t1, M + 1)
+
+
+def _polar(rf, drf):
+    def fn(t):
+        r, dr = rf(t), drf(t)
+        c, s = np.cos(t), np.sin(t)
+        g = np.stack([r * c, r * s], axis=-1)
+        dg = np.stack([dr * c - r * s, dr * s + r * c], axis=-1)
+        return g, dg
+    return fn
+
+
+def starfish(amp: float = 0.25, arms: int = 5) -> Curve:
+    """r(t) = 1 + amp cos(arms t), t in [0, 2 pi)."""
+    return Curve(f"starfish(1+{amp}cos{arms}t)", 0.0, 2 * math.pi,
+                 _polar(lambda t: 1.0 + amp * np.cos(arms * t),
+                        lambda t: -amp * arms * np.sin(arms * t)))
+
+
+def circle(R: float = 1.0) -> Curve:
+    return Curve(f"circle(R={R})", 0.0, 2 * math.pi,
+                 _polar(lambda t: R + 0.0 * t, lambda t: 0.0 * t))
+
+
+def ellipse(alpha: float) -> Curve:
+    """The paper's ellipse family gamma(t) = (cos 2 pi t, sin(2 pi t)/alpha), t in [0,1)."""
+    w = 2 * math.pi
+
+    def fn(t):
+        g = np.stack([np.cos(w * t), np.sin(w * t) / alpha], axis=-1)
+        dg = np.stack([-w * np.sin(w * t), w * np.cos(w * t) / alpha], axis=-1)
+        return g, dg
+    return Curve(f"ellipse({alpha})", 0.0, 1.0, fn)
+
+
+def fourier_curve(a, b) -> Curve:
+    """r(t) = 1 + sum_m (a_m cos m t + b_m sin m t), m = 1..len(a)."""
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    m = np.arange(1, a.size + 1, dtype=np.float64)
+
+    def rf(t):
+        return 1.0 + (a[None, :] * np.cos(np.outer(t, m)) + b[None, :] * np.sin(np.outer(t, m))).sum(-1)
+
+    def drf(t):
+        return (m[None, :] * (-a[None, :] * np.sin(np.outer(t, m)) + b[None, :] * np.cos(np.outer(t, m)))).sum(-1)
+    return Curve("fourier", 0.0, 2 * math.pi, _polar(rf, drf))
+
+
+# ----------------------------------------------------------------------------
+# Densities on the target grid, as functions of the curve parameter.
+# ----------------------------------------------------------------------------
+def density_cfg1(t):
+    """sigma(t) = cos 3t + 0.5 i sin t."""
+    t = np.asarray(t, dtype=np.float64)
+    return np.cos(3 * t) + 0.5j * np.sin(t)
+
+
+def fourier_mode(m: int):
+    def f(t):
+        return np.exp(1j * m * np.asarray(t, dtype=np.float64))
+    return f
+
+
+# ----------------------------------------------------------------------------
+# Named workloads.  Sizes: n_tgt = M*16 targets, n_src = M*64 sources.
+# ----------------------------------------------------------------------------
+@dataclass
+class Workload:
+    name: str
+    curve: Curve
+    M: int
+    k: complex
+    p: int
+    q_tgt: int = 16
+    q_src: int = 64
+    r_factor: float = 0.5
+    sides: str = "int"          # "int", "ext" or "two"
+    ops: tuple = ("S", "D")
+    nrhs: int = 1
+    density: str = "cfg1"       # "cfg1" or "gauss"
+    seed: int = 0
+
+    @property
+    def n_tgt(self):
+        return self.M * self.q_tgt
+
+    @property
+    def n_src(self):
+        return self.M * self.q_src
+
+    @property
+    def n_ctr(self):
+        return self.n_tgt * (2 if self.sides == "two" else 1)
+
+    def terms_per_op(self):
+        """centre x source x order(2p+1) x rhs."""
+        return self.n_ctr * self.n_src * (2 * self.p + 1) * self.nrhs
+
+    def dens(self, t_tgt):
+        if self.density == "cfg1":
+            d = density_cfg1(t_tgt)
+            return np.repeat(d[:, None], self.nrhs, axis=1)
+        g = complex_gaussian(self.seed, self.n_tgt * self.nrhs)
+        return g.reshape(self.n_tgt, self.nrhs)
+
+
+def cfg1() -> Workload:
+    """Starfish 1 + 0.25 cos 5t, 32 panels x 16 targets, 4x sources, k=5, p=8,
+    interior centres, sigma = cos 3t + 0.5 i sin t; S and D."""
+    return Workload("starfish-M32-k5-p8-int", starfish(), 32, 5.0, 8, sides="int",
+                    ops=("S", "D"), density="cfg1")
+
+
+def cfg2() -> Workload:
+    """Starfish, 256 panels (4096 targets, 16384 sources), k=20, p=12, interior
+    and exterior centres (8192), S, D and grad S, CN(0,1) density, seed 2."""
+    return Workload("starfish-M256-k20-p12-two", starfish(), 256, 20.0, 12, sides="two",
+                    ops=("S", "D", "GRAD_S"), density="gauss", seed=2)
