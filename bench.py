@@ -1,0 +1,307 @@
+#!/usr/bin/env python3
+"""Benchmark of the QBX hot path on GB300.
+
+One step = the three on-surface operator applies (S, D, grad S, two-sided) of
+the full-size starfish workload: r(t) = 1 + 0.25 cos 5t, 256 panels x 16
+targets (4096), 16384 oversampled sources, k = 20, p = 12, interior and
+exterior centres (8192), CN(0,1) density (seed 2).  Metric: QBX
+centre x source x order terms per second (term = (centre, source, l),
+l in [-p, p], x rhs), whole job.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+--impl reference times the CPU oracle (the plain FP64 restatement of the
+method) on the host cores, on a bounded sample of targets per step.
+Under torchrun (N > 1) every rank runs an independent replica of the workload
+on its own GPU (no data-path collective; weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "QBX center·source·order terms/s"
+# FP64 ALU peak of the dominant kernel's pipe: 152 SMs x 2 FP64 FMA lanes per
+# SM per clock (4 flops) x 2.07 GHz maximum SM clock (nominal 1.25 TFLOP/s).
+FP64_PEAK_GFLOPS = 152 * 4 * 2.07
+# Frozen algorithmic flop model per (centre, source) pair of the fused apply:
+# 100 flops of pair set-up (distance, H0, H1) + 16 per order (S) or 24 per
+# order (D, grad S), + 8 per extra right-hand side.
+FLOPS_PAIR = {"S": (100, 16), "D": (100, 24), "GRAD_S": (100, 24)}
+
+
+def flops_per_pair(op, p, nrhs=1):
+    a, b = FLOPS_PAIR[op]
+    return a + b * p + 8 * (nrhs - 1)
+
+
+def env_rank():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
+        int(os.environ.get("LOCAL_RANK", "0"))
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def oracle_sample(wl, n_targets, reps=1):
+    """Time the CPU oracle on `n_targets` sampled targets of the workload (all
+    three operators, both sides).  Returns (terms, seconds, threads)."""
+    import oracle
+    go = oracle.geometry(wl.curve, wl.curve.edges(wl.M), wl.q_tgt, wl.q_src)
+    dens = wl.dens(go["t_tgt"])
+    rng = np.random.default_rng(0)
+    sel = np.sort(rng.choice(wl.n_tgt, n_targets, replace=False))
+    ops = {"S": oracle.OP_S, "D": oracle.OP_D, "GRAD_S": oracle.OP_GRAD_S}
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        for name in wl.ops:
+            oracle.apply(go, ops[name], oracle.SIDE_TWO, 0, wl.k, wl.p, dens, sel=sel)
+    dt = time.perf_counter() - t0
+    sides = 2 if wl.sides == "two" else 1
+    terms = reps * len(wl.ops) * n_targets * sides * wl.n_src * (2 * wl.p + 1) * wl.nrhs
+    return terms, dt, oracle.num_threads()
+
+
+def run_reference(args, wl):
+    rank, world, _ = env_rank()
+    if rank != 0:
+        return 0
+    n = args.ref_sample
+    for _ in range(args.warmup):
+        oracle_sample(wl, max(4, n // 8))
+    times, terms = [], 0
+    for _ in range(args.steps):
+        t, dt, cores = oracle_sample(wl, n)
+        times.append(dt)
+        terms += t
+    total = sum(times)
+    value = terms / total
+    sample = (f"{n} of {wl.n_tgt} targets per step (both sides, S, D and grad S, all "
+              f"{wl.n_src} sources), CPU: {cpu_model()}")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "terms/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_dict(wl, args),
+            "cpu_baseline": {"value": value, "unit": "terms/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "terms/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def config_dict(wl, args):
+    return {"workload": f"starfish r=1+0.25cos5t, M={wl.M} panels x {wl.q_tgt} targets "
+                        f"({wl.n_tgt}), {wl.n_src} sources (4x), k={wl.k:g}, p={wl.p}, "
+                        f"two-sided centres ({wl.n_ctr}), ops S+D+gradS, CN(0,1) density seed {wl.seed}",
+            "n_tgt": wl.n_tgt, "n_src": wl.n_src, "n_ctr": wl.n_ctr, "k": wl.k, "p": wl.p,
+            "nrhs": wl.nrhs, "terms_per_step": len(wl.ops) * wl.terms_per_op(),
+            "l2": "flushed between timed steps (256 MiB write outside the event pair)",
+            "parallelism": "replicas" if args.gpus > 1 else "single"}
+
+
+def run_gpu(args, wl):
+    import torch
+    import paper_1207_4461_gb300 as qbx
+
+    rank, world, local = env_rank()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    ops = {"S": qbx.OP_S, "D": qbx.OP_D, "GRAD_S": qbx.OP_GRAD_S}
+    plan = qbx.Plan(wl.q_tgt, wl.q_src, n_src=wl.n_src, n_ctr=wl.n_ctr, ncoef=2, nrhs=wl.nrhs)
+    g = qbx.qbx_geometry(plan, wl.curve, wl.curve.edges(wl.M))
+    dens_np = wl.dens(g.t_tgt)
+    dens = torch.as_tensor(dens_np, device=dev).contiguous()
+    outs = {n: torch.empty((wl.n_tgt, 2, wl.nrhs) if n == "GRAD_S" else (wl.n_tgt, wl.nrhs),
+                           dtype=torch.complex128, device=dev) for n in wl.ops}
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        for n in wl.ops:
+            qbx.qbx_apply(plan, g, ops[n], qbx.SIDE_TWO, 0, wl.k, wl.p, dens, out_on=outs[n])
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    qbx.qbx_sync_status(plan)
+
+    # ---- device-timed region: K steps, per-op events, L2 flushed between steps
+    ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in wl.ops]
+          for _ in range(args.steps)]
+    clocks = ClockSampler(int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0])
+                          if os.environ.get("CUDA_VISIBLE_DEVICES", "").isdigit() else local)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    for s in range(args.steps):
+        flush.fill_(s & 0xFF)
+        for i, n in enumerate(wl.ops):
+            ev[s][i][0].record(stream)
+            qbx.qbx_apply(plan, g, ops[n], qbx.SIDE_TWO, 0, wl.k, wl.p, dens, out_on=outs[n])
+            ev[s][i][1].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    op_ms = {n: [ev[s][i][0].elapsed_time(ev[s][i][1]) for s in range(args.steps)] for i, n in enumerate(wl.ops)}
+    step_ms = sum(sum(v) for v in op_ms.values()) / args.steps
+    qbx.qbx_sync_status(plan)
+    if world > 1:
+        t = torch.tensor([step_ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        step_ms = float(t.item())
+    terms_step = len(wl.ops) * wl.terms_per_op()
+    value = world * terms_step / (step_ms * 1e-3)
+
+    # roofline of the dominant kernel (the fused apply): algorithmic flops / duration
+    pairs = wl.n_ctr * wl.n_src
+    flops = {n: pairs * flops_per_pair(n, wl.p, wl.nrhs) for n in wl.ops}
+    launch_ms = {n: statistics.mean(op_ms[n]) for n in wl.ops}
+    achieved = sum(flops.values()) / (sum(launch_ms.values()) * 1e-3) / 1e9
+    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
+                "frac": achieved / FP64_PEAK_GFLOPS, "traffic": None,
+                "kernel": "k_apply_fused (S, D, grad S instances; per-call events include the tiny "
+                          "oversampling and reduction kernels)",
+                "flops_per_pair": {n: flops_per_pair(n, wl.p, wl.nrhs) for n in wl.ops},
+                "ms_per_launch": launch_ms}
+
+    # ---- end to end through the public API with host buffers (pinned)
+    h_dens = torch.from_numpy(dens_np).pin_memory()
+    h_outs = {n: torch.empty(outs[n].shape, dtype=torch.complex128).pin_memory() for n in wl.ops}
+    d_dens = torch.empty_like(dens)
+    h2d = h_dens.numel() * 16
+    d2h = sum(o.numel() * 16 for o in h_outs.values())
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(2):
+        d_dens.copy_(h_dens, non_blocking=True)
+        step()
+    torch.cuda.synchronize()
+    e2e_ms = 0.0
+    for s in range(args.steps):
+        flush.fill_(s & 0xFF)
+        e0.record(stream)
+        d_dens.copy_(h_dens, non_blocking=True)
+        for n in wl.ops:
+            qbx.qbx_apply(plan, g, ops[n], qbx.SIDE_TWO, 0, wl.k, wl.p, d_dens, out_on=outs[n])
+            h_outs[n].copy_(outs[n], non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        e2e_ms += e0.elapsed_time(e1)
+    e2e_ms /= args.steps
+    e2e = {"value": world * terms_step / (e2e_ms * 1e-3), "unit": "terms/s",
+           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms}
+
+    line = {"metric": METRIC, "value": value, "unit": "terms/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_dict(wl, args),
+            "roofline": roofline, "e2e": e2e, "clocks": clk,
+            "gpu_launches": args.steps * len(wl.ops) * 3,
+            "targets_per_s": world * len(wl.ops) * wl.n_tgt * wl.nrhs / (step_ms * 1e-3),
+            "pairs_per_s": world * len(wl.ops) * pairs / (step_ms * 1e-3)}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        terms, dt, cores = oracle_sample(wl, args.cpu_sample)
+        line["cpu_baseline"] = {"value": terms / dt, "unit": "terms/s", "cores": cores, "kind": "oracle",
+                                "sample": f"{args.cpu_sample} of {wl.n_tgt} targets, both sides, S, D and "
+                                          f"grad S, all {wl.n_src} sources; CPU: {cpu_model()}",
+                                "seconds": dt}
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--cpu-sample", type=int, default=192, help="targets in the CPU-baseline sample")
+    ap.add_argument("--ref-sample", type=int, default=48, help="targets per step of --impl reference")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--panels", type=int, default=None,
+                    help="profiling only: override the panel count (smaller case for ncu)")
+    ap.add_argument("--ops", default=None, help="profiling only: comma list of S,D,GRAD_S")
+    args = ap.parse_args()
+    wl = W.cfg2()
+    if args.panels:
+        wl.M = args.panels
+    if args.ops:
+        wl.ops = tuple(args.ops.split(","))
+    if args.impl == "reference":
+        return run_reference(args, wl)
+    return run_gpu(args, wl)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,202 @@
+/*
+ * qbx.h -- C ABI of the GB300 (sm_103a) QBX library: quadrature by expansion
+ * for 2D Helmholtz layer potentials, complex FP64.
+ *
+ * Method: Kloeckner, Barnett, Greengard, O'Neil, "Quadrature by Expansion: a
+ * new method for the evaluation of layer potentials", arXiv:1207.4461.
+ *
+ * Problem statement (Sec. 3.3): a closed curve Gamma, counter-clockwise, split
+ * into M panels; outward normal n = (gamma'_y, -gamma'_x)/|gamma'| (Sec. 3.2);
+ * a density on Gamma; a wavenumber k with Im k >= 0 (Sec. 1); an expansion
+ * order p.  Return, at the panel nodes, the one-sided limit, the principal
+ * value (jump subtraction) or the two-sided average of
+ *   S sigma(x) = int G(x,x') sigma(x') dx'                    (Sec. 1, eq. kernelint)
+ *   D mu(x)    = int dG/dn_{x'}(x,x') mu(x') dx'              (Sec. 1, eq. kernelintd)
+ *   grad S sigma                                              (Sec. 3.2)
+ * with G(x,x') = (i/4) H0^(1)(k|x-x'|)                        (Sec. 1, eq. helmholtz-ker),
+ * and plain smooth quadrature at far (off-surface) targets.
+ *
+ * Conventions shared by every call:
+ *  - Complex numbers are qbx_c64 {re, im}, interleaved FP64.
+ *  - Unless stated "host", every pointer is a DEVICE pointer owned by the
+ *    caller; the library never frees it.  Arrays are dense, row-major.
+ *  - Density arrays have a right-hand-side axis: [n][nrhs].
+ *  - Every compute call is asynchronous on `stream` (a cudaStream_t passed as
+ *    void*, NULL = legacy default stream) and allocates nothing; only
+ *    qbx_plan_create allocates (its workspace).
+ *  - Return value: QBX_OK or an error code; qbx_last_error() gives a
+ *    thread-local message.  Argument errors are detected on the host before
+ *    anything is launched.  Device-side conditions (non-finite values in the
+ *    result) are recorded in a status word that qbx_sync_status() returns.
+ *  - Grids: target nodes are the q_tgt-point Gauss-Legendre nodes of every
+ *    panel (n_tgt = M q_tgt, the Nystrom unknowns); source nodes the
+ *    q_src-point nodes of the same panels (n_src = M q_src), the oversampled
+ *    grid of Sec. 3.4.2.
+ *  - Centres: index j in [0, n_tgt) is the interior centre of target j,
+ *    index n_tgt + j its exterior centre (Sec. 3.3 step 4a).
+ *  - Phase convention of the coefficients:
+ *      alpha_l = (i/4) sum_s w_s sigma_s H_l(k rho_s) e^{-i l theta_s},
+ *      u(x)    = sum_{l=-p..p} alpha_l J_l(k rho) e^{+i l theta},
+ *    i.e. the paper's eq. graf-coefficient / eq. local-exp with l -> -l
+ *    (alpha^paper_{-l} = (-1)^l alpha_l); the potential is the same.
+ */
+#ifndef QBX_H
+#define QBX_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct { double re, im; } qbx_c64;
+
+enum {
+  QBX_OK = 0,
+  QBX_EINVAL = 1,          /* bad argument (host check, nothing launched) */
+  QBX_ECUDA = 2,           /* a CUDA runtime call failed */
+  QBX_EINADMISSIBLE = 3,   /* reserved: strict admissibility (not raised by default) */
+  QBX_ENONFINITE = 4,      /* a kernel produced a non-finite value */
+  QBX_ENOCONV = 5,         /* reserved: iterative solve did not converge */
+  QBX_ETIMEOUT = 6,        /* reserved: a bounded device wait ran out */
+  QBX_ENOMEM = 7           /* workspace too small / allocation failed */
+};
+
+enum { QBX_OP_S = 0, QBX_OP_D = 1, QBX_OP_GRAD_S = 2 };
+enum { QBX_SIDE_INT = 0, QBX_SIDE_EXT = 1, QBX_SIDE_TWO = 2 };
+enum { QBX_LIMIT_ONE_SIDED = 0, QBX_LIMIT_PV = 1 };
+enum { QBX_VALUE = 0, QBX_GRAD = 1 };
+
+/* Largest supported expansion order and right-hand-side count per launch. */
+#define QBX_MAX_P 40
+#define QBX_MAX_Q 128
+
+typedef struct qbx_plan qbx_plan;
+
+/* Discretised curve.  All pointers are caller-owned device arrays of the
+ * stated length; qbx_geometry fills them. */
+typedef struct {
+  int M, q_tgt, q_src;       /* panels, target and source nodes per panel */
+  int n_tgt, n_src;          /* M*q_tgt, M*q_src */
+  double *src_x, *src_y, *src_nx, *src_ny, *src_w;   /* [n_src] */
+  double *tgt_x, *tgt_y, *tgt_nx, *tgt_ny, *tgt_w;   /* [n_tgt] */
+  double *panel_h;                                  /* [M] panel arc length */
+  double *ctr_x, *ctr_y, *ctr_r, *ctr_ratio;        /* [2*n_tgt] centres */
+} qbx_geom;
+
+/* Thread-local message describing the last error of the calling thread. */
+const char *qbx_last_error(void);
+
+/* Library ABI version (increments on incompatible changes). */
+int qbx_version(void);
+
+/* host.  q-node Gauss-Legendre rule on [-1,1] (the "underlying smooth rule"
+ * of Sec. 3.1 / Sec. 4.1).  nodes, weights: host arrays of length q,
+ * nodes ascending.  1 <= q <= QBX_MAX_Q, else QBX_EINVAL. */
+int qbx_gauss_legendre(int q, double *nodes, double *weights);
+
+/* Create a plan on CUDA device `device` for the grid pair (q_tgt, q_src):
+ * uploads the per-panel interpolation matrix from the target to the source
+ * nodes (Sec. 3.4.2), a device status word, and allocates `workspace_bytes`
+ * of device workspace used by the split-source reductions (see
+ * qbx_workspace_bytes).  *plan receives the handle.  Host call, synchronous. */
+int qbx_plan_create(qbx_plan **plan, int device, int q_tgt, int q_src, size_t workspace_bytes);
+int qbx_plan_destroy(qbx_plan *plan);
+
+/* Workspace a call needs: for qbx_apply / qbx_far / qbx_form_locals with the
+ * given sizes.  n_ctr = number of centres (or far targets) processed, ncoef =
+ * coefficients per centre (1 for S/D values, 2 for grad S, 2p+1 for
+ * form_locals).  Host, pure function. */
+size_t qbx_workspace_bytes(int n_src, int n_ctr, int ncoef, int nrhs);
+
+/* Read (and clear) the plan's device status word: QBX_OK or QBX_ENONFINITE.
+ * Synchronises `stream`. */
+int qbx_sync_status(qbx_plan *plan, void *stream);
+
+/* Geometry and centres (Sec. 3.3 steps 3-4a; Sec. 4.1).
+ * Inputs (device): t_edges [M+1] panel parameter edges; gam_tgt, dgam_tgt
+ * [n_tgt][2] curve point gamma(t) and derivative gamma'(t) at the q_tgt GL
+ * nodes of each panel (t = (t_m + t_{m+1})/2 + (t_{m+1}-t_m)/2 xi_i, xi from
+ * qbx_gauss_legendre); gam_src, dgam_src [n_src][2] likewise at the q_src
+ * nodes.  g->M, q_tgt, q_src must be set (q's equal to the plan's) and all
+ * output pointers valid.  Outputs: normals n = (gamma'_y,-gamma'_x)/|gamma'|,
+ * weights w = w^GL (t_{m+1}-t_m)/2 |gamma'|, panel_h[m] = sum of the panel's
+ * source weights, centres c = x -/+ r n with r = r_factor * panel_h (0.5 in the
+ * paper, Sec. 3.3 step 3), and ctr_ratio = min_s |x_s - c| / r (>= 1 means
+ * eq. x-c-closest holds for every source node).  Sets g->n_tgt, g->n_src. */
+int qbx_geometry(qbx_plan *plan, qbx_geom *g, const double *t_edges,
+                 const double *gam_tgt, const double *dgam_tgt,
+                 const double *gam_src, const double *dgam_src,
+                 double r_factor, void *stream);
+
+/* Source oversampling (Sec. 3.4.2): per panel, polynomial interpolation of
+ * dens_tgt [n_tgt][nrhs] from the target to the source nodes, times the source
+ * weight: wdens_src [n_src][nrhs] = w_s sigma(x_s). */
+int qbx_upsample(qbx_plan *plan, const qbx_geom *g, const qbx_c64 *dens_tgt, int nrhs,
+                 qbx_c64 *wdens_src, void *stream);
+
+/* Expansion coefficients (Sec. 3.3 step 4b):
+ *   kind QBX_OP_S: alpha_l   = (i/4) sum_s wdens_s H_l(k rho_s) e^{-i l theta_s}
+ *                  (Sec. 2, eq. graf-coefficient)
+ *   kind QBX_OP_D: alpha^D_l = (i/4) sum_s wdens_s n_s . grad_{x_s}[H_l(k rho_s) e^{-i l theta_s}]
+ *                  (Sec. 3.2, eq. graf-coefficient-dlp)
+ * for the centres of `side` (INT: n_tgt centres, EXT: n_tgt, TWO: 2 n_tgt,
+ * interior first).  wdens_src [n_src][nrhs] (e.g. from qbx_upsample).
+ * alpha: [n_ctr][2p+1][nrhs], index l+p.  0 <= p <= QBX_MAX_P.
+ * Needs qbx_workspace_bytes(n_src, n_ctr, 2p+1, nrhs) of workspace. */
+int qbx_form_locals(qbx_plan *plan, const qbx_geom *g, int kind, int side, qbx_c64 k, int p,
+                    const qbx_c64 *wdens_src, int nrhs, qbx_c64 *alpha, void *stream);
+
+/* Evaluate local expansions (Sec. 2 eq. local-exp; Sec. 3.3 step 4c) and,
+ * with what = QBX_GRAD, their target gradient (Sec. 3.2).  alpha as produced
+ * by qbx_form_locals for `side`.  If n_eval == 0, every centre of `side` is
+ * evaluated at its own on-surface target (n_eval becomes the centre count);
+ * otherwise target e at (ex[e], ey[e]) uses centre ectr[e] (index within the
+ * side's centres, 0-based).  out: [n_eval][nrhs] (VALUE) or [n_eval][2][nrhs]
+ * (GRAD: d/dx then d/dy).  J_l(k rho) by Miller's backward recurrence. */
+int qbx_eval_locals(qbx_plan *plan, const qbx_geom *g, int side, qbx_c64 k, int p,
+                    const qbx_c64 *alpha, int nrhs, int what,
+                    int n_eval, const double *ex, const double *ey, const int *ectr,
+                    qbx_c64 *out, void *stream);
+
+/* The on-surface operator apply (Sec. 3.3 in full), storage-free: alpha is
+ * never materialised (Sec. 3.3, remark on saving storage; Sec. 2 eq.
+ * qbx-kernel G_p).  dens_tgt [n_tgt][nrhs] is the density on the target grid;
+ * it is oversampled inside.  op: S, D or grad S.  side INT / EXT gives the
+ * one-sided limit (limit = ONE_SIDED) or the principal value by jump
+ * subtraction (limit = PV; Sec. 3.2: D: PV = lim -/+ mu/2, grad S:
+ * PV = lim +/- n sigma/2, + = exterior); side TWO gives the two-sided average
+ * (Sec. 3.2, eq. dlp-twosided; `limit` ignored).  out_on: [n_tgt][nrhs], or
+ * [n_tgt][2][nrhs] for grad S.  If n_far > 0, x_far [n_far][2] are off-surface
+ * targets evaluated by plain quadrature into out_far (same layout); the caller
+ * places them outside every expansion disk (see qbx_assign_centres).
+ * Needs qbx_workspace_bytes(n_src, max(n_ctr, n_far), ncomp, nrhs) of workspace
+ * plus n_src*nrhs complex for the oversampled density. */
+int qbx_apply(qbx_plan *plan, const qbx_geom *g, int op, int side, int limit, qbx_c64 k, int p,
+              const qbx_c64 *dens_tgt, int nrhs, int n_far, const double *x_far,
+              qbx_c64 *out_on, qbx_c64 *out_far, void *stream);
+
+/* Plain smooth quadrature at off-surface points (Sec. 1, Sec. 2):
+ * S = (i/4) sum wdens H0(kd), D = (ik/4) sum wdens H1(kd) (x-x_s).n_s/d,
+ * grad S = -(ik/4) sum wdens H1(kd) (x-x_s)/d.  wdens_src [n_src][nrhs],
+ * x_far [n_far][2], out [n_far][nrhs] or [n_far][2][nrhs]. */
+int qbx_far(qbx_plan *plan, const qbx_geom *g, int op, qbx_c64 k, const qbx_c64 *wdens_src,
+            int nrhs, int n_far, const double *x_far, qbx_c64 *out, void *stream);
+
+/* Which centre serves each off-surface point (Sec. 2: inside a disk use its
+ * expansion).  Among the centres of `side` with |x - c| <= r_c, the smallest
+ * |x - c|/r_c, ties to the lowest index; -1 if no disk contains x.
+ * xy [n][2]; out [n] (index within the side's centres). */
+int qbx_assign_centres(qbx_plan *plan, const qbx_geom *g, int side, int n, const double *xy,
+                       int *out, void *stream);
+
+/* Diagnostics of the device special functions used by the kernels: H0, H1
+ * at z[n] (complex, Im z >= 0, z != 0; the real-argument path is taken when
+ * Im z == 0), and J_0..J_nmax (Miller) at z[n].  For tests. */
+int qbx_debug_hankel01(const qbx_c64 *z, int n, qbx_c64 *h0, qbx_c64 *h1, void *stream);
+int qbx_debug_besselj(const qbx_c64 *z, int n, int nmax, qbx_c64 *j, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QBX_H */

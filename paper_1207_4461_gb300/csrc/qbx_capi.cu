@@ -1,0 +1,526 @@
+// qbx_capi.cu -- host side of the C ABI declared in include/qbx.h: plans,
+// the Gauss-Legendre rule, the per-panel interpolation matrix, argument
+// checks and the launch sequence of each call.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+#include <algorithm>
+#include <string>
+#include <vector>
+#include "../../include/qbx.h"
+#include "qbx_internal.h"
+
+using namespace qbx;
+
+struct qbx_plan {
+  int device;
+  int num_sms;
+  int q_tgt, q_src;
+  double* d_interp;   // [q_src][q_tgt]
+  double* d_wgl_tgt;  // [q_tgt]
+  double* d_wgl_src;  // [q_src]
+  int* d_status;
+  void* ws;
+  size_t ws_bytes;
+};
+
+namespace {
+
+thread_local std::string g_err = "";
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* where) {
+  return fail(QBX_ECUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+#define CK(call, where)                               \
+  do {                                                \
+    cudaError_t e_ = (call);                          \
+    if (e_ != cudaSuccess) return cuda_fail(e_, where); \
+  } while (0)
+
+// Gauss-Legendre by Newton's method on P_q.  P_q and P_q' come from the
+// recurrences (n+1) P_{n+1} = (2n+1) x P_n - n P_{n-1} and
+// P_n' = n (P_{n-1} - x P_n) / (1 - x^2).  Starting guess: Tricomi's
+// asymptotic node formula x_i ~ (1 - (q-1)/(8 q^3)) cos(pi (4i - 1)/(4q + 2)).
+void gl_rule(int q, double* x, double* w) {
+  for (int i = 1; i <= q; ++i) {
+    double th = M_PI * (4.0 * i - 1.0) / (4.0 * q + 2.0);
+    double xi = (1.0 - (q - 1.0) / (8.0 * q * q * q)) * cos(th);
+    double dp = 1.0;
+    for (int it = 0; it < 60; ++it) {
+      double pm = 1.0, p = xi;
+      for (int n = 1; n < q; ++n) {
+        double pn = ((2.0 * n + 1.0) * xi * p - n * pm) / (n + 1.0);
+        pm = p;
+        p = pn;
+      }
+      if (q == 1) { p = xi; pm = 1.0; }
+      dp = q * (pm - xi * p) / (1.0 - xi * xi);
+      double step = p / dp;
+      xi -= step;
+      if (fabs(step) <= 4e-16 * fabs(xi) + 1e-300) {
+        // one more evaluation at the converged point for the weight
+        pm = 1.0;
+        p = xi;
+        for (int n = 1; n < q; ++n) {
+          double pn = ((2.0 * n + 1.0) * xi * p - n * pm) / (n + 1.0);
+          pm = p;
+          p = pn;
+        }
+        if (q == 1) { p = xi; pm = 1.0; }
+        dp = q * (pm - xi * p) / (1.0 - xi * xi);
+        break;
+      }
+    }
+    x[q - i] = xi;
+    w[q - i] = 2.0 / ((1.0 - xi * xi) * dp * dp);
+  }
+}
+
+// Legendre polynomials P_0..P_{n-1} at x.
+void legendre_all(int n, double x, double* P) {
+  P[0] = 1.0;
+  if (n > 1) P[1] = x;
+  for (int j = 1; j + 1 < n; ++j) P[j + 1] = ((2.0 * j + 1.0) * x * P[j] - j * P[j - 1]) / (j + 1.0);
+}
+
+// Interpolation from the q_tgt target nodes to the q_src source nodes of a
+// panel through the Legendre expansion of the interpolant:
+// f(y) = sum_{n<q_tgt} c_n P_n(y), c_n = (2n+1)/2 sum_i w_i f_i P_n(x_i)
+// (exact for degree < q_tgt since the q_tgt-point rule integrates degree
+// 2 q_tgt - 1), so M[j][i] = sum_n (2n+1)/2 w_i P_n(x_i) P_n(y_j).
+void interp_matrix(int qt, int qs, std::vector<double>& Mx) {
+  std::vector<double> xt(qt), wt(qt), xs(qs), ws(qs), Pt(qt * qt), Ps(qt);
+  gl_rule(qt, xt.data(), wt.data());
+  gl_rule(qs, xs.data(), ws.data());
+  for (int i = 0; i < qt; ++i) legendre_all(qt, xt[i], &Pt[i * qt]);
+  Mx.assign((size_t)qs * qt, 0.0);
+  for (int j = 0; j < qs; ++j) {
+    legendre_all(qt, xs[j], Ps.data());
+    for (int i = 0; i < qt; ++i) {
+      double s = 0.0;
+      for (int n = 0; n < qt; ++n) s += (2.0 * n + 1.0) * 0.5 * Pt[i * qt + n] * Ps[n];
+      Mx[(size_t)j * qt + i] = s * wt[i];
+    }
+  }
+}
+
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+int check_plan(const qbx_plan* p) {
+  if (!p) return fail(QBX_EINVAL, "plan is NULL");
+  return QBX_OK;
+}
+
+int check_geom(const qbx_plan* pl, const qbx_geom* g, bool need_ctr) {
+  if (!g) return fail(QBX_EINVAL, "geometry is NULL");
+  if (g->M < 1) return fail(QBX_EINVAL, "geometry: M = %d < 1", g->M);
+  if (g->q_tgt != pl->q_tgt || g->q_src != pl->q_src)
+    return fail(QBX_EINVAL, "geometry q (%d, %d) differs from the plan's (%d, %d)", g->q_tgt,
+                g->q_src, pl->q_tgt, pl->q_src);
+  if (g->n_tgt != g->M * g->q_tgt || g->n_src != g->M * g->q_src)
+    return fail(QBX_EINVAL, "geometry: n_tgt/n_src inconsistent with M*q");
+  if (!g->src_x || !g->src_y || !g->src_nx || !g->src_ny || !g->src_w || !g->tgt_x || !g->tgt_y ||
+      !g->tgt_nx || !g->tgt_ny)
+    return fail(QBX_EINVAL, "geometry: NULL node array");
+  if (need_ctr && (!g->ctr_x || !g->ctr_y || !g->ctr_r))
+    return fail(QBX_EINVAL, "geometry: NULL centre array");
+  return QBX_OK;
+}
+
+int check_k(qbx_c64 k) {
+  if (!isfinite(k.re) || !isfinite(k.im)) return fail(QBX_EINVAL, "k is not finite");
+  if (k.im < 0.0) return fail(QBX_EINVAL, "Im k = %g < 0 (need Im k >= 0)", k.im);
+  if (k.im == 0.0 && !(k.re > 0.0))
+    return fail(QBX_EINVAL, "real k = %g must be > 0 (k = 0 is Laplace; H0 has a cut on the negative axis)", k.re);
+  return QBX_OK;
+}
+
+int check_p(int p) {
+  if (p < 0 || p > QBX_MAX_P) return fail(QBX_EINVAL, "p = %d outside [0, %d]", p, QBX_MAX_P);
+  return QBX_OK;
+}
+
+int side_range(int side, int n_tgt, int* c0, int* nc) {
+  switch (side) {
+    case QBX_SIDE_INT: *c0 = 0; *nc = n_tgt; return QBX_OK;
+    case QBX_SIDE_EXT: *c0 = n_tgt; *nc = n_tgt; return QBX_OK;
+    case QBX_SIDE_TWO: *c0 = 0; *nc = 2 * n_tgt; return QBX_OK;
+    default: return fail(QBX_EINVAL, "side = %d is not INT/EXT/TWO", side);
+  }
+}
+
+// Number of source splits: fill about two waves of 4 CTAs per SM, bounded by
+// kMaxSplit, by one source tile per split, and by the workspace.
+int choose_split(const qbx_plan* pl, int n_units, int n_src, size_t bytes_per_split, size_t avail) {
+  const int target = pl->num_sms * 8;
+  int ns = (target + n_units - 1) / std::max(n_units, 1);
+  ns = std::min(ns, kMaxSplit);
+  ns = std::min(ns, std::max(1, (n_src + kSrcTile - 1) / kSrcTile));
+  ns = std::max(ns, 1);
+  if (bytes_per_split > 0) {
+    size_t fit = avail / bytes_per_split;
+    if ((size_t)ns > fit) ns = (int)fit;
+  }
+  return ns;
+}
+
+int split_len(int n_src, int ns) {
+  // sources per split, rounded up to a multiple of the tile
+  int per = (n_src + ns - 1) / ns;
+  return ((per + kSrcTile - 1) / kSrcTile) * kSrcTile;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* qbx_last_error(void) { return g_err.c_str(); }
+
+int qbx_version(void) { return 1; }
+
+int qbx_gauss_legendre(int q, double* nodes, double* weights) {
+  if (q < 1 || q > QBX_MAX_Q) return fail(QBX_EINVAL, "q = %d outside [1, %d]", q, QBX_MAX_Q);
+  if (!nodes || !weights) return fail(QBX_EINVAL, "NULL output");
+  gl_rule(q, nodes, weights);
+  return QBX_OK;
+}
+
+size_t qbx_workspace_bytes(int n_src, int n_ctr, int ncoef, int nrhs) {
+  if (n_src < 0 || n_ctr < 0 || ncoef < 0 || nrhs < 0) return 0;
+  return align256((size_t)n_src * nrhs * 16) +
+         align256((size_t)kMaxSplit * n_ctr * ncoef * nrhs * 16) + 256;
+}
+
+int qbx_plan_create(qbx_plan** plan, int device, int q_tgt, int q_src, size_t workspace_bytes) {
+  if (!plan) return fail(QBX_EINVAL, "plan out-pointer is NULL");
+  *plan = nullptr;
+  if (q_tgt < 1 || q_tgt > QBX_MAX_Q || q_src < 1 || q_src > QBX_MAX_Q)
+    return fail(QBX_EINVAL, "q_tgt = %d, q_src = %d outside [1, %d]", q_tgt, q_src, QBX_MAX_Q);
+  CK(cudaSetDevice(device), "cudaSetDevice");
+  qbx_plan* p = new qbx_plan();
+  memset(p, 0, sizeof(*p));
+  p->device = device;
+  p->q_tgt = q_tgt;
+  p->q_src = q_src;
+  cudaError_t e = cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, device);
+  std::vector<double> Mx, xt(q_tgt), wt(q_tgt), xs(q_src), ws(q_src);
+  interp_matrix(q_tgt, q_src, Mx);
+  gl_rule(q_tgt, xt.data(), wt.data());
+  gl_rule(q_src, xs.data(), ws.data());
+  if (e == cudaSuccess) e = cudaMalloc(&p->d_interp, Mx.size() * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&p->d_wgl_tgt, q_tgt * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&p->d_wgl_src, q_src * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&p->d_status, sizeof(int));
+  if (e == cudaSuccess && workspace_bytes > 0) e = cudaMalloc(&p->ws, workspace_bytes);
+  if (e == cudaSuccess) e = cudaMemcpy(p->d_interp, Mx.data(), Mx.size() * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(p->d_wgl_tgt, wt.data(), q_tgt * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(p->d_wgl_src, ws.data(), q_src * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(p->d_status, 0, sizeof(int));
+  if (e != cudaSuccess) {
+    qbx_plan_destroy(p);
+    return cuda_fail(e, "qbx_plan_create");
+  }
+  p->ws_bytes = workspace_bytes;
+  *plan = p;
+  return QBX_OK;
+}
+
+int qbx_plan_destroy(qbx_plan* p) {
+  if (!p) return QBX_OK;
+  cudaSetDevice(p->device);
+  cudaFree(p->d_interp);
+  cudaFree(p->d_wgl_tgt);
+  cudaFree(p->d_wgl_src);
+  cudaFree(p->d_status);
+  cudaFree(p->ws);
+  delete p;
+  return QBX_OK;
+}
+
+int qbx_sync_status(qbx_plan* p, void* stream) {
+  if (int rc = check_plan(p)) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  int h = 0;
+  CK(cudaMemcpyAsync(&h, p->d_status, sizeof(int), cudaMemcpyDeviceToHost, st), "status copy");
+  CK(cudaStreamSynchronize(st), "status sync");
+  CK(cudaMemsetAsync(p->d_status, 0, sizeof(int), st), "status clear");
+  CK(cudaStreamSynchronize(st), "status sync");
+  if (h) return fail(QBX_ENONFINITE, "a kernel produced a non-finite value");
+  return QBX_OK;
+}
+
+int qbx_geometry(qbx_plan* p, qbx_geom* g, const double* t_edges, const double* gam_tgt,
+                 const double* dgam_tgt, const double* gam_src, const double* dgam_src,
+                 double r_factor, void* stream) {
+  if (int rc = check_plan(p)) return rc;
+  if (!g) return fail(QBX_EINVAL, "geometry is NULL");
+  g->n_tgt = g->M * g->q_tgt;
+  g->n_src = g->M * g->q_src;
+  if (int rc = check_geom(p, g, true)) return rc;
+  if (!g->panel_h || !g->ctr_ratio || !g->src_w || !g->tgt_w) return fail(QBX_EINVAL, "geometry: NULL output");
+  if (!t_edges || !gam_tgt || !dgam_tgt || !gam_src || !dgam_src) return fail(QBX_EINVAL, "NULL curve samples");
+  if (!(r_factor > 0.0) || !isfinite(r_factor)) return fail(QBX_EINVAL, "r_factor must be > 0");
+  CK(cudaSetDevice(p->device), "cudaSetDevice");
+  CK(launch_geometry(g->M, g->q_tgt, g->q_src, t_edges, gam_tgt, dgam_tgt, gam_src, dgam_src,
+                     p->d_wgl_tgt, p->d_wgl_src, r_factor, *g, (cudaStream_t)stream),
+     "geometry kernels");
+  return QBX_OK;
+}
+
+int qbx_upsample(qbx_plan* p, const qbx_geom* g, const qbx_c64* dens_tgt, int nrhs,
+                 qbx_c64* wdens_src, void* stream) {
+  if (int rc = check_plan(p)) return rc;
+  if (int rc = check_geom(p, g, false)) return rc;
+  if (nrhs < 1) return fail(QBX_EINVAL, "nrhs = %d < 1", nrhs);
+  if (!dens_tgt || !wdens_src) return fail(QBX_EINVAL, "NULL density");
+  CK(cudaSetDevice(p->device), "cudaSetDevice");
+  CK(launch_upsample(g->M, g->q_tgt, g->q_src, nrhs, p->d_interp, g->src_w, dens_tgt, wdens_src,
+                     (cudaStream_t)stream),
+     "upsample kernel");
+  return QBX_OK;
+}
+
+int qbx_form_locals(qbx_plan* p, const qbx_geom* g, int kind, int side, qbx_c64 k, int pp,
+                    const qbx_c64* wdens_src, int nrhs, qbx_c64* alpha, void* stream) {
+  if (int rc = check_plan(p)) return rc;
+  if (int rc = check_geom(p, g, true)) return rc;
+  if (kind != QBX_OP_S && kind != QBX_OP_D) return fail(QBX_EINVAL, "kind must be S or D");
+  if (int rc = check_k(k)) return rc;
+  if (int rc = check_p(pp)) return rc;
+  if (nrhs < 1) return fail(QBX_EINVAL, "nrhs = %d < 1", nrhs);
+  if (!wdens_src || !alpha) return fail(QBX_EINVAL, "NULL array");
+  int c0, nc;
+  if (int rc = side_range(side, g->n_tgt, &c0, &nc)) return rc;
+  CK(cudaSetDevice(p->device), "cudaSetDevice");
+  const int ncoef = 2 * pp + 1;
+  // rhs per pass limited by the shared-memory accumulators
+  int nr = nrhs;
+  while (nr > 1 && form_smem_bytes(pp, nr) > 160 * 1024) nr = (nr + 1) / 2;
+  if (form_smem_bytes(pp, nr) > 200 * 1024) return fail(QBX_EINVAL, "p = %d too large for form_locals", pp);
+  const size_t per_split = (size_t)nc * ncoef * nrhs * 16;
+  const int units = (nc + kFormThreads - 1) / kFormThreads;
+  const int ns = choose_split(p, units, g->n_src, per_split, p->ws_bytes > 256 ? p->ws_bytes - 256 : 0);
+  if (ns < 1) return fail(QBX_ENOMEM, "workspace too small for form_locals (need %zu bytes)", per_split);
+  cudaStream_t st = (cudaStream_t)stream;
+  void* part = (void*)align256((size_t)p->ws);
+  FormArgs a{};
+  a.kind = kind;
+  a.p = pp;
+  a.kre = k.re;
+  a.kim = k.im;
+  a.n_ctr = nc;
+  a.cx = g->ctr_x + c0;
+  a.cy = g->ctr_y + c0;
+  a.src = SrcView{g->src_x, g->src_y, g->src_nx, g->src_ny, g->n_src};
+  a.wd = wdens_src;
+  a.nrhs = nrhs;
+  a.nsplit = ns;
+  a.src_per_split = split_len(g->n_src, ns);
+  a.part = part;
+  for (int r0 = 0; r0 < nrhs; r0 += nr) {
+    a.rhs0 = r0;
+    a.nr = std::min(nr, nrhs - r0);
+    CK(launch_form(a, st), "form kernel");
+  }
+  CK(launch_form_finish(nc, ncoef, ns, nrhs, part, alpha, p->d_status, st), "form finish");
+  return QBX_OK;
+}
+
+int qbx_eval_locals(qbx_plan* p, const qbx_geom* g, int side, qbx_c64 k, int pp, const qbx_c64* alpha,
+                    int nrhs, int what, int n_eval, const double* ex, const double* ey,
+                    const int* ectr, qbx_c64* out, void* stream) {
+  if (int rc = check_plan(p)) return rc;
+  if (int rc = check_geom(p, g, true)) return rc;
+  if (int rc = check_k(k)) return rc;
+  if (int rc = check_p(pp)) return rc;
+  if (nrhs < 1) return fail(QBX_EINVAL, "nrhs = %d < 1", nrhs);
+  if (what != QBX_VALUE && what != QBX_GRAD) return fail(QBX_EINVAL, "what must be VALUE or GRAD");
+  if (!alpha || !out) return fail(QBX_EINVAL, "NULL array");
+  int c0, nc;
+  if (int rc = side_range(side, g->n_tgt, &c0, &nc)) return rc;
+  if (n_eval < 0) return fail(QBX_EINVAL, "n_eval < 0");
+  EvalArgs a{};
+  if (n_eval == 0) {
+    a.n_eval = nc;
+    a.ex = a.ey = nullptr;
+    a.ectr = nullptr;
+  } else {
+    if (!ex || !ey || !ectr) return fail(QBX_EINVAL, "n_eval > 0 needs ex, ey, ectr");
+    a.n_eval = n_eval;
+    a.ex = ex;
+    a.ey = ey;
+    a.ectr = ectr;
+  }
+  CK(cudaSetDevice(p->device), "cudaSetDevice");
+  a.what = what;
+  a.p = pp;
+  a.kre = k.re;
+  a.kim = k.im;
+  a.cx = g->ctr_x + c0;
+  a.cy = g->ctr_y + c0;
+  a.n_tgt = g->n_tgt;
+  a.tx = g->tgt_x;
+  a.ty = g->tgt_y;
+  a.alpha = alpha;
+  a.nrhs = nrhs;
+  a.out = out;
+  a.n_ctr = nc;
+  a.status = p->d_status;
+  CK(launch_eval(a, (cudaStream_t)stream), "eval kernel");
+  return QBX_OK;
+}
+
+static int far_impl(qbx_plan* p, const qbx_geom* g, int op, qbx_c64 k, const qbx_c64* wd, int nrhs,
+                    int n_far, const double* x_far, qbx_c64* out, void* part, size_t avail,
+                    cudaStream_t st) {
+  const int ncomp = op == QBX_OP_GRAD_S ? 2 : 1;
+  const size_t per_split = (size_t)n_far * ncomp * nrhs * 16;
+  const int units = (n_far + kApplyThreads - 1) / kApplyThreads;
+  const int ns = choose_split(p, units, g->n_src, per_split, avail);
+  if (ns < 1) return fail(QBX_ENOMEM, "workspace too small for the far targets");
+  FarArgs a{};
+  a.op = op;
+  a.kre = k.re;
+  a.kim = k.im;
+  a.n_far = n_far;
+  a.xy = x_far;
+  a.src = SrcView{g->src_x, g->src_y, g->src_nx, g->src_ny, g->n_src};
+  a.wd = wd;
+  a.nrhs = nrhs;
+  a.nsplit = ns;
+  a.src_per_split = split_len(g->n_src, ns);
+  a.part = part;
+  for (int r0 = 0; r0 < nrhs; r0 += 8) {
+    a.rhs0 = r0;
+    a.nr = std::min(8, nrhs - r0);
+    CK(launch_far(a, st), "far kernel");
+  }
+  CK(launch_far_finish(op, k.re, k.im, n_far, ns, nrhs, part, out, p->d_status, st), "far finish");
+  return QBX_OK;
+}
+
+int qbx_far(qbx_plan* p, const qbx_geom* g, int op, qbx_c64 k, const qbx_c64* wdens_src, int nrhs,
+            int n_far, const double* x_far, qbx_c64* out, void* stream) {
+  if (int rc = check_plan(p)) return rc;
+  if (int rc = check_geom(p, g, false)) return rc;
+  if (op != QBX_OP_S && op != QBX_OP_D && op != QBX_OP_GRAD_S) return fail(QBX_EINVAL, "bad op %d", op);
+  if (int rc = check_k(k)) return rc;
+  if (nrhs < 1) return fail(QBX_EINVAL, "nrhs = %d < 1", nrhs);
+  if (n_far < 0) return fail(QBX_EINVAL, "n_far < 0");
+  if (n_far == 0) return QBX_OK;
+  if (!wdens_src || !x_far || !out) return fail(QBX_EINVAL, "NULL array");
+  CK(cudaSetDevice(p->device), "cudaSetDevice");
+  void* part = (void*)align256((size_t)p->ws);
+  return far_impl(p, g, op, k, wdens_src, nrhs, n_far, x_far, out, part,
+                  p->ws_bytes > 256 ? p->ws_bytes - 256 : 0, (cudaStream_t)stream);
+}
+
+int qbx_apply(qbx_plan* p, const qbx_geom* g, int op, int side, int limit, qbx_c64 k, int pp,
+              const qbx_c64* dens_tgt, int nrhs, int n_far, const double* x_far, qbx_c64* out_on,
+              qbx_c64* out_far, void* stream) {
+  if (int rc = check_plan(p)) return rc;
+  if (int rc = check_geom(p, g, true)) return rc;
+  if (op != QBX_OP_S && op != QBX_OP_D && op != QBX_OP_GRAD_S) return fail(QBX_EINVAL, "bad op %d", op);
+  if (limit != QBX_LIMIT_ONE_SIDED && limit != QBX_LIMIT_PV) return fail(QBX_EINVAL, "bad limit %d", limit);
+  if (int rc = check_k(k)) return rc;
+  if (int rc = check_p(pp)) return rc;
+  if (nrhs < 1) return fail(QBX_EINVAL, "nrhs = %d < 1", nrhs);
+  if (!dens_tgt || !out_on) return fail(QBX_EINVAL, "NULL density or output");
+  if (n_far < 0) return fail(QBX_EINVAL, "n_far < 0");
+  if (n_far > 0 && (!x_far || !out_far)) return fail(QBX_EINVAL, "n_far > 0 needs x_far and out_far");
+  int c0, nc;
+  if (int rc = side_range(side, g->n_tgt, &c0, &nc)) return rc;
+  const int ncomp = op == QBX_OP_GRAD_S ? 2 : 1;
+  const size_t wd_bytes = align256((size_t)g->n_src * nrhs * 16);
+  if (p->ws_bytes < wd_bytes + 512) return fail(QBX_ENOMEM, "workspace too small (%zu < %zu)", p->ws_bytes, wd_bytes + 512);
+  const size_t avail = p->ws_bytes - wd_bytes - 512;
+  const size_t per_split = (size_t)nc * ncomp * nrhs * 16;
+  const int units = (nc + kApplyThreads - 1) / kApplyThreads;
+  const int ns = choose_split(p, units, g->n_src, per_split, avail);
+  if (ns < 1) return fail(QBX_ENOMEM, "workspace too small for the apply partial sums");
+  if (apply_smem_bytes(op, k.im != 0.0, pp, 8) > 220 * 1024) return fail(QBX_EINVAL, "p = %d too large", pp);
+  CK(cudaSetDevice(p->device), "cudaSetDevice");
+  cudaStream_t st = (cudaStream_t)stream;
+  char* base = (char*)align256((size_t)p->ws);
+  void* wd = base;
+  void* part = base + wd_bytes;
+  // a1: oversample the density
+  CK(launch_upsample(g->M, g->q_tgt, g->q_src, nrhs, p->d_interp, g->src_w, dens_tgt, wd, st), "upsample");
+  // a2-a6 fused, per chunk of up to 8 rhs
+  ApplyArgs a{};
+  a.op = op;
+  a.p = pp;
+  a.kre = k.re;
+  a.kim = k.im;
+  a.n_ctr = nc;
+  a.cx = g->ctr_x + c0;
+  a.cy = g->ctr_y + c0;
+  a.n_tgt = g->n_tgt;
+  a.tx = g->tgt_x;
+  a.ty = g->tgt_y;
+  a.src = SrcView{g->src_x, g->src_y, g->src_nx, g->src_ny, g->n_src};
+  a.wd = wd;
+  a.nrhs = nrhs;
+  a.nsplit = ns;
+  a.src_per_split = split_len(g->n_src, ns);
+  a.part = part;
+  for (int r0 = 0; r0 < nrhs; r0 += 8) {
+    a.rhs0 = r0;
+    a.nr = std::min(8, nrhs - r0);
+    CK(launch_apply_fused(a, st), "apply kernel");
+  }
+  // a7: reduce, i/4, jumps / two-sided average
+  CK(launch_apply_finish(op, side, limit, g->n_tgt, ns, nc, nrhs, part, dens_tgt, g->tgt_nx, g->tgt_ny,
+                         out_on, p->d_status, st),
+     "apply finish");
+  // a8: far targets
+  if (n_far > 0)
+    return far_impl(p, g, op, k, (const qbx_c64*)wd, nrhs, n_far, x_far, out_far, part, avail, st);
+  return QBX_OK;
+}
+
+int qbx_assign_centres(qbx_plan* p, const qbx_geom* g, int side, int n, const double* xy, int* out,
+                       void* stream) {
+  if (int rc = check_plan(p)) return rc;
+  if (int rc = check_geom(p, g, true)) return rc;
+  int c0, nc;
+  if (int rc = side_range(side, g->n_tgt, &c0, &nc)) return rc;
+  if (n < 0) return fail(QBX_EINVAL, "n < 0");
+  if (n == 0) return QBX_OK;
+  if (!xy || !out) return fail(QBX_EINVAL, "NULL array");
+  CK(cudaSetDevice(p->device), "cudaSetDevice");
+  CK(launch_assign(n, xy, nc, g->ctr_x + c0, g->ctr_y + c0, g->ctr_r + c0, out, (cudaStream_t)stream),
+     "assign kernel");
+  return QBX_OK;
+}
+
+int qbx_debug_hankel01(const qbx_c64* z, int n, qbx_c64* h0, qbx_c64* h1, void* stream) {
+  if (n < 0) return fail(QBX_EINVAL, "n < 0");
+  if (n == 0) return QBX_OK;
+  if (!z || !h0 || !h1) return fail(QBX_EINVAL, "NULL array");
+  CK(launch_debug_hankel(z, n, h0, h1, (cudaStream_t)stream), "debug hankel");
+  return QBX_OK;
+}
+
+int qbx_debug_besselj(const qbx_c64* z, int n, int nmax, qbx_c64* j, void* stream) {
+  if (n < 0 || nmax < 0 || nmax > QBX_MAX_P + 1) return fail(QBX_EINVAL, "bad n or nmax");
+  if (n == 0) return QBX_OK;
+  if (!z || !j) return fail(QBX_EINVAL, "NULL array");
+  CK(launch_debug_besselj(z, n, nmax, j, (cudaStream_t)stream), "debug besselj");
+  return QBX_OK;
+}
+
+}  // extern "C"

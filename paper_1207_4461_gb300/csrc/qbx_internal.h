@@ -1,0 +1,110 @@
+// qbx_internal.h -- launch descriptors shared by the library's translation
+// units (host side of the kernels).  Not part of the public ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include "../../include/qbx.h"
+
+namespace qbx {
+
+struct cplx;
+
+constexpr int kApplyThreads = 128;   // centres per CTA of the fused apply
+constexpr int kSrcTile = 128;        // sources staged in shared memory per step
+constexpr int kFormThreads = 64;     // centres per CTA of form_locals
+constexpr int kMaxSplit = 64;        // source splits of the split reductions
+
+struct SrcView {
+  const double *x, *y, *nx, *ny;
+  int n;
+};
+
+// Fused storage-free apply (a2-a6 fused), one launch per chunk of `nr` rhs.
+struct ApplyArgs {
+  int op;                 // QBX_OP_*
+  int p;
+  double kre, kim;
+  int n_ctr;              // centres in this launch
+  const double *cx, *cy;  // [n_ctr]
+  int n_tgt;              // target of centre c is c mod n_tgt
+  const double *tx, *ty;  // [n_tgt]
+  SrcView src;
+  const void* wd;         // [n_src][nrhs] complex
+  int nrhs, rhs0, nr;     // total rhs, first rhs of this chunk, chunk width
+  int nsplit, src_per_split;
+  void* part;             // [nsplit][n_ctr][ncomp][nrhs] complex
+};
+cudaError_t launch_apply_fused(const ApplyArgs& a, cudaStream_t st);
+size_t apply_smem_bytes(int op, bool ck, int p, int nr);
+
+// Far targets: plain quadrature partial sums.
+struct FarArgs {
+  int op;
+  double kre, kim;
+  int n_far;
+  const double* xy;       // [n_far][2]
+  SrcView src;
+  const void* wd;
+  int nrhs, rhs0, nr;
+  int nsplit, src_per_split;
+  void* part;             // [nsplit][n_far][ncomp][nrhs]
+};
+cudaError_t launch_far(const FarArgs& a, cudaStream_t st);
+
+// Unfused coefficients (a4).
+struct FormArgs {
+  int kind, p;
+  double kre, kim;
+  int n_ctr;
+  const double *cx, *cy;
+  SrcView src;
+  const void* wd;
+  int nrhs, rhs0, nr;
+  int nsplit, src_per_split;
+  void* part;             // [nsplit][n_ctr][2p+1][nrhs]
+};
+cudaError_t launch_form(const FormArgs& a, cudaStream_t st);
+size_t form_smem_bytes(int p, int nr);
+
+// Evaluation of stored coefficients (a5 + a6).
+struct EvalArgs {
+  int what, p;
+  double kre, kim;
+  int n_eval;
+  const double *ex, *ey;  // targets (may be null: default on-surface)
+  const int* ectr;        // centre per target (null: identity)
+  const double *cx, *cy;
+  int n_tgt;
+  const double *tx, *ty;
+  const void* alpha;      // [n_ctr][2p+1][nrhs]
+  int nrhs;
+  void* out;
+  int n_ctr;              // centres of the side (bound for ectr)
+  int* status;
+};
+cudaError_t launch_eval(const EvalArgs& a, cudaStream_t st);
+
+// Reductions over splits and epilogues.
+cudaError_t launch_apply_finish(int op, int side, int limit, int n_tgt, int nsplit, int n_ctr,
+                                int nrhs, const void* part, const void* dens_tgt,
+                                const double* tgt_nx, const double* tgt_ny, void* out,
+                                int* status, cudaStream_t st);
+cudaError_t launch_far_finish(int op, double kre, double kim, int n_far, int nsplit, int nrhs,
+                              const void* part, void* out, int* status, cudaStream_t st);
+cudaError_t launch_form_finish(int n_ctr, int ncoef, int nsplit, int nrhs, const void* part,
+                               void* alpha, int* status, cudaStream_t st);
+
+// Geometry, oversampling, centre assignment.
+cudaError_t launch_geometry(int M, int q_tgt, int q_src, const double* t_edges,
+                            const double* gam_tgt, const double* dgam_tgt,
+                            const double* gam_src, const double* dgam_src,
+                            const double* wgl_tgt, const double* wgl_src, double r_factor,
+                            const qbx_geom& g, cudaStream_t st);
+cudaError_t launch_upsample(int M, int q_tgt, int q_src, int nrhs, const double* interp,
+                            const double* src_w, const void* dens_tgt, void* wdens,
+                            cudaStream_t st);
+cudaError_t launch_assign(int n, const double* xy, int n_ctr, const double* cx,
+                          const double* cy, const double* cr, int* out, cudaStream_t st);
+cudaError_t launch_debug_hankel(const void* z, int n, void* h0, void* h1, cudaStream_t st);
+cudaError_t launch_debug_besselj(const void* z, int n, int nmax, void* j, cudaStream_t st);
+
+}  // namespace qbx

@@ -1,0 +1,312 @@
+"""Thin ctypes binding of the C ABI in include/qbx.h (same names, argument
+marshalling only).  Every step of the computation runs in the CUDA library
+libqbx_gb300.so; there is no CPU fallback: if the library cannot be built or
+loaded, every call raises.
+
+Device arrays are torch tensors (float64 / complex128, contiguous, on the
+plan's device); complex128 storage is interleaved (re, im) FP64, the layout of
+qbx_c64.  Calls are asynchronous on torch's current CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import threading
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+OP_S, OP_D, OP_GRAD_S = 0, 1, 2
+SIDE_INT, SIDE_EXT, SIDE_TWO = 0, 1, 2
+LIMIT_ONE_SIDED, LIMIT_PV = 0, 1
+VALUE, GRAD = 0, 1
+MAX_P = 40
+
+_ERR = {0: "QBX_OK", 1: "QBX_EINVAL", 2: "QBX_ECUDA", 3: "QBX_EINADMISSIBLE", 4: "QBX_ENONFINITE",
+        5: "QBX_ENOCONV", 6: "QBX_ETIMEOUT", 7: "QBX_ENOMEM"}
+
+
+class QBXError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_ERR.get(code, code)}: {msg}")
+        self.code = code
+
+
+class c64(ctypes.Structure):
+    _fields_ = [("re", ctypes.c_double), ("im", ctypes.c_double)]
+
+
+_P = ctypes.c_void_p
+
+
+class GeomStruct(ctypes.Structure):
+    _fields_ = [("M", ctypes.c_int), ("q_tgt", ctypes.c_int), ("q_src", ctypes.c_int),
+                ("n_tgt", ctypes.c_int), ("n_src", ctypes.c_int)] + [
+        (n, _P) for n in ("src_x", "src_y", "src_nx", "src_ny", "src_w",
+                          "tgt_x", "tgt_y", "tgt_nx", "tgt_ny", "tgt_w",
+                          "panel_h", "ctr_x", "ctr_y", "ctr_r", "ctr_ratio")]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib():
+    """Load (building first if needed) the CUDA library."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            L = ctypes.CDLL(path)
+            I, D, Z = ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+            G = ctypes.POINTER(GeomStruct)
+            PP = ctypes.POINTER(ctypes.c_void_p)
+            L.qbx_last_error.restype = ctypes.c_char_p
+            L.qbx_version.restype = I
+            L.qbx_gauss_legendre.argtypes = [I, _P, _P]
+            L.qbx_plan_create.argtypes = [PP, I, I, I, Z]
+            L.qbx_plan_destroy.argtypes = [_P]
+            L.qbx_workspace_bytes.argtypes = [I, I, I, I]
+            L.qbx_workspace_bytes.restype = Z
+            L.qbx_sync_status.argtypes = [_P, _P]
+            L.qbx_geometry.argtypes = [_P, G, _P, _P, _P, _P, _P, D, _P]
+            L.qbx_upsample.argtypes = [_P, G, _P, I, _P, _P]
+            L.qbx_form_locals.argtypes = [_P, G, I, I, c64, I, _P, I, _P, _P]
+            L.qbx_eval_locals.argtypes = [_P, G, I, c64, I, _P, I, I, I, _P, _P, _P, _P, _P]
+            L.qbx_apply.argtypes = [_P, G, I, I, I, c64, I, _P, I, I, _P, _P, _P, _P]
+            L.qbx_far.argtypes = [_P, G, I, c64, _P, I, I, _P, _P, _P]
+            L.qbx_assign_centres.argtypes = [_P, G, I, I, _P, _P, _P]
+            L.qbx_debug_hankel01.argtypes = [_P, I, _P, _P, _P]
+            L.qbx_debug_besselj.argtypes = [_P, I, I, _P, _P]
+            for name in ("qbx_gauss_legendre", "qbx_plan_create", "qbx_plan_destroy", "qbx_sync_status",
+                         "qbx_geometry", "qbx_upsample", "qbx_form_locals", "qbx_eval_locals", "qbx_apply",
+                         "qbx_far", "qbx_assign_centres", "qbx_debug_hankel01", "qbx_debug_besselj"):
+                getattr(L, name).restype = I
+            _lib = L
+    return _lib
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def _check(rc):
+    if rc != 0:
+        raise QBXError(rc, lib().qbx_last_error().decode())
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _k(k):
+    k = complex(k)
+    return c64(k.real, k.imag)
+
+
+# ----------------------------------------------------------------------------
+# Host helpers
+# ----------------------------------------------------------------------------
+def qbx_gauss_legendre(q: int):
+    x = np.zeros(q)
+    w = np.zeros(q)
+    _check(lib().qbx_gauss_legendre(q, x.ctypes.data_as(_P), w.ctypes.data_as(_P)))
+    return x, w
+
+
+def qbx_workspace_bytes(n_src, n_ctr, ncoef, nrhs) -> int:
+    return int(lib().qbx_workspace_bytes(n_src, n_ctr, ncoef, nrhs))
+
+
+class Plan:
+    """qbx_plan_create / qbx_plan_destroy."""
+
+    def __init__(self, q_tgt=16, q_src=64, workspace_bytes=None, device=None, n_src=0, n_ctr=0,
+                 ncoef=2, nrhs=1):
+        self.device = torch.cuda.current_device() if device is None else int(device)
+        if workspace_bytes is None:
+            workspace_bytes = max(qbx_workspace_bytes(n_src, n_ctr, ncoef, nrhs), 1 << 20)
+        self.q_tgt, self.q_src, self.workspace_bytes = q_tgt, q_src, int(workspace_bytes)
+        h = ctypes.c_void_p()
+        _check(lib().qbx_plan_create(ctypes.byref(h), self.device, q_tgt, q_src, self.workspace_bytes))
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None) and self.handle.value:
+            lib().qbx_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def qbx_plan_create(q_tgt=16, q_src=64, workspace_bytes=None, device=None, **kw) -> Plan:
+    return Plan(q_tgt, q_src, workspace_bytes, device, **kw)
+
+
+def qbx_sync_status(plan: Plan):
+    _check(lib().qbx_sync_status(plan.handle, _stream()))
+
+
+class Geometry:
+    """Device arrays of a discretised curve (qbx_geom) and the parameter values
+    of the target / source nodes."""
+
+    def __init__(self, M, q_tgt, q_src, device):
+        f64 = dict(dtype=torch.float64, device=device)
+        self.M, self.q_tgt, self.q_src = M, q_tgt, q_src
+        self.n_tgt, self.n_src = M * q_tgt, M * q_src
+        self.t = {}
+        for n in ("src_x", "src_y", "src_nx", "src_ny", "src_w"):
+            self.t[n] = torch.zeros(self.n_src, **f64)
+        for n in ("tgt_x", "tgt_y", "tgt_nx", "tgt_ny", "tgt_w"):
+            self.t[n] = torch.zeros(self.n_tgt, **f64)
+        self.t["panel_h"] = torch.zeros(M, **f64)
+        for n in ("ctr_x", "ctr_y", "ctr_r", "ctr_ratio"):
+            self.t[n] = torch.zeros(2 * self.n_tgt, **f64)
+        self.s = GeomStruct(M, q_tgt, q_src, self.n_tgt, self.n_src,
+                            *[ctypes.c_void_p(self.t[n].data_ptr()) for n in (
+                                "src_x", "src_y", "src_nx", "src_ny", "src_w",
+                                "tgt_x", "tgt_y", "tgt_nx", "tgt_ny", "tgt_w",
+                                "panel_h", "ctr_x", "ctr_y", "ctr_r", "ctr_ratio")])
+
+    def __getitem__(self, name):
+        return self.t[name]
+
+    def ref(self):
+        return ctypes.byref(self.s)
+
+
+def panel_nodes(t_edges, q):
+    """Curve parameter at the q-node GL points of each panel (library's GL rule)."""
+    x, _ = qbx_gauss_legendre(q)
+    t_edges = np.asarray(t_edges, dtype=np.float64)
+    a, b = t_edges[:-1], t_edges[1:]
+    return (0.5 * (a + b)[:, None] + 0.5 * (b - a)[:, None] * x[None, :]).reshape(-1)
+
+
+def qbx_geometry(plan: Plan, curve, t_edges, r_factor=0.5) -> Geometry:
+    """Sample `curve` (t -> (gamma [n,2], gamma' [n,2])) at the panels' GL nodes
+    and run qbx_geometry on the device."""
+    dev = torch.device("cuda", plan.device)
+    t_edges = np.asarray(t_edges, dtype=np.float64)
+    M = t_edges.size - 1
+    g = Geometry(M, plan.q_tgt, plan.q_src, dev)
+    g.t_tgt = panel_nodes(t_edges, plan.q_tgt)
+    g.t_src = panel_nodes(t_edges, plan.q_src)
+    gt, dgt = curve(g.t_tgt)
+    gs, dgs = curve(g.t_src)
+    up = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device=dev)
+    g.inputs = [up(t_edges), up(gt), up(dgt), up(gs), up(dgs)]
+    _check(lib().qbx_geometry(plan.handle, g.ref(), *[_ptr(a) for a in g.inputs], float(r_factor),
+                              _stream()))
+    return g
+
+
+def _dens2d(d, n):
+    if d.dim() == 1:
+        d = d.reshape(n, 1)
+    if d.dtype != torch.complex128:
+        raise TypeError("densities must be complex128")
+    return d.contiguous()
+
+
+def qbx_upsample(plan: Plan, g: Geometry, dens_tgt):
+    d = _dens2d(dens_tgt, g.n_tgt)
+    out = torch.empty((g.n_src, d.shape[1]), dtype=torch.complex128, device=d.device)
+    _check(lib().qbx_upsample(plan.handle, g.ref(), _ptr(d), d.shape[1], _ptr(out), _stream()))
+    return out
+
+
+def _nctr(g, side):
+    return 2 * g.n_tgt if side == SIDE_TWO else g.n_tgt
+
+
+def qbx_form_locals(plan: Plan, g: Geometry, kind, side, k, p, wdens_src):
+    wd = _dens2d(wdens_src, g.n_src)
+    nrhs = wd.shape[1]
+    alpha = torch.empty((_nctr(g, side), 2 * p + 1, nrhs), dtype=torch.complex128, device=wd.device)
+    _check(lib().qbx_form_locals(plan.handle, g.ref(), kind, side, _k(k), p, _ptr(wd), nrhs,
+                                 _ptr(alpha), _stream()))
+    return alpha
+
+
+def qbx_eval_locals(plan: Plan, g: Geometry, side, k, p, alpha, what=VALUE, ex=None, ey=None, ectr=None):
+    nrhs = alpha.shape[2]
+    if ex is None:
+        n = 0
+        n_out = _nctr(g, side)
+    else:
+        n = n_out = ex.numel()
+    shape = (n_out, 2, nrhs) if what == GRAD else (n_out, nrhs)
+    out = torch.empty(shape, dtype=torch.complex128, device=alpha.device)
+    _check(lib().qbx_eval_locals(plan.handle, g.ref(), side, _k(k), p, _ptr(alpha.contiguous()), nrhs, what,
+                                 n, _ptr(ex), _ptr(ey), _ptr(ectr), _ptr(out), _stream()))
+    return out
+
+
+def qbx_apply(plan: Plan, g: Geometry, op, side, limit, k, p, dens_tgt, x_far=None, out_on=None):
+    """On-surface apply of S, D or grad S (plus far targets x_far [n,2])."""
+    d = _dens2d(dens_tgt, g.n_tgt)
+    nrhs = d.shape[1]
+    shape = (g.n_tgt, 2, nrhs) if op == OP_GRAD_S else (g.n_tgt, nrhs)
+    if out_on is None:
+        out_on = torch.empty(shape, dtype=torch.complex128, device=d.device)
+    n_far = 0 if x_far is None else x_far.shape[0]
+    out_far = None
+    if n_far:
+        fshape = (n_far, 2, nrhs) if op == OP_GRAD_S else (n_far, nrhs)
+        out_far = torch.empty(fshape, dtype=torch.complex128, device=d.device)
+    _check(lib().qbx_apply(plan.handle, g.ref(), op, side, limit, _k(k), p, _ptr(d), nrhs, n_far,
+                           _ptr(x_far.contiguous()) if n_far else None, _ptr(out_on), _ptr(out_far),
+                           _stream()))
+    return (out_on, out_far) if n_far else out_on
+
+
+def qbx_far(plan: Plan, g: Geometry, op, k, wdens_src, x_far):
+    wd = _dens2d(wdens_src, g.n_src)
+    nrhs = wd.shape[1]
+    n = x_far.shape[0]
+    shape = (n, 2, nrhs) if op == OP_GRAD_S else (n, nrhs)
+    out = torch.empty(shape, dtype=torch.complex128, device=wd.device)
+    _check(lib().qbx_far(plan.handle, g.ref(), op, _k(k), _ptr(wd), nrhs, n, _ptr(x_far.contiguous()),
+                         _ptr(out), _stream()))
+    return out
+
+
+def qbx_assign_centres(plan: Plan, g: Geometry, side, xy):
+    out = torch.empty(xy.shape[0], dtype=torch.int32, device=xy.device)
+    _check(lib().qbx_assign_centres(plan.handle, g.ref(), side, xy.shape[0], _ptr(xy.contiguous()),
+                                    _ptr(out), _stream()))
+    return out
+
+
+def qbx_debug_hankel01(z):
+    z = z.to(torch.complex128).contiguous()
+    h0 = torch.empty_like(z)
+    h1 = torch.empty_like(z)
+    _check(lib().qbx_debug_hankel01(_ptr(z), z.numel(), _ptr(h0), _ptr(h1), _stream()))
+    return h0, h1
+
+
+def qbx_debug_besselj(z, nmax):
+    z = z.to(torch.complex128).contiguous()
+    out = torch.empty((z.numel(), nmax + 1), dtype=torch.complex128, device=z.device)
+    _check(lib().qbx_debug_besselj(_ptr(z), z.numel(), nmax, _ptr(out), _stream()))
+    return out

@@ -1,0 +1,277 @@
+"""GPU parity: every step of the CUDA path against the CPU oracle, through the
+C ABI, on the same seeded inputs.
+
+Bar (A10 reading of the target): max-norm relative error
+||u_gpu - u_oracle||_inf / ||u_oracle||_inf <= 1e-11 per output array;
+integer outputs bit-exact.  Sizes span several CTA tiles (128 centres, 128
+sources) with ragged tails; the full-size starfish (256 panels, k = 20,
+p = 12, both sides) is checked on sampled targets.
+"""
+import math
+
+import numpy as np
+import pytest
+import scipy.special as sp
+import torch
+
+import oracle
+import paper_1207_4461_gb300 as qbx
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-11
+
+
+def rel(a, b):
+    a = a.detach().cpu().numpy() if torch.is_tensor(a) else np.asarray(a)
+    b = np.asarray(b)
+    return np.abs(a - b).max() / np.abs(b).max()
+
+
+def make(curve, M, q_tgt=16, q_src=64, nrhs=1, p=12, extra_ctr=1):
+    plan = qbx.Plan(q_tgt, q_src, n_src=M * q_src, n_ctr=2 * M * q_tgt * extra_ctr,
+                    ncoef=max(2, 2 * p + 1), nrhs=nrhs)
+    g = qbx.qbx_geometry(plan, curve, curve.edges(M))
+    go = oracle.geometry(curve, curve.edges(M), q_tgt, q_src)
+    return plan, g, go
+
+
+def dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a), device="cuda")
+
+
+# ---------------------------------------------------------------------------
+# special functions (a2, a5) against scipy
+# ---------------------------------------------------------------------------
+def test_device_hankel_real(cuda):
+    # dense grid, the series / fit switch at z = 2, and the fit interval edges z = 64/i
+    z = np.concatenate([np.logspace(-4, np.log10(300), 3000), np.linspace(1.9, 2.1, 101),
+                        64.0 / np.arange(1, 33)])
+    h0, h1 = qbx.qbx_debug_hankel01(dev(z.astype(complex)))
+    r0, r1 = sp.hankel1(0, z), sp.hankel1(1, z)
+    tol = 5e-15 * np.maximum(1.0, z / 8)
+    assert np.all(np.abs(h0.cpu().numpy() - r0) <= tol * np.abs(r0))
+    assert np.all(np.abs(h1.cpu().numpy() - r1) <= tol * np.abs(r1))
+
+
+def test_device_hankel_complex(cuda):
+    z = np.concatenate([np.linspace(0.01, 40, 400) + 0.5j, np.linspace(0.2, 25, 100) + 1.5j,
+                        np.array([1e-3 + 1e-3j, 5.99 + 0.1j, 6.01 + 0.1j, 19.99 + 0.2j, 20.01 + 0.2j])])
+    h0, h1 = qbx.qbx_debug_hankel01(dev(z))
+    r0, r1 = sp.hankel1(0, z), sp.hankel1(1, z)
+    tol = 2e-14 * np.exp(2 * z.imag) * np.maximum(1.0, np.abs(z) / 8)
+    assert np.all(np.abs(h0.cpu().numpy() - r0) <= tol * np.abs(r0))
+    assert np.all(np.abs(h1.cpu().numpy() - r1) <= tol * np.abs(r1))
+
+
+def test_device_besselj(cuda):
+    z = np.concatenate([np.linspace(1e-4, 12, 500), np.linspace(0.05, 6, 60) + 0.4j])
+    nmax = 20
+    J = qbx.qbx_debug_besselj(dev(z), nmax).cpu().numpy()
+    for n in range(nmax + 1):
+        ref = sp.jv(n, z)
+        assert np.all(np.abs(J[:, n] - ref) <= 4e-15 * np.exp(np.abs(z.imag))), n
+
+
+# ---------------------------------------------------------------------------
+# a0, a1: geometry and oversampling
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("curve,M", [(W.starfish(), 37), (W.ellipse(3.0), 50), (W.circle(1.7), 5)])
+def test_geometry_matches_oracle(cuda, curve, M):
+    plan, g, go = make(curve, M)
+    for name in ("src_x", "src_y", "src_nx", "src_ny", "src_w", "tgt_x", "tgt_y", "tgt_nx", "tgt_ny",
+                 "tgt_w", "panel_h", "ctr_x", "ctr_y", "ctr_r", "ctr_ratio"):
+        assert rel(g[name], go[name]) < 1e-14, name
+
+
+def test_upsample_matches_oracle(cuda):
+    plan, g, go = make(W.starfish(), 19, nrhs=3)
+    d = W.complex_gaussian(11, g.n_tgt * 3).reshape(g.n_tgt, 3)
+    got = qbx.qbx_upsample(plan, g, dev(d))
+    assert rel(got, oracle.upsample(go, d)) < 1e-13
+
+
+# ---------------------------------------------------------------------------
+# a4 (unfused) and a5 + a6
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("kind", [qbx.OP_S, qbx.OP_D])
+@pytest.mark.parametrize("k", [5.0, 5 + 0.5j])
+def test_form_locals_matches_oracle(cuda, kind, k):
+    p, nrhs = 9, 2
+    plan, g, go = make(W.starfish(), 10, nrhs=nrhs, p=p)
+    wd = W.complex_gaussian(21, g.n_src * nrhs).reshape(g.n_src, nrhs)
+    got = qbx.qbx_form_locals(plan, g, kind, qbx.SIDE_TWO, k, p, dev(wd))
+    ref = oracle.form_locals(go, kind, oracle.SIDE_TWO, k, p, wd)
+    # per order l: orders differ in magnitude by many decades
+    for l in range(2 * p + 1):
+        assert rel(got[:, l, :], ref[:, l, :]) < TOL, l
+
+
+@pytest.mark.parametrize("what", [qbx.VALUE, qbx.GRAD])
+@pytest.mark.parametrize("k", [20.0, 3 + 0.7j])
+def test_eval_locals_matches_oracle(cuda, what, k):
+    p, nrhs = 12, 2
+    plan, g, go = make(W.starfish(), 11, nrhs=nrhs, p=p)
+    nc = 2 * g.n_tgt
+    alpha = W.complex_gaussian(31, nc * (2 * p + 1) * nrhs).reshape(nc, 2 * p + 1, nrhs)
+    got = qbx.qbx_eval_locals(plan, g, qbx.SIDE_TWO, k, p, dev(alpha), what)
+    ref = oracle.eval_locals(go, oracle.SIDE_TWO, k, p, alpha, what)
+    assert rel(got, ref) < TOL
+    # explicit off-surface targets inside the disks
+    rng = np.random.default_rng(4)
+    ectr = rng.integers(0, nc, 300).astype(np.int32)
+    ang = rng.uniform(0, 2 * np.pi, 300)
+    rad = rng.uniform(0, 1, 300) * go["ctr_r"][ectr]
+    ex = go["ctr_x"][ectr] + rad * np.cos(ang)
+    ey = go["ctr_y"][ectr] + rad * np.sin(ang)
+    got = qbx.qbx_eval_locals(plan, g, qbx.SIDE_TWO, k, p, dev(alpha), what, dev(ex), dev(ey), dev(ectr))
+    ref = oracle.eval_locals(go, oracle.SIDE_TWO, k, p, alpha, what, ex, ey, ectr)
+    assert rel(got, ref) < TOL
+
+
+# ---------------------------------------------------------------------------
+# the fused apply (a1-a7)
+# ---------------------------------------------------------------------------
+def test_apply_starfish_32_panels(cuda):
+    """Starfish 1 + 0.25 cos 5t, 32 panels x 16 nodes, 4x sources, k = 5, p = 8,
+    interior centres, sigma = cos 3t + 0.5 i sin t: S and D (one-sided and PV)."""
+    wl = W.cfg1()
+    plan, g, go = make(wl.curve, wl.M, p=wl.p)
+    dens = wl.dens(g.t_tgt)
+    for op in (qbx.OP_S, qbx.OP_D, qbx.OP_GRAD_S):
+        for limit in (qbx.LIMIT_ONE_SIDED, qbx.LIMIT_PV):
+            got = qbx.qbx_apply(plan, g, op, qbx.SIDE_INT, limit, wl.k, wl.p, dev(dens))
+            ref = oracle.apply(go, op, oracle.SIDE_INT, limit, wl.k, wl.p, dens)
+            assert rel(got, ref) < TOL, (op, limit)
+    qbx.qbx_sync_status(plan)
+
+
+@pytest.mark.parametrize("op", [qbx.OP_S, qbx.OP_D, qbx.OP_GRAD_S])
+@pytest.mark.parametrize("side,limit", [(qbx.SIDE_INT, qbx.LIMIT_ONE_SIDED), (qbx.SIDE_EXT, qbx.LIMIT_PV),
+                                        (qbx.SIDE_TWO, qbx.LIMIT_ONE_SIDED)])
+@pytest.mark.parametrize("k,p,nrhs", [(7.0, 10, 1), (4 + 0.6j, 6, 3), (11.0, 0, 2)])
+def test_apply_variants_ragged(cuda, op, side, limit, k, p, nrhs):
+    """13 panels: 208 targets (416 centres = 3 tiles + 32), 832 sources (6.5 tiles)."""
+    plan, g, go = make(W.starfish(0.2, 3), 13, nrhs=nrhs, p=p)
+    dens = W.complex_gaussian(7, g.n_tgt * nrhs).reshape(g.n_tgt, nrhs)
+    got = qbx.qbx_apply(plan, g, op, side, limit, k, p, dev(dens))
+    ref = oracle.apply(go, op, side, limit, k, p, dens)
+    assert rel(got, ref) < TOL
+
+
+def test_apply_many_rhs(cuda):
+    nrhs = 11
+    plan, g, go = make(W.ellipse(2.0), 9, nrhs=nrhs)
+    dens = W.complex_gaussian(8, g.n_tgt * nrhs).reshape(g.n_tgt, nrhs)
+    for op in (qbx.OP_S, qbx.OP_GRAD_S):
+        got = qbx.qbx_apply(plan, g, op, qbx.SIDE_TWO, 0, 6.0, 9, dev(dens))
+        ref = oracle.apply(go, op, oracle.SIDE_TWO, 0, 6.0, 9, dens)
+        assert rel(got, ref) < TOL
+
+
+def test_apply_full_size_sampled(cuda):
+    """Starfish, 256 panels (4096 targets, 16384 sources), k = 20, p = 12, both
+    sides (8192 centres), S, D and grad S, CN(0,1) density (seed 2): the launch
+    configuration of the benchmark, checked on 40 sampled targets."""
+    wl = W.cfg2()
+    plan, g, go = make(wl.curve, wl.M, p=wl.p)
+    dens = wl.dens(g.t_tgt)
+    rng = np.random.default_rng(12)
+    sel = np.unique(np.concatenate([[0, g.n_tgt - 1], rng.integers(0, g.n_tgt, 38)]))
+    for op in (qbx.OP_S, qbx.OP_D, qbx.OP_GRAD_S):
+        got = qbx.qbx_apply(plan, g, op, qbx.SIDE_TWO, 0, wl.k, wl.p, dev(dens))
+        ref = oracle.apply(go, op, oracle.SIDE_TWO, 0, wl.k, wl.p, dens, sel=sel)
+        assert rel(got.cpu().numpy()[sel], ref) < TOL, op
+        # property at any size: finite everywhere
+        assert torch.isfinite(torch.view_as_real(got)).all()
+    qbx.qbx_sync_status(plan)
+
+
+# ---------------------------------------------------------------------------
+# a8 far targets, centre assignment
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("k", [9.0, 2 + 0.4j])
+def test_far_matches_oracle(cuda, k):
+    nrhs = 2
+    plan, g, go = make(W.starfish(), 16, nrhs=nrhs)
+    th = np.linspace(0, 2 * np.pi, 257)[:-1]
+    xy = np.concatenate([np.stack([2.5 * np.cos(th), 2.5 * np.sin(th)], 1),
+                         np.stack([0.3 * np.cos(th[:70]), 0.3 * np.sin(th[:70])], 1)])
+    dens = W.complex_gaussian(9, g.n_tgt * nrhs).reshape(g.n_tgt, nrhs)
+    wd = oracle.upsample(go, dens)
+    wdg = qbx.qbx_upsample(plan, g, dev(dens))
+    for op in (qbx.OP_S, qbx.OP_D, qbx.OP_GRAD_S):
+        got = qbx.qbx_far(plan, g, op, k, wdg, dev(xy))
+        ref = oracle.far(go, op, k, wd, xy)
+        assert rel(got, ref) < TOL, op
+        on, far = qbx.qbx_apply(plan, g, op, qbx.SIDE_INT, 0, k, 8, dev(dens), x_far=dev(xy))
+        assert rel(far, ref) < TOL, op
+
+
+def test_assign_centres_bit_exact(cuda):
+    plan, g, go = make(W.starfish(), 12)
+    rng = np.random.default_rng(2)
+    xy = rng.uniform(-1.4, 1.4, size=(2000, 2))
+    for side in (qbx.SIDE_INT, qbx.SIDE_EXT, qbx.SIDE_TWO):
+        got = qbx.qbx_assign_centres(plan, g, side, dev(xy)).cpu().numpy()
+        ref = oracle.assign_centres(go, side, xy)
+        c0 = g.n_tgt if side == qbx.SIDE_EXT else 0
+        ref = np.where(ref >= 0, ref - c0, -1)
+        assert np.array_equal(got, ref)
+
+
+# ---------------------------------------------------------------------------
+# determinism, streams, edge cases and errors
+# ---------------------------------------------------------------------------
+def test_deterministic_and_stream_ordered(cuda):
+    wl = W.cfg1()
+    plan, g, go = make(wl.curve, wl.M, p=wl.p)
+    d = dev(wl.dens(g.t_tgt))
+    a = qbx.qbx_apply(plan, g, qbx.OP_D, qbx.SIDE_TWO, 0, wl.k, wl.p, d)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        b = qbx.qbx_apply(plan, g, qbx.OP_D, qbx.SIDE_TWO, 0, wl.k, wl.p, d)
+    s.synchronize()
+    assert torch.equal(a, b)
+
+
+def test_single_panel_and_order_zero(cuda):
+    plan, g, go = make(W.circle(1.0), 1, q_tgt=16, q_src=64)
+    dens = W.density_cfg1(g.t_tgt)
+    for p in (0, 1, 3):
+        got = qbx.qbx_apply(plan, g, qbx.OP_S, qbx.SIDE_INT, 0, 1.5, p, dev(dens))
+        ref = oracle.apply(go, oracle.OP_S, oracle.SIDE_INT, 0, 1.5, p, dens)
+        assert rel(got, ref) < TOL
+
+
+def test_other_grid_sizes(cuda):
+    plan, g, go = make(W.starfish(), 7, q_tgt=10, q_src=30)
+    dens = W.density_cfg1(g.t_tgt)
+    got = qbx.qbx_apply(plan, g, qbx.OP_D, qbx.SIDE_TWO, 0, 4.0, 7, dev(dens))
+    ref = oracle.apply(go, oracle.OP_D, oracle.SIDE_TWO, 0, 4.0, 7, dens)
+    assert rel(got, ref) < TOL
+
+
+def test_errors_are_reported(cuda):
+    plan, g, go = make(W.starfish(), 4)
+    d = dev(W.density_cfg1(g.t_tgt))
+    with pytest.raises(qbx.QBXError) as e:
+        qbx.qbx_apply(plan, g, qbx.OP_S, qbx.SIDE_INT, 0, 5 - 1j, 4, d)
+    assert e.value.code == 1
+    with pytest.raises(qbx.QBXError) as e:
+        qbx.qbx_apply(plan, g, qbx.OP_S, qbx.SIDE_INT, 0, 5.0, qbx.MAX_P + 1, d)
+    assert e.value.code == 1
+    with pytest.raises(qbx.QBXError) as e:
+        qbx.qbx_apply(plan, g, qbx.OP_S, 7, 0, 5.0, 4, d)
+    assert e.value.code == 1
+    small = qbx.Plan(16, 64, workspace_bytes=1024)
+    with pytest.raises(qbx.QBXError) as e:
+        qbx.qbx_apply(small, g, qbx.OP_S, qbx.SIDE_INT, 0, 5.0, 4, d)
+    assert e.value.code == 7
+    bad = d.clone()
+    bad[3] = complex(float("nan"), 0.0)
+    qbx.qbx_apply(plan, g, qbx.OP_S, qbx.SIDE_INT, 0, 5.0, 4, bad)
+    with pytest.raises(qbx.QBXError) as e:
+        qbx.qbx_sync_status(plan)
+    assert e.value.code == 4
+    qbx.qbx_sync_status(plan)   # cleared
