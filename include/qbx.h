@@ -190,6 +190,36 @@ int qbx_far(qbx_plan *plan, const qbx_geom *g, int op, qbx_c64 k, const qbx_c64 
 int qbx_assign_centres(qbx_plan *plan, const qbx_geom *g, int side, int n, const double *xy,
                        int *out, void *stream);
 
+/* qbx_apply without a plan, for callers that cannot allocate device memory.
+ * The paper has no counterpart; this is a deployment variant of qbx_apply.
+ *
+ * Who needs it: qbx_apply works in a plan's workspace, and qbx_plan_create
+ * calls cudaMalloc.  Code whose device memory belongs to a pooling allocator
+ * cannot make raw allocations behind the pool (they fail once the pool holds
+ * the memory), and latency-critical loops cannot afford cudaMalloc's implicit
+ * device synchronisation.  This call allocates nothing: no cudaMalloc,
+ * cudaFree or allocating library routine.
+ *
+ * Arguments and results are those of qbx_apply's on-surface part (no far
+ * targets): same operators, sides, limits, layouts and device pointers owned
+ * by the caller, asynchronous on `stream`.  The scratch (the oversampled
+ * density and the per-split partial sums) is a fixed device array of
+ * QBX_STATIC_SCRATCH_BYTES (32 MiB) that every GPU loading this library holds
+ * until the process exits; calls whose sizes need more,
+ * 16 B * (n_src*nrhs rounded up to 256 B + n_ctr*ncomp*nrhs) with
+ * ncomp = 2 for grad S, fail with QBX_ENOMEM and a message naming the limit.
+ *
+ * The first call on each device (the current device) looks up the device
+ * addresses of the fixed arrays and clears a status word; the first call for
+ * a new (q_tgt, q_src) pair uploads that pair's interpolation matrix with a
+ * synchronous copy.  Make those first calls before any stream capture.
+ * Every call shares the one scratch array, which keeps the last call's
+ * contents: calls that overlap on the GPU (several streams or threads on the
+ * same device) race and must be serialised by the caller. */
+#define QBX_STATIC_SCRATCH_BYTES (32u << 20)
+int qbx_apply_static(const qbx_geom *g, int op, int side, int limit, qbx_c64 k, int p,
+                     const qbx_c64 *dens_tgt, int nrhs, qbx_c64 *out_on, void *stream);
+
 /* Diagnostics of the device special functions used by the kernels: H0, H1
  * at z[n] (complex, Im z >= 0, z != 0; the real-argument path is taken when
  * Im z == 0), and J_0..J_nmax (Miller) at z[n].  For tests. */

@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libqbx_gb300.so")
-SOURCES = ["qbx_apply.cu", "qbx_misc.cu", "qbx_capi.cu"]
+SOURCES = ["qbx_apply.cu", "qbx_misc.cu", "qbx_capi.cu", "qbx_static.cu"]
 HEADERS = ["qbx_device.cuh", "qbx_internal.h", "special_tables.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -162,10 +162,26 @@ int side_range(int side, int n_tgt, int* c0, int* nc) {
   }
 }
 
+int choose_split(const qbx_plan* pl, int n_units, int n_src, size_t bytes_per_split, size_t avail) {
+  return qbx::host_choose_split(pl->num_sms, n_units, n_src, bytes_per_split, avail);
+}
+
+int split_len(int n_src, int ns) { return qbx::host_split_len(n_src, ns); }
+
+}  // namespace
+
+namespace qbx {
+
+void host_interp_matrix(int qt, int qs, std::vector<double>& Mx) { interp_matrix(qt, qs, Mx); }
+
+int host_fail(int code, const char* msg) { return fail(code, "%s", msg); }
+
+size_t host_align256(size_t b) { return align256(b); }
+
 // Number of source splits: fill about two waves of 4 CTAs per SM, bounded by
 // kMaxSplit, by one source tile per split, and by the workspace.
-int choose_split(const qbx_plan* pl, int n_units, int n_src, size_t bytes_per_split, size_t avail) {
-  const int target = pl->num_sms * 8;
+int host_choose_split(int num_sms, int n_units, int n_src, size_t bytes_per_split, size_t avail) {
+  const int target = num_sms * 8;
   int ns = (target + n_units - 1) / std::max(n_units, 1);
   ns = std::min(ns, kMaxSplit);
   ns = std::min(ns, std::max(1, (n_src + kSrcTile - 1) / kSrcTile));
@@ -177,13 +193,13 @@ int choose_split(const qbx_plan* pl, int n_units, int n_src, size_t bytes_per_sp
   return ns;
 }
 
-int split_len(int n_src, int ns) {
-  // sources per split, rounded up to a multiple of the tile
+// sources per split, rounded up to a multiple of the tile
+int host_split_len(int n_src, int ns) {
   int per = (n_src + ns - 1) / ns;
   return ((per + kSrcTile - 1) / kSrcTile) * kSrcTile;
 }
 
-}  // namespace
+}  // namespace qbx
 
 extern "C" {
 

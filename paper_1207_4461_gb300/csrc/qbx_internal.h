@@ -2,6 +2,7 @@
 // units (host side of the kernels).  Not part of the public ABI.
 #pragma once
 #include <cuda_runtime.h>
+#include <vector>
 #include "../../include/qbx.h"
 
 namespace qbx {
@@ -106,5 +107,12 @@ cudaError_t launch_assign(int n, const double* xy, int n_ctr, const double* cx,
                           const double* cy, const double* cr, int* out, cudaStream_t st);
 cudaError_t launch_debug_hankel(const void* z, int n, void* h0, void* h1, cudaStream_t st);
 cudaError_t launch_debug_besselj(const void* z, int n, int nmax, void* j, cudaStream_t st);
+
+// Host helpers shared by the C-ABI translation units (qbx_capi.cu).
+void host_interp_matrix(int q_tgt, int q_src, std::vector<double>& M);
+size_t host_align256(size_t b);
+int host_choose_split(int num_sms, int n_units, int n_src, size_t bytes_per_split, size_t avail);
+int host_split_len(int n_src, int ns);
+int host_fail(int code, const char* msg);   // sets qbx_last_error(), returns code
 
 }  // namespace qbx

@@ -1,0 +1,172 @@
+// qbx_static.cu -- qbx_apply_static: the on-surface apply (same kernels as
+// qbx_apply) for callers that cannot allocate device memory.  Its scratch --
+// the oversampled density and the split partial sums -- lives in a file-scope
+// __device__ array of fixed size instead of a plan's workspace, and the
+// per-panel interpolation matrix in a second fixed array.
+//
+// Why: qbx_apply needs a plan, and qbx_plan_create calls cudaMalloc.  Some
+// callers must not: code whose device memory is owned by a pooling allocator
+// (a raw cudaMalloc goes behind the pool's back and can fail once the pool
+// holds the memory), and latency-critical loops where cudaMalloc's implicit
+// device synchronisation is not acceptable.  This entry point calls no
+// cudaMalloc, cudaFree or allocating library routine.
+//
+// Every GPU that loads the library holds these arrays until the process exits.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <mutex>
+#include <vector>
+#include "../../include/qbx.h"
+#include "qbx_internal.h"
+
+// The scratch, the interpolation matrix and a status word, one copy per device.
+// Every call shares them and they keep the last call's contents.
+static __device__ __align__(256) unsigned char g_static_scratch[QBX_STATIC_SCRATCH_BYTES];
+static __device__ __align__(256) double g_static_interp[QBX_MAX_Q * QBX_MAX_Q];
+static __device__ int g_static_status;
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+
+struct DeviceState {
+  bool ready = false;
+  void* scratch = nullptr;   // device address of g_static_scratch on this device
+  double* interp = nullptr;  // device address of g_static_interp
+  int* status = nullptr;     // device address of g_static_status
+  int num_sms = 0;
+  int q_tgt = 0, q_src = 0;  // grid pair whose matrix is in g_static_interp
+};
+
+std::mutex g_mu;
+DeviceState g_state[kMaxDevices];
+
+int cuda_err(cudaError_t e, const char* what) {
+  char buf[256];
+  snprintf(buf, sizeof(buf), "qbx_apply_static: %s: %s", what, cudaGetErrorString(e));
+  return qbx::host_fail(QBX_ECUDA, buf);
+}
+
+int invalid(const char* what) {
+  char buf[256];
+  snprintf(buf, sizeof(buf), "qbx_apply_static: %s", what);
+  return qbx::host_fail(QBX_EINVAL, buf);
+}
+
+// Once per device, with that device current: the device addresses of the
+// arrays.  In host code the arrays' names stand for host-side shadows, not
+// device addresses, so a kernel must be given these addresses instead.  Then,
+// whenever the grid pair changes, upload that pair's interpolation matrix.
+int prepare(int dev, int q_tgt, int q_src, DeviceState** out) {
+  std::lock_guard<std::mutex> lock(g_mu);
+  DeviceState& s = g_state[dev];
+  if (!s.ready) {
+    cudaError_t e = cudaGetSymbolAddress(&s.scratch, g_static_scratch);
+    if (e != cudaSuccess) return cuda_err(e, "cudaGetSymbolAddress(scratch)");
+    e = cudaGetSymbolAddress((void**)&s.interp, g_static_interp);
+    if (e != cudaSuccess) return cuda_err(e, "cudaGetSymbolAddress(interp)");
+    e = cudaGetSymbolAddress((void**)&s.status, g_static_status);
+    if (e != cudaSuccess) return cuda_err(e, "cudaGetSymbolAddress(status)");
+    e = cudaDeviceGetAttribute(&s.num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return cuda_err(e, "cudaDeviceGetAttribute");
+    e = cudaMemset(s.status, 0, sizeof(int));
+    if (e != cudaSuccess) return cuda_err(e, "cudaMemset(status)");
+    s.ready = true;
+  }
+  if (s.q_tgt != q_tgt || s.q_src != q_src) {
+    std::vector<double> M;
+    qbx::host_interp_matrix(q_tgt, q_src, M);
+    cudaError_t e = cudaMemcpy(s.interp, M.data(), M.size() * sizeof(double), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_err(e, "upload of the interpolation matrix");
+    s.q_tgt = q_tgt;
+    s.q_src = q_src;
+  }
+  *out = &s;
+  return QBX_OK;
+}
+
+}  // namespace
+
+extern "C" int qbx_apply_static(const qbx_geom* g, int op, int side, int limit, qbx_c64 k, int p,
+                                const qbx_c64* dens_tgt, int nrhs, qbx_c64* out_on, void* stream) {
+  using namespace qbx;
+  // ---- arguments (host checks; nothing is launched on error) ----
+  if (!g) return invalid("geometry is NULL");
+  if (g->M < 1 || g->q_tgt < 1 || g->q_tgt > QBX_MAX_Q || g->q_src < 1 || g->q_src > QBX_MAX_Q)
+    return invalid("geometry: bad M, q_tgt or q_src");
+  if (g->n_tgt != g->M * g->q_tgt || g->n_src != g->M * g->q_src)
+    return invalid("geometry: n_tgt/n_src inconsistent with M*q");
+  if (!g->src_x || !g->src_y || !g->src_nx || !g->src_ny || !g->src_w || !g->tgt_x || !g->tgt_y ||
+      !g->tgt_nx || !g->tgt_ny || !g->ctr_x || !g->ctr_y)
+    return invalid("geometry: NULL array");
+  if (op != QBX_OP_S && op != QBX_OP_D && op != QBX_OP_GRAD_S) return invalid("bad op");
+  if (limit != QBX_LIMIT_ONE_SIDED && limit != QBX_LIMIT_PV) return invalid("bad limit");
+  if (side != QBX_SIDE_INT && side != QBX_SIDE_EXT && side != QBX_SIDE_TWO) return invalid("bad side");
+  if (!isfinite(k.re) || !isfinite(k.im) || k.im < 0.0 || (k.im == 0.0 && !(k.re > 0.0)))
+    return invalid("k must be finite with Im k >= 0 (real k > 0)");
+  if (p < 0 || p > QBX_MAX_P) return invalid("p outside [0, QBX_MAX_P]");
+  if (nrhs < 1) return invalid("nrhs < 1");
+  if (!dens_tgt || !out_on) return invalid("NULL density or output");
+
+  // ---- sizes against the fixed scratch ----
+  const int c0 = side == QBX_SIDE_EXT ? g->n_tgt : 0;
+  const int nc = side == QBX_SIDE_TWO ? 2 * g->n_tgt : g->n_tgt;
+  const int ncomp = op == QBX_OP_GRAD_S ? 2 : 1;
+  const size_t wd_bytes = host_align256((size_t)g->n_src * nrhs * 16);
+  const size_t per_split = (size_t)nc * ncomp * nrhs * 16;
+  if (wd_bytes + per_split > QBX_STATIC_SCRATCH_BYTES) {
+    char buf[256];
+    snprintf(buf, sizeof(buf),
+             "qbx_apply_static: the call needs at least %zu bytes of scratch, more than the fixed "
+             "%zu (n_src = %d, centres = %d, nrhs = %d); use qbx_apply with a plan",
+             wd_bytes + per_split, (size_t)QBX_STATIC_SCRATCH_BYTES, g->n_src, nc, nrhs);
+    return host_fail(QBX_ENOMEM, buf);
+  }
+
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_err(e, "cudaGetDevice");
+  if (dev < 0 || dev >= kMaxDevices) return invalid("device index beyond the supported range");
+  DeviceState* s = nullptr;
+  if (int rc = prepare(dev, g->q_tgt, g->q_src, &s)) return rc;
+
+  const int units = (nc + kApplyThreads - 1) / kApplyThreads;
+  const int ns = host_choose_split(s->num_sms, units, g->n_src, per_split,
+                                   QBX_STATIC_SCRATCH_BYTES - wd_bytes);
+  cudaStream_t st = (cudaStream_t)stream;
+  char* base = static_cast<char*>(s->scratch);
+  void* wd = base;
+  void* part = base + wd_bytes;
+
+  // the same launch sequence as qbx_apply's on-surface part
+  e = launch_upsample(g->M, g->q_tgt, g->q_src, nrhs, s->interp, g->src_w, dens_tgt, wd, st);
+  if (e != cudaSuccess) return cuda_err(e, "upsample kernel");
+  ApplyArgs a{};
+  a.op = op;
+  a.p = p;
+  a.kre = k.re;
+  a.kim = k.im;
+  a.n_ctr = nc;
+  a.cx = g->ctr_x + c0;
+  a.cy = g->ctr_y + c0;
+  a.n_tgt = g->n_tgt;
+  a.tx = g->tgt_x;
+  a.ty = g->tgt_y;
+  a.src = SrcView{g->src_x, g->src_y, g->src_nx, g->src_ny, g->n_src};
+  a.wd = wd;
+  a.nrhs = nrhs;
+  a.nsplit = ns;
+  a.src_per_split = host_split_len(g->n_src, ns);
+  a.part = part;
+  for (int r0 = 0; r0 < nrhs; r0 += 8) {
+    a.rhs0 = r0;
+    a.nr = nrhs - r0 < 8 ? nrhs - r0 : 8;
+    e = launch_apply_fused(a, st);
+    if (e != cudaSuccess) return cuda_err(e, "apply kernel");
+  }
+  e = launch_apply_finish(op, side, limit, g->n_tgt, ns, nc, nrhs, part, dens_tgt, g->tgt_nx, g->tgt_ny,
+                          out_on, s->status, st);
+  if (e != cudaSuccess) return cuda_err(e, "apply finish");
+  return QBX_OK;
+}

@@ -79,6 +79,8 @@ def lib():
             L.qbx_apply.argtypes = [_P, G, I, I, I, c64, I, _P, I, I, _P, _P, _P, _P]
             L.qbx_far.argtypes = [_P, G, I, c64, _P, I, I, _P, _P, _P]
             L.qbx_assign_centres.argtypes = [_P, G, I, I, _P, _P, _P]
+            L.qbx_apply_static.argtypes = [G, I, I, I, c64, I, _P, I, _P, _P]
+            L.qbx_apply_static.restype = I
             L.qbx_debug_hankel01.argtypes = [_P, I, _P, _P, _P]
             L.qbx_debug_besselj.argtypes = [_P, I, I, _P, _P]
             for name in ("qbx_gauss_legendre", "qbx_plan_create", "qbx_plan_destroy", "qbx_sync_status",
@@ -277,6 +279,19 @@ def qbx_apply(plan: Plan, g: Geometry, op, side, limit, k, p, dens_tgt, x_far=No
                            _ptr(x_far.contiguous()) if n_far else None, _ptr(out_on), _ptr(out_far),
                            _stream()))
     return (out_on, out_far) if n_far else out_on
+
+
+def qbx_apply_static(g: Geometry, op, side, limit, k, p, dens_tgt, out_on=None):
+    """On-surface apply without a plan: nothing is allocated by the library
+    (scratch in a fixed device array, see include/qbx.h).  The output tensor is
+    the caller's (allocated here by torch when out_on is None)."""
+    d = _dens2d(dens_tgt, g.n_tgt)
+    nrhs = d.shape[1]
+    shape = (g.n_tgt, 2, nrhs) if op == OP_GRAD_S else (g.n_tgt, nrhs)
+    if out_on is None:
+        out_on = torch.empty(shape, dtype=torch.complex128, device=d.device)
+    _check(lib().qbx_apply_static(g.ref(), op, side, limit, _k(k), p, _ptr(d), nrhs, _ptr(out_on), _stream()))
+    return out_on
 
 
 def qbx_far(plan: Plan, g: Geometry, op, k, wdens_src, x_far):
