@@ -37,15 +37,32 @@ METRIC = "QBX center·source·order terms/s"
 # FP64 ALU peak of the dominant kernel's pipe: 152 SMs x 2 FP64 FMA lanes per
 # SM per clock (4 flops) x 2.07 GHz maximum SM clock (nominal 1.25 TFLOP/s).
 FP64_PEAK_GFLOPS = 152 * 4 * 2.07
-# Frozen algorithmic flop model per (centre, source) pair of the fused apply:
-# 100 flops of pair set-up (distance, H0, H1) + 16 per order (S) or 24 per
-# order (D, grad S), + 8 per extra right-hand side.
+# Algorithmic FP64 flop model per (centre, source) pair of the fused apply
+# (FMA = 2 flops), counted from the algorithm the kernel runs, real k:
+#   one operator alone: 100 flops of pair set-up (distance, H0, H1) + 16 per
+#   order (S) or 24 per order (D, grad S), + 8 per extra right-hand side;
+#   S, D and grad S in one pass (shared set-up and recurrences): 180 flops of
+#   set-up + 35 per order (S 5, D 7, grad S 10, shared recurrences 13),
+#   + 32 per extra right-hand side.
 FLOPS_PAIR = {"S": (100, 16), "D": (100, 24), "GRAD_S": (100, 24)}
 
 
 def flops_per_pair(op, p, nrhs=1):
     a, b = FLOPS_PAIR[op]
     return a + b * p + 8 * (nrhs - 1)
+
+
+def flops_per_pair_ops(ops, p, nrhs=1):
+    if len(ops) == 1:
+        return flops_per_pair(ops[0], p, nrhs)
+    if set(ops) == {"S", "D", "GRAD_S"}:
+        return 180 + 35 * p + 32 * (nrhs - 1)
+    # other subsets: shared set-up once, each operator's own products
+    per = {"S": 5, "D": 7, "GRAD_S": 10}
+    acc = {"S": 8, "D": 8, "GRAD_S": 16}
+    rec = 7 + (4 if "D" in ops else 0) + (2 if "GRAD_S" in ops else 0)
+    return 140 + sum(acc[o] for o in ops) + p * (rec + sum(per[o] for o in ops)) + \
+        (nrhs - 1) * sum(acc[o] for o in ops)
 
 
 def env_rank():
@@ -158,7 +175,8 @@ def config_dict(wl, args):
             "n_tgt": wl.n_tgt, "n_src": wl.n_src, "n_ctr": wl.n_ctr, "k": wl.k, "p": wl.p,
             "nrhs": wl.nrhs, "terms_per_step": len(wl.ops) * wl.terms_per_op(),
             "l2": "flushed between timed steps (256 MiB write outside the event pair)",
-            "parallelism": "replicas" if args.gpus > 1 else "single"}
+            "parallelism": "replicas" if args.gpus > 1 else "single",
+            "call": "qbx_apply per operator" if args.separate else "qbx_apply_ops (one pass for all operators)"}
 
 
 def run_gpu(args, wl):
@@ -174,27 +192,31 @@ def run_gpu(args, wl):
         torch.cuda.set_device(0)
     dev = torch.device("cuda", torch.cuda.current_device())
     ops = {"S": qbx.OP_S, "D": qbx.OP_D, "GRAD_S": qbx.OP_GRAD_S}
-    plan = qbx.Plan(wl.q_tgt, wl.q_src, n_src=wl.n_src, n_ctr=wl.n_ctr, ncoef=2, nrhs=wl.nrhs)
+    codes = [ops[n] for n in wl.ops]
+    ncomp = sum(2 if n == "GRAD_S" else 1 for n in wl.ops)
+    plan = qbx.Plan(wl.q_tgt, wl.q_src, n_src=wl.n_src, n_ctr=wl.n_ctr, ncoef=ncomp, nrhs=wl.nrhs)
     g = qbx.qbx_geometry(plan, wl.curve, wl.curve.edges(wl.M))
     dens_np = wl.dens(g.t_tgt)
     dens = torch.as_tensor(dens_np, device=dev).contiguous()
-    outs = {n: torch.empty((wl.n_tgt, 2, wl.nrhs) if n == "GRAD_S" else (wl.n_tgt, wl.nrhs),
-                           dtype=torch.complex128, device=dev) for n in wl.ops}
+    outs = {ops[n]: torch.empty((wl.n_tgt, 2, wl.nrhs) if n == "GRAD_S" else (wl.n_tgt, wl.nrhs),
+                                dtype=torch.complex128, device=dev) for n in wl.ops}
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
 
-    def step():
-        for n in wl.ops:
-            qbx.qbx_apply(plan, g, ops[n], qbx.SIDE_TWO, 0, wl.k, wl.p, dens, out_on=outs[n])
+    def step(d):
+        if args.separate:
+            for c in codes:
+                qbx.qbx_apply(plan, g, c, qbx.SIDE_TWO, 0, wl.k, wl.p, d, out_on=outs[c])
+        else:  # all operators in one pass over the pairs
+            qbx.qbx_apply_ops(plan, g, codes, qbx.SIDE_TWO, 0, wl.k, wl.p, d, out=outs)
 
     for _ in range(args.warmup):
-        step()
+        step(dens)
     torch.cuda.synchronize()
     qbx.qbx_sync_status(plan)
 
-    # ---- device-timed region: K steps, per-op events, L2 flushed between steps
-    ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in wl.ops]
-          for _ in range(args.steps)]
+    # ---- device-timed region: K steps, events per step, L2 flushed between steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     clocks = ClockSampler(int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0])
                           if os.environ.get("CUDA_VISIBLE_DEVICES", "").isdigit() else local)
     if world > 1:
@@ -204,16 +226,15 @@ def run_gpu(args, wl):
     time.sleep(0.3)
     for s in range(args.steps):
         flush.fill_(s & 0xFF)
-        for i, n in enumerate(wl.ops):
-            ev[s][i][0].record(stream)
-            qbx.qbx_apply(plan, g, ops[n], qbx.SIDE_TWO, 0, wl.k, wl.p, dens, out_on=outs[n])
-            ev[s][i][1].record(stream)
+        ev[s][0].record(stream)
+        step(dens)
+        ev[s][1].record(stream)
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
     clk = clocks.stop()
-    op_ms = {n: [ev[s][i][0].elapsed_time(ev[s][i][1]) for s in range(args.steps)] for i, n in enumerate(wl.ops)}
-    step_ms = sum(sum(v) for v in op_ms.values()) / args.steps
+    steps_ms = [a.elapsed_time(b) for a, b in ev]
+    step_ms = sum(steps_ms) / args.steps
     qbx.qbx_sync_status(plan)
     if world > 1:
         t = torch.tensor([step_ms], device=dev, dtype=torch.float64)
@@ -224,35 +245,38 @@ def run_gpu(args, wl):
 
     # roofline of the dominant kernel (the fused apply): algorithmic flops / duration
     pairs = wl.n_ctr * wl.n_src
-    flops = {n: pairs * flops_per_pair(n, wl.p, wl.nrhs) for n in wl.ops}
-    launch_ms = {n: statistics.mean(op_ms[n]) for n in wl.ops}
-    achieved = sum(flops.values()) / (sum(launch_ms.values()) * 1e-3) / 1e9
+    if args.separate:
+        fpp = sum(flops_per_pair(n, wl.p, wl.nrhs) for n in wl.ops)
+        kname = "k_apply_fused, one launch per operator"
+    else:
+        fpp = flops_per_pair_ops(list(wl.ops), wl.p, wl.nrhs)
+        kname = "k_apply_fused, operators " + "+".join(wl.ops) + " in one pass"
+    achieved = pairs * fpp / (step_ms * 1e-3) / 1e9
     roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
                 "frac": achieved / FP64_PEAK_GFLOPS, "traffic": None,
-                "kernel": "k_apply_fused (S, D, grad S instances; per-call events include the tiny "
-                          "oversampling and reduction kernels)",
-                "flops_per_pair": {n: flops_per_pair(n, wl.p, wl.nrhs) for n in wl.ops},
-                "ms_per_launch": launch_ms}
+                "kernel": kname + " (step events also cover the oversampling and reduction kernels, "
+                                  "<1% of the time)",
+                "flops_per_pair": fpp, "peak_basis": "152 SMs x 4 FP64 flop/clk x 2.07 GHz"}
 
     # ---- end to end through the public API with host buffers (pinned)
     h_dens = torch.from_numpy(dens_np).pin_memory()
-    h_outs = {n: torch.empty(outs[n].shape, dtype=torch.complex128).pin_memory() for n in wl.ops}
+    h_outs = {c: torch.empty(outs[c].shape, dtype=torch.complex128).pin_memory() for c in outs}
     d_dens = torch.empty_like(dens)
     h2d = h_dens.numel() * 16
     d2h = sum(o.numel() * 16 for o in h_outs.values())
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     for _ in range(2):
         d_dens.copy_(h_dens, non_blocking=True)
-        step()
+        step(d_dens)
     torch.cuda.synchronize()
     e2e_ms = 0.0
     for s in range(args.steps):
         flush.fill_(s & 0xFF)
         e0.record(stream)
         d_dens.copy_(h_dens, non_blocking=True)
-        for n in wl.ops:
-            qbx.qbx_apply(plan, g, ops[n], qbx.SIDE_TWO, 0, wl.k, wl.p, d_dens, out_on=outs[n])
-            h_outs[n].copy_(outs[n], non_blocking=True)
+        step(d_dens)
+        for c in outs:
+            h_outs[c].copy_(outs[c], non_blocking=True)
         e1.record(stream)
         e1.synchronize()
         e2e_ms += e0.elapsed_time(e1)
@@ -260,11 +284,12 @@ def run_gpu(args, wl):
     e2e = {"value": world * terms_step / (e2e_ms * 1e-3), "unit": "terms/s",
            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms}
 
+    launches = (3 * len(wl.ops)) if args.separate else (2 + len(wl.ops))   # upsample, fused, finish(es)
     line = {"metric": METRIC, "value": value, "unit": "terms/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_dict(wl, args),
             "roofline": roofline, "e2e": e2e, "clocks": clk,
-            "gpu_launches": args.steps * len(wl.ops) * 3,
+            "gpu_launches": args.steps * launches,
             "targets_per_s": world * len(wl.ops) * wl.n_tgt * wl.nrhs / (step_ms * 1e-3),
             "pairs_per_s": world * len(wl.ops) * pairs / (step_ms * 1e-3)}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -289,6 +314,8 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=192, help="targets in the CPU-baseline sample")
     ap.add_argument("--ref-sample", type=int, default=48, help="targets per step of --impl reference")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--separate", action="store_true",
+                    help="one qbx_apply launch per operator instead of one pass for all")
     ap.add_argument("--panels", type=int, default=None,
                     help="profiling only: override the panel count (smaller case for ncu)")
     ap.add_argument("--ops", default=None, help="profiling only: comma list of S,D,GRAD_S")

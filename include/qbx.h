@@ -171,10 +171,28 @@ int qbx_eval_locals(qbx_plan *plan, const qbx_geom *g, int side, qbx_c64 k, int 
  * targets evaluated by plain quadrature into out_far (same layout); the caller
  * places them outside every expansion disk (see qbx_assign_centres).
  * Needs qbx_workspace_bytes(n_src, max(n_ctr, n_far), ncomp, nrhs) of workspace
- * plus n_src*nrhs complex for the oversampled density. */
+ * (ncomp = 2 for grad S, else 1); that figure includes the oversampled
+ * densities. */
 int qbx_apply(qbx_plan *plan, const qbx_geom *g, int op, int side, int limit, qbx_c64 k, int p,
               const qbx_c64 *dens_tgt, int nrhs, int n_far, const double *x_far,
               qbx_c64 *out_on, qbx_c64 *out_far, void *stream);
+
+/* Several operators in one pass over the (centre, source) pairs: `ops` is a
+ * non-empty subset of {S, D, grad S} as bits (1 << QBX_OP_S) | (1 << QBX_OP_D)
+ * | (1 << QBX_OP_GRAD_S).  dens[op] / out[op] (host arrays of three device
+ * pointers, entries of operators not in `ops` ignored) are the density and
+ * output of each operator, with qbx_apply's layouts; densities may alias
+ * (e.g. one density for all three).  The pair set-up (distance, H0, H1) and
+ * the Hankel / Chebyshev recurrences are computed once per pair for all the
+ * requested operators, which is why this is faster than separate qbx_apply
+ * calls.  side / limit as in qbx_apply; no far targets.  Needs
+ * qbx_workspace_bytes(n_src, n_ctr, ncomp, nrhs) with ncomp = 1 (S) + 1 (D)
+ * + 2 (grad S) over the requested operators. */
+#define QBX_OPS_S (1 << QBX_OP_S)
+#define QBX_OPS_D (1 << QBX_OP_D)
+#define QBX_OPS_GRAD_S (1 << QBX_OP_GRAD_S)
+int qbx_apply_ops(qbx_plan *plan, const qbx_geom *g, int ops, int side, int limit, qbx_c64 k, int p,
+                  const qbx_c64 *const dens[3], int nrhs, qbx_c64 *const out[3], void *stream);
 
 /* Plain smooth quadrature at off-surface points (Sec. 1, Sec. 2):
  * S = (i/4) sum wdens H0(kd), D = (ik/4) sum wdens H1(kd) (x-x_s).n_s/d,

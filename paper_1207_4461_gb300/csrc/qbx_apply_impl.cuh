@@ -1,0 +1,380 @@
+// qbx_apply_impl.cuh -- the storage-free QBX apply (the G_p kernel of Sec. 2,
+// eq. qbx-kernel; "each source adds its contribution directly", Sec. 3.3),
+// for any subset of {S, D, grad S} in one pass over the (centre, source)
+// pairs.  Included by qbx_apply_real.cu (real k) and qbx_apply_cplx.cu
+// (complex k), which instantiate it.
+//
+// One thread owns one expansion centre c with its on-surface target x
+// (x - c = r e^{i theta_t}); a CTA owns 128 consecutive centres and one
+// contiguous range of sources (a split), staged through shared memory in
+// tiles of 128.  For a pair with x_s - c = rho e^{i theta_s}, psi = theta_t -
+// theta_s, z = k rho, the orders come from H0(z), H1(z) by the upward
+// recurrence H_{l+1} = (2l/z) H_l - H_{l-1} and from the Chebyshev recurrence
+// for cos(l psi), sin(l psi); the kernels are the truncated Graf sums folded
+// over +-l (H_{-l} J_{-l} = H_l J_l):
+//   S : J0 H0 + 2 sum_{l=1..p} J_l(kr) H_l cos(l psi)        (eq. graf-addition)
+//   D : n_s . grad_{x_s} G_p = sum_{m=0..p} e_m H_m - k a J0 H1,
+//       e_m = J_{m+1} C_{m+1} + m J_m V_m,  C_m = 2 k a cos(m psi),
+//       V_m = (2/rho)(b sin(m psi) - a cos(m psi)),  a = n_s.e_rho, b = n_s.e_theta
+//       (eq. graf-coefficient-dlp with H_l' = H_{l-1} - (l/z) H_l)
+//   grad S: e_r k [J0' H0 + 2 sum J_l' H_l cos(l psi)] - e_theta (2/r) sum l J_l H_l sin(l psi)
+//       (derivative of the local expansion, Sec. 3.2)
+// The pair set-up (distance, H0, H1) and the recurrences are shared by all
+// requested operators; each operator adds only its own products.  The factor
+// i/4, the fixed-order sum over splits and the jump terms are applied by the
+// finishing kernel.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include "qbx_device.cuh"
+#include "qbx_internal.h"
+
+namespace qbx {
+
+enum { OPB_S = 1, OPB_D = 2, OPB_G = 4 };
+
+// ---- scalar helpers for T = double (real k) or cplx (complex k) ----------
+__device__ __forceinline__ void madd(cplx& acc, double e, cplx h) {
+  acc.re = fma(e, h.re, acc.re);
+  acc.im = fma(e, h.im, acc.im);
+}
+__device__ __forceinline__ void madd(cplx& acc, cplx e, cplx h) {
+  acc.re = fma(e.re, h.re, acc.re);
+  acc.re = fma(-e.im, h.im, acc.re);
+  acc.im = fma(e.re, h.im, acc.im);
+  acc.im = fma(e.im, h.re, acc.im);
+}
+__device__ __forceinline__ cplx smul(double e, cplx h) { return cplx{e * h.re, e * h.im}; }
+__device__ __forceinline__ cplx smul(cplx e, cplx h) { return e * h; }
+__device__ __forceinline__ double rmul(double a, double c) { return a * c; }
+__device__ __forceinline__ cplx rmul(cplx a, double c) { return cplx{a.re * c, a.im * c}; }
+__device__ __forceinline__ double fmsub_r(double t, double c, double cp) { return fma(t, c, -cp); }
+__device__ __forceinline__ cplx fmsub_r(double t, cplx c, cplx cp) {
+  return cplx{fma(t, c.re, -cp.re), fma(t, c.im, -cp.im)};
+}
+// e = a1 * c + a3 * v  (a1, c of type T; a3 of type T; v real)
+__device__ __forceinline__ double dcoef(double a2, double c, double a3, double v) { return fma(a2, c, a3 * v); }
+__device__ __forceinline__ cplx dcoef(cplx a2, cplx c, cplx a3, double v) {
+  return cplx{fma(a3.re, v, a2.re * c.re - a2.im * c.im), fma(a3.im, v, a2.re * c.im + a2.im * c.re)};
+}
+// H_{l+1} = s_l H_l - H_{l-1},  s_l = 2l/z
+__device__ __forceinline__ cplx hrec(double s, cplx h, cplx hm) {
+  return cplx{fma(s, h.re, -hm.re), fma(s, h.im, -hm.im)};
+}
+__device__ __forceinline__ cplx hrec(cplx s, cplx h, cplx hm) { return s * h - hm; }
+__device__ __forceinline__ double sadd(double a, double b) { return a + b; }
+__device__ __forceinline__ cplx sadd(cplx a, cplx b) { return a + b; }
+
+template <typename T> struct KW;
+template <> struct KW<double> {
+  double k, ik;
+  __device__ __forceinline__ void init(double kre, double) { k = kre; ik = 1.0 / kre; }
+  __device__ __forceinline__ double kval() const { return k; }
+  __device__ __forceinline__ void hankel(double rho, double inv, cplx& h0, cplx& h1, double& twoz) const {
+    const double z = k * rho, invz = ik * inv;
+    twoz = 2.0 * invz;
+    hankel01_real(z, invz, h0, h1);
+  }
+};
+template <> struct KW<cplx> {
+  cplx k;
+  __device__ __forceinline__ void init(double kre, double kim) { k = cplx{kre, kim}; }
+  __device__ __forceinline__ cplx kval() const { return k; }
+  __device__ __forceinline__ void hankel(double rho, double inv, cplx& h0, cplx& h1, cplx& twoz) const {
+    const cplx z = cplx{k.re * rho, k.im * rho};
+    twoz = 2.0 * cinv(z);
+    hankel01_cplx(z, h0, h1);
+  }
+};
+
+__host__ __device__ constexpr int popc3(int m) { return (m & 1) + ((m >> 1) & 1) + ((m >> 2) & 1); }
+// partial-sum components: S -> 1, D -> 1, grad S -> 2 (in this order)
+__host__ __device__ constexpr int ops_ncomp(int m) { return (m & 1) + ((m >> 1) & 1) + 2 * ((m >> 2) & 1); }
+
+// Shared memory layout (bytes): source tile x, y [, nx, ny] ; densities
+// [nops][tile][NR] ; coefficient slots [(p+2)][kApplyThreads] of type T:
+// slot J (raw J_l, then l J_l), slot S (2 J_l), slot D (J_{l+1}), slot G
+// (J_{l-1} - J_{l+1}); only the slots the operator set needs are present.
+template <int OPS, typename T, int NR>
+struct ApplySmem {
+  static constexpr int kNops = popc3(OPS);
+  static constexpr bool kS = OPS & OPB_S, kD = OPS & OPB_D, kG = OPS & OPB_G;
+  static constexpr int kGeo = kD ? 4 : 2;
+  static __host__ __device__ size_t tile_bytes() {
+    return (size_t)kGeo * kSrcTile * 8 + (size_t)kNops * kSrcTile * NR * 16;
+  }
+  static __host__ __device__ int nslots() { return 1 + (kS ? 1 : 0) + (kD ? 1 : 0) + (kG ? 1 : 0); }
+  static __host__ __device__ size_t bytes(int p) {
+    return tile_bytes() + (size_t)nslots() * (p + 2) * kApplyThreads * sizeof(T);
+  }
+};
+
+template <int OPS, typename T, int NR>
+__global__ void __launch_bounds__(kApplyThreads)
+k_apply_fused(ApplyArgs a) {
+  using L = ApplySmem<OPS, T, NR>;
+  constexpr bool kS = L::kS, kD = L::kD, kG = L::kG;
+  constexpr int kNops = L::kNops;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* s_x = reinterpret_cast<double*>(smem_raw);
+  double* s_y = s_x + kSrcTile;
+  double* s_nx = s_y + kSrcTile;            // only with D
+  double* s_ny = s_nx + kSrcTile;
+  cplx* s_wd = reinterpret_cast<cplx*>(smem_raw + (size_t)L::kGeo * kSrcTile * 8);  // [nops][tile][NR]
+  T* slot = reinterpret_cast<T*>(smem_raw + L::tile_bytes());
+  const int p = a.p;
+  const int P2 = (p + 2) * kApplyThreads;
+  T* sJ = slot;                              // raw J, later l J_l
+  T* sS = slot + P2;                         // 2 J_l
+  T* sD = sS + (kS ? P2 : 0);                // J_{l+1}
+  T* sG = sD + (kD ? P2 : 0);                // J_{l-1} - J_{l+1}
+
+  const int tid = threadIdx.x;
+  const int c = blockIdx.x * kApplyThreads + tid;
+  const bool active = c < a.n_ctr;
+  const int cc = active ? c : a.n_ctr - 1;
+
+  // ---- per-centre set-up: target direction, J_l(k r) (a5) ----
+  const double cx = a.cx[cc], cy = a.cy[cc];
+  const int t = cc % a.n_tgt;
+  double ux = a.tx[t] - cx, uy = a.ty[t] - cy;
+  const double r = hypot(ux, uy);
+  const double ir = 1.0 / r;
+  ux *= ir;
+  uy *= ir;
+  KW<T> kw;
+  kw.init(a.kre, a.kim);
+  const T kk = kw.kval();
+  T* colJ = sJ + tid;
+  besselj_seq<T>(rmul(kk, r), p + 1, colJ, kApplyThreads);
+  const T J0 = colJ[0];
+  for (int l = 0; l <= p; ++l) {
+    const T jl = colJ[l * kApplyThreads];
+    const T jn = colJ[(l + 1) * kApplyThreads];
+    if (kS) sS[l * kApplyThreads + tid] = (l == 0) ? jl : rmul(jl, 2.0);
+    if (kD) {
+      T z0;
+      sc_zero(z0);
+      sD[l * kApplyThreads + tid] = (l < p) ? jn : z0;
+    }
+    if (kG) {
+      const T jp = (l == 0) ? jn : colJ[(l - 1) * kApplyThreads];
+      sG[l * kApplyThreads + tid] = (l == 0) ? rmul(jn, -1.0) : sc_sub(jp, jn);
+    }
+  }
+  // l J_l in place (needs the raw J's above first)
+  for (int l = 0; l <= p; ++l) colJ[l * kApplyThreads] = rmul(colJ[l * kApplyThreads], (double)l);
+  const T kneg_j0 = rmul(sc_mul(kk, J0), -1.0);  // -k J0 (D)
+
+  cplx accS[NR], accD[NR], accA[NR], accB[NR];
+#pragma unroll
+  for (int q = 0; q < NR; ++q) accS[q] = accD[q] = accA[q] = accB[q] = cplx{0.0, 0.0};
+
+  const int s_begin = blockIdx.y * a.src_per_split;
+  const int s_end = min(a.src.n, s_begin + a.src_per_split);
+  const cplx* wdp[3] = {reinterpret_cast<const cplx*>(a.wd[0]), reinterpret_cast<const cplx*>(a.wd[1]),
+                        reinterpret_cast<const cplx*>(a.wd[2])};
+
+  for (int base = s_begin; base < s_end; base += kSrcTile) {
+    const int nt = min(kSrcTile, s_end - base);
+    __syncthreads();
+    for (int i = tid; i < nt; i += kApplyThreads) {
+      s_x[i] = a.src.x[base + i];
+      s_y[i] = a.src.y[base + i];
+      if (kD) {
+        s_nx[i] = a.src.nx[base + i];
+        s_ny[i] = a.src.ny[base + i];
+      }
+    }
+    {
+      int slotn = 0;
+#pragma unroll
+      for (int o = 0; o < 3; ++o) {
+        if (!(OPS & (1 << o))) continue;
+        const cplx* w = wdp[o];
+        cplx* dst = s_wd + (size_t)slotn * kSrcTile * NR;
+        for (int i = tid; i < nt * NR; i += kApplyThreads) {
+          const int s = i / NR, rr = i - s * NR;
+          dst[i] = (rr < a.nr) ? w[(size_t)(base + s) * a.nrhs + a.rhs0 + rr] : cplx{0.0, 0.0};
+        }
+        ++slotn;
+      }
+    }
+    __syncthreads();
+    if (!active) continue;
+
+    const T* cS = sS + tid;
+    const T* cD = sD + tid;
+    const T* cG = sG + tid;
+    const T* cJ = colJ;  // l J_l
+
+    for (int j = 0; j < nt; ++j) {
+      // ---- a2: pair geometry and H0, H1 ----
+      const double dx = s_x[j] - cx, dy = s_y[j] - cy;
+      const double rho2 = fma(dx, dx, dy * dy);
+      const double inv = rsqrt(rho2);
+      const double rho = rho2 * inv;
+      const double cs = fma(ux, dx, uy * dy) * inv;  // cos psi
+      cplx H0, H1;
+      T twoz;
+      kw.hankel(rho, inv, H0, H1, twoz);
+      const double tw = 2.0 * cs;
+      double sn = 0.0;
+      if (kD || kG) sn = fma(uy, dx, -ux * dy) * inv;  // sin psi
+
+      // ---- order-0 terms and recurrence seeds ----
+      cplx GS, K, GA, GB;
+      T Cp, Cc;
+      double Vp = 0.0, Vc = 0.0;
+      if (kS) GS = smul(cS[0], H0);
+      if (kG) {
+        GA = smul(cG[0], H0);
+        GB = cplx{0.0, 0.0};
+      }
+      if (kD) {
+        const double nx = s_nx[j], ny = s_ny[j];
+        const double av = fma(nx, dx, ny * dy) * inv;    // n_s . e_rho
+        const double bv = fma(ny, dx, -nx * dy) * inv;   // n_s . e_theta
+        const T tka = rmul(kk, 2.0 * av);                // C_0 = 2 k a
+        const double i2 = 2.0 * inv;
+        Cp = tka;
+        Cc = rmul(tka, cs);                              // C_1
+        K = smul(rmul(kneg_j0, av), H1);                 // -k a J0 H1
+        madd(K, sc_mul(cD[0], Cc), H0);                  // e_0 = J_1 C_1
+        const T Cn = fmsub_r(tw, Cc, Cp);                // C_2
+        Cp = Cc;
+        Cc = Cn;
+        Vp = -i2 * av;                                   // V_0
+        Vc = i2 * fma(bv, sn, -av * cs);                 // V_1
+      }
+      cplx Hm = H0, H = H1;
+      T s = twoz;
+      double cp = 1.0, cl = cs, sp = 0.0, sl = sn;
+      for (int l = 1; l <= p; ++l) {
+        const int o = l * kApplyThreads;
+        if (kS) madd(GS, rmul(cS[o], cl), H);
+        if (kD) madd(K, dcoef(cD[o], Cc, cJ[o], Vc), H);
+        if (kG) {
+          madd(GA, rmul(cG[o], cl), H);
+          madd(GB, rmul(cJ[o], sl), H);
+        }
+        if (l < p) {
+          const cplx Hn = hrec(s, H, Hm);
+          Hm = H;
+          H = Hn;
+          s = sadd(s, twoz);
+          const double cn = fma(tw, cl, -cp);
+          cp = cl;
+          cl = cn;
+          if (kG) {
+            const double sq = fma(tw, sl, -sp);
+            sp = sl;
+            sl = sq;
+          }
+          if (kD) {
+            const T Cn = fmsub_r(tw, Cc, Cp);
+            Cp = Cc;
+            Cc = Cn;
+            const double Vn = fma(tw, Vc, -Vp);
+            Vp = Vc;
+            Vc = Vn;
+          }
+        }
+      }
+      // ---- weighted densities ----
+      int slotn = 0;
+      if (kS) {
+        const cplx* w = s_wd + ((size_t)slotn * kSrcTile + j) * NR;
+#pragma unroll
+        for (int q = 0; q < NR; ++q) accS[q] = accS[q] + w[q] * GS;
+        ++slotn;
+      }
+      if (kD) {
+        const cplx* w = s_wd + ((size_t)slotn * kSrcTile + j) * NR;
+#pragma unroll
+        for (int q = 0; q < NR; ++q) accD[q] = accD[q] + w[q] * K;
+        ++slotn;
+      }
+      if (kG) {
+        const cplx* w = s_wd + ((size_t)slotn * kSrcTile + j) * NR;
+#pragma unroll
+        for (int q = 0; q < NR; ++q) {
+          accA[q] = accA[q] + w[q] * GA;
+          accB[q] = accB[q] + w[q] * GB;
+        }
+      }
+    }
+  }
+  if (!active) return;
+  cplx* part = reinterpret_cast<cplx*>(a.part);
+  constexpr int ncomp = ops_ncomp(OPS);
+  const size_t row = ((size_t)blockIdx.y * a.n_ctr + c) * ncomp;
+#pragma unroll
+  for (int q = 0; q < NR; ++q) {
+    if (q >= a.nr) break;
+    int comp = 0;
+    if (kS) part[(row + comp++) * a.nrhs + a.rhs0 + q] = accS[q];
+    if (kD) part[(row + comp++) * a.nrhs + a.rhs0 + q] = accD[q];
+    if (kG) {
+      // grad = e_r k A - e_theta (1/r) B, B = 2 sum l J_l H_l sin: e_r = (ux, uy), e_theta = (-uy, ux)
+      const cplx kA = smul(kk, accA[q]);
+      const cplx Bi = accB[q] * (2.0 * ir);
+      part[(row + comp++) * a.nrhs + a.rhs0 + q] = kA * ux + Bi * uy;
+      part[(row + comp++) * a.nrhs + a.rhs0 + q] = kA * uy - Bi * ux;
+    }
+  }
+}
+
+template <int OPS, typename T, int NR>
+static cudaError_t launch_apply_t(const ApplyArgs& a, cudaStream_t st) {
+  const size_t smem = ApplySmem<OPS, T, NR>::bytes(a.p);
+  auto kern = k_apply_fused<OPS, T, NR>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid((a.n_ctr + kApplyThreads - 1) / kApplyThreads, a.nsplit);
+  kern<<<grid, kApplyThreads, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+// rhs per pass: single operator up to 8, several operators up to 4
+template <int OPS, typename T>
+static cudaError_t launch_apply_nr(const ApplyArgs& a, cudaStream_t st) {
+  if (a.nr <= 1) return launch_apply_t<OPS, T, 1>(a, st);
+  if constexpr (popc3(OPS) > 1) {
+    return launch_apply_t<OPS, T, 4>(a, st);
+  } else {
+    if (a.nr <= 4) return launch_apply_t<OPS, T, 4>(a, st);
+    return launch_apply_t<OPS, T, 8>(a, st);
+  }
+}
+
+template <typename T>
+static size_t apply_smem_t(int ops, int p, int nr) {
+  const int nr_t = nr <= 1 ? 1 : (nr <= 4 || popc3(ops) > 1 ? 4 : 8);
+#define QBX_SM(O)                                                                   \
+  case O:                                                                           \
+    return nr_t == 1 ? ApplySmem<O, T, 1>::bytes(p)                                 \
+                     : (nr_t == 4 ? ApplySmem<O, T, 4>::bytes(p) : ApplySmem<O, T, 8>::bytes(p));
+  // (ApplySmem is a size calculator only; no kernel is instantiated here)
+  switch (ops) {
+    QBX_SM(1) QBX_SM(2) QBX_SM(3) QBX_SM(4) QBX_SM(5) QBX_SM(6) QBX_SM(7)
+    default: return 0;
+  }
+#undef QBX_SM
+}
+
+template <typename T>
+static cudaError_t launch_apply_ops(const ApplyArgs& a, cudaStream_t st) {
+  switch (a.ops) {
+    case OPB_S: return launch_apply_nr<OPB_S, T>(a, st);
+    case OPB_D: return launch_apply_nr<OPB_D, T>(a, st);
+    case OPB_G: return launch_apply_nr<OPB_G, T>(a, st);
+    case OPB_S | OPB_D: return launch_apply_nr<OPB_S | OPB_D, T>(a, st);
+    case OPB_S | OPB_G: return launch_apply_nr<OPB_S | OPB_G, T>(a, st);
+    case OPB_D | OPB_G: return launch_apply_nr<OPB_D | OPB_G, T>(a, st);
+    case OPB_S | OPB_D | OPB_G: return launch_apply_nr<OPB_S | OPB_D | OPB_G, T>(a, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace qbx

@@ -216,8 +216,8 @@ int qbx_gauss_legendre(int q, double* nodes, double* weights) {
 
 size_t qbx_workspace_bytes(int n_src, int n_ctr, int ncoef, int nrhs) {
   if (n_src < 0 || n_ctr < 0 || ncoef < 0 || nrhs < 0) return 0;
-  return align256((size_t)n_src * nrhs * 16) +
-         align256((size_t)kMaxSplit * n_ctr * ncoef * nrhs * 16) + 256;
+  return 3 * align256((size_t)n_src * nrhs * 16) +
+         align256((size_t)kMaxSplit * n_ctr * ncoef * nrhs * 16) + 512;
 }
 
 int qbx_plan_create(qbx_plan** plan, int device, int q_tgt, int q_src, size_t workspace_bytes) {
@@ -444,40 +444,63 @@ int qbx_far(qbx_plan* p, const qbx_geom* g, int op, qbx_c64 k, const qbx_c64* wd
                   p->ws_bytes > 256 ? p->ws_bytes - 256 : 0, (cudaStream_t)stream);
 }
 
-int qbx_apply(qbx_plan* p, const qbx_geom* g, int op, int side, int limit, qbx_c64 k, int pp,
-              const qbx_c64* dens_tgt, int nrhs, int n_far, const double* x_far, qbx_c64* out_on,
-              qbx_c64* out_far, void* stream) {
+// On-surface apply of the operator subset `ops` (one pass over the pairs for
+// all of them), plus far targets when a single operator is requested.
+static int apply_impl(qbx_plan* p, const qbx_geom* g, int ops, int side, int limit, qbx_c64 k, int pp,
+                      const qbx_c64* const dens[3], int nrhs, qbx_c64* const out[3], int n_far,
+                      const double* x_far, qbx_c64* out_far, void* stream) {
   if (int rc = check_plan(p)) return rc;
   if (int rc = check_geom(p, g, true)) return rc;
-  if (op != QBX_OP_S && op != QBX_OP_D && op != QBX_OP_GRAD_S) return fail(QBX_EINVAL, "bad op %d", op);
+  if (ops < 1 || ops > 7) return fail(QBX_EINVAL, "operator set %d is not a non-empty subset of {S, D, grad S}", ops);
   if (limit != QBX_LIMIT_ONE_SIDED && limit != QBX_LIMIT_PV) return fail(QBX_EINVAL, "bad limit %d", limit);
   if (int rc = check_k(k)) return rc;
   if (int rc = check_p(pp)) return rc;
   if (nrhs < 1) return fail(QBX_EINVAL, "nrhs = %d < 1", nrhs);
-  if (!dens_tgt || !out_on) return fail(QBX_EINVAL, "NULL density or output");
+  for (int o = 0; o < 3; ++o)
+    if ((ops >> o & 1) && (!dens[o] || !out[o])) return fail(QBX_EINVAL, "NULL density or output of operator %d", o);
   if (n_far < 0) return fail(QBX_EINVAL, "n_far < 0");
   if (n_far > 0 && (!x_far || !out_far)) return fail(QBX_EINVAL, "n_far > 0 needs x_far and out_far");
   int c0, nc;
   if (int rc = side_range(side, g->n_tgt, &c0, &nc)) return rc;
-  const int ncomp = op == QBX_OP_GRAD_S ? 2 : 1;
-  const size_t wd_bytes = align256((size_t)g->n_src * nrhs * 16);
+  // components of a partial-sum row: S 1, D 1, grad S 2
+  int comp0[3], ncomp = 0;
+  for (int o = 0; o < 3; ++o) {
+    comp0[o] = ncomp;
+    if (ops >> o & 1) ncomp += (o == QBX_OP_GRAD_S) ? 2 : 1;
+  }
+  // one oversampled density per distinct input array
+  const qbx_c64* distinct[3];
+  int slot_of[3] = {0, 0, 0}, nd = 0;
+  for (int o = 0; o < 3; ++o) {
+    if (!(ops >> o & 1)) continue;
+    int s = 0;
+    while (s < nd && distinct[s] != dens[o]) ++s;
+    if (s == nd) distinct[nd++] = dens[o];
+    slot_of[o] = s;
+  }
+  const size_t wd_one = align256((size_t)g->n_src * nrhs * 16);
+  const size_t wd_bytes = wd_one * nd;
   if (p->ws_bytes < wd_bytes + 512) return fail(QBX_ENOMEM, "workspace too small (%zu < %zu)", p->ws_bytes, wd_bytes + 512);
   const size_t avail = p->ws_bytes - wd_bytes - 512;
   const size_t per_split = (size_t)nc * ncomp * nrhs * 16;
   const int units = (nc + kApplyThreads - 1) / kApplyThreads;
   const int ns = choose_split(p, units, g->n_src, per_split, avail);
   if (ns < 1) return fail(QBX_ENOMEM, "workspace too small for the apply partial sums");
-  if (apply_smem_bytes(op, k.im != 0.0, pp, 8) > 220 * 1024) return fail(QBX_EINVAL, "p = %d too large", pp);
+  const int chunk = apply_chunk(ops);
+  if (apply_smem_bytes(ops, k.im != 0.0, pp, chunk) > 220 * 1024) return fail(QBX_EINVAL, "p = %d too large", pp);
   CK(cudaSetDevice(p->device), "cudaSetDevice");
   cudaStream_t st = (cudaStream_t)stream;
   char* base = (char*)align256((size_t)p->ws);
-  void* wd = base;
   void* part = base + wd_bytes;
-  // a1: oversample the density
-  CK(launch_upsample(g->M, g->q_tgt, g->q_src, nrhs, p->d_interp, g->src_w, dens_tgt, wd, st), "upsample");
-  // a2-a6 fused, per chunk of up to 8 rhs
+  // a1: oversample the densities
+  for (int s = 0; s < nd; ++s)
+    CK(launch_upsample(g->M, g->q_tgt, g->q_src, nrhs, p->d_interp, g->src_w, distinct[s], base + s * wd_one, st),
+       "upsample");
+  const void* wd = base;  // far targets (single operator): its oversampled density
+  // a2-a6 fused, per chunk of rhs
   ApplyArgs a{};
-  a.op = op;
+  a.ops = ops;
+  for (int o = 0; o < 3; ++o) a.wd[o] = base + slot_of[o] * wd_one;
   a.p = pp;
   a.kre = k.re;
   a.kim = k.im;
@@ -488,24 +511,44 @@ int qbx_apply(qbx_plan* p, const qbx_geom* g, int op, int side, int limit, qbx_c
   a.tx = g->tgt_x;
   a.ty = g->tgt_y;
   a.src = SrcView{g->src_x, g->src_y, g->src_nx, g->src_ny, g->n_src};
-  a.wd = wd;
   a.nrhs = nrhs;
   a.nsplit = ns;
   a.src_per_split = split_len(g->n_src, ns);
   a.part = part;
-  for (int r0 = 0; r0 < nrhs; r0 += 8) {
+  for (int r0 = 0; r0 < nrhs; r0 += chunk) {
     a.rhs0 = r0;
-    a.nr = std::min(8, nrhs - r0);
+    a.nr = std::min(chunk, nrhs - r0);
     CK(launch_apply_fused(a, st), "apply kernel");
   }
-  // a7: reduce, i/4, jumps / two-sided average
-  CK(launch_apply_finish(op, side, limit, g->n_tgt, ns, nc, nrhs, part, dens_tgt, g->tgt_nx, g->tgt_ny,
-                         out_on, p->d_status, st),
-     "apply finish");
-  // a8: far targets
-  if (n_far > 0)
+  // a7: reduce, i/4, jumps / two-sided average, per operator
+  for (int o = 0; o < 3; ++o) {
+    if (!(ops >> o & 1)) continue;
+    CK(launch_apply_finish(o, side, limit, g->n_tgt, ns, nc, nrhs, comp0[o], ncomp, part, dens[o], g->tgt_nx,
+                           g->tgt_ny, out[o], p->d_status, st),
+       "apply finish");
+  }
+  // a8: far targets (single operator)
+  if (n_far > 0) {
+    int op = 0;
+    while (!(ops >> op & 1)) ++op;
     return far_impl(p, g, op, k, (const qbx_c64*)wd, nrhs, n_far, x_far, out_far, part, avail, st);
+  }
   return QBX_OK;
+}
+
+int qbx_apply(qbx_plan* p, const qbx_geom* g, int op, int side, int limit, qbx_c64 k, int pp,
+              const qbx_c64* dens_tgt, int nrhs, int n_far, const double* x_far, qbx_c64* out_on,
+              qbx_c64* out_far, void* stream) {
+  if (op != QBX_OP_S && op != QBX_OP_D && op != QBX_OP_GRAD_S) return fail(QBX_EINVAL, "bad op %d", op);
+  const qbx_c64* dens[3] = {dens_tgt, dens_tgt, dens_tgt};
+  qbx_c64* out[3] = {out_on, out_on, out_on};
+  return apply_impl(p, g, 1 << op, side, limit, k, pp, dens, nrhs, out, n_far, x_far, out_far, stream);
+}
+
+int qbx_apply_ops(qbx_plan* p, const qbx_geom* g, int ops, int side, int limit, qbx_c64 k, int pp,
+                  const qbx_c64* const dens[3], int nrhs, qbx_c64* const out[3], void* stream) {
+  if (!dens || !out) return fail(QBX_EINVAL, "NULL density or output table");
+  return apply_impl(p, g, ops, side, limit, k, pp, dens, nrhs, out, 0, nullptr, nullptr, stream);
 }
 
 int qbx_assign_centres(qbx_plan* p, const qbx_geom* g, int side, int n, const double* xy, int* out,

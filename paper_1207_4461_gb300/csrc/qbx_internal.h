@@ -19,9 +19,10 @@ struct SrcView {
   int n;
 };
 
-// Fused storage-free apply (a2-a6 fused), one launch per chunk of `nr` rhs.
+// Fused storage-free apply (a2-a6 fused) of an operator subset, one launch
+// per chunk of `nr` rhs.
 struct ApplyArgs {
-  int op;                 // QBX_OP_*
+  int ops;                // bit (1 << QBX_OP_S) | (1 << QBX_OP_D) | (1 << QBX_OP_GRAD_S)
   int p;
   double kre, kim;
   int n_ctr;              // centres in this launch
@@ -29,13 +30,18 @@ struct ApplyArgs {
   int n_tgt;              // target of centre c is c mod n_tgt
   const double *tx, *ty;  // [n_tgt]
   SrcView src;
-  const void* wd;         // [n_src][nrhs] complex
+  const void* wd[3];      // per operator (S, D, grad S): [n_src][nrhs] complex
   int nrhs, rhs0, nr;     // total rhs, first rhs of this chunk, chunk width
   int nsplit, src_per_split;
-  void* part;             // [nsplit][n_ctr][ncomp][nrhs] complex
+  void* part;             // [nsplit][n_ctr][ncomp][nrhs] complex, comps S, D, grad S (x, y)
 };
 cudaError_t launch_apply_fused(const ApplyArgs& a, cudaStream_t st);
-size_t apply_smem_bytes(int op, bool ck, int p, int nr);
+cudaError_t launch_apply_fused_real(const ApplyArgs& a, cudaStream_t st);
+cudaError_t launch_apply_fused_cplx(const ApplyArgs& a, cudaStream_t st);
+size_t apply_smem_bytes(int ops, bool ck, int p, int nr);
+size_t apply_smem_bytes_real(int ops, int p, int nr);
+size_t apply_smem_bytes_cplx(int ops, int p, int nr);
+int apply_chunk(int ops);   // rhs per launch for an operator subset
 
 // Far targets: plain quadrature partial sums.
 struct FarArgs {
@@ -85,10 +91,12 @@ struct EvalArgs {
 cudaError_t launch_eval(const EvalArgs& a, cudaStream_t st);
 
 // Reductions over splits and epilogues.
+// comp0: first component of operator `op` among the ncomp_total components
+// of each partial-sum row.
 cudaError_t launch_apply_finish(int op, int side, int limit, int n_tgt, int nsplit, int n_ctr,
-                                int nrhs, const void* part, const void* dens_tgt,
-                                const double* tgt_nx, const double* tgt_ny, void* out,
-                                int* status, cudaStream_t st);
+                                int nrhs, int comp0, int ncomp_total, const void* part,
+                                const void* dens_tgt, const double* tgt_nx, const double* tgt_ny,
+                                void* out, int* status, cudaStream_t st);
 cudaError_t launch_far_finish(int op, double kre, double kim, int n_far, int nsplit, int nrhs,
                               const void* part, void* out, int* status, cudaStream_t st);
 cudaError_t launch_form_finish(int n_ctr, int ncoef, int nsplit, int nrhs, const void* part,

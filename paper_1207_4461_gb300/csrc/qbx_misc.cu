@@ -130,8 +130,8 @@ cudaError_t launch_upsample(int M, int q_tgt, int q_src, int nrhs, const double*
 // n_tgt + t (exterior) are averaged.
 // ---------------------------------------------------------------------------
 __global__ void k_apply_finish(int op, int side, int limit, int n_tgt, int nsplit, int n_ctr,
-                               int nrhs, const cplx* part, const cplx* dens, const double* tnx,
-                               const double* tny, cplx* out, int* status) {
+                               int nrhs, int comp0, int ncomp_total, const cplx* part, const cplx* dens,
+                               const double* tnx, const double* tny, cplx* out, int* status) {
   const int ncomp = op == QBX_OP_GRAD_S ? 2 : 1;
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= n_tgt * ncomp * nrhs) return;
@@ -143,7 +143,8 @@ __global__ void k_apply_finish(int op, int side, int limit, int n_tgt, int nspli
   for (int sd = 0; sd < nsides; ++sd) {
     const int c = t + sd * n_tgt;
     cplx u{0.0, 0.0};
-    for (int k = 0; k < nsplit; ++k) u = u + part[(((size_t)k * n_ctr + c) * ncomp + comp) * nrhs + r];
+    for (int k = 0; k < nsplit; ++k)
+      u = u + part[(((size_t)k * n_ctr + c) * ncomp_total + comp0 + comp) * nrhs + r];
     u = mul_i(0.25 * u);
     if (side != QBX_SIDE_TWO && limit == QBX_LIMIT_PV) {
       const double sg = side == QBX_SIDE_EXT ? 1.0 : -1.0;
@@ -159,16 +160,29 @@ __global__ void k_apply_finish(int op, int side, int limit, int n_tgt, int nspli
 }
 
 cudaError_t launch_apply_finish(int op, int side, int limit, int n_tgt, int nsplit, int n_ctr,
-                                int nrhs, const void* part, const void* dens_tgt,
-                                const double* tgt_nx, const double* tgt_ny, void* out,
-                                int* status, cudaStream_t st) {
+                                int nrhs, int comp0, int ncomp_total, const void* part,
+                                const void* dens_tgt, const double* tgt_nx, const double* tgt_ny,
+                                void* out, int* status, cudaStream_t st) {
   const int ncomp = op == QBX_OP_GRAD_S ? 2 : 1;
   const int n = n_tgt * ncomp * nrhs;
-  k_apply_finish<<<(n + 255) / 256, 256, 0, st>>>(op, side, limit, n_tgt, nsplit, n_ctr, nrhs,
-                                                  (const cplx*)part, (const cplx*)dens_tgt, tgt_nx,
-                                                  tgt_ny, (cplx*)out, status);
+  k_apply_finish<<<(n + 255) / 256, 256, 0, st>>>(op, side, limit, n_tgt, nsplit, n_ctr, nrhs, comp0,
+                                                  ncomp_total, (const cplx*)part, (const cplx*)dens_tgt,
+                                                  tgt_nx, tgt_ny, (cplx*)out, status);
   return cudaGetLastError();
 }
+
+// Fused apply dispatch: real k (fitted real-argument Hankel path) or complex k.
+cudaError_t launch_apply_fused(const ApplyArgs& a, cudaStream_t st) {
+  return a.kim == 0.0 ? launch_apply_fused_real(a, st) : launch_apply_fused_cplx(a, st);
+}
+
+size_t apply_smem_bytes(int ops, bool ck, int p, int nr) {
+  return ck ? apply_smem_bytes_cplx(ops, p, nr) : apply_smem_bytes_real(ops, p, nr);
+}
+
+// rhs per launch: accumulators for one operator take 8 rhs in registers,
+// several operators together 4.
+int apply_chunk(int ops) { return (ops == 1 || ops == 2 || ops == 4) ? 8 : 4; }
 
 __global__ void k_far_finish(int op, double kre, double kim, int n_far, int nsplit, int nrhs,
                              const cplx* part, cplx* out, int* status) {

@@ -143,7 +143,8 @@ extern "C" int qbx_apply_static(const qbx_geom* g, int op, int side, int limit, 
   e = launch_upsample(g->M, g->q_tgt, g->q_src, nrhs, s->interp, g->src_w, dens_tgt, wd, st);
   if (e != cudaSuccess) return cuda_err(e, "upsample kernel");
   ApplyArgs a{};
-  a.op = op;
+  a.ops = 1 << op;
+  a.wd[0] = a.wd[1] = a.wd[2] = wd;
   a.p = p;
   a.kre = k.re;
   a.kim = k.im;
@@ -154,7 +155,6 @@ extern "C" int qbx_apply_static(const qbx_geom* g, int op, int side, int limit, 
   a.tx = g->tgt_x;
   a.ty = g->tgt_y;
   a.src = SrcView{g->src_x, g->src_y, g->src_nx, g->src_ny, g->n_src};
-  a.wd = wd;
   a.nrhs = nrhs;
   a.nsplit = ns;
   a.src_per_split = host_split_len(g->n_src, ns);
@@ -165,8 +165,8 @@ extern "C" int qbx_apply_static(const qbx_geom* g, int op, int side, int limit, 
     e = launch_apply_fused(a, st);
     if (e != cudaSuccess) return cuda_err(e, "apply kernel");
   }
-  e = launch_apply_finish(op, side, limit, g->n_tgt, ns, nc, nrhs, part, dens_tgt, g->tgt_nx, g->tgt_ny,
-                          out_on, s->status, st);
+  e = launch_apply_finish(op, side, limit, g->n_tgt, ns, nc, nrhs, 0, ncomp, part, dens_tgt, g->tgt_nx,
+                          g->tgt_ny, out_on, s->status, st);
   if (e != cudaSuccess) return cuda_err(e, "apply finish");
   return QBX_OK;
 }

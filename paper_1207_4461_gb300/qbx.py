@@ -79,6 +79,8 @@ def lib():
             L.qbx_apply.argtypes = [_P, G, I, I, I, c64, I, _P, I, I, _P, _P, _P, _P]
             L.qbx_far.argtypes = [_P, G, I, c64, _P, I, I, _P, _P, _P]
             L.qbx_assign_centres.argtypes = [_P, G, I, I, _P, _P, _P]
+            L.qbx_apply_ops.argtypes = [_P, G, I, I, I, c64, I, ctypes.POINTER(_P), I, ctypes.POINTER(_P), _P]
+            L.qbx_apply_ops.restype = I
             L.qbx_apply_static.argtypes = [G, I, I, I, c64, I, _P, I, _P, _P]
             L.qbx_apply_static.restype = I
             L.qbx_debug_hankel01.argtypes = [_P, I, _P, _P, _P]
@@ -279,6 +281,31 @@ def qbx_apply(plan: Plan, g: Geometry, op, side, limit, k, p, dens_tgt, x_far=No
                            _ptr(x_far.contiguous()) if n_far else None, _ptr(out_on), _ptr(out_far),
                            _stream()))
     return (out_on, out_far) if n_far else out_on
+
+
+OPS_S, OPS_D, OPS_GRAD_S = 1, 2, 4
+
+
+def qbx_apply_ops(plan: Plan, g: Geometry, ops, side, limit, k, p, dens, out=None):
+    """Several operators in one pass.  `ops`: iterable of OP_* codes; `dens`:
+    one density tensor for all, or a dict {op: tensor}; returns {op: output}."""
+    ops = sorted(set(ops))
+    if not isinstance(dens, dict):
+        dens = {o: dens for o in ops}
+    dd = {o: _dens2d(dens[o], g.n_tgt) for o in ops}
+    nrhs = dd[ops[0]].shape[1]
+    dev = dd[ops[0]].device
+    if out is None:
+        out = {}
+    for o in ops:
+        if o not in out:
+            shape = (g.n_tgt, 2, nrhs) if o == OP_GRAD_S else (g.n_tgt, nrhs)
+            out[o] = torch.empty(shape, dtype=torch.complex128, device=dev)
+    dp = (_P * 3)(*[_ptr(dd[o]) if o in dd else None for o in range(3)])
+    op_ = (_P * 3)(*[_ptr(out[o]) if o in out else None for o in range(3)])
+    mask = sum(1 << o for o in ops)
+    _check(lib().qbx_apply_ops(plan.handle, g.ref(), mask, side, limit, _k(k), p, dp, nrhs, op_, _stream()))
+    return {o: out[o] for o in ops}
 
 
 def qbx_apply_static(g: Geometry, op, side, limit, k, p, dens_tgt, out_on=None):

@@ -159,6 +159,24 @@ def test_apply_variants_ragged(cuda, op, side, limit, k, p, nrhs):
     assert rel(got, ref) < TOL
 
 
+ALL_SUBSETS = [(0, 1), (0, 2), (1, 2), (0, 1, 2), (0,), (1,), (2,)]
+
+
+@pytest.mark.parametrize("ops", ALL_SUBSETS)
+@pytest.mark.parametrize("side,limit,k,nrhs", [(qbx.SIDE_TWO, 0, 8.0, 1), (qbx.SIDE_INT, 1, 3 + 0.4j, 6),
+                                               (qbx.SIDE_EXT, 1, 12.0, 3)])
+def test_apply_ops_subsets(cuda, ops, side, limit, k, nrhs):
+    """One pass for several operators, each with its own density, 11 panels
+    (176 targets; 352 centres two-sided), 704 sources; 6 rhs = 2 launches."""
+    p = 9
+    plan, g, go = make(W.starfish(0.3, 4), 11, nrhs=nrhs, p=p, extra_ctr=2)
+    dens = {o: W.complex_gaussian(40 + o, g.n_tgt * nrhs).reshape(g.n_tgt, nrhs) for o in ops}
+    got = qbx.qbx_apply_ops(plan, g, ops, side, limit, k, p, {o: dev(dens[o]) for o in ops})
+    for o in ops:
+        ref = oracle.apply(go, o, side, limit, k, p, dens[o])
+        assert rel(got[o], ref) < TOL, o
+
+
 def test_apply_many_rhs(cuda):
     nrhs = 11
     plan, g, go = make(W.ellipse(2.0), 9, nrhs=nrhs)
@@ -178,12 +196,17 @@ def test_apply_full_size_sampled(cuda):
     dens = wl.dens(g.t_tgt)
     rng = np.random.default_rng(12)
     sel = np.unique(np.concatenate([[0, g.n_tgt - 1], rng.integers(0, g.n_tgt, 38)]))
-    for op in (qbx.OP_S, qbx.OP_D, qbx.OP_GRAD_S):
-        got = qbx.qbx_apply(plan, g, op, qbx.SIDE_TWO, 0, wl.k, wl.p, dev(dens))
+    ops = (qbx.OP_S, qbx.OP_D, qbx.OP_GRAD_S)
+    together = qbx.qbx_apply_ops(plan, g, ops, qbx.SIDE_TWO, 0, wl.k, wl.p, dev(dens))  # benchmark call
+    for op in ops:
         ref = oracle.apply(go, op, oracle.SIDE_TWO, 0, wl.k, wl.p, dens, sel=sel)
-        assert rel(got.cpu().numpy()[sel], ref) < TOL, op
-        # property at any size: finite everywhere
-        assert torch.isfinite(torch.view_as_real(got)).all()
+        alone = qbx.qbx_apply(plan, g, op, qbx.SIDE_TWO, 0, wl.k, wl.p, dev(dens))
+        for got in (together[op], alone):
+            assert rel(got.cpu().numpy()[sel], ref) < TOL, op
+            # property at any size: finite everywhere
+            assert torch.isfinite(torch.view_as_real(got)).all()
+        # the one-pass and per-operator kernels agree everywhere to rounding
+        assert rel(together[op], alone.cpu().numpy()) < 1e-13
     qbx.qbx_sync_status(plan)
 
 
