@@ -292,6 +292,8 @@ def run_gpu(args, wl):
             "gpu_launches": args.steps * launches,
             "targets_per_s": world * len(wl.ops) * wl.n_tgt * wl.nrhs / (step_ms * 1e-3),
             "pairs_per_s": world * len(wl.ops) * pairs / (step_ms * 1e-3)}
+    if rank == 0 and not args.no_batch and not args.panels:
+        line["batched"] = run_batch_compare(args, qbx, torch)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         terms, dt, cores = oracle_sample(wl, args.cpu_sample)
         line["cpu_baseline"] = {"value": terms / dt, "unit": "terms/s", "cores": cores, "kind": "oracle",
@@ -305,6 +307,62 @@ def run_gpu(args, wl):
     return 0
 
 
+def run_batch_compare(args, qbx, torch):
+    """64 random curves (16..512 panels, k in (1, 40), p = 10, 32 densities,
+    S and D): one batched launch (CUDA graph) against one qbx_apply_ops call
+    per curve.  Returns the figures for the JSON line."""
+    bw = W.cfg3()
+    insts = bw.instances()
+    Mmax = max(M for _, M, _ in insts)
+    plan = qbx.Plan(bw.q_tgt, bw.q_src, n_src=bw.q_src * Mmax, n_ctr=bw.q_tgt * Mmax, ncoef=2, nrhs=bw.nrhs)
+    geoms = [qbx.qbx_geometry(plan, c, c.edges(M)) for c, M, _ in insts]
+    dens = [torch.as_tensor(bw.dens(i, g.n_tgt), device="cuda").contiguous() for i, g in enumerate(geoms)]
+    ks = [k for _, _, k in insts]
+    batch = qbx.Batch(plan, geoms, ks, bw.p, (qbx.OP_S, qbx.OP_D), qbx.SIDE_INT, 0, dens)
+    outs = [{o: torch.empty_like(batch.out[i][o]) for o in (qbx.OP_S, qbx.OP_D)} for i in range(len(geoms))]
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def per_instance():
+        for i, g in enumerate(geoms):
+            qbx.qbx_apply_ops(plan, g, (qbx.OP_S, qbx.OP_D), qbx.SIDE_INT, 0, ks[i], bw.p, dens[i], out=outs[i])
+
+    def timed(fn, steps):
+        fn()
+        torch.cuda.synchronize()
+        tot = 0.0
+        for s in range(steps):
+            flush.fill_(s & 0xFF)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            tot += e0.elapsed_time(e1)
+        return tot / steps
+
+    steps = max(1, min(args.steps, 3))
+    ms_batch = timed(batch.apply, steps)
+    batch.status()
+    ms_inst = timed(per_instance, steps)
+    qbx.qbx_sync_status(plan)
+    pairs = sum(g.n_tgt * g.n_src for g in geoms)
+    terms = pairs * (2 * bw.p + 1) * bw.nrhs * 2
+    fpp = flops_per_pair_ops(["S", "D"], bw.p, bw.nrhs)
+    achieved = pairs * fpp / (ms_batch * 1e-3) / 1e9
+    return {"workload": "64 random Fourier curves r=1+sum_{m<=8}(a_m cos mt+b_m sin mt), a,b~U(-0.04,0.04), "
+                        "M~U{16..512} x 16 targets, 4x sources, k~U(1,40), p=10, 32 CN(0,1) densities, "
+                        "interior, S and D (seed 3)",
+            "pairs": pairs, "terms_per_step": terms, "steps": steps,
+            "batched_ms": ms_batch, "per_instance_ms": ms_inst,
+            "batched_terms_per_s": terms / (ms_batch * 1e-3),
+            "per_instance_terms_per_s": terms / (ms_inst * 1e-3),
+            "speedup": ms_inst / ms_batch,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
+                         "frac": achieved / FP64_PEAK_GFLOPS, "flops_per_pair": fpp,
+                         "kernel": "k_apply_group (persistent, longest-first items, CUDA graph)"}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -314,6 +372,8 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=192, help="targets in the CPU-baseline sample")
     ap.add_argument("--ref-sample", type=int, default=48, help="targets per step of --impl reference")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="skip the batched vs per-curve comparison (64 random curves)")
     ap.add_argument("--separate", action="store_true",
                     help="one qbx_apply launch per operator instead of one pass for all")
     ap.add_argument("--panels", type=int, default=None,

@@ -208,6 +208,82 @@ int qbx_far(qbx_plan *plan, const qbx_geom *g, int op, qbx_c64 k, const qbx_c64 
 int qbx_assign_centres(qbx_plan *plan, const qbx_geom *g, int side, int n, const double *xy,
                        int *out, void *stream);
 
+/* Adjoint of the on-surface apply with respect to the density (op S or D):
+ * for u = qbx_apply(sigma) = A sigma, returns gdens = A^H gout, the
+ * vector-Jacobian product that reverse-mode differentiation of a loss of u
+ * needs (A = (i/4) K W P with kernel values K(c, x_s) of the truncated Graf
+ * sum, source weights W and the per-panel interpolation P of Sec. 3.4.2, so
+ * A^H = P^T W K^H (-i/4), plus the self-adjoint jump term of a PV).  The
+ * transposed sweep runs over (source, centre) pairs and recomputes the
+ * Hankel recurrences; nothing of the forward apply is stored.  gout, gdens:
+ * [n_tgt][nrhs] device arrays; other arguments as qbx_apply.  Uses the plan's
+ * workspace. */
+int qbx_apply_adjoint(qbx_plan *plan, const qbx_geom *g, int op, int side, int limit, qbx_c64 k, int p,
+                      const qbx_c64 *gout, int nrhs, qbx_c64 *gdens, void *stream);
+
+/* Second-kind exterior Dirichlet (sound-soft) solve, Sec. 4.2 eq.
+ * dirichlet-inteq with the exterior sign and the combined-field coupling
+ * alpha = -i eta:  (1/2) mu + D mu - i eta S mu = f  on Gamma, D and S as
+ * two-sided averages (Sec. 3.5: two-sided averaging gives a spectrum that
+ * clusters at zero), unknowns scaled by sqrt(w) (Sec. 4.2), by restarted
+ * GMRES(restart) for nrhs right-hand sides f [n_tgt][nrhs] at once (every
+ * system its own Krylov space; one S+D apply per iteration serves all).
+ * Arnoldi by classical Gram-Schmidt with re-orthogonalisation on the device;
+ * Givens rotations on the host.  mu [n_tgt][nrhs]: initial guess in,
+ * solution out.  Stops when every relative residual ||f - A mu||/||f|| (in
+ * the sqrt-weighted norm, GMRES estimate) is below tol, or after maxiter
+ * matvecs (QBX_ENOCONV).  iters (host, may be NULL) receives the matvec
+ * count, resid (host [nrhs], may be NULL) the final relative residuals.
+ * Allocates its Krylov basis ((restart+1) n_tgt nrhs complex) for the
+ * duration of the call; synchronous. */
+int qbx_solve_exterior_dirichlet(qbx_plan *plan, const qbx_geom *g, qbx_c64 k, qbx_c64 eta, int p,
+                                 const qbx_c64 *f, int nrhs, double tol, int restart, int maxiter,
+                                 qbx_c64 *mu, int *iters, double *resid, void *stream);
+
+/* Vector kernels of the solve, also usable on their own.  Vectors are
+ * [n][nrhs] complex device arrays; bases [nv][n][nrhs].
+ *   qbx_vec_scale_sqrtw: out = in * sqrt(w) (inverse = 0) or in / sqrt(w).
+ *   qbx_cfie_combine: y = sqrt(w) (xden/2 + dmu - i eta smu).
+ *   qbx_vec_dots: out[j][r] = sum_i conj(V_j[i][r]) w[i][r], j < nv (fixed
+ *     reduction order); work needs qbx_vec_dots_work_bytes(nrhs, nv) bytes.
+ *   qbx_vec_orth_update: w -= sum_j V_j h[j][r].
+ *   qbx_vec_scale_cols: out[i][r] = a[r] in[i][r] (a: device [nrhs] real).
+ *   qbx_vec_combine: x += sum_j V_j y[j][r]. */
+int qbx_vec_scale_sqrtw(int n, int nrhs, const double *w, const qbx_c64 *in, qbx_c64 *out, int inverse,
+                        void *stream);
+int qbx_cfie_combine(int n, int nrhs, const double *w, const qbx_c64 *xden, const qbx_c64 *dmu,
+                     const qbx_c64 *smu, qbx_c64 eta, qbx_c64 *y, void *stream);
+int qbx_vec_dots(int n, int nrhs, int nv, const qbx_c64 *V, const qbx_c64 *w, qbx_c64 *work, qbx_c64 *out,
+                 void *stream);
+size_t qbx_vec_dots_work_bytes(int nrhs, int nv);
+int qbx_vec_orth_update(int n, int nrhs, int nv, const qbx_c64 *V, const qbx_c64 *h, qbx_c64 *w, void *stream);
+int qbx_vec_scale_cols(int n, int nrhs, const double *a, const qbx_c64 *in, qbx_c64 *out, void *stream);
+int qbx_vec_combine(int n, int nrhs, int nv, const qbx_c64 *V, const qbx_c64 *y, qbx_c64 *x, void *stream);
+
+/* Batched apply: many curves, each with its own panels, wavenumber and nrhs
+ * densities, in one persistent launch run as a CUDA graph (the paper's cost
+ * remark, Sec. 5: the work is O(N N_t) per curve; many small curves would
+ * under-fill the GPU one launch at a time).  Every curve uses the same order
+ * p, operator set (S, D, S+D or S+D+grad S, as QBX_OPS_* bits), side and
+ * limit, and the plan's (q_tgt, q_src); geoms[i] is curve i's geometry from
+ * qbx_geometry, k[i] its wavenumber (host arrays).  dens[i] (host array of
+ * device pointers, [n_tgt_i][nrhs]) and out[3*i + op] (device pointers in
+ * qbx_apply's layout, NULL for operators not requested) are bound at
+ * creation: every qbx_batch_apply reads the current contents of dens and
+ * writes out.  Work items are 32 centres of one curve against all its
+ * sources, taken longest first by persistent CTAs through an atomic counter;
+ * no CTA ever waits for another.  qbx_batch_create allocates the batch's
+ * device memory and builds and instantiates the graph (synchronous);
+ * qbx_batch_apply launches the graph on `stream`. */
+typedef struct qbx_batch qbx_batch;
+int qbx_batch_create(qbx_batch **batch, qbx_plan *plan, int n_inst, const qbx_geom *geoms,
+                     const qbx_c64 *k, int p, int ops, int side, int limit, int nrhs,
+                     const qbx_c64 *const *dens, qbx_c64 *const *out);
+int qbx_batch_apply(qbx_batch *batch, void *stream);
+/* Read (and clear) the batch's device status word, as qbx_sync_status. */
+int qbx_batch_status(qbx_batch *batch, void *stream);
+int qbx_batch_destroy(qbx_batch *batch);
+
 /* qbx_apply without a plan, for callers that cannot allocate device memory.
  * The paper has no counterpart; this is a deployment variant of qbx_apply.
  *

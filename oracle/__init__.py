@@ -242,6 +242,15 @@ def apply(g, op, side, limit, k, p, dens_tgt, sel=None):
     return out
 
 
+def matrix(g, op, side, limit, k, p):
+    """The discrete operator as a matrix: column j is apply() of the j-th unit
+    density (all columns at once, as nrhs = n_tgt right-hand sides).  Shape
+    [n_tgt][n_tgt] for S and D, [n_tgt][2][n_tgt] for grad S.  For small
+    problems: the adjoint of the apply is then conj(A).T."""
+    n = g["n_tgt"]
+    return apply(g, op, side, limit, k, p, np.eye(n, dtype=np.complex128))
+
+
 def far(g, op, k, wdens, xy):
     """Plain smooth quadrature of S, D or grad S at off-surface points xy [n,2]."""
     wd = _dens2d(wdens, g["n_src"])

@@ -5,13 +5,15 @@ The output header is committed; the build does not run this script.
 
 Real argument z > 0 is split in two regions.
 
-Large z (z >= Z_SPLIT): Hankel's form H_n(z) = sqrt(2/(pi z)) e^{i(z - n pi/2 - pi/4)}
-(P_n(w) + i Q_n(w)), w = 1/z (DLMF 10.17.3-10.17.5 define the same amplitude).
-P_n and Q_n are smooth on w in [0, 1/Z_SPLIT]; they are approximated piecewise
-on NI equal intervals by polynomials in u = w - w_mid.  The coefficients come
-from Chebyshev interpolation of 34-digit mpmath values at the Chebyshev nodes of
-each interval (converted to the monomial basis in u).  The degree is the
-smallest one for which every interval is within MAX_ERR on a dense check grid.
+Large z (z >= Z_SPLIT): the modulated amplitudes B_n(s) = H_n(z) e^{-i(z - pi/4)},
+s = z^{-1/2}, n = 0, 1.  By Hankel's expansion (DLMF 10.17.3-10.17.5)
+B_n(s) = sqrt(2/pi) s e^{-i n pi/2} (P_n(s^2) + i Q_n(s^2)) with P, Q smooth, so
+B_n is smooth in s on [0, Z_SPLIT^{-1/2}] (no square root left to evaluate).
+B_n is approximated piecewise on intervals of width 1/NI_PER_UNIT in s by
+polynomials in u = s - s_mid.  The coefficients come from Chebyshev
+interpolation of 34-digit mpmath values at the Chebyshev nodes of each
+interval (converted to the monomial basis in u).  The degree is the smallest
+one for which every interval is within MAX_ERR on a dense check grid.
 
 Small z (z < Z_SPLIT): ascending series in t = (z/2)^2 (DLMF 10.2.2, 10.8.1):
   J0 = sum_m (-t)^m/(m!)^2,   J1 = (z/2) sum_m (-t)^m/(m!(m+1)!)
@@ -29,18 +31,18 @@ import numpy as np
 mp.mp.dps = 40
 
 Z_SPLIT = 2.0          # series below, amplitude fits above
-NI = 32                # intervals on w in [0, 1/Z_SPLIT]
-MAX_ERR = 2.5e-16      # absolute, amplitude ~ 1
-NT = 256               # phase table size
+NI_PER_UNIT = 128      # intervals per unit of s (a power of two)
+NI = int(mp.ceil(NI_PER_UNIT / mp.sqrt(Z_SPLIT)))   # intervals covering s in [0, Z_SPLIT^-1/2]
+MAX_ERR = 3.5e-16      # absolute; |B_n| <= 0.6 on the range
+NT = 1024              # phase table size
 NSER = 14              # series terms (t <= 1: 1/(13!)^2 ~ 2.6e-20)
 
 
-def amp(n, w):
-    if w == 0:
-        return mp.mpc(1, 0)
-    z = 1 / mp.mpf(w)
-    h = mp.hankel1(n, z)
-    return h * mp.expj(-(z - n * mp.pi / 2 - mp.pi / 4)) * mp.sqrt(mp.pi * z / 2)
+def amp(n, s):
+    if s == 0:
+        return mp.mpc(0, 0)
+    z = 1 / mp.mpf(s) ** 2
+    return mp.hankel1(n, z) * mp.expj(-(z - mp.pi / 4))
 
 
 def fit_interval(n, a, b, deg):
@@ -86,16 +88,15 @@ def check(n, a, b, mid, coefs):
     err = 0.0
     for w in np.linspace(a, b, 41):
         v = amp(n, w)
-        u = w - mid
+        u = (1.0 + w) - (1.0 + mid)   # the kernel forms u from s + 1
         err = max(err, abs(float(v.real) - horner([float(c) for c in coefs[0]], u)),
                   abs(float(v.imag) - horner([float(c) for c in coefs[1]], u)))
     return err
 
 
 def build_amp_tables():
-    wmax = 1.0 / Z_SPLIT
-    width = wmax / NI
-    for deg in range(5, 12):
+    width = 1.0 / NI_PER_UNIT
+    for deg in range(4, 12):
         tabs, worst = {}, 0.0
         for n in (0, 1):
             rows = []
@@ -150,14 +151,15 @@ def main():
     lines.append(f"#define QBX_HK_ZSPLIT {fmt(Z_SPLIT)}")
     lines.append(f"#define QBX_HK_NI {NI}")
     lines.append(f"#define QBX_HK_DEG {deg}")
-    lines.append(f"#define QBX_HK_INV_WIDTH {fmt(1.0 / width)}")
+    lines.append(f"#define QBX_HK_S_MAX {fmt(mp.sqrt(1 / mp.mpf(Z_SPLIT)))}")
+    lines.append(f"#define QBX_HK_LOG2_PER_UNIT {int(mp.log(NI_PER_UNIT, 2))}")
     lines.append(f"#define QBX_HK_NSER {NSER}")
     lines.append(f"#define QBX_HK_NT {NT}")
     lines.append(f"#define QBX_HK_RED_SCALE {fmt(NT / (2 * mp.pi))}")
     lines.append(f"#define QBX_HK_RED_HI {fmt(hi)}")
     lines.append(f"#define QBX_HK_RED_LO {fmt(lo)}")
     lines.append(f"// worst fitted amplitude error on the check grid: {worst:.2e}")
-    # amplitude table: [NI][4 funcs P0,Q0,P1,Q1][DEG+1] plus mids
+    # amplitude table: [NI][4 parts Re B0, Im B0, Re B1, Im B1][DEG+1] plus 1 + mids
     lines.append(f"QBX_HK_GQUAL double qbx_hk_mid1[{NI}] = {{")
     lines.append("  " + ", ".join(fmt(1.0 + tabs[0][i][0]) for i in range(NI)) + "};")
     lines.append(f"QBX_HK_GQUAL double qbx_hk_amp[{NI}][4][{deg + 1}] = {{")

@@ -65,22 +65,37 @@ __device__ __forceinline__ cplx hrec(cplx s, cplx h, cplx hm) { return s * h - h
 __device__ __forceinline__ double sadd(double a, double b) { return a + b; }
 __device__ __forceinline__ cplx sadd(cplx a, cplx b) { return a + b; }
 
+// Per-pair distance powers and H0, H1 for real k (fitted path, needs
+// rho^{-1/2}) or complex k.
 template <typename T> struct KW;
 template <> struct KW<double> {
-  double k, ik;
-  __device__ __forceinline__ void init(double kre, double) { k = kre; ik = 1.0 / kre; }
+  double k, ik, ksq;  // k, 1/k, k^{-1/2}
+  __device__ __forceinline__ void init(double kre, double) {
+    k = kre;
+    ik = 1.0 / kre;
+    ksq = rsqrt(kre);
+  }
   __device__ __forceinline__ double kval() const { return k; }
-  __device__ __forceinline__ void hankel(double rho, double inv, cplx& h0, cplx& h1, double& twoz) const {
+  __device__ __forceinline__ void geom(double rho2, double& inv, double& rho, double& y) const {
+    rho_powers(rho2, y, inv, rho);
+  }
+  __device__ __forceinline__ void hankel(double rho, double inv, double y, cplx& h0, cplx& h1,
+                                         double& twoz) const {
     const double z = k * rho, invz = ik * inv;
-    twoz = 2.0 * invz;
-    hankel01_real(z, invz, h0, h1);
+    twoz = invz + invz;
+    hankel01_real(z, invz, y * ksq, h0, h1);
   }
 };
 template <> struct KW<cplx> {
   cplx k;
   __device__ __forceinline__ void init(double kre, double kim) { k = cplx{kre, kim}; }
   __device__ __forceinline__ cplx kval() const { return k; }
-  __device__ __forceinline__ void hankel(double rho, double inv, cplx& h0, cplx& h1, cplx& twoz) const {
+  __device__ __forceinline__ void geom(double rho2, double& inv, double& rho, double& y) const {
+    inv = rsqrt(rho2);
+    rho = rho2 * inv;
+    y = 0.0;
+  }
+  __device__ __forceinline__ void hankel(double rho, double, double, cplx& h0, cplx& h1, cplx& twoz) const {
     const cplx z = cplx{k.re * rho, k.im * rho};
     twoz = 2.0 * cinv(z);
     hankel01_cplx(z, h0, h1);
@@ -92,9 +107,9 @@ __host__ __device__ constexpr int popc3(int m) { return (m & 1) + ((m >> 1) & 1)
 __host__ __device__ constexpr int ops_ncomp(int m) { return (m & 1) + ((m >> 1) & 1) + 2 * ((m >> 2) & 1); }
 
 // Shared memory layout (bytes): source tile x, y [, nx, ny] ; densities
-// [nops][tile][NR] ; coefficient slots [(p+2)][kApplyThreads] of type T:
-// slot J (raw J_l, then l J_l), slot S (2 J_l), slot D (J_{l+1}), slot G
-// (J_{l-1} - J_{l+1}); only the slots the operator set needs are present.
+// [nops][tile][NR] ; per-centre coefficient slots [(p+2)][kApplyThreads] of
+// type T: slot J (J_l), slot L (l J_l; with D or grad S), slot G
+// (J_{l-1} - J_{l+1}; with grad S).
 template <int OPS, typename T, int NR>
 struct ApplySmem {
   static constexpr int kNops = popc3(OPS);
@@ -103,18 +118,121 @@ struct ApplySmem {
   static __host__ __device__ size_t tile_bytes() {
     return (size_t)kGeo * kSrcTile * 8 + (size_t)kNops * kSrcTile * NR * 16;
   }
-  static __host__ __device__ int nslots() { return 1 + (kS ? 1 : 0) + (kD ? 1 : 0) + (kG ? 1 : 0); }
+  static __host__ __device__ int nslots() { return 1 + ((kD || kG) ? 1 : 0) + (kG ? 1 : 0); }
   static __host__ __device__ size_t bytes(int p) {
     return tile_bytes() + (size_t)nslots() * (p + 2) * kApplyThreads * sizeof(T);
   }
 };
 
+// The kernel values of one (centre, source) pair for the operator set OPS,
+// without the factor i/4: GS (S), K (D), GA and GB (grad S: the e_r and
+// e_theta sums before scaling).  (dx, dy) = x_s - c, (nx, ny) = n_s,
+// (ux, uy) = unit vector from c to its target; cJ, cL, cG: the centre's
+// coefficient columns (J_l, l J_l, J_{l-1} - J_{l+1}) with stride STRIDE.
+template <int OPS, typename T, int STRIDE>
+__device__ __forceinline__ void pair_kernels(const KW<T>& kw, const T kk, const T J0, const T kneg_j0,
+                                             const T* cJ, const T* cL, const T* cG, int p, double dx,
+                                             double dy, double nx, double ny, double ux, double uy,
+                                             cplx& GS, cplx& K, cplx& GA, cplx& GB) {
+  constexpr bool kS = OPS & OPB_S, kD = OPS & OPB_D, kG = OPS & OPB_G;
+  constexpr bool kDsum = kD && kG;
+  // ---- a2: pair geometry and H0, H1 ----
+  const double rho2 = fma(dx, dx, dy * dy);
+  double inv, rho, yq;
+  kw.geom(rho2, inv, rho, yq);
+  const double cs = fma(ux, dx, uy * dy) * inv;  // cos psi
+  cplx H0, H1;
+  T twoz;
+  kw.hankel(rho, inv, yq, H0, H1, twoz);
+  const double tw = 2.0 * cs;
+  double sn = 0.0;
+  if (kD || kG) sn = fma(uy, dx, -ux * dy) * inv;  // sin psi
+  double av = 0.0, bv = 0.0;
+  if (kD) {
+    av = fma(nx, dx, ny * dy) * inv;   // n_s . e_rho
+    bv = fma(ny, dx, -nx * dy) * inv;  // n_s . e_theta
+  }
+
+  // ---- order sums; l = 0 terms and recurrence seeds ----
+  GS = K = GA = GB = cplx{0.0, 0.0};
+  cplx D1 = cplx{0.0, 0.0}, D3 = cplx{0.0, 0.0};
+  T Cp, Cc;
+  double Vp = 0.0, Vc = 0.0;
+  if (kG) GA = smul(cG[0], H0);
+  if (kD && !kDsum) {
+    const T tka = rmul(kk, 2.0 * av);                // C_0 = 2 k a
+    const double i2 = 2.0 * inv;
+    Cp = tka;
+    Cc = rmul(tka, cs);                              // C_1
+    K = smul(rmul(kneg_j0, av), H1);                 // -k a J0 H1
+    madd(K, sc_mul(cJ[STRIDE], Cc), H0);      // e_0 = J_1 C_1
+    const T Cn = fmsub_r(tw, Cc, Cp);                // C_2
+    Cp = Cc;
+    Cc = Cn;
+    Vp = -i2 * av;                                   // V_0
+    Vc = i2 * fma(bv, sn, -av * cs);                 // V_1
+  }
+  cplx Hm = H0, H = H1;
+  T s = twoz;
+  double cp = 1.0, cl = cs, sp = 0.0, sl = sn;
+  for (int l = 1; l <= p; ++l) {
+    const int o = l * STRIDE;
+    if (kS || kDsum) {
+      const T tS = rmul(cJ[o], cl);                  // J_l cos(l psi)
+      if (kS) madd(GS, tS, H);
+      if (kDsum) madd(D1, tS, Hm);
+    }
+    if (kDsum) madd(D3, rmul(cL[o], cl), H);
+    if (kD && !kDsum) madd(K, dcoef(cJ[o + STRIDE], Cc, cL[o], Vc), H);
+    if (kG) {
+      madd(GA, rmul(cG[o], cl), H);
+      madd(GB, rmul(cL[o], sl), H);
+    }
+    if (l < p) {
+      const cplx Hn = hrec(s, H, Hm);
+      Hm = H;
+      H = Hn;
+      s = sadd(s, twoz);
+      const double cn = fma(tw, cl, -cp);
+      cp = cl;
+      cl = cn;
+      if (kG) {
+        const double sq = fma(tw, sl, -sp);
+        sp = sl;
+        sl = sq;
+      }
+      if (kD && !kDsum) {
+        const T Cn = fmsub_r(tw, Cc, Cp);
+        Cp = Cc;
+        Cc = Cn;
+        const double Vn = fma(tw, Vc, -Vp);
+        Vp = Vc;
+        Vc = Vn;
+      }
+    }
+  }
+  if (kS) {  // J0 H0 + 2 sum_{l>=1}
+    GS = smul(J0, H0) + 2.0 * GS;
+  }
+  if (kDsum) {
+    // -k a J0 H1 + 2 k a D1 + (2/rho)(b D2 - a D3), D2 = GB
+    const T ka = rmul(kk, av);
+    const double i2 = 2.0 * inv;
+    K = smul(sc_mul(ka, rmul(J0, -1.0)), H1) + smul(rmul(ka, 2.0), D1) +
+        (i2 * bv) * GB - (i2 * av) * D3;
+  }
+}
+
+// D through sums shared with grad S when both are requested:
+//   D = -k a J0 H1 + 2 k a D1 + (2/rho)(b D2 - a D3),
+//   D1 = sum_{l>=1} J_l cos(l psi) H_{l-1},  D2 = sum l J_l sin(l psi) H_l (= grad S's B / 2),
+//   D3 = sum l J_l cos(l psi) H_l,
+// otherwise by the coefficients e_m with the C_m, V_m recurrences.
 template <int OPS, typename T, int NR>
 __global__ void __launch_bounds__(kApplyThreads)
 k_apply_fused(ApplyArgs a) {
   using L = ApplySmem<OPS, T, NR>;
   constexpr bool kS = L::kS, kD = L::kD, kG = L::kG;
-  constexpr int kNops = L::kNops;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* s_x = reinterpret_cast<double*>(smem_raw);
   double* s_y = s_x + kSrcTile;
@@ -124,10 +242,9 @@ k_apply_fused(ApplyArgs a) {
   T* slot = reinterpret_cast<T*>(smem_raw + L::tile_bytes());
   const int p = a.p;
   const int P2 = (p + 2) * kApplyThreads;
-  T* sJ = slot;                              // raw J, later l J_l
-  T* sS = slot + P2;                         // 2 J_l
-  T* sD = sS + (kS ? P2 : 0);                // J_{l+1}
-  T* sG = sD + (kD ? P2 : 0);                // J_{l-1} - J_{l+1}
+  T* sJ = slot;                              // J_l
+  T* sL = slot + P2;                         // l J_l
+  T* sG = sL + ((kD || kG) ? P2 : 0);        // J_{l-1} - J_{l+1}
 
   const int tid = threadIdx.x;
   const int c = blockIdx.x * kApplyThreads + tid;
@@ -146,24 +263,24 @@ k_apply_fused(ApplyArgs a) {
   kw.init(a.kre, a.kim);
   const T kk = kw.kval();
   T* colJ = sJ + tid;
+  T* colL = sL + tid;
+  T* colG = sG + tid;
   besselj_seq<T>(rmul(kk, r), p + 1, colJ, kApplyThreads);
   const T J0 = colJ[0];
   for (int l = 0; l <= p; ++l) {
     const T jl = colJ[l * kApplyThreads];
-    const T jn = colJ[(l + 1) * kApplyThreads];
-    if (kS) sS[l * kApplyThreads + tid] = (l == 0) ? jl : rmul(jl, 2.0);
-    if (kD) {
-      T z0;
-      sc_zero(z0);
-      sD[l * kApplyThreads + tid] = (l < p) ? jn : z0;
-    }
+    if (kD || kG) colL[l * kApplyThreads] = rmul(jl, (double)l);
     if (kG) {
+      const T jn = colJ[(l + 1) * kApplyThreads];
       const T jp = (l == 0) ? jn : colJ[(l - 1) * kApplyThreads];
-      sG[l * kApplyThreads + tid] = (l == 0) ? rmul(jn, -1.0) : sc_sub(jp, jn);
+      colG[l * kApplyThreads] = (l == 0) ? rmul(jn, -1.0) : sc_sub(jp, jn);
     }
   }
-  // l J_l in place (needs the raw J's above first)
-  for (int l = 0; l <= p; ++l) colJ[l * kApplyThreads] = rmul(colJ[l * kApplyThreads], (double)l);
+  {
+    T z0;
+    sc_zero(z0);
+    colJ[(p + 1) * kApplyThreads] = z0;  // e_p has no J_{p+1} term (orders |l| <= p)
+  }
   const T kneg_j0 = rmul(sc_mul(kk, J0), -1.0);  // -k J0 (D)
 
   cplx accS[NR], accD[NR], accA[NR], accB[NR];
@@ -203,84 +320,20 @@ k_apply_fused(ApplyArgs a) {
     __syncthreads();
     if (!active) continue;
 
-    const T* cS = sS + tid;
-    const T* cD = sD + tid;
-    const T* cG = sG + tid;
-    const T* cJ = colJ;  // l J_l
+    const T* cJ = colJ;
+    const T* cL = colL;
+    const T* cG = colG;
 
     for (int j = 0; j < nt; ++j) {
-      // ---- a2: pair geometry and H0, H1 ----
       const double dx = s_x[j] - cx, dy = s_y[j] - cy;
-      const double rho2 = fma(dx, dx, dy * dy);
-      const double inv = rsqrt(rho2);
-      const double rho = rho2 * inv;
-      const double cs = fma(ux, dx, uy * dy) * inv;  // cos psi
-      cplx H0, H1;
-      T twoz;
-      kw.hankel(rho, inv, H0, H1, twoz);
-      const double tw = 2.0 * cs;
-      double sn = 0.0;
-      if (kD || kG) sn = fma(uy, dx, -ux * dy) * inv;  // sin psi
-
-      // ---- order-0 terms and recurrence seeds ----
-      cplx GS, K, GA, GB;
-      T Cp, Cc;
-      double Vp = 0.0, Vc = 0.0;
-      if (kS) GS = smul(cS[0], H0);
-      if (kG) {
-        GA = smul(cG[0], H0);
-        GB = cplx{0.0, 0.0};
-      }
+      double nx = 0.0, ny = 0.0;
       if (kD) {
-        const double nx = s_nx[j], ny = s_ny[j];
-        const double av = fma(nx, dx, ny * dy) * inv;    // n_s . e_rho
-        const double bv = fma(ny, dx, -nx * dy) * inv;   // n_s . e_theta
-        const T tka = rmul(kk, 2.0 * av);                // C_0 = 2 k a
-        const double i2 = 2.0 * inv;
-        Cp = tka;
-        Cc = rmul(tka, cs);                              // C_1
-        K = smul(rmul(kneg_j0, av), H1);                 // -k a J0 H1
-        madd(K, sc_mul(cD[0], Cc), H0);                  // e_0 = J_1 C_1
-        const T Cn = fmsub_r(tw, Cc, Cp);                // C_2
-        Cp = Cc;
-        Cc = Cn;
-        Vp = -i2 * av;                                   // V_0
-        Vc = i2 * fma(bv, sn, -av * cs);                 // V_1
+        nx = s_nx[j];
+        ny = s_ny[j];
       }
-      cplx Hm = H0, H = H1;
-      T s = twoz;
-      double cp = 1.0, cl = cs, sp = 0.0, sl = sn;
-      for (int l = 1; l <= p; ++l) {
-        const int o = l * kApplyThreads;
-        if (kS) madd(GS, rmul(cS[o], cl), H);
-        if (kD) madd(K, dcoef(cD[o], Cc, cJ[o], Vc), H);
-        if (kG) {
-          madd(GA, rmul(cG[o], cl), H);
-          madd(GB, rmul(cJ[o], sl), H);
-        }
-        if (l < p) {
-          const cplx Hn = hrec(s, H, Hm);
-          Hm = H;
-          H = Hn;
-          s = sadd(s, twoz);
-          const double cn = fma(tw, cl, -cp);
-          cp = cl;
-          cl = cn;
-          if (kG) {
-            const double sq = fma(tw, sl, -sp);
-            sp = sl;
-            sl = sq;
-          }
-          if (kD) {
-            const T Cn = fmsub_r(tw, Cc, Cp);
-            Cp = Cc;
-            Cc = Cn;
-            const double Vn = fma(tw, Vc, -Vp);
-            Vp = Vc;
-            Vc = Vn;
-          }
-        }
-      }
+      cplx GS, K, GA, GB;
+      pair_kernels<OPS, T, kApplyThreads>(kw, kk, J0, kneg_j0, cJ, cL, cG, p, dx, dy, nx, ny, ux, uy, GS,
+                                           K, GA, GB);
       // ---- weighted densities ----
       int slotn = 0;
       if (kS) {
@@ -361,6 +414,39 @@ static size_t apply_smem_t(int ops, int p, int nr) {
     default: return 0;
   }
 #undef QBX_SM
+}
+
+// CTAs of the kernel instance that one SM holds at once.
+template <int OPS, typename T>
+static int occupancy_t(int p, int nr) {
+  // (the shared-memory opt-in must be set before the query when above 48 KB)
+  auto occ = [](auto kern, size_t smem) {
+    int n = 0;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, kApplyThreads, smem);
+    return n;
+  };
+  if (nr <= 1) return occ(k_apply_fused<OPS, T, 1>, ApplySmem<OPS, T, 1>::bytes(p));
+  if constexpr (popc3(OPS) > 1) {
+    return occ(k_apply_fused<OPS, T, 4>, ApplySmem<OPS, T, 4>::bytes(p));
+  } else {
+    if (nr <= 4) return occ(k_apply_fused<OPS, T, 4>, ApplySmem<OPS, T, 4>::bytes(p));
+    return occ(k_apply_fused<OPS, T, 8>, ApplySmem<OPS, T, 8>::bytes(p));
+  }
+}
+
+template <typename T>
+static int apply_occupancy_t(int ops, int p, int nr) {
+  switch (ops) {
+    case OPB_S: return occupancy_t<OPB_S, T>(p, nr);
+    case OPB_D: return occupancy_t<OPB_D, T>(p, nr);
+    case OPB_G: return occupancy_t<OPB_G, T>(p, nr);
+    case OPB_S | OPB_D: return occupancy_t<OPB_S | OPB_D, T>(p, nr);
+    case OPB_S | OPB_G: return occupancy_t<OPB_S | OPB_G, T>(p, nr);
+    case OPB_D | OPB_G: return occupancy_t<OPB_D | OPB_G, T>(p, nr);
+    case OPB_S | OPB_D | OPB_G: return occupancy_t<OPB_S | OPB_D | OPB_G, T>(p, nr);
+    default: return 0;
+  }
 }
 
 template <typename T>

@@ -1,0 +1,346 @@
+// qbx_batch.cu -- many curves (each with its own panels, wavenumber and
+// densities) applied in one persistent launch of the group kernel, run as a
+// CUDA graph: [zero the item counter] -> [oversample every curve's
+// densities] -> [group kernel over the longest-first item list] -> [scale,
+// jump terms / two-sided average into every curve's outputs].
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <algorithm>
+#include <numeric>
+#include <vector>
+#include "../../include/qbx.h"
+#include "qbx_device.cuh"
+#include "qbx_internal.h"
+
+using namespace qbx;
+
+struct qbx_batch {
+  int device = 0, n_inst = 0, p = 0, ops = 0, side = 0, limit = 0, nrhs = 0, ncomp = 0, rg = 8;
+  bool ck = false;
+  int n_items = 0, grid = 0, max_src = 0, max_tgt = 0;
+  GroupInst* d_inst = nullptr;
+  GroupItem* d_items = nullptr;
+  int* d_counter = nullptr;
+  int* d_status = nullptr;
+  void* d_wd = nullptr;
+  void* d_part = nullptr;
+  const double* d_interp = nullptr;  // the plan's
+  int q_tgt = 0, q_src = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+int bfail(int code, const char* what) {
+  char buf[320];
+  snprintf(buf, sizeof(buf), "qbx_batch: %s", what);
+  return host_fail(code, buf);
+}
+
+int bcuda(cudaError_t e, const char* what) {
+  char buf[320];
+  snprintf(buf, sizeof(buf), "qbx_batch: %s: %s", what, cudaGetErrorString(e));
+  return host_fail(QBX_ECUDA, buf);
+}
+
+// a1 for every curve: blockIdx.y = curve, wd[s][r] = w_s sum_i P[j][i] dens[m q_tgt + i][r]
+__global__ void k_batch_upsample(const GroupInst* inst, int q_tgt, int q_src, int nrhs, const double* P) {
+  const GroupInst& in = inst[blockIdx.y];
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= in.n_src * nrhs) return;
+  const int s = idx / nrhs, r = idx - s * nrhs;
+  const int m = s / q_src, j = s - m * q_src;
+  const double* row = P + (size_t)j * q_tgt;
+  const cplx* d = reinterpret_cast<const cplx*>(in.dens) + (size_t)m * q_tgt * nrhs + r;
+  double re = 0.0, im = 0.0;
+  for (int i = 0; i < q_tgt; ++i) {
+    const double c = row[i];
+    const cplx v = d[(size_t)i * nrhs];
+    re = fma(c, v.re, re);
+    im = fma(c, v.im, im);
+  }
+  const double w = in.sw[s];
+  reinterpret_cast<cplx*>(const_cast<void*>(in.wd))[idx] = cplx{w * re, w * im};
+}
+
+// a7 for every curve: blockIdx.y = curve; component q of the partial rows
+// belongs to operator op_of[q] (S, D, grad S x, grad S y in that order).
+__global__ void k_batch_finish(const GroupInst* inst, int ops, int ncomp, int limit, int nrhs, int* status) {
+  const GroupInst& in = inst[blockIdx.y];
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= in.n_tgt * ncomp * nrhs) return;
+  const int t = idx / (ncomp * nrhs);
+  const int rem = idx - t * ncomp * nrhs;
+  const int q = rem / nrhs, r = rem - q * nrhs;
+  // operator and component within it
+  int op = 0, comp = 0, qq = q;
+  for (int o = 0; o < 3; ++o) {
+    if (!(ops >> o & 1)) continue;
+    const int n = (o == QBX_OP_GRAD_S) ? 2 : 1;
+    if (qq < n) {
+      op = o;
+      comp = qq;
+      break;
+    }
+    qq -= n;
+  }
+  const cplx* part = reinterpret_cast<const cplx*>(in.part);
+  const int nsides = in.side == QBX_SIDE_TWO ? 2 : 1;
+  cplx res{0.0, 0.0};
+  for (int sd = 0; sd < nsides; ++sd) {
+    const int c = t + sd * in.n_tgt;
+    cplx u{0.0, 0.0};
+    for (int k = 0; k < in.nsplit; ++k) u = u + part[(((size_t)k * in.n_ctr + c) * ncomp + q) * nrhs + r];
+    u = mul_i(0.25 * u);
+    if (in.side != QBX_SIDE_TWO && limit == QBX_LIMIT_PV) {
+      const double sg = in.side == QBX_SIDE_EXT ? 1.0 : -1.0;
+      const cplx dv = reinterpret_cast<const cplx*>(in.dens)[(size_t)t * nrhs + r];
+      if (op == QBX_OP_D) u = u - (0.5 * sg) * dv;
+      else if (op == QBX_OP_GRAD_S) u = u + (0.5 * sg * (comp == 0 ? in.tnx[t] : in.tny[t])) * dv;
+    }
+    res = res + u;
+  }
+  if (nsides == 2) res = 0.5 * res;
+  const int nc_op = op == QBX_OP_GRAD_S ? 2 : 1;
+  cplx* out = reinterpret_cast<cplx*>(in.out[op]);
+  out[((size_t)t * nc_op + comp) * nrhs + r] = res;
+  if (!(isfinite(res.re) && isfinite(res.im))) atomicOr(status, 1);
+}
+
+void destroy(qbx_batch* b) {
+  if (!b) return;
+  cudaSetDevice(b->device);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  cudaFree(b->d_inst);
+  cudaFree(b->d_items);
+  cudaFree(b->d_counter);
+  cudaFree(b->d_status);
+  cudaFree(b->d_wd);
+  cudaFree(b->d_part);
+  delete b;
+}
+
+}  // namespace
+
+extern "C" {
+
+int qbx_batch_create(qbx_batch** batch, qbx_plan* plan, int n_inst, const qbx_geom* geoms, const qbx_c64* k,
+                     int p, int ops, int side, int limit, int nrhs, const qbx_c64* const* dens,
+                     qbx_c64* const* out) {
+  if (!batch) return bfail(QBX_EINVAL, "batch out-pointer is NULL");
+  *batch = nullptr;
+  if (!plan) return bfail(QBX_EINVAL, "plan is NULL");
+  if (n_inst < 1 || !geoms || !k || !dens || !out) return bfail(QBX_EINVAL, "empty batch or NULL table");
+  if (ops != QBX_OPS_S && ops != QBX_OPS_D && ops != (QBX_OPS_S | QBX_OPS_D) &&
+      ops != (QBX_OPS_S | QBX_OPS_D | QBX_OPS_GRAD_S))
+    return bfail(QBX_EINVAL, "operator set must be S, D, S+D or S+D+grad S");
+  if (side != QBX_SIDE_INT && side != QBX_SIDE_EXT && side != QBX_SIDE_TWO) return bfail(QBX_EINVAL, "bad side");
+  if (limit != QBX_LIMIT_ONE_SIDED && limit != QBX_LIMIT_PV) return bfail(QBX_EINVAL, "bad limit");
+  if (p < 0 || p > QBX_MAX_P) return bfail(QBX_EINVAL, "p outside [0, QBX_MAX_P]");
+  if (nrhs < 1) return bfail(QBX_EINVAL, "nrhs < 1");
+  qbx_batch* b = new qbx_batch();
+  b->n_inst = n_inst;
+  b->p = p;
+  b->ops = ops;
+  b->side = side;
+  b->limit = limit;
+  b->nrhs = nrhs;
+  b->ncomp = (ops & 1) + ((ops >> 1) & 1) + 2 * ((ops >> 2) & 1);
+  b->rg = nrhs > 8 ? 8 : 2;
+  // the plan's device, grid pair and interpolation matrix
+  int num_sms = 0;
+  host_plan_info(plan, &b->device, &b->q_tgt, &b->q_src, &b->d_interp);
+  cudaError_t e = cudaSetDevice(b->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, b->device);
+  if (e != cudaSuccess) {
+    destroy(b);
+    return bcuda(e, "device");
+  }
+  // ---- instances ----
+  std::vector<GroupInst> inst(n_inst);
+  size_t wd_total = 0, part_total = 0;
+  std::vector<size_t> wd_off(n_inst), part_off(n_inst);
+  for (int i = 0; i < n_inst; ++i) {
+    const qbx_geom& g = geoms[i];
+    if (g.q_tgt != b->q_tgt || g.q_src != b->q_src || g.M < 1 || g.n_tgt != g.M * g.q_tgt ||
+        g.n_src != g.M * g.q_src || !g.src_x || !g.ctr_x || !g.tgt_x || !g.src_w) {
+      destroy(b);
+      return bfail(QBX_EINVAL, "geometry of an instance inconsistent with the plan");
+    }
+    if (!isfinite(k[i].re) || !isfinite(k[i].im) || k[i].im < 0.0 || (k[i].im == 0.0 && !(k[i].re > 0.0))) {
+      destroy(b);
+      return bfail(QBX_EINVAL, "k of an instance must be finite with Im k >= 0 (real k > 0)");
+    }
+    if (!dens[i]) {
+      destroy(b);
+      return bfail(QBX_EINVAL, "NULL density");
+    }
+    for (int o = 0; o < 3; ++o)
+      if ((ops >> o & 1) && !out[3 * i + o]) {
+        destroy(b);
+        return bfail(QBX_EINVAL, "NULL output of a requested operator");
+      }
+    if (k[i].im != 0.0) b->ck = true;
+    GroupInst& in = inst[i];
+    in.kre = k[i].re;
+    in.kim = k[i].im;
+    in.n_src = g.n_src;
+    in.n_tgt = g.n_tgt;
+    in.M = g.M;
+    in.side = side;
+    in.n_ctr = side == QBX_SIDE_TWO ? 2 * g.n_tgt : g.n_tgt;
+    const int c0 = side == QBX_SIDE_EXT ? g.n_tgt : 0;
+    in.nsplit = 1;
+    in.sx = g.src_x;
+    in.sy = g.src_y;
+    in.snx = g.src_nx;
+    in.sny = g.src_ny;
+    in.sw = g.src_w;
+    in.cx = g.ctr_x + c0;
+    in.cy = g.ctr_y + c0;
+    in.tx = g.tgt_x;
+    in.ty = g.tgt_y;
+    in.tnx = g.tgt_nx;
+    in.tny = g.tgt_ny;
+    in.dens = dens[i];
+    for (int o = 0; o < 3; ++o) in.out[o] = out[3 * i + o];
+    wd_off[i] = wd_total;
+    wd_total += host_align256((size_t)g.n_src * nrhs * 16);
+    part_off[i] = part_total;
+    part_total += host_align256((size_t)in.n_ctr * b->ncomp * nrhs * 16);
+    b->max_src = std::max(b->max_src, g.n_src);
+    b->max_tgt = std::max(b->max_tgt, g.n_tgt);
+  }
+  // ---- items: 32 centres x all sources, longest first ----
+  std::vector<GroupItem> items;
+  for (int i = 0; i < n_inst; ++i)
+    for (int c = 0; c < inst[i].n_ctr; c += kGrpCentres) items.push_back(GroupItem{i, c, 0, 0, inst[i].n_src});
+  std::stable_sort(items.begin(), items.end(), [&](const GroupItem& x, const GroupItem& y) {
+    const long cx = (long)std::min(kGrpCentres, inst[x.inst].n_ctr - x.ctr0) * inst[x.inst].n_src;
+    const long cy = (long)std::min(kGrpCentres, inst[y.inst].n_ctr - y.ctr0) * inst[y.inst].n_src;
+    return cx > cy;
+  });
+  b->n_items = (int)items.size();
+  // ---- device memory ----
+  e = cudaMalloc(&b->d_wd, wd_total);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_part, part_total);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_inst, sizeof(GroupInst) * n_inst);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_items, sizeof(GroupItem) * items.size());
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_counter, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_status, sizeof(int));
+  if (e != cudaSuccess) {
+    destroy(b);
+    return bcuda(e, "allocation");
+  }
+  for (int i = 0; i < n_inst; ++i) {
+    inst[i].wd = static_cast<char*>(b->d_wd) + wd_off[i];
+    inst[i].part = static_cast<char*>(b->d_part) + part_off[i];
+  }
+  e = cudaMemcpy(b->d_inst, inst.data(), sizeof(GroupInst) * n_inst, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(b->d_items, items.data(), sizeof(GroupItem) * items.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(b->d_status, 0, sizeof(int));
+  if (e != cudaSuccess) {
+    destroy(b);
+    return bcuda(e, "upload");
+  }
+  // ---- persistent grid: every resident CTA slot ----
+  const int occ = b->ck ? group_occupancy_cplx(ops, p, b->rg) : group_occupancy_real(ops, p, b->rg);
+  const size_t gsmem = b->ck ? group_smem_cplx(ops, p, b->rg) : group_smem_real(ops, p, b->rg);
+  if (occ < 1 || gsmem > 220 * 1024) {
+    destroy(b);
+    return bfail(QBX_EINVAL, "p too large for the group kernel");
+  }
+  b->grid = std::min(b->n_items, num_sms * occ);
+  // ---- the graph ----
+  GroupArgs ga{};
+  ga.ops = ops;
+  ga.p = p;
+  ga.nrhs = nrhs;
+  ga.inst = b->d_inst;
+  ga.n_items = b->n_items;
+  ga.items = b->d_items;
+  ga.counter = b->d_counter;
+  const void* gk = b->ck ? group_ptr_cplx(ops, b->rg) : group_ptr_real(ops, b->rg);
+  e = cudaFuncSetAttribute(gk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsmem);
+  if (e == cudaSuccess) e = cudaGraphCreate(&b->graph, 0);
+  cudaGraphNode_t n_memset, n_up, n_group, n_fin;
+  if (e == cudaSuccess) {
+    cudaMemsetParams mp{};
+    mp.dst = b->d_counter;
+    mp.value = 0;
+    mp.elementSize = sizeof(int);
+    mp.width = 1;
+    mp.height = 1;
+    e = cudaGraphAddMemsetNode(&n_memset, b->graph, nullptr, 0, &mp);
+  }
+  int q_tgt = b->q_tgt, q_src = b->q_src, nr = nrhs, ncomp = b->ncomp, lim = limit, opsv = ops;
+  const GroupInst* di = b->d_inst;
+  const double* P = b->d_interp;
+  int* st = b->d_status;
+  if (e == cudaSuccess) {
+    void* args[] = {(void*)&di, &q_tgt, &q_src, &nr, (void*)&P};
+    cudaKernelNodeParams kp{};
+    kp.func = (void*)k_batch_upsample;
+    kp.gridDim = dim3((b->max_src * nrhs + 255) / 256, n_inst);
+    kp.blockDim = dim3(256);
+    kp.kernelParams = args;
+    e = cudaGraphAddKernelNode(&n_up, b->graph, &n_memset, 1, &kp);
+  }
+  if (e == cudaSuccess) {
+    void* args[] = {&ga};
+    cudaKernelNodeParams kp{};
+    kp.func = const_cast<void*>(gk);
+    kp.gridDim = dim3(b->grid);
+    kp.blockDim = dim3(kGrpCentres * kGrpWarps);
+    kp.sharedMemBytes = (unsigned)gsmem;
+    kp.kernelParams = args;
+    e = cudaGraphAddKernelNode(&n_group, b->graph, &n_up, 1, &kp);
+  }
+  if (e == cudaSuccess) {
+    void* args[] = {(void*)&di, &opsv, &ncomp, &lim, &nr, &st};
+    cudaKernelNodeParams kp{};
+    kp.func = (void*)k_batch_finish;
+    kp.gridDim = dim3((b->max_tgt * ncomp * nrhs + 255) / 256, n_inst);
+    kp.blockDim = dim3(256);
+    kp.kernelParams = args;
+    e = cudaGraphAddKernelNode(&n_fin, b->graph, &n_group, 1, &kp);
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+  if (e != cudaSuccess) {
+    destroy(b);
+    return bcuda(e, "graph construction");
+  }
+  *batch = b;
+  return QBX_OK;
+}
+
+int qbx_batch_apply(qbx_batch* b, void* stream) {
+  if (!b) return bfail(QBX_EINVAL, "batch is NULL");
+  cudaError_t e = cudaSetDevice(b->device);
+  if (e == cudaSuccess) e = cudaGraphLaunch(b->exec, (cudaStream_t)stream);
+  if (e != cudaSuccess) return bcuda(e, "graph launch");
+  return QBX_OK;
+}
+
+int qbx_batch_status(qbx_batch* b, void* stream) {
+  if (!b) return bfail(QBX_EINVAL, "batch is NULL");
+  int h = 0;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaMemcpyAsync(&h, b->d_status, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_status, 0, sizeof(int), st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return bcuda(e, "status");
+  if (h) return bfail(QBX_ENONFINITE, "a kernel produced a non-finite value");
+  return QBX_OK;
+}
+
+int qbx_batch_destroy(qbx_batch* b) {
+  destroy(b);
+  return QBX_OK;
+}
+
+}  // extern "C"

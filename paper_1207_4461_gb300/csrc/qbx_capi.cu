@@ -176,6 +176,20 @@ void host_interp_matrix(int qt, int qs, std::vector<double>& Mx) { interp_matrix
 
 int host_fail(int code, const char* msg) { return fail(code, "%s", msg); }
 
+void host_plan_workspace(const qbx_plan* plan, void** ws, size_t* bytes, int* num_sms, int** status) {
+  *ws = plan->ws;
+  *bytes = plan->ws_bytes;
+  *num_sms = plan->num_sms;
+  *status = plan->d_status;
+}
+
+void host_plan_info(const qbx_plan* plan, int* device, int* q_tgt, int* q_src, const double** interp) {
+  *device = plan->device;
+  *q_tgt = plan->q_tgt;
+  *q_src = plan->q_src;
+  *interp = plan->d_interp;
+}
+
 size_t host_align256(size_t b) { return align256(b); }
 
 // Number of source splits: fill about two waves of 4 CTAs per SM, bounded by
@@ -193,11 +207,29 @@ int host_choose_split(int num_sms, int n_units, int n_src, size_t bytes_per_spli
   return ns;
 }
 
-// sources per split, rounded up to a multiple of the tile
-int host_split_len(int n_src, int ns) {
-  int per = (n_src + ns - 1) / ns;
-  return ((per + kSrcTile - 1) / kSrcTile) * kSrcTile;
+// Source splits for the fused apply: at least two full waves of the kernel's
+// resident CTAs (occ per SM), then as many splits as fill the last wave, so
+// that every SM gets the same number of equal-sized items; at least 64
+// sources per split, at most kMaxSplit, and within the workspace.
+int host_choose_split_waves(int num_sms, int occ, int n_units, int n_src, size_t bytes_per_split,
+                            size_t avail) {
+  if (occ < 1) return host_choose_split(num_sms, n_units, n_src, bytes_per_split, avail);
+  const long slots = (long)num_sms * occ;
+  long ns = (2 * slots + n_units - 1) / std::max(n_units, 1);
+  const long waves = (n_units * ns + slots - 1) / slots;
+  ns = std::max(ns, waves * slots / std::max(n_units, 1));
+  ns = std::min<long>(ns, kMaxSplit);
+  ns = std::min<long>(ns, std::max(1, n_src / 64));
+  ns = std::max<long>(ns, 1);
+  if (bytes_per_split > 0) {
+    size_t fit = avail / bytes_per_split;
+    if ((size_t)ns > fit) ns = (long)fit;
+  }
+  return (int)ns;
 }
+
+// sources per split (equal shares; the last tile of a split may be partial)
+int host_split_len(int n_src, int ns) { return (n_src + ns - 1) / ns; }
 
 }  // namespace qbx
 
@@ -483,12 +515,22 @@ static int apply_impl(qbx_plan* p, const qbx_geom* g, int ops, int side, int lim
   if (p->ws_bytes < wd_bytes + 512) return fail(QBX_ENOMEM, "workspace too small (%zu < %zu)", p->ws_bytes, wd_bytes + 512);
   const size_t avail = p->ws_bytes - wd_bytes - 512;
   const size_t per_split = (size_t)nc * ncomp * nrhs * 16;
-  const int units = (nc + kApplyThreads - 1) / kApplyThreads;
-  const int ns = choose_split(p, units, g->n_src, per_split, avail);
-  if (ns < 1) return fail(QBX_ENOMEM, "workspace too small for the apply partial sums");
+  // many right-hand sides of one density: the group kernel (kernel values
+  // formed once per pair for all rhs); otherwise the fused kernel
+  const bool ck = k.im != 0.0;
+  const bool group = nrhs >= 16 && nd == 1 && (ops == 1 || ops == 2 || ops == 3 || ops == 7);
+  const int rg = 8;
+  const int units = group ? (nc + kGrpCentres - 1) / kGrpCentres : (nc + kApplyThreads - 1) / kApplyThreads;
   const int chunk = apply_chunk(ops);
-  if (apply_smem_bytes(ops, k.im != 0.0, pp, chunk) > 220 * 1024) return fail(QBX_EINVAL, "p = %d too large", pp);
   CK(cudaSetDevice(p->device), "cudaSetDevice");
+  int occ;
+  if (group) occ = ck ? group_occupancy_cplx(ops, pp, rg) : group_occupancy_real(ops, pp, rg);
+  else occ = ck ? apply_occupancy_cplx(ops, pp, std::min(chunk, nrhs)) : apply_occupancy_real(ops, pp, std::min(chunk, nrhs));
+  const int ns = host_choose_split_waves(p->num_sms, occ, units, g->n_src, per_split, avail);
+  if (ns < 1) return fail(QBX_ENOMEM, "workspace too small for the apply partial sums");
+  if (group ? (ck ? group_smem_cplx(ops, pp, rg) : group_smem_real(ops, pp, rg)) > 220 * 1024
+            : apply_smem_bytes(ops, ck, pp, chunk) > 220 * 1024)
+    return fail(QBX_EINVAL, "p = %d too large", pp);
   cudaStream_t st = (cudaStream_t)stream;
   char* base = (char*)align256((size_t)p->ws);
   void* part = base + wd_bytes;
@@ -515,10 +557,43 @@ static int apply_impl(qbx_plan* p, const qbx_geom* g, int ops, int side, int lim
   a.nsplit = ns;
   a.src_per_split = split_len(g->n_src, ns);
   a.part = part;
-  for (int r0 = 0; r0 < nrhs; r0 += chunk) {
-    a.rhs0 = r0;
-    a.nr = std::min(chunk, nrhs - r0);
-    CK(launch_apply_fused(a, st), "apply kernel");
+  if (group) {
+    GroupArgs ga{};
+    ga.ops = ops;
+    ga.p = pp;
+    ga.nrhs = nrhs;
+    GroupInst& in = ga.inst0;
+    in.kre = k.re;
+    in.kim = k.im;
+    in.n_src = g->n_src;
+    in.n_tgt = g->n_tgt;
+    in.n_ctr = nc;
+    in.side = side;
+    in.nsplit = ns;
+    in.M = g->M;
+    in.sx = g->src_x;
+    in.sy = g->src_y;
+    in.snx = g->src_nx;
+    in.sny = g->src_ny;
+    in.sw = g->src_w;
+    in.cx = g->ctr_x + c0;
+    in.cy = g->ctr_y + c0;
+    in.tx = g->tgt_x;
+    in.ty = g->tgt_y;
+    in.tnx = g->tgt_nx;
+    in.tny = g->tgt_ny;
+    in.wd = base;
+    in.part = part;
+    ga.st_units = units;
+    ga.st_nsplit = ns;
+    ga.st_split_len = split_len(g->n_src, ns);
+    CK(ck ? launch_group_cplx(ga, rg, units * ns, st) : launch_group_real(ga, rg, units * ns, st), "group kernel");
+  } else {
+    for (int r0 = 0; r0 < nrhs; r0 += chunk) {
+      a.rhs0 = r0;
+      a.nr = std::min(chunk, nrhs - r0);
+      CK(launch_apply_fused(a, st), "apply kernel");
+    }
   }
   // a7: reduce, i/4, jumps / two-sided average, per operator
   for (int o = 0; o < 3; ++o) {

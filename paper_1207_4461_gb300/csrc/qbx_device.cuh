@@ -5,9 +5,11 @@
 // (special_tables.h, produced by gen_special_tables.py from 34-digit mpmath
 // values):
 //   z <  2 : ascending series in (z/2)^2 (DLMF 10.2.2, 10.8.1) with log(z/2)
-//   z >= 2 : H_n = sqrt(2/(pi z)) e^{i(z - n pi/2 - pi/4)} (P_n(1/z) + i Q_n(1/z))
-//            (DLMF 10.17.3), P_n, Q_n by degree-6 polynomials on 32 intervals,
-//            e^{i(z - pi/4)} by table + Taylor after Cody-Waite reduction.
+//   z >= 2 : H_n = e^{i(z - pi/4)} B_n(s), s = z^{-1/2}, where
+//            B_n = sqrt(2/pi) s e^{-i n pi/2} (P_n + i Q_n) (DLMF 10.17.3) is a
+//            degree-5 polynomial on each of 91 intervals of s, and
+//            e^{i(z - pi/4)} comes from a 1024-entry table + Taylor after
+//            Cody-Waite reduction.
 // Complex argument (Im z > 0): series for |z| <= 6, Miller's backward
 // recurrence with the Neumann series for Y0, Y1 for 6 < |z| <= 20 (DLMF
 // 10.23.? / A&S 9.1.88-89), Hankel's asymptotic expansion (DLMF 10.17.5) above.
@@ -77,49 +79,61 @@ QBX_HD cplx to_c(cplx a) { return a; }
 // integer held in the low mantissa bits.
 #define QBX_ROUND_MAGIC 6755399441055744.0
 
-// e^{i(z - pi/4)} for real z >= 0, |z| < 2e5.
+// e^{i(z - pi/4)} for real z >= 0 (full accuracy for z < 5e4): Cody-Waite
+// reduction by 2 pi/1024, a table of e^{i(2 pi j/1024 - pi/4)} and Taylor
+// polynomials on |r| <= pi/1024, where cos r = 1 - t/2 + t^2/24 and
+// sin r = r (1 - t/6 + t^2/120), t = r^2, are exact to below 1e-17.
 __device__ __forceinline__ cplx expi_shift(double z) {
-  double nd = fma(z, QBX_HK_RED_SCALE, QBX_ROUND_MAGIC);
-  double n = nd - QBX_ROUND_MAGIC;
-  int idx = (int)(__double2loint(nd) & (QBX_HK_NT - 1));
+  const double nd = fma(z, QBX_HK_RED_SCALE, QBX_ROUND_MAGIC);
+  const double n = nd - QBX_ROUND_MAGIC;
+  const int idx = (int)(__double2loint(nd) & (QBX_HK_NT - 1));
   double r = fma(-n, QBX_HK_RED_HI, z);
   r = fma(-n, QBX_HK_RED_LO, r);
-  double t = r * r;
-  // Taylor polynomials of cos r and sin r, |r| <= pi/256
-  double c = fma(fma(fma(-1.0 / 720.0, t, 1.0 / 24.0), t, -0.5), t, 1.0);
-  double sp = fma(fma(-1.0 / 5040.0, t, 1.0 / 120.0), t, -1.0 / 6.0);
-  double s = fma(r * t, sp, r);
-  double tc = __ldg(&qbx_hk_phase[idx][0]);
-  double ts = __ldg(&qbx_hk_phase[idx][1]);
-  return cplx{tc * c - ts * s, tc * s + ts * c};
+  const double t = r * r;
+  const double c = fma(fma(1.0 / 24.0, t, -0.5), t, 1.0);
+  const double s = fma(r * t, fma(1.0 / 120.0, t, -1.0 / 6.0), r);
+  const double tc = __ldg(&qbx_hk_phase[idx][0]);
+  const double ts = __ldg(&qbx_hk_phase[idx][1]);
+  return cplx{fma(tc, c, -ts * s), fma(tc, s, ts * c)};
 }
 
-// H0(z), H1(z) for real z > 0.  invz = 1/z must be supplied.
-__device__ __forceinline__ void hankel01_real(double z, double invz, cplx& h0, cplx& h1) {
+// From rho^2 > 0: y = rho^{-1/2}, inv = 1/rho and rho.  An FP32 seed
+// (about 23 bits) is refined by one step of the third-order iteration for
+// x^{-1/4}: y <- y (1 + e/4 + 5 e^2/32), e = 1 - x y^4 (the next term,
+// 15 e^3/128, is below 1e-19).
+__device__ __forceinline__ void rho_powers(double rho2, double& y, double& inv, double& rho) {
+  const float r2f = __double2float_rn(rho2);
+  const double y0 = (double)sqrtf(rsqrtf(r2f));
+  const double y2 = y0 * y0;
+  const double e = fma(-rho2, y2 * y2, 1.0);
+  y = fma(y0 * e, fma(5.0 / 32.0, e, 0.25), y0);
+  inv = y * y;
+  rho = rho2 * inv;
+}
+
+// H0(z), H1(z) for real z > 0, given invz = 1/z and s = z^{-1/2}.
+__device__ __forceinline__ void hankel01_real(double z, double invz, double s, cplx& h0, cplx& h1) {
   if (z >= QBX_HK_ZSPLIT) {
-    double y = invz + 1.0;
-    int i = (int)((__double2hiint(y) >> 14) & 63);  // floor(w * 64) for w in [0, 1)
-    i = i < QBX_HK_NI ? i : QBX_HK_NI - 1;
-    double u = y - __ldg(&qbx_hk_mid1[i]);
+    // B_n(s) = H_n(z) e^{-i(z - pi/4)}: piecewise polynomials in s
+    const double y = s + 1.0;
+    int i = (int)((__double2hiint(y) >> (20 - QBX_HK_LOG2_PER_UNIT)) & ((1 << QBX_HK_LOG2_PER_UNIT) - 1));
+    i = i < QBX_HK_NI ? i : QBX_HK_NI - 1;   // floor(s * 2^LOG2_PER_UNIT)
+    const double u = y - __ldg(&qbx_hk_mid1[i]);
     const double* A = &qbx_hk_amp[i][0][0];
-    double p0 = __ldg(&A[0 * (QBX_HK_DEG + 1) + QBX_HK_DEG]);
-    double q0 = __ldg(&A[1 * (QBX_HK_DEG + 1) + QBX_HK_DEG]);
-    double p1 = __ldg(&A[2 * (QBX_HK_DEG + 1) + QBX_HK_DEG]);
-    double q1 = __ldg(&A[3 * (QBX_HK_DEG + 1) + QBX_HK_DEG]);
+    double b0r = __ldg(&A[0 * (QBX_HK_DEG + 1) + QBX_HK_DEG]);
+    double b0i = __ldg(&A[1 * (QBX_HK_DEG + 1) + QBX_HK_DEG]);
+    double b1r = __ldg(&A[2 * (QBX_HK_DEG + 1) + QBX_HK_DEG]);
+    double b1i = __ldg(&A[3 * (QBX_HK_DEG + 1) + QBX_HK_DEG]);
 #pragma unroll
     for (int d = QBX_HK_DEG - 1; d >= 0; --d) {
-      p0 = fma(p0, u, __ldg(&A[0 * (QBX_HK_DEG + 1) + d]));
-      q0 = fma(q0, u, __ldg(&A[1 * (QBX_HK_DEG + 1) + d]));
-      p1 = fma(p1, u, __ldg(&A[2 * (QBX_HK_DEG + 1) + d]));
-      q1 = fma(q1, u, __ldg(&A[3 * (QBX_HK_DEG + 1) + d]));
+      b0r = fma(b0r, u, __ldg(&A[0 * (QBX_HK_DEG + 1) + d]));
+      b0i = fma(b0i, u, __ldg(&A[1 * (QBX_HK_DEG + 1) + d]));
+      b1r = fma(b1r, u, __ldg(&A[2 * (QBX_HK_DEG + 1) + d]));
+      b1i = fma(b1i, u, __ldg(&A[3 * (QBX_HK_DEG + 1) + d]));
     }
-    // sqrt(2/(pi z)) e^{i(z - pi/4)}
-    double a = 0.79788456080286535588 * sqrt(invz);  // sqrt(2/pi)
-    cplx e = expi_shift(z);
-    e.re *= a;
-    e.im *= a;
-    h0 = e * cplx{p0, q0};
-    h1 = e * cplx{q1, -p1};  // e^{-i pi/2} (P1 + i Q1)
+    const cplx e = expi_shift(z);
+    h0 = e * cplx{b0r, b0i};
+    h1 = e * cplx{b1r, b1i};
   } else {
     double t = 0.25 * z * z;
     double sj0 = qbx_hk_ser[0][QBX_HK_NSER - 1], sj1 = qbx_hk_ser[1][QBX_HK_NSER - 1];

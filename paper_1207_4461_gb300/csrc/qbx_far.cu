@@ -42,11 +42,11 @@ k_far(FarArgs a) {
     for (int j = 0; j < nt; ++j) {
       const double rx = x - s_x[j], ry = y - s_y[j];
       const double d2 = fma(rx, rx, ry * ry);
-      const double inv = rsqrt(d2);
-      const double d = d2 * inv;
+      double inv, d, yq;
+      kw.geom(d2, inv, d, yq);
       cplx H0, H1;
       T twoz;
-      kw.hankel(d, inv, H0, H1, twoz);
+      kw.hankel(d, inv, yq, H0, H1, twoz);
       if (OP == QBX_OP_S) {
 #pragma unroll
         for (int r2 = 0; r2 < NR; ++r2) acc[r2] = acc[r2] + s_wd[j * NR + r2] * H0;

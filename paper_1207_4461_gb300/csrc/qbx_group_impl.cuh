@@ -1,0 +1,278 @@
+// qbx_group_impl.cuh -- the QBX apply for many right-hand sides and for
+// batches of curves (the "group" kernel).  Same per-pair mathematics as
+// k_apply_fused (pair_kernels), different work decomposition:
+//
+// A CTA of 4 warps owns 32 centres of one curve (one per lane) and works
+// through a range of its sources in tiles of 32.  Phase 1: warp w forms the
+// kernel values of its 8 sources of the tile for the 32 centres (H0, H1 and
+// the order recurrences once per pair) and stores them in shared memory.
+// Phase 2: warp g multiplies them into its own group of RG right-hand sides.
+// Kernel generation is therefore paid once per pair however many densities
+// there are, and each thread keeps only RG accumulators per component.
+//
+// Items (32 centres x a source range) come either from blockIdx (one curve,
+// static split of the sources) or from a longest-first item list through an
+// atomic counter (a batch: persistent CTAs, no waits between CTAs).
+#pragma once
+#include "qbx_apply_impl.cuh"
+
+namespace qbx {
+
+template <int OPS, typename T, int RG>
+struct GroupSmem {
+  static constexpr int kNc = ops_ncomp(OPS);   // raw components: S 1, D 1, grad S 2
+  static constexpr bool kD = OPS & OPB_D, kG = OPS & OPB_G;
+  static __host__ __device__ int nslots() { return 1 + ((kD || kG) ? 1 : 0) + (kG ? 1 : 0); }
+  static __host__ __device__ size_t bytes(int p) {
+    return 4 * kGrpTile * 8 +                                  // x, y, nx, ny
+           (size_t)kGrpTile * kGrpWarps * RG * 16 +             // densities [tile][4 RG]
+           (size_t)kNc * kGrpTile * kGrpCentres * 16 +          // kernel values [comp][tile][centre]
+           (size_t)nslots() * (p + 2) * kGrpCentres * sizeof(T) +  // coefficient columns
+           16;                                                  // item index
+  }
+};
+
+template <int OPS, typename T, int RG>
+__global__ void __launch_bounds__(kGrpCentres * kGrpWarps)
+k_apply_group(GroupArgs a) {
+  using L = GroupSmem<OPS, T, RG>;
+  constexpr bool kS = OPS & OPB_S, kD = OPS & OPB_D, kG = OPS & OPB_G;
+  constexpr int kNc = L::kNc;
+  constexpr int kRP = kGrpWarps * RG;   // rhs per pass
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* s_x = reinterpret_cast<double*>(smem_raw);
+  double* s_y = s_x + kGrpTile;
+  double* s_nx = s_y + kGrpTile;
+  double* s_ny = s_nx + kGrpTile;
+  cplx* s_wd = reinterpret_cast<cplx*>(s_ny + kGrpTile);      // [tile][kRP]
+  cplx* s_kv = s_wd + kGrpTile * kRP;                          // [comp][tile][centre]
+  T* slot = reinterpret_cast<T*>(s_kv + kNc * kGrpTile * kGrpCentres);
+  const int p = a.p;
+  const int P2 = (p + 2) * kGrpCentres;
+  T* sJ = slot;
+  T* sL = slot + P2;
+  T* sG = sL + ((kD || kG) ? P2 : 0);
+  int* s_item = reinterpret_cast<int*>(slot + L::nslots() * P2);
+
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const bool dynamic = a.items != nullptr;
+  const int n_items = dynamic ? a.n_items : a.st_units * a.st_nsplit;
+
+  for (int it = dynamic ? -1 : (int)blockIdx.x;;) {
+    // ---- next item ----
+    if (dynamic) {
+      __syncthreads();
+      if (threadIdx.x == 0) s_item[0] = atomicAdd(a.counter, 1);
+      __syncthreads();
+      it = s_item[0];
+    }
+    if (it >= n_items) break;
+    GroupItem item;
+    if (dynamic) {
+      item = a.items[it];
+    } else {
+      item.inst = 0;
+      item.ctr0 = (it / a.st_nsplit) * kGrpCentres;
+      item.split = it % a.st_nsplit;
+      item.src0 = item.split * a.st_split_len;
+      item.src1 = min(a.inst0.n_src, item.src0 + a.st_split_len);
+    }
+    const GroupInst& in = dynamic ? a.inst[item.inst] : a.inst0;
+
+    // ---- per-centre set-up (every warp keeps its lane's centre geometry) ----
+    const int c = item.ctr0 + lane;
+    const bool active = c < in.n_ctr;
+    const int cc = active ? c : in.n_ctr - 1;
+    const double cx = in.cx[cc], cy = in.cy[cc];
+    const int t = cc % in.n_tgt;
+    double ux = in.tx[t] - cx, uy = in.ty[t] - cy;
+    const double r = hypot(ux, uy);
+    const double ir = 1.0 / r;
+    ux *= ir;
+    uy *= ir;
+    KW<T> kw;
+    kw.init(in.kre, in.kim);
+    const T kk = kw.kval();
+    T* colJ = sJ + lane;
+    T* colL = sL + lane;
+    T* colG = sG + lane;
+    __syncthreads();   // previous item's coefficient columns are no longer read
+    if (warp == 0) {
+      besselj_seq<T>(rmul(kk, r), p + 1, colJ, kGrpCentres);
+      for (int l = 0; l <= p; ++l) {
+        const T jl = colJ[l * kGrpCentres];
+        if (kD || kG) colL[l * kGrpCentres] = rmul(jl, (double)l);
+        if (kG) {
+          const T jn = colJ[(l + 1) * kGrpCentres];
+          const T jp = (l == 0) ? jn : colJ[(l - 1) * kGrpCentres];
+          colG[l * kGrpCentres] = (l == 0) ? rmul(jn, -1.0) : sc_sub(jp, jn);
+        }
+      }
+      T z0;
+      sc_zero(z0);
+      colJ[(p + 1) * kGrpCentres] = z0;
+    }
+    __syncthreads();
+    const T J0 = colJ[0];
+    const T kneg_j0 = rmul(sc_mul(kk, J0), -1.0);
+    const cplx* wd = reinterpret_cast<const cplx*>(in.wd);
+
+    for (int r0 = 0; r0 < a.nrhs; r0 += kRP) {
+      cplx acc[kNc][RG];
+#pragma unroll
+      for (int q = 0; q < kNc; ++q)
+#pragma unroll
+        for (int g = 0; g < RG; ++g) acc[q][g] = cplx{0.0, 0.0};
+
+      for (int base = item.src0; base < item.src1; base += kGrpTile) {
+        const int nt = min(kGrpTile, item.src1 - base);
+        __syncthreads();   // previous tile's values consumed
+        for (int i = threadIdx.x; i < nt; i += blockDim.x) {
+          s_x[i] = in.sx[base + i];
+          s_y[i] = in.sy[base + i];
+          if (kD) {
+            s_nx[i] = in.snx[base + i];
+            s_ny[i] = in.sny[base + i];
+          }
+        }
+        for (int i = threadIdx.x; i < kGrpTile * kRP; i += blockDim.x) {
+          const int s = i / kRP, rr = i - s * kRP;
+          s_wd[i] = (s < nt && r0 + rr < a.nrhs) ? wd[(size_t)(base + s) * a.nrhs + r0 + rr] : cplx{0.0, 0.0};
+        }
+        __syncthreads();
+        // ---- phase 1: kernel values of this warp's sources ----
+        for (int j = warp; j < nt; j += kGrpWarps) {
+          const double dx = s_x[j] - cx, dy = s_y[j] - cy;
+          double nx = 0.0, ny = 0.0;
+          if (kD) {
+            nx = s_nx[j];
+            ny = s_ny[j];
+          }
+          cplx GS, K, GA, GB;
+          pair_kernels<OPS, T, kGrpCentres>(kw, kk, J0, kneg_j0, colJ, colL, colG, p, dx, dy, nx, ny, ux,
+                                            uy, GS, K, GA, GB);
+          int q = 0;
+          if (kS) s_kv[(q++ * kGrpTile + j) * kGrpCentres + lane] = GS;
+          if (kD) s_kv[(q++ * kGrpTile + j) * kGrpCentres + lane] = K;
+          if (kG) {
+            s_kv[(q++ * kGrpTile + j) * kGrpCentres + lane] = GA;
+            s_kv[(q++ * kGrpTile + j) * kGrpCentres + lane] = GB;
+          }
+        }
+        __syncthreads();
+        // ---- phase 2: this warp's rhs group ----
+        for (int j = 0; j < nt; ++j) {
+          const cplx* w = s_wd + j * kRP + warp * RG;
+#pragma unroll
+          for (int q = 0; q < kNc; ++q) {
+            const cplx kv = s_kv[(q * kGrpTile + j) * kGrpCentres + lane];
+#pragma unroll
+            for (int g = 0; g < RG; ++g) acc[q][g] = acc[q][g] + w[g] * kv;
+          }
+        }
+      }
+      // ---- raw sums of this item (grad S already turned into x, y) ----
+      if (active) {
+        cplx* part = reinterpret_cast<cplx*>(in.part);
+        const size_t row = ((size_t)item.split * in.n_ctr + c) * kNc;
+#pragma unroll
+        for (int g = 0; g < RG; ++g) {
+          const int rr = r0 + warp * RG + g;
+          if (rr >= a.nrhs) break;
+          int q = 0;
+          if (kS) {
+            part[(row + q) * a.nrhs + rr] = acc[q][g];
+            ++q;
+          }
+          if (kD) {
+            part[(row + q) * a.nrhs + rr] = acc[q][g];
+            ++q;
+          }
+          if (kG) {
+            const cplx kA = smul(kk, acc[q][g]);
+            const cplx Bi = acc[q + 1][g] * (2.0 * ir);
+            part[(row + q) * a.nrhs + rr] = kA * ux + Bi * uy;
+            part[(row + q + 1) * a.nrhs + rr] = kA * uy - Bi * ux;
+          }
+        }
+      }
+    }
+    if (!dynamic) break;
+  }
+}
+
+template <int OPS, typename T, int RG>
+static cudaError_t launch_group_t(const GroupArgs& a, int grid, cudaStream_t st) {
+  const size_t smem = GroupSmem<OPS, T, RG>::bytes(a.p);
+  auto kern = k_apply_group<OPS, T, RG>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<grid, kGrpCentres * kGrpWarps, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+#define QBX_GROUP_OPS(X, T, RG)                                          \
+  switch (ops) {                                                         \
+    case OPB_S: X(OPB_S, T, RG);                                         \
+    case OPB_D: X(OPB_D, T, RG);                                         \
+    case OPB_S | OPB_D: X(OPB_S | OPB_D, T, RG);                         \
+    case OPB_S | OPB_D | OPB_G: X(OPB_S | OPB_D | OPB_G, T, RG);         \
+    default: break;                                                      \
+  }
+
+template <typename T>
+static cudaError_t launch_group_any(const GroupArgs& a, int rg, int grid, cudaStream_t st) {
+  const int ops = a.ops;
+#define X(O, TT, R) return launch_group_t<O, TT, R>(a, grid, st)
+  if (rg == 8) {
+    QBX_GROUP_OPS(X, T, 8)
+  } else {
+    QBX_GROUP_OPS(X, T, 2)
+  }
+#undef X
+  return cudaErrorInvalidValue;
+}
+
+template <typename T>
+static int group_occupancy_any(int ops, int p, int rg) {
+  int n = 0;
+#define X(O, TT, R)                                                                                 \
+  cudaFuncSetAttribute(k_apply_group<O, TT, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,        \
+                       (int)GroupSmem<O, TT, R>::bytes(p));                                         \
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_apply_group<O, TT, R>, kGrpCentres * kGrpWarps, \
+                                                GroupSmem<O, TT, R>::bytes(p));                     \
+  return n
+  if (rg == 8) {
+    QBX_GROUP_OPS(X, T, 8)
+  } else {
+    QBX_GROUP_OPS(X, T, 2)
+  }
+#undef X
+  return 0;
+}
+
+template <typename T>
+static const void* group_ptr_any(int ops, int rg) {
+#define X(O, TT, R) return (const void*)k_apply_group<O, TT, R>
+  if (rg == 8) {
+    QBX_GROUP_OPS(X, T, 8)
+  } else {
+    QBX_GROUP_OPS(X, T, 2)
+  }
+#undef X
+  return nullptr;
+}
+
+template <typename T>
+static size_t group_smem_any(int ops, int p, int rg) {
+#define X(O, TT, R) return GroupSmem<O, TT, R>::bytes(p)
+  if (rg == 8) {
+    QBX_GROUP_OPS(X, T, 8)
+  } else {
+    QBX_GROUP_OPS(X, T, 2)
+  }
+#undef X
+  return 0;
+}
+
+}  // namespace qbx

@@ -42,6 +42,8 @@ size_t apply_smem_bytes(int ops, bool ck, int p, int nr);
 size_t apply_smem_bytes_real(int ops, int p, int nr);
 size_t apply_smem_bytes_cplx(int ops, int p, int nr);
 int apply_chunk(int ops);   // rhs per launch for an operator subset
+int apply_occupancy_real(int ops, int p, int nr);   // resident CTAs per SM
+int apply_occupancy_cplx(int ops, int p, int nr);
 
 // Far targets: plain quadrature partial sums.
 struct FarArgs {
@@ -120,7 +122,76 @@ cudaError_t launch_debug_besselj(const void* z, int n, int nmax, void* j, cudaSt
 void host_interp_matrix(int q_tgt, int q_src, std::vector<double>& M);
 size_t host_align256(size_t b);
 int host_choose_split(int num_sms, int n_units, int n_src, size_t bytes_per_split, size_t avail);
+int host_choose_split_waves(int num_sms, int occ, int n_units, int n_src, size_t bytes_per_split,
+                            size_t avail);
 int host_split_len(int n_src, int ns);
 int host_fail(int code, const char* msg);   // sets qbx_last_error(), returns code
+void host_plan_info(const qbx_plan* plan, int* device, int* q_tgt, int* q_src, const double** interp);
+
+}  // namespace qbx
+
+namespace qbx {
+
+// ---- many right-hand sides and batches: the group kernel ------------------
+constexpr int kGrpCentres = 32;   // centres per CTA (one per lane)
+constexpr int kGrpWarps = 4;      // warps per CTA: rhs groups in phase 2
+constexpr int kGrpTile = 32;      // sources per shared-memory tile
+
+// One curve of a batch (or the single curve of a many-rhs apply).
+struct GroupInst {
+  double kre, kim;
+  int n_src, n_tgt, n_ctr;        // n_ctr: centres of the side set
+  int side, nsplit, M;
+  const double *sx, *sy, *snx, *sny, *sw;
+  const double *cx, *cy;          // centres of the side set
+  const double *tx, *ty, *tnx, *tny;
+  const void* wd;                 // [n_src][nrhs] oversampled weighted density
+  const void* dens;               // [n_tgt][nrhs] density on the target grid (jump terms)
+  void* part;                     // [nsplit][n_ctr][ncomp][nrhs] raw sums
+  void* out[3];                   // per operator (S, D, grad S) outputs, for the finish
+};
+// A work item: 32 centres from ctr0 of instance inst, sources [src0, src1),
+// partial-sum slot `split`.
+struct GroupItem {
+  int inst, ctr0, split, src0, src1;
+};
+struct GroupArgs {
+  int ops, p, nrhs;
+  const GroupInst* inst;          // dynamic mode: instance table
+  GroupInst inst0;                // static mode: the one instance
+  int n_items;
+  const GroupItem* items;         // dynamic mode: item list (longest first)
+  int* counter;                   // dynamic mode: next item (zeroed before launch)
+  int st_units, st_nsplit, st_split_len;   // static mode (items == nullptr): one instance
+};
+cudaError_t launch_group_real(const GroupArgs& a, int rg, int grid, cudaStream_t st);
+cudaError_t launch_group_cplx(const GroupArgs& a, int rg, int grid, cudaStream_t st);
+size_t group_smem_real(int ops, int p, int rg);
+size_t group_smem_cplx(int ops, int p, int rg);
+int group_occupancy_real(int ops, int p, int rg);
+int group_occupancy_cplx(int ops, int p, int rg);
+const void* group_ptr_real(int ops, int rg);
+const void* group_ptr_cplx(int ops, int rg);
+
+}  // namespace qbx
+
+namespace qbx {
+
+// ---- adjoint (transposed sweep) -------------------------------------------
+struct AdjArgs {
+  int ops, p, nrhs;
+  double kre, kim;
+  int n_ctr, n_tgt, n_src;
+  const double *cx, *cy, *tx, *ty;
+  const double *sx, *sy, *snx, *sny;
+  const void* gc;        // [n_ctr][nrhs] gradient carried to each centre
+  void* coef;            // [n_ctr][nslots][p+2] coefficient columns (workspace)
+  double* cgeo;          // [n_ctr][3] target direction and 1/r (workspace)
+  int nsplit, ctr_per_split;
+  void* part;            // [nsplit][n_src][1][nrhs]
+};
+cudaError_t launch_adjoint_real(const AdjArgs& a, cudaStream_t st);
+cudaError_t launch_adjoint_cplx(const AdjArgs& a, cudaStream_t st);
+void host_plan_workspace(const qbx_plan* plan, void** ws, size_t* bytes, int* num_sms, int** status);
 
 }  // namespace qbx

@@ -262,7 +262,7 @@ k_form(FormArgs a) {
       cplx twoz;
       if (a.kim == 0.0) {
         const double z = a.kre * rho, invz = inv / a.kre;
-        hankel01_real(z, invz, H0, H1);
+        hankel01_real(z, invz, sqrt(invz), H0, H1);
         twoz = cplx{2.0 * invz, 0.0};
       } else {
         const cplx z = cplx{a.kre * rho, a.kim * rho};
@@ -507,7 +507,7 @@ __global__ void k_debug_hankel(const cplx* z, int n, cplx* h0, cplx* h1) {
   if (i >= n) return;
   const cplx zz = z[i];
   cplx a, b;
-  if (zz.im == 0.0 && zz.re > 0.0) hankel01_real(zz.re, 1.0 / zz.re, a, b);
+  if (zz.im == 0.0 && zz.re > 0.0) hankel01_real(zz.re, 1.0 / zz.re, sqrt(1.0 / zz.re), a, b);
   else hankel01_cplx(zz, a, b);
   h0[i] = a;
   h1[i] = b;

@@ -81,6 +81,18 @@ def lib():
             L.qbx_assign_centres.argtypes = [_P, G, I, I, _P, _P, _P]
             L.qbx_apply_ops.argtypes = [_P, G, I, I, I, c64, I, ctypes.POINTER(_P), I, ctypes.POINTER(_P), _P]
             L.qbx_apply_ops.restype = I
+            L.qbx_batch_create.argtypes = [PP, _P, I, G, ctypes.POINTER(c64), I, I, I, I, I,
+                                           ctypes.POINTER(_P), ctypes.POINTER(_P)]
+            L.qbx_batch_apply.argtypes = [_P, _P]
+            L.qbx_batch_status.argtypes = [_P, _P]
+            L.qbx_batch_destroy.argtypes = [_P]
+            for name in ("qbx_batch_create", "qbx_batch_apply", "qbx_batch_status", "qbx_batch_destroy"):
+                getattr(L, name).restype = I
+            L.qbx_solve_exterior_dirichlet.argtypes = [_P, G, c64, c64, I, _P, I, D, I, I, _P,
+                                                       ctypes.POINTER(I), ctypes.POINTER(D), _P]
+            L.qbx_solve_exterior_dirichlet.restype = I
+            L.qbx_apply_adjoint.argtypes = [_P, G, I, I, I, c64, I, _P, I, _P, _P]
+            L.qbx_apply_adjoint.restype = I
             L.qbx_apply_static.argtypes = [G, I, I, I, c64, I, _P, I, _P, _P]
             L.qbx_apply_static.restype = I
             L.qbx_debug_hankel01.argtypes = [_P, I, _P, _P, _P]
@@ -283,6 +295,54 @@ def qbx_apply(plan: Plan, g: Geometry, op, side, limit, k, p, dens_tgt, x_far=No
     return (out_on, out_far) if n_far else out_on
 
 
+def qbx_apply_adjoint(plan: Plan, g: Geometry, op, side, limit, k, p, gout):
+    """A^H gout for u = qbx_apply(..., op, ...) = A sigma (op S or D)."""
+    go = _dens2d(gout, g.n_tgt)
+    nrhs = go.shape[1]
+    out = torch.empty_like(go)
+    _check(lib().qbx_apply_adjoint(plan.handle, g.ref(), op, side, limit, _k(k), p, _ptr(go), nrhs, _ptr(out),
+                                   _stream()))
+    return out
+
+
+class QBXApply(torch.autograd.Function):
+    """u = A sigma through qbx_apply; backward = qbx_apply_adjoint (the
+    transposed sweep), i.e. grad_sigma = A^H grad_u as torch's complex
+    autograd expects for a complex-linear map."""
+
+    @staticmethod
+    def forward(ctx, dens, plan, g, op, side, limit, k, p):
+        ctx.args = (plan, g, op, side, limit, k, p)
+        return qbx_apply(plan, g, op, side, limit, k, p, dens.detach().contiguous())
+
+    @staticmethod
+    def backward(ctx, grad_u):
+        plan, g, op, side, limit, k, p = ctx.args
+        gd = qbx_apply_adjoint(plan, g, op, side, limit, k, p, grad_u.contiguous())
+        return gd, None, None, None, None, None, None, None
+
+
+def apply_autograd(plan: Plan, g: Geometry, op, side, limit, k, p, dens):
+    """Differentiable on-surface apply of S or D (density gradients)."""
+    return QBXApply.apply(dens, plan, g, op, side, limit, k, p)
+
+
+def qbx_solve_exterior_dirichlet(plan: Plan, g: Geometry, k, eta, p, f, tol=1e-10, restart=40, maxiter=200,
+                                 mu0=None, raise_on_noconv=True):
+    """GMRES for (1/2 + D - i eta S) mu = f (two-sided D and S, sqrt-weight
+    unknowns).  Returns (mu, matvecs, relative residuals)."""
+    ff = _dens2d(f, g.n_tgt)
+    nrhs = ff.shape[1]
+    mu = torch.zeros_like(ff) if mu0 is None else _dens2d(mu0, g.n_tgt).clone()
+    it = ctypes.c_int(0)
+    res = (ctypes.c_double * nrhs)()
+    rc = lib().qbx_solve_exterior_dirichlet(plan.handle, g.ref(), _k(k), _k(eta), p, _ptr(ff), nrhs, float(tol),
+                                            restart, maxiter, _ptr(mu), ctypes.byref(it), res, _stream())
+    if rc != 0 and (raise_on_noconv or rc != 5):
+        _check(rc)
+    return mu, it.value, np.array(res[:])
+
+
 OPS_S, OPS_D, OPS_GRAD_S = 1, 2, 4
 
 
@@ -306,6 +366,53 @@ def qbx_apply_ops(plan: Plan, g: Geometry, ops, side, limit, k, p, dens, out=Non
     mask = sum(1 << o for o in ops)
     _check(lib().qbx_apply_ops(plan.handle, g.ref(), mask, side, limit, _k(k), p, dp, nrhs, op_, _stream()))
     return {o: out[o] for o in ops}
+
+
+class Batch:
+    """qbx_batch_create / qbx_batch_apply / qbx_batch_destroy: many curves in
+    one persistent launch run as a CUDA graph.  `geoms`: Geometry objects made
+    with `plan`; `ks`: wavenumbers; `dens`: per curve [n_tgt][nrhs] complex128
+    device tensors, read at every apply; outputs are allocated here
+    (self.out[i][op])."""
+
+    def __init__(self, plan: Plan, geoms, ks, p, ops, side, limit, dens):
+        n = len(geoms)
+        self.plan, self.geoms = plan, list(geoms)
+        self.dens = [_dens2d(d, g.n_tgt) for d, g in zip(dens, geoms)]
+        nrhs = self.dens[0].shape[1]
+        self.ops = sorted(set(ops))
+        self.out = []
+        for g, d in zip(self.geoms, self.dens):
+            self.out.append({o: torch.empty((g.n_tgt, 2, nrhs) if o == OP_GRAD_S else (g.n_tgt, nrhs),
+                                            dtype=torch.complex128, device=d.device) for o in self.ops})
+        garr = (GeomStruct * n)(*[g.s for g in self.geoms])
+        karr = (c64 * n)(*[_k(k) for k in ks])
+        darr = (_P * n)(*[_ptr(d) for d in self.dens])
+        oarr = (_P * (3 * n))(*[(_ptr(self.out[i][o]) if o in self.out[i] else None)
+                                for i in range(n) for o in range(3)])
+        mask = sum(1 << o for o in self.ops)
+        h = ctypes.c_void_p()
+        _check(lib().qbx_batch_create(ctypes.byref(h), plan.handle, n, garr, karr, p, mask, side, limit, nrhs,
+                                      darr, oarr))
+        self.handle = h
+
+    def apply(self):
+        _check(lib().qbx_batch_apply(self.handle, _stream()))
+        return self.out
+
+    def status(self):
+        _check(lib().qbx_batch_status(self.handle, _stream()))
+
+    def close(self):
+        if getattr(self, "handle", None) and self.handle.value:
+            lib().qbx_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def qbx_apply_static(g: Geometry, op, side, limit, k, p, dens_tgt, out_on=None):

@@ -1,0 +1,114 @@
+"""GPU parity of the many-rhs group kernel and of the batched persistent apply
+(many curves, one launch, CUDA graph) against the CPU oracle."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1207_4461_gb300 as qbx
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-11
+
+
+def rel(a, b):
+    a = a.detach().cpu().numpy() if torch.is_tensor(a) else np.asarray(a)
+    return np.abs(a - b).max() / np.abs(b).max()
+
+
+def dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a), device="cuda")
+
+
+@pytest.mark.parametrize("ops", [(0,), (1,), (0, 1), (0, 1, 2)])
+@pytest.mark.parametrize("side,limit,k,nrhs", [(qbx.SIDE_TWO, 0, 9.0, 20), (qbx.SIDE_INT, 1, 3 + 0.5j, 37),
+                                               (qbx.SIDE_EXT, 1, 14.0, 16)])
+def test_group_kernel_many_rhs(cuda, ops, side, limit, k, nrhs):
+    """qbx_apply_ops with >= 16 rhs of one density takes the group kernel:
+    9 panels (144 targets -> 4.5 tiles of 32 centres), 576 sources
+    (18 tiles of 32); 37 rhs = 2 passes of 32."""
+    p = 8
+    cur = W.starfish(0.2, 3)
+    M = 9
+    plan = qbx.Plan(16, 64, n_src=M * 64, n_ctr=2 * M * 16, ncoef=4, nrhs=nrhs)
+    g = qbx.qbx_geometry(plan, cur, cur.edges(M))
+    go = oracle.geometry(cur, cur.edges(M), 16, 64)
+    dens = W.complex_gaussian(77, g.n_tgt * nrhs).reshape(g.n_tgt, nrhs)
+    got = qbx.qbx_apply_ops(plan, g, ops, side, limit, k, p, dev(dens))
+    for o in ops:
+        ref = oracle.apply(go, o, side, limit, k, p, dens)
+        assert rel(got[o], ref) < TOL, o
+
+
+def small_batch(ks, Ms, nrhs, seed=5):
+    bw = W.BatchWorkload("t", len(Ms), 7, nrhs, seed)
+    ins = bw.instances()
+    return [(ins[i][0], Ms[i], ks[i]) for i in range(len(Ms))], bw
+
+
+@pytest.mark.parametrize("ops", [(0, 1), (0,), (0, 1, 2)])
+@pytest.mark.parametrize("ks,side,limit", [((5.0, 11.0, 2.0, 30.0, 7.5), qbx.SIDE_INT, 0),
+                                           ((5.0, 3 + 0.4j, 8.0, 1.5, 20.0), qbx.SIDE_TWO, 0),
+                                           ((6.0, 6.5, 7.0, 7.5, 8.0), qbx.SIDE_EXT, 1)])
+def test_batch_matches_oracle(cuda, ops, ks, side, limit):
+    Ms = (1, 3, 7, 12, 5)
+    nrhs, p = 5, 7
+    insts, bw = small_batch(ks, Ms, nrhs)
+    plan = qbx.Plan(16, 64, n_src=64 * max(Ms), n_ctr=2 * 16 * max(Ms), ncoef=4, nrhs=nrhs)
+    geoms = [qbx.qbx_geometry(plan, c, c.edges(M)) for c, M, _ in insts]
+    dens = [dev(bw.dens(i, g.n_tgt)) for i, g in enumerate(geoms)]
+    batch = qbx.Batch(plan, geoms, [k for _, _, k in insts], p, ops, side, limit, dens)
+    out = batch.apply()
+    batch.status()
+    for i, (c, M, k) in enumerate(insts):
+        go = oracle.geometry(c, c.edges(M), 16, 64)
+        d = bw.dens(i, go["n_tgt"])
+        for o in ops:
+            ref = oracle.apply(go, o, side, limit, k, p, d)
+            assert rel(out[i][o], ref) < TOL, (i, o)
+
+
+def test_batch_reads_current_densities(cuda):
+    """Densities are bound at creation; each apply reads their current values."""
+    insts, bw = small_batch((4.0, 9.0), (4, 6), 3)
+    plan = qbx.Plan(16, 64, n_src=64 * 6, n_ctr=2 * 16 * 6, ncoef=2, nrhs=3)
+    geoms = [qbx.qbx_geometry(plan, c, c.edges(M)) for c, M, _ in insts]
+    dens = [dev(bw.dens(i, g.n_tgt)) for i, g in enumerate(geoms)]
+    batch = qbx.Batch(plan, geoms, [4.0, 9.0], 6, (0, 1), qbx.SIDE_INT, qbx.LIMIT_PV, dens)
+    first = [{o: t.clone() for o, t in d.items()} for d in batch.apply()]
+    for d in dens:
+        d.mul_(2.0 - 1.0j)
+    second = batch.apply()
+    for i in range(2):
+        for o in (0, 1):
+            assert torch.allclose(second[i][o], first[i][o] * (2.0 - 1.0j), rtol=1e-12, atol=1e-14)
+
+
+def test_batch_full_size_sampled(cuda):
+    """The 64-curve workload (16..512 panels, k in (1, 40), p = 10, 32 rhs, S
+    and D) in the benchmark's launch configuration: every curve against the
+    per-curve apply, and three curves against the oracle on sampled targets."""
+    bw = W.cfg3()
+    insts = bw.instances()
+    Mmax = max(M for _, M, _ in insts)
+    plan = qbx.Plan(16, 64, n_src=64 * Mmax, n_ctr=16 * Mmax, ncoef=2, nrhs=bw.nrhs)
+    geoms = [qbx.qbx_geometry(plan, c, c.edges(M)) for c, M, _ in insts]
+    dens = [dev(bw.dens(i, g.n_tgt)) for i, g in enumerate(geoms)]
+    batch = qbx.Batch(plan, geoms, [k for _, _, k in insts], bw.p, (0, 1), qbx.SIDE_INT, 0, dens)
+    out = batch.apply()
+    batch.status()
+    for i, g in enumerate(geoms):
+        ref = qbx.qbx_apply_ops(plan, g, (0, 1), qbx.SIDE_INT, 0, insts[i][2], bw.p, dens[i])
+        for o in (0, 1):
+            assert (torch.abs(out[i][o] - ref[o]).max() / torch.abs(ref[o]).max()).item() < 1e-12
+    order = np.argsort([M for _, M, _ in insts])
+    rng = np.random.default_rng(9)
+    for i in (order[0], order[len(order) // 2], order[-1]):
+        c, M, k = insts[i]
+        go = oracle.geometry(c, c.edges(M), 16, 64)
+        sel = np.unique(np.concatenate([[0, go["n_tgt"] - 1], rng.integers(0, go["n_tgt"], 2)]))
+        d = bw.dens(i, go["n_tgt"])
+        for o in (0, 1):
+            ref = oracle.apply(go, o, oracle.SIDE_INT, 0, k, bw.p, d, sel=sel)
+            assert rel(out[i][o].cpu().numpy()[sel], ref) < TOL, (i, o)

@@ -1,0 +1,66 @@
+"""Batched GMRES for the exterior sound-soft problem (1/2 + D - i eta S) mu = f
+(two-sided D and S, sqrt-weight unknowns) on the teardrop with a 90-degree
+corner and dyadic refinement: the solution's residual under the oracle's
+operator, and the field of a point source inside the curve reproduced
+outside it (the paper's test: charges in the complement, Sec. 4.2)."""
+import numpy as np
+import pytest
+import scipy.special as sp
+import torch
+
+import oracle
+import paper_1207_4461_gb300 as qbx
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a), device="cuda")
+
+
+def setup(m_base=20, levels=3, k=5.0, p=8):
+    cur = W.teardrop(True)
+    edges = W.dyadic_edges(m_base, levels)
+    M = len(edges) - 1
+    plan = qbx.Plan(16, 64, n_src=M * 64, n_ctr=2 * M * 16, ncoef=4, nrhs=8)
+    g = qbx.qbx_geometry(plan, cur, edges)
+    go = oracle.geometry(cur, edges, 16, 64)
+    return cur, edges, plan, g, go, k, p
+
+
+def test_gmres_residual_under_oracle_operator(cuda):
+    cur, edges, plan, g, go, k, p = setup()
+    eta = k
+    # right-hand sides: two plane waves and a point-source trace
+    tx, ty = go["tgt_x"], go["tgt_y"]
+    f = np.stack([-np.exp(1j * k * tx), -np.exp(1j * k * (0.6 * tx + 0.8 * ty)),
+                  0.25j * sp.hankel1(0, k * np.hypot(tx - 0.1, ty + 0.05))], 1)
+    mu, its, res = qbx.qbx_solve_exterior_dirichlet(plan, g, k, eta, p, dev(f), tol=1e-10, restart=40,
+                                                     maxiter=200)
+    assert np.all(res <= 1e-10) and its < 200
+    mu = mu.cpu().numpy()
+    S = oracle.apply(go, oracle.OP_S, oracle.SIDE_TWO, 0, k, p, mu)
+    D = oracle.apply(go, oracle.OP_D, oracle.SIDE_TWO, 0, k, p, mu)
+    r = 0.5 * mu + D - 1j * eta * S - f
+    sw = np.sqrt(go["tgt_w"])[:, None]
+    rel = np.linalg.norm(sw * r, axis=0) / np.linalg.norm(sw * f, axis=0)
+    assert np.all(rel <= 1.1e-10 * 2), rel
+
+
+def test_gmres_point_source_field_outside(cuda):
+    """f = G(., x0) on Gamma with x0 inside: u = (D - i eta S) mu equals
+    G(x, x0) everywhere outside (evaluated by plain quadrature far away)."""
+    cur, edges, plan, g, go, k, p = setup(m_base=32, levels=4, k=4.0, p=10)
+    eta = k
+    x0 = np.array([0.15, -0.05])
+    f = 0.25j * sp.hankel1(0, k * np.hypot(g["tgt_x"].cpu().numpy() - x0[0], g["tgt_y"].cpu().numpy() - x0[1]))
+    mu, its, res = qbx.qbx_solve_exterior_dirichlet(plan, g, k, eta, p, dev(f.reshape(-1, 1)), tol=1e-11)
+    th = np.linspace(0, 2 * np.pi, 41)[:-1]
+    xy = np.stack([3 * np.cos(th), 3 * np.sin(th)], 1)
+    wd = qbx.qbx_upsample(plan, g, mu)
+    uD = qbx.qbx_far(plan, g, qbx.OP_D, k, wd, dev(xy)).cpu().numpy()[:, 0]
+    uS = qbx.qbx_far(plan, g, qbx.OP_S, k, wd, dev(xy)).cpu().numpy()[:, 0]
+    u = uD - 1j * eta * uS
+    ref = 0.25j * sp.hankel1(0, k * np.hypot(xy[:, 0] - x0[0], xy[:, 1] - x0[1]))
+    assert np.abs(u - ref).max() / np.abs(ref).max() < 1e-6

@@ -20,16 +20,12 @@ _MASK = (1 << 64) - 1
 
 
 def splitmix64(seed: int, n: int) -> np.ndarray:
-    """n successive outputs of splitmix64 started at `seed` (uint64)."""
-    out = np.empty(n, dtype=np.uint64)
-    s = seed & _MASK
-    for i in range(n):
-        s = (s + 0x9E3779B97F4A7C15) & _MASK
-        z = s
-        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _MASK
-        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _MASK
-        out[i] = z ^ (z >> 31)
-    return out
+    """n successive outputs of splitmix64 started at `seed` (uint64; numpy
+    uint64 arithmetic wraps modulo 2^64 as the generator requires)."""
+    s = np.uint64(int(seed) & _MASK) + np.arange(1, n + 1, dtype=np.uint64) * np.uint64(0x9E3779B97F4A7C15)
+    z = (s ^ (s >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+    z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+    return z ^ (z >> np.uint64(31))
 
 
 def uniform(seed: int, n: int) -> np.ndarray:
@@ -111,6 +107,34 @@ def fourier_curve(a, b) -> Curve:
     return Curve("fourier", 0.0, 2 * math.pi, _polar(rf, drf))
 
 
+def teardrop(right_angle: bool = True) -> Curve:
+    """gamma(t) = 1.7 (sin(pi t) - 0.5, c cos(pi t)(pi t - pi) pi t), t in [0, 1],
+    a closed counter-clockwise curve with one corner at t = 0 = 1.  c = 1/pi
+    gives an interior angle of exactly 90 degrees; c = 1/2 (right_angle=False)
+    is the paper's teardrop (about 115 degrees)."""
+    c = 1.0 / math.pi if right_angle else 0.5
+    pi = math.pi
+
+    def fn(t):
+        x = 1.7 * (np.sin(pi * t) - 0.5)
+        y = 1.7 * c * np.cos(pi * t) * (pi * t - pi) * pi * t
+        dx = 1.7 * pi * np.cos(pi * t)
+        dy = 1.7 * c * (-pi * np.sin(pi * t) * (pi * t - pi) * pi * t + np.cos(pi * t) * pi * (2 * pi * t - pi))
+        return np.stack([x, y], -1), np.stack([dx, dy], -1)
+    return Curve("teardrop90" if right_angle else "teardrop", 0.0, 1.0, fn)
+
+
+def dyadic_edges(m_base: int, levels: int, t0: float = 0.0, t1: float = 1.0) -> np.ndarray:
+    """m_base panels equispaced in t, then the panel next to each end (the
+    corner at t0 = t1) bisected `levels` times toward the end: m_base +
+    2 levels panels, neighbours differing in length by at most 2."""
+    e = np.linspace(t0, t1, m_base + 1)
+    h = e[1] - e[0]
+    left = [t0 + h / 2 ** j for j in range(levels, 0, -1)]
+    right = [t1 - h / 2 ** j for j in range(1, levels + 1)]
+    return np.concatenate([[t0], left, e[1:-1], right, [t1]])
+
+
 # ----------------------------------------------------------------------------
 # Densities on the target grid, as functions of the curve parameter.
 # ----------------------------------------------------------------------------
@@ -174,6 +198,49 @@ def cfg1() -> Workload:
     interior centres, sigma = cos 3t + 0.5 i sin t; S and D."""
     return Workload("starfish-M32-k5-p8-int", starfish(), 32, 5.0, 8, sides="int",
                     ops=("S", "D"), density="cfg1")
+
+
+@dataclass
+class BatchWorkload:
+    """Many random smooth curves r(t) = 1 + sum_{m=1..8} (a_m cos mt + b_m sin mt),
+    a_m, b_m ~ U(-0.04, 0.04), panel counts M ~ U{m_lo..m_hi}, k ~ U(k_lo, k_hi),
+    nrhs CN(0,1) densities per curve, interior centres, S and D."""
+    name: str
+    n_inst: int
+    p: int
+    nrhs: int
+    seed: int
+    m_lo: int = 16
+    m_hi: int = 512
+    k_lo: float = 1.0
+    k_hi: float = 40.0
+    q_tgt: int = 16
+    q_src: int = 64
+    ops: tuple = ("S", "D")
+    sides: str = "int"
+
+    def instances(self):
+        """[(curve, M, k)] drawn from splitmix64 with this workload's seed."""
+        u = uniform(self.seed, self.n_inst * 18)
+        out = []
+        for i in range(self.n_inst):
+            v = u[18 * i:18 * i + 18]
+            a = -0.04 + 0.08 * v[0:8]
+            b = -0.04 + 0.08 * v[8:16]
+            M = self.m_lo + min(int(v[16] * (self.m_hi - self.m_lo + 1)), self.m_hi - self.m_lo)
+            k = self.k_lo + (self.k_hi - self.k_lo) * v[17]
+            out.append((fourier_curve(a, b), M, float(k)))
+        return out
+
+    def dens(self, i, n_tgt):
+        """Curve i's densities on its target grid, [n_tgt][nrhs]."""
+        return complex_gaussian(self.seed * 1000003 + 17 * i + 1, n_tgt * self.nrhs).reshape(n_tgt, self.nrhs)
+
+
+def cfg3() -> BatchWorkload:
+    """64 random curves, 16..512 panels x 16 nodes, k ~ U(1, 40), p = 10,
+    32 CN(0,1) densities each (seed 3), interior centres, S and D."""
+    return BatchWorkload("fourier-batch-64-p10-32rhs", 64, 10, 32, 3)
 
 
 def cfg2() -> Workload:
