@@ -1,8 +1,9 @@
 """Batched GMRES for the exterior sound-soft problem (1/2 + D - i eta S) mu = f
-(two-sided D and S, sqrt-weight unknowns) on the teardrop with a 90-degree
-corner and dyadic refinement: the solution's residual under the oracle's
-operator, and the field of a point source inside the curve reproduced
-outside it (the paper's test: charges in the complement, Sec. 4.2)."""
+(two-sided D and S, sqrt-weight unknowns) on the paper's teardrop (a corner
+of about 115 degrees, Sec. 4.2) with dyadic refinement toward the corner: the
+solution's residual under the oracle's operator, and the field of a point
+source inside the curve reproduced outside it (the paper's test: charges in
+the complement, Sec. 4.2)."""
 import numpy as np
 import pytest
 import scipy.special as sp
@@ -20,7 +21,7 @@ def dev(a):
 
 
 def setup(m_base=20, levels=3, k=5.0, p=8):
-    cur = W.teardrop(True)
+    cur = W.teardrop()
     edges = W.dyadic_edges(m_base, levels)
     M = len(edges) - 1
     plan = qbx.Plan(16, 64, n_src=M * 64, n_ctr=2 * M * 16, ncoef=4, nrhs=8)
@@ -63,4 +64,5 @@ def test_gmres_point_source_field_outside(cuda):
     uS = qbx.qbx_far(plan, g, qbx.OP_S, k, wd, dev(xy)).cpu().numpy()[:, 0]
     u = uD - 1j * eta * uS
     ref = 0.25j * sp.hankel1(0, k * np.hypot(xy[:, 0] - x0[0], xy[:, 1] - x0[1]))
-    assert np.abs(u - ref).max() / np.abs(ref).max() < 1e-6
+    # the oracle's dense solve of the same system reproduces the field to 7e-11
+    assert np.abs(u - ref).max() / np.abs(ref).max() < 1e-7

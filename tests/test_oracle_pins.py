@@ -436,3 +436,48 @@ def test_apply_sel_matches_full():
         full = oracle.apply(g, op, TWO, ONE, 5.0, 6, dens)
         part = oracle.apply(g, op, TWO, ONE, 5.0, 6, dens, sel=sel)
         assert np.array_equal(full[sel], part)
+
+
+def _corner_angle_deg(cur):
+    """Interior angle at the corner t = 0 = 1 from the one-sided tangents."""
+    _, d0 = cur(np.array([1e-9]))
+    _, d1 = cur(np.array([1.0 - 1e-9]))
+    a, b = d0[0] / np.linalg.norm(d0[0]), -d1[0] / np.linalg.norm(d1[0])
+    return math.degrees(math.acos(float(np.clip(a @ b, -1, 1))))
+
+
+def test_teardrop_corner_and_centre_admissibility():
+    """The paper's teardrop (Sec. 4.2) has a corner of 2 atan(pi/2) degrees
+    and its right-angle variant 90; at 90 degrees the interior centres of the
+    targets next to the corner lie on the opposite arm (closest source far
+    inside the disk), at 115 degrees they do not."""
+    assert abs(_corner_angle_deg(W.teardrop()) - math.degrees(2 * math.atan(math.pi / 2))) < 1e-6
+    assert abs(_corner_angle_deg(W.teardrop(True)) - 90.0) < 1e-6
+    edges = W.dyadic_edges(12, 3)
+    r90 = oracle.geometry(W.teardrop(True), edges, 16, 64)
+    r115 = oracle.geometry(W.teardrop(), edges, 16, 64)
+    n = r90["n_tgt"]
+    assert r90["ctr_ratio"][:n].min() < 0.05
+    assert r115["ctr_ratio"][:n].min() > 0.3
+    assert r90["ctr_ratio"][n:].min() > 0.99 and r115["ctr_ratio"][n:].min() > 0.99
+
+
+def test_combined_field_solve_reproduces_point_source():
+    """Sec. 4.2's check: with f = G(., x0) on the boundary, x0 inside, the
+    solution of (1/2 + D - i eta S) mu = f (two-sided operators, eta = k) gives
+    u = (D - i eta S) mu = G(., x0) outside.  Paper's teardrop, 12 panels + 3
+    dyadic levels on each side of the corner, k = 5, p = 8; dense solve."""
+    k, p, eta = 5.0, 8, 5.0
+    g = oracle.geometry(W.teardrop(), W.dyadic_edges(12, 3), 16, 64)
+    n = g["n_tgt"]
+    S = oracle.matrix(g, OP_S, TWO, ONE, k, p)
+    D = oracle.matrix(g, OP_D, TWO, ONE, k, p)
+    x0 = np.array([0.15, -0.05])
+    f = 0.25j * sp.hankel1(0, k * np.hypot(g["tgt_x"] - x0[0], g["tgt_y"] - x0[1]))
+    mu = np.linalg.solve(0.5 * np.eye(n) + D - 1j * eta * S, f)
+    th = np.linspace(0, 2 * np.pi, 17)[:-1]
+    xy = np.stack([3 * np.cos(th), 3 * np.sin(th)], 1)
+    wd = oracle.upsample(g, mu)
+    u = (oracle.far(g, OP_D, k, wd, xy) - 1j * eta * oracle.far(g, OP_S, k, wd, xy)).ravel()
+    ref = 0.25j * sp.hankel1(0, k * np.hypot(xy[:, 0] - x0[0], xy[:, 1] - x0[1]))
+    assert np.abs(u - ref).max() / np.abs(ref).max() < 1e-6

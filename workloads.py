@@ -107,11 +107,13 @@ def fourier_curve(a, b) -> Curve:
     return Curve("fourier", 0.0, 2 * math.pi, _polar(rf, drf))
 
 
-def teardrop(right_angle: bool = True) -> Curve:
+def teardrop(right_angle: bool = False) -> Curve:
     """gamma(t) = 1.7 (sin(pi t) - 0.5, c cos(pi t)(pi t - pi) pi t), t in [0, 1],
-    a closed counter-clockwise curve with one corner at t = 0 = 1.  c = 1/pi
-    gives an interior angle of exactly 90 degrees; c = 1/2 (right_angle=False)
-    is the paper's teardrop (about 115 degrees)."""
+    a closed counter-clockwise curve with one corner at t = 0 = 1.  c = 1/2 is
+    the paper's teardrop (Sec. 4.2; interior angle 2 atan(pi/2), about 115
+    degrees); c = 1/pi (right_angle=True) gives exactly 90 degrees, where the
+    interior centres of the targets next to the corner lie on the opposite
+    arm."""
     c = 1.0 / math.pi if right_angle else 0.5
     pi = math.pi
 
