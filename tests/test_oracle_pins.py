@@ -481,3 +481,100 @@ def test_combined_field_solve_reproduces_point_source():
     u = (oracle.far(g, OP_D, k, wd, xy) - 1j * eta * oracle.far(g, OP_S, k, wd, xy)).ravel()
     ref = 0.25j * sp.hankel1(0, k * np.hypot(xy[:, 0] - x0[0], xy[:, 1] - x0[1]))
     assert np.abs(u - ref).max() / np.abs(ref).max() < 1e-6
+
+
+# ---------------------------------------------------------------------------
+# Shape derivative of S (forward mode): the reference for the shape adjoint
+# ---------------------------------------------------------------------------
+def _fourier_pert(m, kind):
+    """d gamma, d gamma' for r(t) -> r(t) + eps f(t), f = cos(mt) or sin(mt),
+    of a polar curve gamma = r(t) (cos t, sin t)."""
+    def fn(t):
+        t = np.asarray(t, dtype=np.float64)
+        c, s = np.cos(t), np.sin(t)
+        f = np.cos(m * t) if kind == "cos" else np.sin(m * t)
+        df = -m * np.sin(m * t) if kind == "cos" else m * np.cos(m * t)
+        return np.stack([f * c, f * s], -1), np.stack([df * c - f * s, df * s + f * c], -1)
+    return fn
+
+
+def _moved(curve, pert, eps):
+    def fn(t):
+        g, dg = curve(t)
+        pg, pdg = pert(t)
+        return g + eps * pg, dg + eps * pdg
+    return W.Curve(curve.name, curve.t0, curve.t1, fn)
+
+
+@pytest.mark.parametrize("side,k,pert", [(INT, 5.0, ("cos", 3)), (EXT, 5.0, ("sin", 2)),
+                                         (TWO, 3 + 0.5j, ("cos", 0)), (INT, 8.0, ("sin", 5))])
+def test_shape_tangent_vs_central_differences(side, k, pert):
+    """The forward-mode derivative against central differences (h = 1e-6) of
+    the oracle's own apply on moved curves: starfish, 12 panels, p = 8."""
+    cur, M, p, h = W.starfish(), 12, 8, 1e-6
+    pf = _fourier_pert(pert[1], pert[0])
+    edges = cur.edges(M)
+    dens = W.density_cfg1(oracle.panel_nodes(edges, 16))
+    u, du = oracle.apply_s_tangent(cur, pf, edges, 16, 64, side, k, p, dens)
+    up = oracle.apply(oracle.geometry(_moved(cur, pf, h), edges, 16, 64), OP_S, side, ONE, k, p, dens)
+    um = oracle.apply(oracle.geometry(_moved(cur, pf, -h), edges, 16, 64), OP_S, side, ONE, k, p, dens)
+    u0 = oracle.apply(oracle.geometry(cur, edges, 16, 64), OP_S, side, ONE, k, p, dens)
+    assert relerr(u, u0) < 1e-14
+    assert relerr(du, (up - um) / (2 * h)) < 2e-9
+
+
+def test_shape_tangent_rigid_motions():
+    """S is invariant under translations and rotations of the whole curve, and
+    the discrete operator is too (only differences of positions and of polar
+    angles enter): the derivative along a rigid motion vanishes."""
+    cur, M, p, k = W.starfish(), 10, 8, 5.0
+    edges = cur.edges(M)
+    dens = W.density_cfg1(oracle.panel_nodes(edges, 16))
+
+    def shift(t):
+        n = np.asarray(t).size
+        return np.tile([0.3, -0.7], (n, 1)), np.zeros((n, 2))
+
+    def rot(t):
+        g, dg = cur(t)
+        return np.stack([-g[:, 1], g[:, 0]], -1), np.stack([-dg[:, 1], dg[:, 0]], -1)
+    for side in (INT, EXT, TWO):
+        u, du_t = oracle.apply_s_tangent(cur, shift, edges, 16, 64, side, k, p, dens)
+        _, du_r = oracle.apply_s_tangent(cur, rot, edges, 16, 64, side, k, p, dens)
+        assert np.abs(du_t).max() < 1e-13 * np.abs(u).max()
+        assert np.abs(du_r).max() < 1e-11 * np.abs(u).max()
+
+
+def test_shape_tangent_scaling_identity():
+    """Scaling the curve by lambda scales every length of the discretisation
+    (nodes, weights, h, r, centres), so the discrete S obeys
+    u_lambda(k) = lambda u(lambda k) exactly; at lambda = 1 the derivative
+    along gamma -> gamma is u + k du/dk (du/dk by central differences)."""
+    cur, M, p, k, h = W.starfish(), 12, 8, 6.0, 1e-5
+    edges = cur.edges(M)
+    dens = W.density_cfg1(oracle.panel_nodes(edges, 16))
+    g = oracle.geometry(cur, edges, 16, 64)
+    for side in (INT, TWO):
+        u, du = oracle.apply_s_tangent(cur, lambda t: cur(t), edges, 16, 64, side, k, p, dens)
+        dk = (oracle.apply(g, OP_S, side, ONE, k + h, p, dens) - oracle.apply(g, OP_S, side, ONE, k - h, p, dens)) / (2 * h)
+        assert relerr(du, u + k * dk) < 1e-8
+
+
+@pytest.mark.parametrize("m,k", [(0, 5.0), (3, 5.0), (2, 4 + 0.5j)])
+def test_shape_tangent_circle_radius(m, k):
+    """Unit circle, sigma = e^{imt}: S sigma = lambda(R) e^{imt} with
+    lambda(R) = (i pi R/2) J_m(kR) H_m(kR), so moving every point radially
+    (R -> R + eps) gives du = lambda'(1) e^{imt},
+    lambda'(1) = (i pi/2) [J_m H_m + k (J_m' H_m + J_m H_m')]."""
+    cur = W.circle(1.0)
+    edges = cur.edges(32)
+    t = oracle.panel_nodes(edges, 16)
+    dens = np.exp(1j * m * t)
+
+    def radial(tt):
+        tt = np.asarray(tt, dtype=np.float64)
+        return np.stack([np.cos(tt), np.sin(tt)], -1), np.stack([-np.sin(tt), np.cos(tt)], -1)
+    J, H, Jp, Hp = sp.jv(m, k), sp.hankel1(m, k), sp.jvp(m, k), sp.h1vp(m, k)
+    dlam = 0.5j * np.pi * (J * H + k * (Jp * H + J * Hp))
+    _, du = oracle.apply_s_tangent(cur, radial, edges, 16, 64, INT, k, 12, dens)
+    assert relerr(du[:, 0], dlam * dens) < 1e-9
