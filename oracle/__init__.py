@@ -62,7 +62,7 @@ def lib():
             L.orc_apply.argtypes = [I, I, I, D, D, I, I, I, I] + [P] * 11 + [P, I, I, P, P]
             L.orc_far.argtypes = [I, I, P, I, P, P, P, P, P, I, D, D, P]
             L.orc_assign_centres.argtypes = [I, P, I, I, P, P, P, P]
-            L.orc_apply_s_tangent.argtypes = [I, D, D, I, I, I, I, P, D] + [P] * 8 + [P, I, P, P]
+            L.orc_apply_s_tangent.argtypes = [I, D, D, I, I, I, I, P, D] + [P] * 4 + [I] + [P] * 4 + [P, I, P, P]
             L.orc_num_threads.restype = I
             _lib = L
     return _lib
@@ -278,26 +278,32 @@ def assign_centres(g, side, xy):
 
 def apply_s_tangent(curve, pert, t_edges, q_tgt: int, q_src: int, side, k, p, dens_tgt, r_factor: float = 0.5):
     """Shape derivative of the on-surface S apply, forward mode: with the curve
-    samples moving along `pert` (callable t -> (d gamma [n,2], d gamma' [n,2]))
-    and the density fixed on the target grid as a function of t, returns
-    (u, du/d eps), both [n_tgt][nrhs].  Geometry of Sec. 3.3 step 4a and the
-    sums of eqs. graf-coefficient / local-exp differentiated by the chain rule."""
+    samples moving along `pert` (callable t -> (d gamma [n,2], d gamma' [n,2]),
+    or a list of such directions) and the density fixed on the target grid as
+    a function of t, returns (u, du/d eps): u [n_tgt][nrhs], du the same shape
+    (one direction) or [ndir][n_tgt][nrhs] (a list).  Geometry of Sec. 3.3
+    step 4a and the sums of eqs. graf-coefficient / local-exp differentiated
+    by the chain rule."""
     t_edges = _f64(t_edges)
     M = t_edges.size - 1
     tt = panel_nodes(t_edges, q_tgt)
     ts = panel_nodes(t_edges, q_src)
     gt, dgt = (_f64(a) for a in curve(tt))
     gs, dgs = (_f64(a) for a in curve(ts))
-    pgt, pdgt = (_f64(a) for a in pert(tt))
-    pgs, pdgs = (_f64(a) for a in pert(ts))
+    perts = list(pert) if isinstance(pert, (list, tuple)) else [pert]
+    nd = len(perts)
+    pgt = _f64(np.stack([_f64(q(tt)[0]) for q in perts]))
+    pdgt = _f64(np.stack([_f64(q(tt)[1]) for q in perts]))
+    pgs = _f64(np.stack([_f64(q(ts)[0]) for q in perts]))
+    pdgs = _f64(np.stack([_f64(q(ts)[1]) for q in perts]))
     d = _dens2d(dens_tgt, M * q_tgt)
     nrhs = d.shape[1]
     k = complex(k)
     u = np.zeros((M * q_tgt, nrhs), dtype=np.complex128)
-    du = np.zeros_like(u)
+    du = np.zeros((nd, M * q_tgt, nrhs), dtype=np.complex128)
     rc = lib().orc_apply_s_tangent(side, k.real, k.imag, p, M, q_tgt, q_src, _p(t_edges), float(r_factor),
-                                   _p(gt), _p(dgt), _p(gs), _p(dgs), _p(pgt), _p(pdgt), _p(pgs), _p(pdgs),
+                                   _p(gt), _p(dgt), _p(gs), _p(dgs), nd, _p(pgt), _p(pdgt), _p(pgs), _p(pdgs),
                                    _p(d), nrhs, _p(u), _p(du))
     if rc != 0:
         raise ValueError(f"orc_apply_s_tangent failed ({rc})")
-    return u, du
+    return u, (du if isinstance(pert, (list, tuple)) else du[0])

@@ -669,7 +669,8 @@ int orc_assign_centres(int n, const double *xy, int c0, int c1,
 /* vector d = x_s - c (sources) or x - c (target), and for signed orders       */
 /* Z_l' = (Z_{l-1} - Z_{l+1})/2, Z = H or J (DLMF 10.6.1).  S has no jump, so  */
 /* the one-sided limit and the PV agree; side TWO averages the two centres.    */
-/* u, du: [n_tgt][nrhs].  Returns 0, 1 on bad sizes, 2 on allocation failure.  */
+/* ndir directions at once (pg_*, pdg_*: [ndir][n][2]).  u: [n_tgt][nrhs],     */
+/* du: [ndir][n_tgt][nrhs].  Returns 0, 1 on bad sizes, 2 on allocation failure.*/
 /* ------------------------------------------------------------------------- */
 static cplx Z_signed(int l, const cplx *Z)
 {
@@ -682,69 +683,79 @@ static cplx Z_signed(int l, const cplx *Z)
 int orc_apply_s_tangent(int side, double kre, double kim, int p, int M, int q_tgt, int q_src,
                         const double *t_edges, double r_factor,
                         const double *gam_tgt, const double *dgam_tgt,
-                        const double *gam_src, const double *dgam_src,
+                        const double *gam_src, const double *dgam_src, int ndir,
                         const double *pg_tgt, const double *pdg_tgt,
                         const double *pg_src, const double *pdg_src,
                         const cplx *dens_tgt, int nrhs, cplx *u, cplx *du)
 {
     if (p < 0 || p + 2 >= ORC_MAXN || q_tgt < 1 || q_src < 1 || q_tgt > ORC_MAXN || q_src > ORC_MAXN ||
-        M < 1 || nrhs < 1)
+        M < 1 || nrhs < 1 || ndir < 1)
         return 1;
     cplx k = kre + I * kim;
     int n_tgt = M * q_tgt, n_src = M * q_src, nl = 2 * p + 1;
-    size_t nd_s = (size_t)n_src, nd_t = (size_t)n_tgt;
-    double *buf = malloc(sizeof(double) * (10 * nd_s + 17 * nd_t + 2 * (size_t)M));
+    size_t nd_s = (size_t)n_src, nd_t = (size_t)n_tgt, nd = (size_t)ndir;
+    double *buf = malloc(sizeof(double) * (7 * nd_s + 17 * nd_t + (size_t)M));
+    double *dbuf = malloc(sizeof(double) * nd * (3 * nd_s + 4 * nd_t + (size_t)M));
     cplx *psig = malloc(sizeof(cplx) * nd_s * nrhs);
     cplx *wd = malloc(sizeof(cplx) * nd_s * nrhs);
-    if (!buf || !psig || !wd) { free(buf); free(psig); free(wd); return 2; }
+    if (!buf || !dbuf || !psig || !wd) { free(buf); free(dbuf); free(psig); free(wd); return 2; }
     double *src_x = buf, *src_y = src_x + nd_s, *src_nx = src_y + nd_s, *src_ny = src_nx + nd_s;
-    double *src_w = src_ny + nd_s, *ones = src_w + nd_s;
-    double *d_sx = ones + nd_s, *d_sy = d_sx + nd_s, *d_sw = d_sy + nd_s, *unused = d_sw + nd_s;
-    double *tgt_x = unused + nd_s, *tgt_y = tgt_x + nd_t, *tgt_nx = tgt_y + nd_t, *tgt_ny = tgt_nx + nd_t;
+    double *src_w = src_ny + nd_s, *ones = src_w + nd_s, *spare = ones + nd_s;
+    double *tgt_x = spare + nd_s, *tgt_y = tgt_x + nd_t, *tgt_nx = tgt_y + nd_t, *tgt_ny = tgt_nx + nd_t;
     double *tgt_w = tgt_ny + nd_t;
     double *ctr_x = tgt_w + nd_t, *ctr_y = ctr_x + 2 * nd_t, *ctr_r = ctr_y + 2 * nd_t;
-    double *ctr_ratio = ctr_r + 2 * nd_t, *d_cx = ctr_ratio + 2 * nd_t, *d_cy = d_cx + 2 * nd_t;
-    double *panel_h = d_cy + 2 * nd_t, *d_h = panel_h + M;
-    (void)unused;
+    double *ctr_ratio = ctr_r + 2 * nd_t, *spare2 = ctr_ratio + 2 * nd_t;
+    double *panel_h = spare2 + 4 * nd_t;
+    /* per direction: d_sx, d_sy, d_sw [n_src]; d_cx, d_cy [2 n_tgt]; d_h [M] */
+    double *d_sx = dbuf, *d_sy = d_sx + nd * nd_s, *d_sw = d_sy + nd * nd_s;
+    double *d_cx = d_sw + nd * nd_s, *d_cy = d_cx + nd * 2 * nd_t, *d_h = d_cy + nd * 2 * nd_t;
+    (void)spare; (void)spare2;
     orc_geometry(M, q_tgt, q_src, t_edges, gam_tgt, dgam_tgt, gam_src, dgam_src, r_factor,
                  src_x, src_y, src_nx, src_ny, src_w, tgt_x, tgt_y, tgt_nx, tgt_ny, tgt_w,
                  panel_h, ctr_x, ctr_y, ctr_r, ctr_ratio);
     double xs[ORC_MAXN], ws[ORC_MAXN];
     orc_gauss_legendre(q_src, xs, ws);
-    /* tangents of the source nodes, weights and panel lengths */
-    for (int m = 0; m < M; ++m) {
-        double half = 0.5 * (t_edges[m + 1] - t_edges[m]), dh = 0.0;
-        for (int j = 0; j < q_src; ++j) {
-            int s = m * q_src + j;
-            double vx = dgam_src[2 * s], vy = dgam_src[2 * s + 1];
-            double sp = sqrt(vx * vx + vy * vy);
-            double tp = (vx * pdg_src[2 * s] + vy * pdg_src[2 * s + 1]) / sp;   /* tau . pdg */
-            d_sw[s] = ws[j] * half * tp;
-            dh += d_sw[s];
-            d_sx[s] = pg_src[2 * s];
-            d_sy[s] = pg_src[2 * s + 1];
-            ones[s] = 1.0;
+    for (int s = 0; s < n_src; ++s) ones[s] = 1.0;
+    for (int d = 0; d < ndir; ++d) {
+        const double *pgs = pg_src + (size_t)d * 2 * nd_s, *pdgs = pdg_src + (size_t)d * 2 * nd_s;
+        const double *pgt = pg_tgt + (size_t)d * 2 * nd_t, *pdgt = pdg_tgt + (size_t)d * 2 * nd_t;
+        double *dsx = d_sx + d * nd_s, *dsy = d_sy + d * nd_s, *dsw = d_sw + d * nd_s;
+        double *dcx = d_cx + d * 2 * nd_t, *dcy = d_cy + d * 2 * nd_t, *dh = d_h + (size_t)d * M;
+        /* tangents of the source nodes, weights and panel lengths */
+        for (int m = 0; m < M; ++m) {
+            double half = 0.5 * (t_edges[m + 1] - t_edges[m]), acc = 0.0;
+            for (int j = 0; j < q_src; ++j) {
+                int s = m * q_src + j;
+                double vx = dgam_src[2 * s], vy = dgam_src[2 * s + 1];
+                double sp = sqrt(vx * vx + vy * vy);
+                double tp = (vx * pdgs[2 * s] + vy * pdgs[2 * s + 1]) / sp;   /* tau . pdg */
+                dsw[s] = ws[j] * half * tp;
+                acc += dsw[s];
+                dsx[s] = pgs[2 * s];
+                dsy[s] = pgs[2 * s + 1];
+            }
+            dh[m] = acc;
         }
-        d_h[m] = dh;
-    }
-    /* tangents of the centres */
-    for (int t = 0; t < n_tgt; ++t) {
-        int m = t / q_tgt;
-        double vx = dgam_tgt[2 * t], vy = dgam_tgt[2 * t + 1];
-        double sp = sqrt(vx * vx + vy * vy);
-        double px = pdg_tgt[2 * t], py = pdg_tgt[2 * t + 1];
-        double tp = (vx * px + vy * py) / sp;
-        double dnx = (py - tgt_nx[t] * tp) / sp, dny = (-px - tgt_ny[t] * tp) / sp;
-        double r = ctr_r[t], dr = r_factor * d_h[m];
-        double ox = dr * tgt_nx[t] + r * dnx, oy = dr * tgt_ny[t] + r * dny;
-        d_cx[t] = pg_tgt[2 * t] - ox;
-        d_cy[t] = pg_tgt[2 * t + 1] - oy;
-        d_cx[n_tgt + t] = pg_tgt[2 * t] + ox;
-        d_cy[n_tgt + t] = pg_tgt[2 * t + 1] + oy;
+        /* tangents of the centres */
+        for (int t = 0; t < n_tgt; ++t) {
+            int m = t / q_tgt;
+            double vx = dgam_tgt[2 * t], vy = dgam_tgt[2 * t + 1];
+            double sp = sqrt(vx * vx + vy * vy);
+            double px = pdgt[2 * t], py = pdgt[2 * t + 1];
+            double tp = (vx * px + vy * py) / sp;
+            double dnx = (py - tgt_nx[t] * tp) / sp, dny = (-px - tgt_ny[t] * tp) / sp;
+            double r = ctr_r[t], dr = r_factor * dh[m];
+            double ox = dr * tgt_nx[t] + r * dnx, oy = dr * tgt_ny[t] + r * dny;
+            dcx[t] = pgt[2 * t] - ox;
+            dcy[t] = pgt[2 * t + 1] - oy;
+            dcx[n_tgt + t] = pgt[2 * t] + ox;
+            dcy[n_tgt + t] = pgt[2 * t + 1] + oy;
+        }
     }
     orc_upsample(M, q_tgt, q_src, nrhs, ones, dens_tgt, psig);     /* P sigma */
     for (size_t i = 0; i < nd_s * nrhs; ++i) wd[i] = src_w[i / nrhs] * psig[i];
-    for (size_t i = 0; i < nd_t * nrhs; ++i) u[i] = du[i] = 0.0;
+    for (size_t i = 0; i < nd_t * nrhs; ++i) u[i] = 0.0;
+    for (size_t i = 0; i < nd * nd_t * nrhs; ++i) du[i] = 0.0;
     int s0 = (side == SIDE_TWO) ? SIDE_INT : side;
     int s1 = (side == SIDE_TWO) ? SIDE_EXT : side;
     double wgt = (side == SIDE_TWO) ? 0.5 : 1.0;
@@ -753,58 +764,66 @@ int orc_apply_s_tangent(int side, double kre, double kim, int p, int M, int q_tg
         #pragma omp parallel for schedule(dynamic, 4)
         for (int t = 0; t < n_tgt; ++t) {
             cplx H[ORC_MAXN], J[ORC_MAXN];
-            cplx *al = malloc(sizeof(cplx) * 2 * (size_t)nl * nrhs);
+            cplx *al = malloc(sizeof(cplx) * (1 + nd) * (size_t)nl * nrhs);
             if (!al) {
                 #pragma omp atomic write
                 fail = 1;
                 continue;
             }
-            cplx *dal = al + (size_t)nl * nrhs;
-            for (size_t i = 0; i < 2 * (size_t)nl * nrhs; ++i) al[i] = 0.0;
+            cplx *dal = al + (size_t)nl * nrhs;             /* [ndir][nl][nrhs] */
+            for (size_t i = 0; i < (1 + nd) * (size_t)nl * nrhs; ++i) al[i] = 0.0;
             int c = sd * n_tgt + t;
-            double cx = ctr_x[c], cy = ctr_y[c], dcx = d_cx[c], dcy = d_cy[c];
+            double cx = ctr_x[c], cy = ctr_y[c];
             for (int s = 0; s < n_src; ++s) {
                 double dx = src_x[s] - cx, dy = src_y[s] - cy;
-                double ddx = d_sx[s] - dcx, ddy = d_sy[s] - dcy;
                 double rho = hypot(dx, dy), th = atan2(dy, dx);
-                double drho = (dx * ddx + dy * ddy) / rho;
-                double dth = (dx * ddy - dy * ddx) / (rho * rho);
                 orc_hankel_seq(k * rho, p + 1, H);
                 for (int l = -p; l <= p; ++l) {
                     cplx hl = Z_signed(l, H);
                     cplx hd = (Z_signed(l - 1, H) - Z_signed(l + 1, H)) / 2.0;
                     cplx e = cexp(-I * (double)l * th);
                     cplx kern = hl * e;
-                    cplx dkern = (k * hd * drho - I * (double)l * hl * dth) * e;
-                    for (int r = 0; r < nrhs; ++r) {
-                        size_t sr = (size_t)s * nrhs + r;
-                        cplx dwd = d_sw[s] * psig[sr];
-                        al[(size_t)(l + p) * nrhs + r] += (I / 4.0) * wd[sr] * kern;
-                        dal[(size_t)(l + p) * nrhs + r] += (I / 4.0) * (dwd * kern + wd[sr] * dkern);
+                    for (int r = 0; r < nrhs; ++r)
+                        al[(size_t)(l + p) * nrhs + r] += (I / 4.0) * wd[(size_t)s * nrhs + r] * kern;
+                    for (int d = 0; d < ndir; ++d) {
+                        double ddx = d_sx[d * nd_s + s] - d_cx[d * 2 * nd_t + c];
+                        double ddy = d_sy[d * nd_s + s] - d_cy[d * 2 * nd_t + c];
+                        double drho = (dx * ddx + dy * ddy) / rho;
+                        double dth = (dx * ddy - dy * ddx) / (rho * rho);
+                        cplx dkern = (k * hd * drho - I * (double)l * hl * dth) * e;
+                        for (int r = 0; r < nrhs; ++r) {
+                            size_t sr = (size_t)s * nrhs + r;
+                            cplx dwd = d_sw[d * nd_s + s] * psig[sr];
+                            dal[((size_t)d * nl + (l + p)) * nrhs + r] += (I / 4.0) * (dwd * kern + wd[sr] * dkern);
+                        }
                     }
                 }
             }
             double ex = tgt_x[t] - cx, ey = tgt_y[t] - cy;
-            double dex = pg_tgt[2 * t] - dcx, dey = pg_tgt[2 * t + 1] - dcy;
             double rt = hypot(ex, ey), tht = atan2(ey, ex);
-            double drt = (ex * dex + ey * dey) / rt;
-            double dtht = (ex * dey - ey * dex) / (rt * rt);
             orc_besselj_seq(k * rt, p + 1, J);
             for (int l = -p; l <= p; ++l) {
                 cplx jl = Z_signed(l, J);
                 cplx jd = (Z_signed(l - 1, J) - Z_signed(l + 1, J)) / 2.0;
                 cplx e = cexp(I * (double)l * tht);
-                cplx dfac = (k * jd * drt + I * (double)l * jl * dtht) * e;
-                for (int r = 0; r < nrhs; ++r) {
-                    cplx a = al[(size_t)(l + p) * nrhs + r], da = dal[(size_t)(l + p) * nrhs + r];
-                    u[(size_t)t * nrhs + r] += wgt * a * jl * e;
-                    du[(size_t)t * nrhs + r] += wgt * (da * jl * e + a * dfac);
+                for (int r = 0; r < nrhs; ++r)
+                    u[(size_t)t * nrhs + r] += wgt * al[(size_t)(l + p) * nrhs + r] * jl * e;
+                for (int d = 0; d < ndir; ++d) {
+                    const double *pgt = pg_tgt + (size_t)d * 2 * nd_t;
+                    double dex = pgt[2 * t] - d_cx[d * 2 * nd_t + c], dey = pgt[2 * t + 1] - d_cy[d * 2 * nd_t + c];
+                    double drt = (ex * dex + ey * dey) / rt;
+                    double dtht = (ex * dey - ey * dex) / (rt * rt);
+                    cplx dfac = (k * jd * drt + I * (double)l * jl * dtht) * e;
+                    for (int r = 0; r < nrhs; ++r) {
+                        cplx a = al[(size_t)(l + p) * nrhs + r], da = dal[((size_t)d * nl + (l + p)) * nrhs + r];
+                        du[((size_t)d * nd_t + t) * nrhs + r] += wgt * (da * jl * e + a * dfac);
+                    }
                 }
             }
             free(al);
         }
     }
-    free(buf); free(psig); free(wd);
+    free(buf); free(dbuf); free(psig); free(wd);
     return fail ? 2 : 0;
 }
 

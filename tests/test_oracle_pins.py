@@ -543,6 +543,10 @@ def test_shape_tangent_rigid_motions():
         _, du_r = oracle.apply_s_tangent(cur, rot, edges, 16, 64, side, k, p, dens)
         assert np.abs(du_t).max() < 1e-13 * np.abs(u).max()
         assert np.abs(du_r).max() < 1e-11 * np.abs(u).max()
+    # several directions in one call give the same derivatives
+    _, both = oracle.apply_s_tangent(cur, [shift, rot, _fourier_pert(3, "cos")], edges, 16, 64, TWO, k, p, dens)
+    _, one = oracle.apply_s_tangent(cur, _fourier_pert(3, "cos"), edges, 16, 64, TWO, k, p, dens)
+    assert both.shape[0] == 3 and np.array_equal(both[2], one)
 
 
 def test_shape_tangent_scaling_identity():
