@@ -369,7 +369,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--cpu-sample", type=int, default=192, help="targets in the CPU-baseline sample")
+    ap.add_argument("--cpu-sample", type=int, default=1536, help="targets in the CPU-baseline sample (about 15 s of oracle work)")
     ap.add_argument("--ref-sample", type=int, default=48, help="targets per step of --impl reference")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true",

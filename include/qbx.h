@@ -221,6 +221,35 @@ int qbx_assign_centres(qbx_plan *plan, const qbx_geom *g, int side, int n, const
 int qbx_apply_adjoint(qbx_plan *plan, const qbx_geom *g, int op, int side, int limit, qbx_c64 k, int p,
                       const qbx_c64 *gout, int nrhs, qbx_c64 *gdens, void *stream);
 
+/* Shape adjoint of the on-surface S apply: for u = S sigma at the targets
+ * (side INT, EXT or TWO; S is continuous, so the limit does not enter) and
+ * the real functional L = Re sum_{t,r} conj(gout[t][r]) u[t][r], the
+ * gradient of L with respect to the curve samples that qbx_geometry
+ * consumed: gamma and gamma' at the target nodes and at the source nodes
+ * (every quantity of Sec. 3.3 step 4a -- normals, weights, panel lengths,
+ * radii, centres -- is differentiated; the density stays fixed on the
+ * target grid as a function of the curve parameter).  With torch's complex
+ * convention gout = dL/dRe u + i dL/dIm u this is the vector-Jacobian
+ * product of u.  Two sweeps recompute the Hankel recurrences (centres ->
+ * sources for grad_x and grad_{x_s} of the Graf sum of eq. graf-addition,
+ * sources -> centres for the transposed sums); nothing is stored from the
+ * forward apply.
+ *   dens_tgt, gout: [n_tgt][nrhs] complex device arrays;
+ *   dgam_tgt [n_tgt][2], dgam_src [n_src][2]: the gamma' samples given to
+ *     qbx_geometry (device);
+ *   g_gam_tgt, g_dgam_tgt [n_tgt][2], g_gam_src, g_dgam_src [n_src][2]:
+ *     device outputs, overwritten (summed over the right-hand sides).
+ * Uses the plan's workspace (qbx_shape_adjoint_workspace_bytes); too small
+ * a workspace gives QBX_ENOMEM, bad arguments QBX_EINVAL, nothing launched. */
+int qbx_apply_shape_adjoint(qbx_plan *plan, const qbx_geom *g, int side, qbx_c64 k, int p,
+                            const qbx_c64 *dens_tgt, const qbx_c64 *gout, int nrhs,
+                            const double *dgam_tgt, const double *dgam_src, double *g_gam_tgt,
+                            double *g_dgam_tgt, double *g_gam_src, double *g_dgam_src, void *stream);
+
+/* Workspace for qbx_apply_shape_adjoint with up to 64 splits of each sweep
+ * (any side).  Host, pure function; 0 on bad arguments. */
+size_t qbx_shape_adjoint_workspace_bytes(int M, int q_tgt, int q_src, int p, int nrhs);
+
 /* Second-kind exterior Dirichlet (sound-soft) solve, Sec. 4.2 eq.
  * dirichlet-inteq with the exterior sign and the combined-field coupling
  * alpha = -i eta:  (1/2) mu + D mu - i eta S mu = f  on Gamma, D and S as

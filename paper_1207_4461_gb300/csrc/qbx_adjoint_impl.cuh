@@ -1,5 +1,7 @@
 // qbx_adjoint_impl.cuh -- the transposed QBX sweep: the adjoint of the
-// on-surface apply of S or D with respect to the density.  For
+// on-surface apply of S or D with respect to the density, and (operator set
+// S|X) the sums over centres that the shape adjoint of S needs: conj(K) g_c
+// and conj(grad_{x_s} K) g_c per source.  For
 // u = (i/4) K W P sigma (kernel values K(c, x_s), source weights W, per-panel
 // interpolation P), the vector-Jacobian product of a gradient g on the
 // targets is  P^T W K^H (-i/4) g  (plus the self-adjoint jump term for PV).
@@ -19,8 +21,8 @@ template <int OPS, typename T>
 __global__ void k_coef_columns(AdjArgs a) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= a.n_ctr) return;
-  constexpr bool kD = OPS & OPB_D, kG = OPS & OPB_G;
-  constexpr int ns = 1 + ((kD || kG) ? 1 : 0) + (kG ? 1 : 0);
+  constexpr bool kD = OPS & OPB_D, kG = OPS & OPB_G, kX = OPS & OPB_X;
+  constexpr int ns = 1 + ((kD || kG || kX) ? 1 : 0) + (kG ? 1 : 0);
   const int P2 = a.p + 2;
   T* col = reinterpret_cast<T*>(a.coef) + (size_t)c * ns * P2;
   KW<T> kw;
@@ -33,7 +35,7 @@ __global__ void k_coef_columns(AdjArgs a) {
   besselj_seq<T>(rmul(kk, r), a.p + 1, col, 1);
   for (int l = 0; l <= a.p; ++l) {
     const T jl = col[l];
-    if (kD || kG) col[P2 + l] = rmul(jl, (double)l);
+    if (kD || kG || kX) col[P2 + l] = rmul(jl, (double)l);
     if (kG) {
       const T jn = col[l + 1];
       const T jp = (l == 0) ? jn : col[l - 1];
@@ -52,8 +54,8 @@ __global__ void k_coef_columns(AdjArgs a) {
 template <int OPS, typename T, int RG>
 struct AdjSmem {
   static constexpr int kNc = ops_ncomp(OPS);
-  static constexpr bool kD = OPS & OPB_D, kG = OPS & OPB_G;
-  static __host__ __device__ constexpr int nslots() { return 1 + ((kD || kG) ? 1 : 0) + (kG ? 1 : 0); }
+  static constexpr bool kD = OPS & OPB_D, kG = OPS & OPB_G, kX = OPS & OPB_X;
+  static __host__ __device__ constexpr int nslots() { return 1 + ((kD || kG || kX) ? 1 : 0) + (kG ? 1 : 0); }
   static __host__ __device__ size_t bytes(int p) {
     return 5 * kGrpTile * 8 +                                   // centre x, y, ux, uy, 1/r
            (size_t)kGrpTile * kGrpWarps * RG * 16 +              // gradients [centre][4 RG]
@@ -67,7 +69,7 @@ template <int OPS, typename T, int RG>
 __global__ void __launch_bounds__(kGrpCentres * kGrpWarps)
 k_adjoint(AdjArgs a) {
   using L = AdjSmem<OPS, T, RG>;
-  constexpr bool kS = OPS & OPB_S, kD = OPS & OPB_D;
+  constexpr bool kS = OPS & OPB_S, kD = OPS & OPB_D, kX = OPS & OPB_X;
   constexpr int kNc = L::kNc;
   constexpr int kRP = kGrpWarps * RG;
   constexpr int ns = L::nslots();
@@ -135,12 +137,16 @@ k_adjoint(AdjArgs a) {
         const T* cG = s_col + 2 * P2 * kGrpTile + j;
         const T J0 = cJ[0];
         const T kneg_j0 = rmul(sc_mul(kk, J0), -1.0);
-        cplx GS, K, GA, GB;
+        cplx GS, K, GA, GB, EX, EY;
         pair_kernels<OPS, T, kGrpTile>(kw, kk, J0, kneg_j0, cJ, cL, cG, p, dx, dy, snx, sny, s_ux[j], s_uy[j],
-                                       GS, K, GA, GB);
+                                       GS, K, GA, GB, EX, EY);
         int q = 0;
         if (kS) s_kv[(q++ * kGrpTile + j) * kGrpCentres + lane] = GS;
         if (kD) s_kv[(q++ * kGrpTile + j) * kGrpCentres + lane] = K;
+        if (kX) {
+          s_kv[(q++ * kGrpTile + j) * kGrpCentres + lane] = EX;
+          s_kv[(q++ * kGrpTile + j) * kGrpCentres + lane] = EY;
+        }
       }
       __syncthreads();
       // ---- phase 2: sum_c conj(K) g_c for this warp's rhs ----
@@ -188,6 +194,8 @@ static cudaError_t launch_adjoint_any(const AdjArgs& a, cudaStream_t st) {
   switch (a.ops) {
     case OPB_S: return many ? launch_adjoint_t<OPB_S, T, 8>(a, st) : launch_adjoint_t<OPB_S, T, 2>(a, st);
     case OPB_D: return many ? launch_adjoint_t<OPB_D, T, 8>(a, st) : launch_adjoint_t<OPB_D, T, 2>(a, st);
+    case OPB_S | OPB_X:
+      return many ? launch_adjoint_t<OPB_S | OPB_X, T, 8>(a, st) : launch_adjoint_t<OPB_S | OPB_X, T, 2>(a, st);
     default: return cudaErrorInvalidValue;
   }
 }

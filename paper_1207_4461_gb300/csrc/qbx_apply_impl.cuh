@@ -31,7 +31,7 @@
 
 namespace qbx {
 
-enum { OPB_S = 1, OPB_D = 2, OPB_G = 4 };
+enum { OPB_S = 1, OPB_D = 2, OPB_G = 4, OPB_X = 8 };
 
 // ---- scalar helpers for T = double (real k) or cplx (complex k) ----------
 __device__ __forceinline__ void madd(cplx& acc, double e, cplx h) {
@@ -103,8 +103,12 @@ template <> struct KW<cplx> {
 };
 
 __host__ __device__ constexpr int popc3(int m) { return (m & 1) + ((m >> 1) & 1) + ((m >> 2) & 1); }
-// partial-sum components: S -> 1, D -> 1, grad S -> 2 (in this order)
-__host__ __device__ constexpr int ops_ncomp(int m) { return (m & 1) + ((m >> 1) & 1) + 2 * ((m >> 2) & 1); }
+// several accumulator sets per rhs: at most 4 rhs per launch
+__host__ __device__ constexpr bool multi_op(int m) { return popc3(m) > 1 || (m & 8) != 0; }
+// partial-sum components: S -> 1, D -> 1, grad S -> 2, grad_{x_s} S -> 2 (in this order)
+__host__ __device__ constexpr int ops_ncomp(int m) {
+  return (m & 1) + ((m >> 1) & 1) + 2 * ((m >> 2) & 1) + 2 * ((m >> 3) & 1);
+}
 
 // Shared memory layout (bytes): source tile x, y [, nx, ny] ; densities
 // [nops][tile][NR] ; per-centre coefficient slots [(p+2)][kApplyThreads] of
@@ -112,7 +116,7 @@ __host__ __device__ constexpr int ops_ncomp(int m) { return (m & 1) + ((m >> 1) 
 // (J_{l-1} - J_{l+1}; with grad S).
 template <int OPS, typename T, int NR>
 struct ApplySmem {
-  static constexpr int kNops = popc3(OPS);
+  static constexpr int kNops = popc3(OPS);   // density slots (X shares grad S's)
   static constexpr bool kS = OPS & OPB_S, kD = OPS & OPB_D, kG = OPS & OPB_G;
   static constexpr int kGeo = kD ? 4 : 2;
   static __host__ __device__ size_t tile_bytes() {
@@ -126,16 +130,20 @@ struct ApplySmem {
 
 // The kernel values of one (centre, source) pair for the operator set OPS,
 // without the factor i/4: GS (S), K (D), GA and GB (grad S: the e_r and
-// e_theta sums before scaling).  (dx, dy) = x_s - c, (nx, ny) = n_s,
+// e_theta sums before scaling), EX and EY (X: the gradient of the S kernel
+// with respect to the source position).  (dx, dy) = x_s - c, (nx, ny) = n_s,
 // (ux, uy) = unit vector from c to its target; cJ, cL, cG: the centre's
 // coefficient columns (J_l, l J_l, J_{l-1} - J_{l+1}) with stride STRIDE.
 template <int OPS, typename T, int STRIDE>
 __device__ __forceinline__ void pair_kernels(const KW<T>& kw, const T kk, const T J0, const T kneg_j0,
                                              const T* cJ, const T* cL, const T* cG, int p, double dx,
                                              double dy, double nx, double ny, double ux, double uy,
-                                             cplx& GS, cplx& K, cplx& GA, cplx& GB) {
-  constexpr bool kS = OPS & OPB_S, kD = OPS & OPB_D, kG = OPS & OPB_G;
+                                             cplx& GS, cplx& K, cplx& GA, cplx& GB, cplx& EX, cplx& EY) {
+  constexpr bool kS = OPS & OPB_S, kD = OPS & OPB_D, kG = OPS & OPB_G, kX = OPS & OPB_X;
+  static_assert(!(kX && kD), "the source-position gradient is not combined with D");
   constexpr bool kDsum = kD && kG;
+  constexpr bool kSums = kDsum || kX;   // D1, D3 (and the sin sum GB)
+  constexpr bool kB = kG || kX;         // GB = sum l J_l sin(l psi) H_l
   // ---- a2: pair geometry and H0, H1 ----
   const double rho2 = fma(dx, dx, dy * dy);
   double inv, rho, yq;
@@ -146,7 +154,7 @@ __device__ __forceinline__ void pair_kernels(const KW<T>& kw, const T kk, const 
   kw.hankel(rho, inv, yq, H0, H1, twoz);
   const double tw = 2.0 * cs;
   double sn = 0.0;
-  if (kD || kG) sn = fma(uy, dx, -ux * dy) * inv;  // sin psi
+  if (kD || kB) sn = fma(uy, dx, -ux * dy) * inv;  // sin psi
   double av = 0.0, bv = 0.0;
   if (kD) {
     av = fma(nx, dx, ny * dy) * inv;   // n_s . e_rho
@@ -177,17 +185,15 @@ __device__ __forceinline__ void pair_kernels(const KW<T>& kw, const T kk, const 
   double cp = 1.0, cl = cs, sp = 0.0, sl = sn;
   for (int l = 1; l <= p; ++l) {
     const int o = l * STRIDE;
-    if (kS || kDsum) {
+    if (kS || kSums) {
       const T tS = rmul(cJ[o], cl);                  // J_l cos(l psi)
       if (kS) madd(GS, tS, H);
-      if (kDsum) madd(D1, tS, Hm);
+      if (kSums) madd(D1, tS, Hm);
     }
-    if (kDsum) madd(D3, rmul(cL[o], cl), H);
+    if (kSums) madd(D3, rmul(cL[o], cl), H);
     if (kD && !kDsum) madd(K, dcoef(cJ[o + STRIDE], Cc, cL[o], Vc), H);
-    if (kG) {
-      madd(GA, rmul(cG[o], cl), H);
-      madd(GB, rmul(cL[o], sl), H);
-    }
+    if (kG) madd(GA, rmul(cG[o], cl), H);
+    if (kB) madd(GB, rmul(cL[o], sl), H);
     if (l < p) {
       const cplx Hn = hrec(s, H, Hm);
       Hm = H;
@@ -196,7 +202,7 @@ __device__ __forceinline__ void pair_kernels(const KW<T>& kw, const T kk, const 
       const double cn = fma(tw, cl, -cp);
       cp = cl;
       cl = cn;
-      if (kG) {
+      if (kB) {
         const double sq = fma(tw, sl, -sp);
         sp = sl;
         sl = sq;
@@ -221,6 +227,16 @@ __device__ __forceinline__ void pair_kernels(const KW<T>& kw, const T kk, const 
     K = smul(sc_mul(ka, rmul(J0, -1.0)), H1) + smul(rmul(ka, 2.0), D1) +
         (i2 * bv) * GB - (i2 * av) * D3;
   }
+  if (kX) {
+    // grad_{x_s} of the S kernel: the D kernel is linear in the normal,
+    // n . (e_rho R + e_theta Q), R = -k J0 H1 + 2 k D1 - (2/rho) D3,
+    // Q = (2/rho) D2; e_rho = (dx, dy)/rho, e_theta = (-dy, dx)/rho
+    const double i2 = 2.0 * inv;
+    const cplx R = smul(kneg_j0, H1) + smul(rmul(kk, 2.0), D1) - i2 * D3;
+    const cplx Q = i2 * GB;
+    EX = (dx * R - dy * Q) * inv;
+    EY = (dy * R + dx * Q) * inv;
+  }
 }
 
 // D through sums shared with grad S when both are requested:
@@ -232,7 +248,8 @@ template <int OPS, typename T, int NR>
 __global__ void __launch_bounds__(kApplyThreads)
 k_apply_fused(ApplyArgs a) {
   using L = ApplySmem<OPS, T, NR>;
-  constexpr bool kS = L::kS, kD = L::kD, kG = L::kG;
+  constexpr bool kS = L::kS, kD = L::kD, kG = L::kG, kX = OPS & OPB_X;
+  static_assert(!kX || kG, "X is formed with grad S and shares its density");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* s_x = reinterpret_cast<double*>(smem_raw);
   double* s_y = s_x + kSrcTile;
@@ -283,9 +300,9 @@ k_apply_fused(ApplyArgs a) {
   }
   const T kneg_j0 = rmul(sc_mul(kk, J0), -1.0);  // -k J0 (D)
 
-  cplx accS[NR], accD[NR], accA[NR], accB[NR];
+  cplx accS[NR], accD[NR], accA[NR], accB[NR], accX[NR], accY[NR];
 #pragma unroll
-  for (int q = 0; q < NR; ++q) accS[q] = accD[q] = accA[q] = accB[q] = cplx{0.0, 0.0};
+  for (int q = 0; q < NR; ++q) accS[q] = accD[q] = accA[q] = accB[q] = accX[q] = accY[q] = cplx{0.0, 0.0};
 
   const int s_begin = blockIdx.y * a.src_per_split;
   const int s_end = min(a.src.n, s_begin + a.src_per_split);
@@ -331,9 +348,9 @@ k_apply_fused(ApplyArgs a) {
         nx = s_nx[j];
         ny = s_ny[j];
       }
-      cplx GS, K, GA, GB;
+      cplx GS, K, GA, GB, EX, EY;
       pair_kernels<OPS, T, kApplyThreads>(kw, kk, J0, kneg_j0, cJ, cL, cG, p, dx, dy, nx, ny, ux, uy, GS,
-                                           K, GA, GB);
+                                           K, GA, GB, EX, EY);
       // ---- weighted densities ----
       int slotn = 0;
       if (kS) {
@@ -354,6 +371,10 @@ k_apply_fused(ApplyArgs a) {
         for (int q = 0; q < NR; ++q) {
           accA[q] = accA[q] + w[q] * GA;
           accB[q] = accB[q] + w[q] * GB;
+          if (kX) {
+            accX[q] = accX[q] + w[q] * EX;
+            accY[q] = accY[q] + w[q] * EY;
+          }
         }
       }
     }
@@ -375,6 +396,10 @@ k_apply_fused(ApplyArgs a) {
       part[(row + comp++) * a.nrhs + a.rhs0 + q] = kA * ux + Bi * uy;
       part[(row + comp++) * a.nrhs + a.rhs0 + q] = kA * uy - Bi * ux;
     }
+    if (kX) {
+      part[(row + comp++) * a.nrhs + a.rhs0 + q] = accX[q];
+      part[(row + comp++) * a.nrhs + a.rhs0 + q] = accY[q];
+    }
   }
 }
 
@@ -393,7 +418,7 @@ static cudaError_t launch_apply_t(const ApplyArgs& a, cudaStream_t st) {
 template <int OPS, typename T>
 static cudaError_t launch_apply_nr(const ApplyArgs& a, cudaStream_t st) {
   if (a.nr <= 1) return launch_apply_t<OPS, T, 1>(a, st);
-  if constexpr (popc3(OPS) > 1) {
+  if constexpr (multi_op(OPS)) {
     return launch_apply_t<OPS, T, 4>(a, st);
   } else {
     if (a.nr <= 4) return launch_apply_t<OPS, T, 4>(a, st);
@@ -403,14 +428,14 @@ static cudaError_t launch_apply_nr(const ApplyArgs& a, cudaStream_t st) {
 
 template <typename T>
 static size_t apply_smem_t(int ops, int p, int nr) {
-  const int nr_t = nr <= 1 ? 1 : (nr <= 4 || popc3(ops) > 1 ? 4 : 8);
+  const int nr_t = nr <= 1 ? 1 : (nr <= 4 || multi_op(ops) ? 4 : 8);
 #define QBX_SM(O)                                                                   \
   case O:                                                                           \
     return nr_t == 1 ? ApplySmem<O, T, 1>::bytes(p)                                 \
                      : (nr_t == 4 ? ApplySmem<O, T, 4>::bytes(p) : ApplySmem<O, T, 8>::bytes(p));
   // (ApplySmem is a size calculator only; no kernel is instantiated here)
   switch (ops) {
-    QBX_SM(1) QBX_SM(2) QBX_SM(3) QBX_SM(4) QBX_SM(5) QBX_SM(6) QBX_SM(7)
+    QBX_SM(1) QBX_SM(2) QBX_SM(3) QBX_SM(4) QBX_SM(5) QBX_SM(6) QBX_SM(7) QBX_SM(12)
     default: return 0;
   }
 #undef QBX_SM
@@ -427,7 +452,7 @@ static int occupancy_t(int p, int nr) {
     return n;
   };
   if (nr <= 1) return occ(k_apply_fused<OPS, T, 1>, ApplySmem<OPS, T, 1>::bytes(p));
-  if constexpr (popc3(OPS) > 1) {
+  if constexpr (multi_op(OPS)) {
     return occ(k_apply_fused<OPS, T, 4>, ApplySmem<OPS, T, 4>::bytes(p));
   } else {
     if (nr <= 4) return occ(k_apply_fused<OPS, T, 4>, ApplySmem<OPS, T, 4>::bytes(p));
@@ -445,6 +470,7 @@ static int apply_occupancy_t(int ops, int p, int nr) {
     case OPB_S | OPB_G: return occupancy_t<OPB_S | OPB_G, T>(p, nr);
     case OPB_D | OPB_G: return occupancy_t<OPB_D | OPB_G, T>(p, nr);
     case OPB_S | OPB_D | OPB_G: return occupancy_t<OPB_S | OPB_D | OPB_G, T>(p, nr);
+    case OPB_G | OPB_X: return occupancy_t<OPB_G | OPB_X, T>(p, nr);
     default: return 0;
   }
 }
@@ -459,6 +485,7 @@ static cudaError_t launch_apply_ops(const ApplyArgs& a, cudaStream_t st) {
     case OPB_S | OPB_G: return launch_apply_nr<OPB_S | OPB_G, T>(a, st);
     case OPB_D | OPB_G: return launch_apply_nr<OPB_D | OPB_G, T>(a, st);
     case OPB_S | OPB_D | OPB_G: return launch_apply_nr<OPB_S | OPB_D | OPB_G, T>(a, st);
+    case OPB_G | OPB_X: return launch_apply_nr<OPB_G | OPB_X, T>(a, st);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -148,9 +148,9 @@ k_apply_group(GroupArgs a) {
             nx = s_nx[j];
             ny = s_ny[j];
           }
-          cplx GS, K, GA, GB;
+          cplx GS, K, GA, GB, EX, EY;
           pair_kernels<OPS, T, kGrpCentres>(kw, kk, J0, kneg_j0, colJ, colL, colG, p, dx, dy, nx, ny, ux,
-                                            uy, GS, K, GA, GB);
+                                            uy, GS, K, GA, GB, EX, EY);
           int q = 0;
           if (kS) s_kv[(q++ * kGrpTile + j) * kGrpCentres + lane] = GS;
           if (kD) s_kv[(q++ * kGrpTile + j) * kGrpCentres + lane] = K;

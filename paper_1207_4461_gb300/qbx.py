@@ -93,6 +93,10 @@ def lib():
             L.qbx_solve_exterior_dirichlet.restype = I
             L.qbx_apply_adjoint.argtypes = [_P, G, I, I, I, c64, I, _P, I, _P, _P]
             L.qbx_apply_adjoint.restype = I
+            L.qbx_apply_shape_adjoint.argtypes = [_P, G, I, c64, I, _P, _P, I, _P, _P, _P, _P, _P, _P, _P]
+            L.qbx_apply_shape_adjoint.restype = I
+            L.qbx_shape_adjoint_workspace_bytes.argtypes = [I, I, I, I, I]
+            L.qbx_shape_adjoint_workspace_bytes.restype = ctypes.c_size_t
             L.qbx_apply_static.argtypes = [G, I, I, I, c64, I, _P, I, _P, _P]
             L.qbx_apply_static.restype = I
             L.qbx_debug_hankel01.argtypes = [_P, I, _P, _P, _P]
@@ -222,14 +226,31 @@ def qbx_geometry(plan: Plan, curve, t_edges, r_factor=0.5) -> Geometry:
     and run qbx_geometry on the device."""
     dev = torch.device("cuda", plan.device)
     t_edges = np.asarray(t_edges, dtype=np.float64)
+    t_tgt = panel_nodes(t_edges, plan.q_tgt)
+    t_src = panel_nodes(t_edges, plan.q_src)
+    gt, dgt = curve(t_tgt)
+    gs, dgs = curve(t_src)
+    up = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device=dev)
+    return qbx_geometry_samples(plan, t_edges, up(gt), up(dgt), up(gs), up(dgs), r_factor)
+
+
+def qbx_geometry_samples(plan: Plan, t_edges, gam_tgt, dgam_tgt, gam_src, dgam_src, r_factor=0.5) -> Geometry:
+    """qbx_geometry from curve samples already on the device: gamma, gamma' at
+    the target nodes [n_tgt, 2] and at the source nodes [n_src, 2] (float64,
+    at panel_nodes(t_edges, q) of the plan's grids)."""
+    dev = torch.device("cuda", plan.device)
+    t_edges = np.asarray(t_edges, dtype=np.float64)
     M = t_edges.size - 1
     g = Geometry(M, plan.q_tgt, plan.q_src, dev)
+    arrs = [gam_tgt, dgam_tgt, gam_src, dgam_src]
+    shapes = [(g.n_tgt, 2), (g.n_tgt, 2), (g.n_src, 2), (g.n_src, 2)]
+    for a, shp in zip(arrs, shapes):
+        if tuple(a.shape) != shp or a.dtype != torch.float64:
+            raise ValueError(f"curve samples must be float64 of shape {shp}")
+    g.inputs = [torch.as_tensor(t_edges, device=dev)] + [a.detach().contiguous() for a in arrs]
+    g.r_factor = float(r_factor)
     g.t_tgt = panel_nodes(t_edges, plan.q_tgt)
     g.t_src = panel_nodes(t_edges, plan.q_src)
-    gt, dgt = curve(g.t_tgt)
-    gs, dgs = curve(g.t_src)
-    up = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device=dev)
-    g.inputs = [up(t_edges), up(gt), up(dgt), up(gs), up(dgs)]
     _check(lib().qbx_geometry(plan.handle, g.ref(), *[_ptr(a) for a in g.inputs], float(r_factor),
                               _stream()))
     return g
@@ -325,6 +346,58 @@ class QBXApply(torch.autograd.Function):
 def apply_autograd(plan: Plan, g: Geometry, op, side, limit, k, p, dens):
     """Differentiable on-surface apply of S or D (density gradients)."""
     return QBXApply.apply(dens, plan, g, op, side, limit, k, p)
+
+
+def qbx_shape_adjoint_workspace_bytes(M, q_tgt, q_src, p, nrhs):
+    return int(lib().qbx_shape_adjoint_workspace_bytes(M, q_tgt, q_src, p, nrhs))
+
+
+def qbx_apply_shape_adjoint(plan: Plan, g: Geometry, side, k, p, dens, gout):
+    """Gradient of L = Re sum conj(gout) (S dens) with respect to the curve
+    samples given to qbx_geometry: returns (d gamma_tgt, d gamma'_tgt,
+    d gamma_src, d gamma'_src), [n, 2] float64 each."""
+    d = _dens2d(dens, g.n_tgt)
+    go = _dens2d(gout, g.n_tgt)
+    if go.shape != d.shape:
+        raise ValueError("gout and dens must have the same shape")
+    f64 = dict(dtype=torch.float64, device=d.device)
+    outs = [torch.empty((g.n_tgt, 2), **f64), torch.empty((g.n_tgt, 2), **f64),
+            torch.empty((g.n_src, 2), **f64), torch.empty((g.n_src, 2), **f64)]
+    dgt, dgs = g.inputs[2], g.inputs[4]
+    _check(lib().qbx_apply_shape_adjoint(plan.handle, g.ref(), side, _k(k), p, _ptr(d), _ptr(go), d.shape[1],
+                                         _ptr(dgt), _ptr(dgs), *[_ptr(o) for o in outs], _stream()))
+    return tuple(outs)
+
+
+class QBXShapeS(torch.autograd.Function):
+    """u = S sigma on the curve given by its samples (gamma, gamma' at the
+    target and source nodes): forward = qbx_geometry + qbx_apply; backward =
+    qbx_apply_adjoint for sigma and qbx_apply_shape_adjoint for the samples."""
+
+    @staticmethod
+    def forward(ctx, dens, gam_tgt, dgam_tgt, gam_src, dgam_src, plan, t_edges, side, k, p, r_factor):
+        g = qbx_geometry_samples(plan, t_edges, gam_tgt, dgam_tgt, gam_src, dgam_src, r_factor)
+        d = dens.detach().contiguous()
+        ctx.args = (plan, g, side, k, p, d)
+        return qbx_apply(plan, g, OP_S, side, LIMIT_ONE_SIDED, k, p, d)
+
+    @staticmethod
+    def backward(ctx, grad_u):
+        plan, g, side, k, p, d = ctx.args
+        go = grad_u.contiguous()
+        gd = qbx_apply_adjoint(plan, g, OP_S, side, LIMIT_ONE_SIDED, k, p, go) if ctx.needs_input_grad[0] else None
+        shp = qbx_apply_shape_adjoint(plan, g, side, k, p, d, go) if any(ctx.needs_input_grad[1:5]) else (None,) * 4
+        if gd is not None and gd.shape != grad_u.shape:
+            gd = gd.reshape(grad_u.shape)
+        return (gd,) + tuple(shp) + (None,) * 6
+
+
+def apply_s_shape_autograd(plan: Plan, t_edges, gam_tgt, dgam_tgt, gam_src, dgam_src, dens, side, k, p,
+                           r_factor=0.5):
+    """Differentiable S sigma with respect to the density and to the curve
+    samples (for shape optimisation: build the samples in torch from the
+    curve's parameters and let autograd carry the chain)."""
+    return QBXShapeS.apply(dens, gam_tgt, dgam_tgt, gam_src, dgam_src, plan, t_edges, side, k, p, r_factor)
 
 
 def qbx_solve_exterior_dirichlet(plan: Plan, g: Geometry, k, eta, p, f, tol=1e-10, restart=40, maxiter=200,

@@ -62,3 +62,15 @@ def test_workspace_bytes_formula():
     b = qbx.qbx_workspace_bytes(16384, 8192, 2, 1)
     assert b >= 16384 * 16 + 64 * 8192 * 2 * 16
     assert qbx.qbx_workspace_bytes(-1, 1, 1, 1) == 0
+
+
+def test_shape_adjoint_workspace_bytes():
+    """Holds the oversampled density, the centre gradients, coefficient
+    columns and 64 splits of both sweeps; 0 for bad arguments."""
+    M, p, nrhs = 128, 10, 1
+    b = qbx.qbx_shape_adjoint_workspace_bytes(M, 16, 64, p, nrhs)
+    n_t, n_s = M * 16, M * 64
+    assert b >= n_s * 16 + 64 * (2 * n_t) * 4 * 16 + 64 * n_s * 3 * 16
+    assert qbx.qbx_shape_adjoint_workspace_bytes(M, 16, 64, p, 2) > b
+    assert qbx.qbx_shape_adjoint_workspace_bytes(0, 16, 64, p, 1) == 0
+    assert qbx.qbx_shape_adjoint_workspace_bytes(M, 16, 64, -1, 1) == 0
