@@ -65,6 +65,29 @@ def flops_per_pair_ops(ops, p, nrhs=1):
         (nrhs - 1) * sum(acc[o] for o in ops)
 
 
+# DRAM bytes (read + write) of one launch of the fused S + D + grad S kernel
+# on the full-size starfish workload, from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum); valid only for the kernel
+# sources it was taken with, identified by their hash.
+TRAFFIC = {"3107441e03059061": 1.89e6}   # profiles/k_apply_fused_S_D_gradS_starfish_M256_dram.md
+KERNEL_SOURCES = ["qbx_apply_impl.cuh", "qbx_device.cuh", "special_tables.h", "qbx_apply_real.cu"]
+
+
+def kernel_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1207_4461_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def kernel_traffic(wl, args):
+    if args.separate or args.panels or args.ops:
+        return None
+    return TRAFFIC.get(kernel_source_hash())
+
+
 def env_rank():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
         int(os.environ.get("LOCAL_RANK", "0"))
@@ -203,13 +226,18 @@ def run_gpu(args, wl):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
 
-    def step(d):
+    def step(d, kernel_ms=None):
         if args.separate:
             for c in codes:
                 qbx.qbx_apply(plan, g, c, qbx.SIDE_TWO, 0, wl.k, wl.p, d, out_on=outs[c])
+                if kernel_ms is not None:
+                    kernel_ms[-1] += qbx.qbx_plan_kernel_ms(plan)
         else:  # all operators in one pass over the pairs
             qbx.qbx_apply_ops(plan, g, codes, qbx.SIDE_TWO, 0, wl.k, wl.p, d, out=outs)
+            if kernel_ms is not None:
+                kernel_ms[-1] += qbx.qbx_plan_kernel_ms(plan)
 
+    qbx.qbx_plan_set_timing(plan, True)   # events around the pair-sum kernel of every call
     for _ in range(args.warmup):
         step(dens)
     torch.cuda.synchronize()
@@ -224,15 +252,18 @@ def run_gpu(args, wl):
     torch.cuda.synchronize()
     clocks.start()
     time.sleep(0.3)
+    kernel_ms = []
     for s in range(args.steps):
         flush.fill_(s & 0xFF)
         ev[s][0].record(stream)
-        step(dens)
+        kernel_ms.append(0.0)
+        step(dens, kernel_ms)
         ev[s][1].record(stream)
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
     clk = clocks.stop()
+    kern_ms = sum(kernel_ms) / len(kernel_ms)
     steps_ms = [a.elapsed_time(b) for a, b in ev]
     step_ms = sum(steps_ms) / args.steps
     qbx.qbx_sync_status(plan)
@@ -251,11 +282,12 @@ def run_gpu(args, wl):
     else:
         fpp = flops_per_pair_ops(list(wl.ops), wl.p, wl.nrhs)
         kname = "k_apply_fused, operators " + "+".join(wl.ops) + " in one pass"
-    achieved = pairs * fpp / (step_ms * 1e-3) / 1e9
+    achieved = pairs * fpp / (kern_ms * 1e-3) / 1e9
     roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
-                "frac": achieved / FP64_PEAK_GFLOPS, "traffic": None,
-                "kernel": kname + " (step events also cover the oversampling and reduction kernels, "
-                                  "<1% of the time)",
+                "frac": achieved / FP64_PEAK_GFLOPS, "traffic": kernel_traffic(wl, args),
+                "kernel": kname, "kernel_ms": kern_ms,
+                "timing": "CUDA events recorded by the library around the kernel launch(es) of every "
+                          "timed call, on the launching stream",
                 "flops_per_pair": fpp, "peak_basis": "152 SMs x 4 FP64 flop/clk x 2.07 GHz"}
 
     # ---- end to end through the public API with host buffers (pinned)
@@ -313,12 +345,19 @@ def run_batch_compare(args, qbx, torch):
     per curve.  Returns the figures for the JSON line."""
     bw = W.cfg3()
     insts = bw.instances()
+    if args.batch_curves:
+        insts = insts[:args.batch_curves]
     Mmax = max(M for _, M, _ in insts)
     plan = qbx.Plan(bw.q_tgt, bw.q_src, n_src=bw.q_src * Mmax, n_ctr=bw.q_tgt * Mmax, ncoef=2, nrhs=bw.nrhs)
     geoms = [qbx.qbx_geometry(plan, c, c.edges(M)) for c, M, _ in insts]
     dens = [torch.as_tensor(bw.dens(i, g.n_tgt), device="cuda").contiguous() for i, g in enumerate(geoms)]
     ks = [k for _, _, k in insts]
     batch = qbx.Batch(plan, geoms, ks, bw.p, (qbx.OP_S, qbx.OP_D), qbx.SIDE_INT, 0, dens)
+    model_cfg = batch.info()
+    t_tune = time.perf_counter()
+    batch.tune()   # outside the timed region: measured choice of items and rhs grouping
+    t_tune = time.perf_counter() - t_tune
+    tuned_cfg = batch.info()
     outs = [{o: torch.empty_like(batch.out[i][o]) for o in (qbx.OP_S, qbx.OP_D)} for i in range(len(geoms))]
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
@@ -350,17 +389,93 @@ def run_batch_compare(args, qbx, torch):
     terms = pairs * (2 * bw.p + 1) * bw.nrhs * 2
     fpp = flops_per_pair_ops(["S", "D"], bw.p, bw.nrhs)
     achieved = pairs * fpp / (ms_batch * 1e-3) / 1e9
-    return {"workload": "64 random Fourier curves r=1+sum_{m<=8}(a_m cos mt+b_m sin mt), a,b~U(-0.04,0.04), "
-                        "M~U{16..512} x 16 targets, 4x sources, k~U(1,40), p=10, 32 CN(0,1) densities, "
-                        "interior, S and D (seed 3)",
+    return {"workload": f"{len(insts)} random Fourier curves r=1+sum_{{m<=8}}(a_m cos mt+b_m sin mt), "
+                        "a,b~U(-0.04,0.04), M~U{16..512} x 16 targets, 4x sources, k~U(1,40), p=10, "
+                        "32 CN(0,1) densities, interior, S and D (seed 3)",
             "pairs": pairs, "terms_per_step": terms, "steps": steps,
             "batched_ms": ms_batch, "per_instance_ms": ms_inst,
             "batched_terms_per_s": terms / (ms_batch * 1e-3),
             "per_instance_terms_per_s": terms / (ms_inst * 1e-3),
             "speedup": ms_inst / ms_batch,
+            "items": {"model": dict(zip(("rhs_per_warp", "src_chunk", "items", "ctas"), model_cfg)),
+                      "tuned": dict(zip(("rhs_per_warp", "src_chunk", "items", "ctas"), tuned_cfg)),
+                      "tune_s": t_tune},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
                          "frac": achieved / FP64_PEAK_GFLOPS, "flops_per_pair": fpp,
                          "kernel": "k_apply_group (persistent, longest-first items, CUDA graph)"}}
+
+
+def run_solve(args):
+    """Exterior sound-soft scattering (Sec. 4.2): (1/2 + D - i eta S) mu = f,
+    eta = k, two-sided D and S, on the paper's teardrop with 1008 panels
+    equispaced in t and the panel on each side of the corner bisected 8
+    times (1024 panels, 16384 targets, 65536 sources, 32768 centres), k = 30,
+    p = 14, f = -e^{i k d_m . x} for 64 plane waves d_m = (cos 2 pi m/64,
+    sin 2 pi m/64), GMRES(restart) on the device to 1e-10.  Prints one JSON
+    line (not the benchmark metric): solve time, matvecs, time per matvec,
+    residuals, and the oracle's residual at sampled targets for 4 of the
+    right-hand sides."""
+    import torch
+    import paper_1207_4461_gb300 as qbx
+    torch.cuda.set_device(0)
+    k, p, nrhs, m_base, levels = 30.0, 14, 64, 1008, 8
+    cur = W.teardrop()
+    edges = W.dyadic_edges(m_base, levels)
+    M = len(edges) - 1
+    plan = qbx.Plan(16, 64, n_src=64 * M, n_ctr=32 * M, ncoef=2, nrhs=nrhs)
+    g = qbx.qbx_geometry(plan, cur, edges)
+    tx, ty = g["tgt_x"], g["tgt_y"]
+    ang = 2 * math.pi * torch.arange(nrhs, dtype=torch.float64, device="cuda") / nrhs
+    f = -torch.exp(1j * k * (tx[:, None] * torch.cos(ang)[None, :] + ty[:, None] * torch.sin(ang)[None, :]))
+    f = f.contiguous()
+    # one matvec alone (both operators, 64 rhs), timed after a warm-up
+    d = f.clone()
+    outs = {qbx.OP_S: torch.empty_like(d), qbx.OP_D: torch.empty_like(d)}
+    qbx.qbx_plan_set_timing(plan, True)
+    qbx.qbx_apply_ops(plan, g, (qbx.OP_S, qbx.OP_D), qbx.SIDE_TWO, 0, k, p, d, out=outs)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    qbx.qbx_apply_ops(plan, g, (qbx.OP_S, qbx.OP_D), qbx.SIDE_TWO, 0, k, p, d, out=outs)
+    e1.record()
+    e1.synchronize()
+    mv_ms = e0.elapsed_time(e1)
+    mv_kernel_ms = qbx.qbx_plan_kernel_ms(plan)
+    qbx.qbx_plan_set_timing(plan, False)
+    clocks = ClockSampler(0)
+    clocks.start()
+    e0.record()
+    mu, its, res = qbx.qbx_solve_exterior_dirichlet(plan, g, k, k, p, f, tol=1e-10, restart=args.solve_restart,
+                                                     maxiter=args.solve_maxiter, raise_on_noconv=False)
+    e1.record()
+    e1.synchronize()
+    clk = clocks.stop()
+    solve_ms = e0.elapsed_time(e1)
+    qbx.qbx_sync_status(plan)
+    # oracle residual at sampled targets (away from nothing: every 1024th target)
+    import oracle
+    go = oracle.geometry(cur, edges, 16, 64)
+    sel = np.arange(7, g.n_tgt, 1024)
+    cols = [0, 16, 33, 50]
+    mu_h = mu.cpu().numpy()[:, cols]
+    f_h = f.cpu().numpy()[:, cols]
+    So = oracle.apply(go, oracle.OP_S, oracle.SIDE_TWO, 0, k, p, mu_h, sel=sel)
+    Do = oracle.apply(go, oracle.OP_D, oracle.SIDE_TWO, 0, k, p, mu_h, sel=sel)
+    r = 0.5 * mu_h[sel] + Do - 1j * k * So - f_h[sel]
+    pairs = 2 * g.n_tgt * g.n_src
+    line = {"solve": "exterior sound-soft, paper's teardrop, 1008+16 panels (dyadic toward the corner), "
+                     "k=30, p=14, eta=k, 64 plane waves, two-sided D and S, GMRES on the device",
+            "n_tgt": g.n_tgt, "n_src": g.n_src, "n_ctr": 2 * g.n_tgt, "nrhs": nrhs,
+            "restart": args.solve_restart, "tol": 1e-10, "matvecs": its,
+            "converged": bool(np.all(res <= 1e-10)), "max_resid": float(np.max(res)),
+            "solve_s": solve_ms * 1e-3, "matvec_ms": mv_ms, "matvec_kernel_ms": mv_kernel_ms,
+            "pairs_per_matvec": pairs,
+            "terms_per_s_matvec": 2 * pairs * (2 * p + 1) * nrhs / (mv_ms * 1e-3),
+            "oracle_pointwise_resid": float(np.abs(r).max() / np.abs(f_h).max()),
+            "oracle_sample": f"targets {sel.tolist()}, rhs {cols}",
+            "clocks": clk}
+    print(json.dumps(line))
+    return 0
 
 
 def main():
@@ -379,7 +494,23 @@ def main():
     ap.add_argument("--panels", type=int, default=None,
                     help="profiling only: override the panel count (smaller case for ncu)")
     ap.add_argument("--ops", default=None, help="profiling only: comma list of S,D,GRAD_S")
+    ap.add_argument("--batch-curves", type=int, default=None,
+                    help="profiling only: the first N curves of the batch")
+    ap.add_argument("--batch-only", action="store_true",
+                    help="profiling only: run the batched comparison alone and print it")
+    ap.add_argument("--solve", action="store_true",
+                    help="run the exterior scattering solve (1024-panel teardrop, 64 plane waves) instead")
+    ap.add_argument("--solve-restart", type=int, default=60)
+    ap.add_argument("--solve-maxiter", type=int, default=400)
     args = ap.parse_args()
+    if args.solve:
+        return run_solve(args)
+    if args.batch_only:
+        import torch
+        import paper_1207_4461_gb300 as qbx
+        torch.cuda.set_device(0)
+        print(json.dumps({"batched": run_batch_compare(args, qbx, torch)}))
+        return 0
     wl = W.cfg2()
     if args.panels:
         wl.M = args.panels

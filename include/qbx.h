@@ -103,6 +103,15 @@ int qbx_gauss_legendre(int q, double *nodes, double *weights);
 int qbx_plan_create(qbx_plan **plan, int device, int q_tgt, int q_src, size_t workspace_bytes);
 int qbx_plan_destroy(qbx_plan *plan);
 
+/* Kernel timing (no counterpart in the paper; for measurement).  With timing
+ * on, every qbx_apply / qbx_apply_ops call on the plan records two CUDA
+ * events on its stream around its pair-sum launches (the fused or group
+ * kernel, without oversampling and finishing); qbx_plan_kernel_ms waits for
+ * the second event and returns the elapsed milliseconds of the last call.
+ * QBX_EINVAL if timing is off.  Host calls. */
+int qbx_plan_set_timing(qbx_plan *plan, int on);
+int qbx_plan_kernel_ms(qbx_plan *plan, float *ms);
+
 /* Workspace a call needs: for qbx_apply / qbx_far / qbx_form_locals with the
  * given sizes.  n_ctr = number of centres (or far targets) processed, ncoef =
  * coefficients per centre (1 for S/D values, 2 for grad S, 2p+1 for
@@ -299,10 +308,13 @@ int qbx_vec_combine(int n, int nrhs, int nv, const qbx_c64 *V, const qbx_c64 *y,
  * device pointers, [n_tgt_i][nrhs]) and out[3*i + op] (device pointers in
  * qbx_apply's layout, NULL for operators not requested) are bound at
  * creation: every qbx_batch_apply reads the current contents of dens and
- * writes out.  Work items are 32 centres of one curve against all its
- * sources, taken longest first by persistent CTAs through an atomic counter;
- * no CTA ever waits for another.  qbx_batch_create allocates the batch's
- * device memory and builds and instantiates the graph (synchronous);
+ * writes out.  Work items are 32 centres of one curve against one range of
+ * at most `chunk` of its sources (equal ranges per curve; the ranges' partial
+ * sums are added in a fixed order), taken longest first by persistent CTAs
+ * through an atomic counter; no CTA ever waits for another.
+ * qbx_batch_create allocates the batch's device memory, picks the chunk
+ * with the smallest predicted makespan of that schedule (a model of the
+ * persistent grid), and builds and instantiates the graph (synchronous);
  * qbx_batch_apply launches the graph on `stream`. */
 typedef struct qbx_batch qbx_batch;
 int qbx_batch_create(qbx_batch **batch, qbx_plan *plan, int n_inst, const qbx_geom *geoms,
@@ -311,6 +323,15 @@ int qbx_batch_create(qbx_batch **batch, qbx_plan *plan, int n_inst, const qbx_ge
 int qbx_batch_apply(qbx_batch *batch, void *stream);
 /* Read (and clear) the batch's device status word, as qbx_sync_status. */
 int qbx_batch_status(qbx_batch *batch, void *stream);
+/* Autotuner (no counterpart in the paper): times the whole batch (one untimed
+ * and one timed graph launch on `stream`) for the model's chunk, half and
+ * twice it, and for the applicable rhs groupings per warp (2 or 8), then
+ * rebuilds the batch with the fastest; *rg, *chunk (may be NULL) receive the
+ * choice.  Writes the outputs as an apply does.  Host call, synchronous. */
+int qbx_batch_tune(qbx_batch *batch, void *stream, int *rg, int *chunk);
+/* The batch's current configuration: rhs per warp group, sources per item,
+ * work items, persistent CTAs.  Host, no device work. */
+int qbx_batch_info(const qbx_batch *batch, int *rg, int *chunk, int *n_items, int *grid);
 int qbx_batch_destroy(qbx_batch *batch);
 
 /* qbx_apply without a plan, for callers that cannot allocate device memory.

@@ -156,7 +156,7 @@ k_adjoint(AdjArgs a) {
         for (int q = 0; q < kNc; ++q) {
           const cplx kv = conj(s_kv[(q * kGrpTile + j) * kGrpCentres + lane]);
 #pragma unroll
-          for (int gg = 0; gg < RG; ++gg) acc[q][gg] = acc[q][gg] + g[gg] * kv;
+          for (int gg = 0; gg < RG; ++gg) cfma(acc[q][gg], g[gg], kv);
         }
       }
     }

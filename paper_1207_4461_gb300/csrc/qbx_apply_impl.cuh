@@ -356,24 +356,24 @@ k_apply_fused(ApplyArgs a) {
       if (kS) {
         const cplx* w = s_wd + ((size_t)slotn * kSrcTile + j) * NR;
 #pragma unroll
-        for (int q = 0; q < NR; ++q) accS[q] = accS[q] + w[q] * GS;
+        for (int q = 0; q < NR; ++q) cfma(accS[q], w[q], GS);
         ++slotn;
       }
       if (kD) {
         const cplx* w = s_wd + ((size_t)slotn * kSrcTile + j) * NR;
 #pragma unroll
-        for (int q = 0; q < NR; ++q) accD[q] = accD[q] + w[q] * K;
+        for (int q = 0; q < NR; ++q) cfma(accD[q], w[q], K);
         ++slotn;
       }
       if (kG) {
         const cplx* w = s_wd + ((size_t)slotn * kSrcTile + j) * NR;
 #pragma unroll
         for (int q = 0; q < NR; ++q) {
-          accA[q] = accA[q] + w[q] * GA;
-          accB[q] = accB[q] + w[q] * GB;
+          cfma(accA[q], w[q], GA);
+          cfma(accB[q], w[q], GB);
           if (kX) {
-            accX[q] = accX[q] + w[q] * EX;
-            accY[q] = accY[q] + w[q] * EY;
+            cfma(accX[q], w[q], EX);
+            cfma(accY[q], w[q], EY);
           }
         }
       }

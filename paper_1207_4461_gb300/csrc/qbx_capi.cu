@@ -24,6 +24,9 @@ struct qbx_plan {
   int* d_status;
   void* ws;
   size_t ws_bytes;
+  // optional timing of the pair-sum launches of the last apply
+  bool timing = false;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 };
 
 namespace {
@@ -207,25 +210,31 @@ int host_choose_split(int num_sms, int n_units, int n_src, size_t bytes_per_spli
   return ns;
 }
 
-// Source splits for the fused apply: at least two full waves of the kernel's
-// resident CTAs (occ per SM), then as many splits as fill the last wave, so
-// that every SM gets the same number of equal-sized items; at least 64
+// Source splits for the fused and group applies: the fewest splits whose
+// items (n_units x ns equal CTAs) fill the waves of the kernel's resident
+// CTAs (occ per SM) to at least 95 %, else the best filling; at least 64
 // sources per split, at most kMaxSplit, and within the workspace.
 int host_choose_split_waves(int num_sms, int occ, int n_units, int n_src, size_t bytes_per_split,
                             size_t avail) {
   if (occ < 1) return host_choose_split(num_sms, n_units, n_src, bytes_per_split, avail);
   const long slots = (long)num_sms * occ;
-  long ns = (2 * slots + n_units - 1) / std::max(n_units, 1);
-  const long waves = (n_units * ns + slots - 1) / slots;
-  ns = std::max(ns, waves * slots / std::max(n_units, 1));
-  ns = std::min<long>(ns, kMaxSplit);
-  ns = std::min<long>(ns, std::max(1, n_src / 64));
-  ns = std::max<long>(ns, 1);
-  if (bytes_per_split > 0) {
-    size_t fit = avail / bytes_per_split;
-    if ((size_t)ns > fit) ns = (long)fit;
+  long ns_max = std::min<long>(kMaxSplit, std::max(1, n_src / 64));
+  if (bytes_per_split > 0) ns_max = std::min<long>(ns_max, (long)(avail / bytes_per_split));
+  if (ns_max < 1) return 0;
+  const long units = std::max(n_units, 1);
+  long best = 1;
+  double best_fill = -1.0;
+  for (long ns = 1; ns <= ns_max; ++ns) {
+    const long items = units * ns;
+    const long waves = (items + slots - 1) / slots;
+    const double fill = (double)items / (double)(waves * slots);
+    if (fill >= 0.95) return (int)ns;
+    if (fill > best_fill + 1e-12) {
+      best_fill = fill;
+      best = ns;
+    }
   }
-  return (int)ns;
+  return (int)best;
 }
 
 // sources per split (equal shares; the last tile of a split may be partial)
@@ -289,12 +298,35 @@ int qbx_plan_create(qbx_plan** plan, int device, int q_tgt, int q_src, size_t wo
 int qbx_plan_destroy(qbx_plan* p) {
   if (!p) return QBX_OK;
   cudaSetDevice(p->device);
+  if (p->ev0) cudaEventDestroy(p->ev0);
+  if (p->ev1) cudaEventDestroy(p->ev1);
   cudaFree(p->d_interp);
   cudaFree(p->d_wgl_tgt);
   cudaFree(p->d_wgl_src);
   cudaFree(p->d_status);
   cudaFree(p->ws);
   delete p;
+  return QBX_OK;
+}
+
+int qbx_plan_set_timing(qbx_plan* p, int on) {
+  if (int rc = check_plan(p)) return rc;
+  CK(cudaSetDevice(p->device), "cudaSetDevice");
+  if (on && !p->ev0) {
+    CK(cudaEventCreate(&p->ev0), "cudaEventCreate");
+    CK(cudaEventCreate(&p->ev1), "cudaEventCreate");
+  }
+  p->timing = on != 0;
+  return QBX_OK;
+}
+
+int qbx_plan_kernel_ms(qbx_plan* p, float* ms) {
+  if (int rc = check_plan(p)) return rc;
+  if (!ms) return fail(QBX_EINVAL, "NULL output");
+  if (!p->timing) return fail(QBX_EINVAL, "timing is off (qbx_plan_set_timing)");
+  CK(cudaSetDevice(p->device), "cudaSetDevice");
+  CK(cudaEventSynchronize(p->ev1), "cudaEventSynchronize");
+  CK(cudaEventElapsedTime(ms, p->ev0, p->ev1), "cudaEventElapsedTime");
   return QBX_OK;
 }
 
@@ -539,6 +571,7 @@ static int apply_impl(qbx_plan* p, const qbx_geom* g, int ops, int side, int lim
     CK(launch_upsample(g->M, g->q_tgt, g->q_src, nrhs, p->d_interp, g->src_w, distinct[s], base + s * wd_one, st),
        "upsample");
   const void* wd = base;  // far targets (single operator): its oversampled density
+  if (p->timing) CK(cudaEventRecord(p->ev0, st), "timing event");
   // a2-a6 fused, per chunk of rhs
   ApplyArgs a{};
   a.ops = ops;
@@ -595,6 +628,7 @@ static int apply_impl(qbx_plan* p, const qbx_geom* g, int ops, int side, int lim
       CK(launch_apply_fused(a, st), "apply kernel");
     }
   }
+  if (p->timing) CK(cudaEventRecord(p->ev1, st), "timing event");
   // a7: reduce, i/4, jumps / two-sided average, per operator
   for (int o = 0; o < 3; ++o) {
     if (!(ops >> o & 1)) continue;

@@ -42,6 +42,14 @@ __host__ __device__ __forceinline__ cplx operator*(cplx a, cplx b) {
 __host__ __device__ __forceinline__ cplx operator*(double s, cplx a) { return cplx{s * a.re, s * a.im}; }
 __host__ __device__ __forceinline__ cplx operator*(cplx a, double s) { return cplx{s * a.re, s * a.im}; }
 __host__ __device__ __forceinline__ cplx conj(cplx a) { return cplx{a.re, -a.im}; }
+// acc += a b in four FMAs (written out: acc + a * b through the operators
+// above costs two extra instructions per part)
+__host__ __device__ __forceinline__ void cfma(cplx& acc, cplx a, cplx b) {
+  acc.re = fma(a.re, b.re, acc.re);
+  acc.re = fma(-a.im, b.im, acc.re);
+  acc.im = fma(a.re, b.im, acc.im);
+  acc.im = fma(a.im, b.re, acc.im);
+}
 __host__ __device__ __forceinline__ double abs2(cplx a) { return a.re * a.re + a.im * a.im; }
 QBX_HD double cabs_(cplx a) { return hypot(a.re, a.im); }
 // 1/b and a/b with the divisor scaled by its larger component, so that

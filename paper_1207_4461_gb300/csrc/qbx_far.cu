@@ -49,17 +49,17 @@ k_far(FarArgs a) {
       kw.hankel(d, inv, yq, H0, H1, twoz);
       if (OP == QBX_OP_S) {
 #pragma unroll
-        for (int r2 = 0; r2 < NR; ++r2) acc[r2] = acc[r2] + s_wd[j * NR + r2] * H0;
+        for (int r2 = 0; r2 < NR; ++r2) cfma(acc[r2], s_wd[j * NR + r2], H0);
       } else if (OP == QBX_OP_D) {
         const cplx g = H1 * (fma(rx, s_nx[j], ry * s_ny[j]) * inv);
 #pragma unroll
-        for (int r2 = 0; r2 < NR; ++r2) acc[r2] = acc[r2] + s_wd[j * NR + r2] * g;
+        for (int r2 = 0; r2 < NR; ++r2) cfma(acc[r2], s_wd[j * NR + r2], g);
       } else {
         const cplx gx = H1 * (rx * inv), gy = H1 * (ry * inv);
 #pragma unroll
         for (int r2 = 0; r2 < NR; ++r2) {
-          acc[r2] = acc[r2] + s_wd[j * NR + r2] * gx;
-          accb[r2] = accb[r2] + s_wd[j * NR + r2] * gy;
+          cfma(acc[r2], s_wd[j * NR + r2], gx);
+          cfma(accb[r2], s_wd[j * NR + r2], gy);
         }
       }
     }

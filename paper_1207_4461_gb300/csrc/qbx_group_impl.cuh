@@ -167,7 +167,7 @@ k_apply_group(GroupArgs a) {
           for (int q = 0; q < kNc; ++q) {
             const cplx kv = s_kv[(q * kGrpTile + j) * kGrpCentres + lane];
 #pragma unroll
-            for (int g = 0; g < RG; ++g) acc[q][g] = acc[q][g] + w[g] * kv;
+            for (int g = 0; g < RG; ++g) cfma(acc[q][g], w[g], kv);
           }
         }
       }

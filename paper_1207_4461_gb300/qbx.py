@@ -96,6 +96,15 @@ def lib():
             L.qbx_apply_shape_adjoint.argtypes = [_P, G, I, c64, I, _P, _P, I, _P, _P, _P, _P, _P, _P, _P]
             L.qbx_apply_shape_adjoint.restype = I
             L.qbx_shape_adjoint_workspace_bytes.argtypes = [I, I, I, I, I]
+            L.qbx_batch_tune.argtypes = [_P, _P, ctypes.POINTER(I), ctypes.POINTER(I)]
+            L.qbx_batch_tune.restype = I
+            L.qbx_batch_info.argtypes = [_P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I),
+                                         ctypes.POINTER(I)]
+            L.qbx_batch_info.restype = I
+            L.qbx_plan_set_timing.argtypes = [_P, I]
+            L.qbx_plan_set_timing.restype = I
+            L.qbx_plan_kernel_ms.argtypes = [_P, ctypes.POINTER(ctypes.c_float)]
+            L.qbx_plan_kernel_ms.restype = I
             L.qbx_shape_adjoint_workspace_bytes.restype = ctypes.c_size_t
             L.qbx_apply_static.argtypes = [G, I, I, I, c64, I, _P, I, _P, _P]
             L.qbx_apply_static.restype = I
@@ -174,6 +183,17 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+def qbx_plan_set_timing(plan: Plan, on=True):
+    _check(lib().qbx_plan_set_timing(plan.handle, 1 if on else 0))
+
+
+def qbx_plan_kernel_ms(plan: Plan) -> float:
+    """Device milliseconds of the pair-sum launches of the plan's last apply."""
+    ms = ctypes.c_float(0.0)
+    _check(lib().qbx_plan_kernel_ms(plan.handle, ctypes.byref(ms)))
+    return float(ms.value)
 
 
 def qbx_plan_create(q_tgt=16, q_src=64, workspace_bytes=None, device=None, **kw) -> Plan:
@@ -472,6 +492,18 @@ class Batch:
     def apply(self):
         _check(lib().qbx_batch_apply(self.handle, _stream()))
         return self.out
+
+    def tune(self):
+        """qbx_batch_tune: time the candidate configurations, keep the fastest."""
+        rg, ch = ctypes.c_int(0), ctypes.c_int(0)
+        _check(lib().qbx_batch_tune(self.handle, _stream(), ctypes.byref(rg), ctypes.byref(ch)))
+        return rg.value, ch.value
+
+    def info(self):
+        """(rhs per warp group, sources per item, items, persistent CTAs)."""
+        v = [ctypes.c_int(0) for _ in range(4)]
+        _check(lib().qbx_batch_info(self.handle, *[ctypes.byref(x) for x in v]))
+        return tuple(x.value for x in v)
 
     def status(self):
         _check(lib().qbx_batch_status(self.handle, _stream()))

@@ -96,6 +96,7 @@ def test_batch_full_size_sampled(cuda):
     geoms = [qbx.qbx_geometry(plan, c, c.edges(M)) for c, M, _ in insts]
     dens = [dev(bw.dens(i, g.n_tgt)) for i, g in enumerate(geoms)]
     batch = qbx.Batch(plan, geoms, [k for _, _, k in insts], bw.p, (0, 1), qbx.SIDE_INT, 0, dens)
+    batch.tune()
     out = batch.apply()
     batch.status()
     for i, g in enumerate(geoms):
@@ -112,3 +113,30 @@ def test_batch_full_size_sampled(cuda):
         for o in (0, 1):
             ref = oracle.apply(go, o, oracle.SIDE_INT, 0, k, bw.p, d, sel=sel)
             assert rel(out[i][o].cpu().numpy()[sel], ref) < TOL, (i, o)
+
+
+@pytest.mark.parametrize("nrhs", [12, 3])
+def test_batch_tuner_configurations(cuda, nrhs):
+    """The tuner times its candidates (source chunks around the model's, rhs
+    groupings 2 and 8 per warp where both apply) and keeps the fastest; the
+    result of every configuration it leaves behind matches the oracle."""
+    Ms = (2, 9, 17, 4, 30, 11)
+    ks = (5.0, 12.0, 3 + 0.3j, 8.0, 2.5, 16.0)
+    p = 6
+    insts, bw = small_batch(ks, Ms, nrhs, seed=8)
+    plan = qbx.Plan(16, 64, n_src=64 * max(Ms), n_ctr=2 * 16 * max(Ms), ncoef=4, nrhs=nrhs)
+    geoms = [qbx.qbx_geometry(plan, c, c.edges(M)) for c, M, _ in insts]
+    dens = [dev(bw.dens(i, g.n_tgt)) for i, g in enumerate(geoms)]
+    batch = qbx.Batch(plan, geoms, [k for _, _, k in insts], p, (0, 1), qbx.SIDE_TWO, 0, dens)
+    rg0, chunk0, items0, grid0 = batch.info()
+    assert rg0 in (2, 8) and chunk0 % 32 == 0 and items0 >= grid0 >= 1
+    rg, chunk = batch.tune()
+    assert (rg, chunk) == batch.info()[:2]
+    out = batch.apply()
+    batch.status()
+    for i, (c, M, k) in enumerate(insts):
+        go = oracle.geometry(c, c.edges(M), 16, 64)
+        d = bw.dens(i, go["n_tgt"])
+        for o in (0, 1):
+            ref = oracle.apply(go, o, qbx.SIDE_TWO, 0, k, p, d)
+            assert rel(out[i][o], ref) < TOL, (i, o, rg, chunk)

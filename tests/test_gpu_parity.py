@@ -298,3 +298,26 @@ def test_errors_are_reported(cuda):
         qbx.qbx_sync_status(plan)
     assert e.value.code == 4
     qbx.qbx_sync_status(plan)   # cleared
+
+
+def test_kernel_timing_events(cuda):
+    """With timing on, the plan records events around the pair-sum launch of
+    every apply: the kernel time is positive, below the whole call's time,
+    and the results are unchanged; with timing off the query is refused."""
+    wl = W.cfg1()
+    plan, g, go = make(wl.curve, wl.M, p=wl.p)
+    d = dev(wl.dens(g.t_tgt))
+    with pytest.raises(qbx.QBXError) as e:
+        qbx.qbx_plan_kernel_ms(plan)
+    assert e.value.code == 1
+    ref = qbx.qbx_apply(plan, g, qbx.OP_S, qbx.SIDE_TWO, 0, wl.k, wl.p, d)
+    qbx.qbx_plan_set_timing(plan, True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    out = qbx.qbx_apply_ops(plan, g, (qbx.OP_S, qbx.OP_D), qbx.SIDE_TWO, 0, wl.k, wl.p, d)
+    e1.record()
+    kms = qbx.qbx_plan_kernel_ms(plan)
+    e1.synchronize()
+    assert 0.0 < kms <= e0.elapsed_time(e1)
+    assert torch.equal(out[qbx.OP_S], ref) or rel(out[qbx.OP_S], ref.cpu().numpy()) < 1e-13
+    qbx.qbx_plan_set_timing(plan, False)
