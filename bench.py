@@ -71,15 +71,35 @@ def flops_per_pair_ops(ops, p, nrhs=1):
 # sources it was taken with, identified by their hash.
 TRAFFIC = {"3107441e03059061": 1.89e6}   # profiles/k_apply_fused_S_D_gradS_starfish_M256_dram.md
 KERNEL_SOURCES = ["qbx_apply_impl.cuh", "qbx_device.cuh", "special_tables.h", "qbx_apply_real.cu"]
+GROUP_SOURCES = ["qbx_group_impl.cuh", "qbx_apply_impl.cuh", "qbx_device.cuh", "special_tables.h"]
+# Hardware-counted FP64 operations per (centre, source) pair, 2 DFMA + DMUL +
+# DADD from ncu's smsp__sass_thread_inst_executed_op_{dfma,dmul,dadd}_pred_on
+# counters divided by the pairs of the captured launch, for the kernel
+# sources with the given hash (profiles/*_fp64_counts.md).
+HW_FP64_PER_PAIR = {"3107441e03059061": 572.3}         # fused S + D + grad S, p = 12, one rhs
+HW_FP64_PER_PAIR_GROUP = {"b0837c18d2fe8557": 763.4}   # group kernel, S + D, p = 10, 32 rhs
 
 
-def kernel_source_hash():
+def source_hash(names=KERNEL_SOURCES):
     import hashlib
     h = hashlib.sha256()
-    for name in KERNEL_SOURCES:
+    for name in names:
         with open(os.path.join(ROOT, "paper_1207_4461_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
+
+
+def kernel_source_hash():
+    return source_hash(KERNEL_SOURCES)
+
+
+def hw_roofline(ops_per_pair, pairs, seconds):
+    if ops_per_pair is None:
+        return None
+    a = pairs * ops_per_pair / seconds / 1e9
+    return {"fp64_ops_per_pair": ops_per_pair, "achieved": a, "frac": a / FP64_PEAK_GFLOPS,
+            "unit": "GFLOP/s", "source": "ncu FP64 instruction counters (2 DFMA + DMUL + DADD) of the same "
+                                         "kernel sources, per pair, x pairs / measured kernel time"}
 
 
 def kernel_traffic(wl, args):
@@ -289,6 +309,8 @@ def run_gpu(args, wl):
                 "timing": "CUDA events recorded by the library around the kernel launch(es) of every "
                           "timed call, on the launching stream",
                 "flops_per_pair": fpp, "peak_basis": "152 SMs x 4 FP64 flop/clk x 2.07 GHz"}
+    if not (args.separate or args.panels or args.ops):
+        roofline["hw"] = hw_roofline(HW_FP64_PER_PAIR.get(kernel_source_hash()), pairs, kern_ms * 1e-3)
 
     # ---- end to end through the public API with host buffers (pinned)
     h_dens = torch.from_numpy(dens_np).pin_memory()
@@ -402,7 +424,10 @@ def run_batch_compare(args, qbx, torch):
                       "tune_s": t_tune},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
                          "frac": achieved / FP64_PEAK_GFLOPS, "flops_per_pair": fpp,
-                         "kernel": "k_apply_group (persistent, longest-first items, CUDA graph)"}}
+                         "kernel": "k_apply_group (persistent, longest-first items, CUDA graph)",
+                         "timing": "whole graph (oversampling, group kernel, finishing) per apply",
+                         "hw": None if args.batch_curves else hw_roofline(
+                             HW_FP64_PER_PAIR_GROUP.get(source_hash(GROUP_SOURCES)), pairs, ms_batch * 1e-3)}}
 
 
 def run_solve(args):

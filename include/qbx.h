@@ -327,7 +327,11 @@ int qbx_batch_status(qbx_batch *batch, void *stream);
  * and one timed graph launch on `stream`) for the model's chunk, half and
  * twice it, and for the applicable rhs groupings per warp (2 or 8), then
  * rebuilds the batch with the fastest; *rg, *chunk (may be NULL) receive the
- * choice.  Writes the outputs as an apply does.  Host call, synchronous. */
+ * choice.  Writes the outputs as an apply does.  Host call, synchronous.
+ * The choice is cached in the process per (device, p, operators, side,
+ * nrhs, real/complex k, and power-of-two buckets of the largest curve's
+ * sources, the total pairs and the curve count); qbx_batch_create starts
+ * from a cached choice when one matches. */
 int qbx_batch_tune(qbx_batch *batch, void *stream, int *rg, int *chunk);
 /* The batch's current configuration: rhs per warp group, sources per item,
  * work items, persistent CTAs.  Host, no device work. */

@@ -7,7 +7,10 @@
 #include <math.h>
 #include <stdio.h>
 #include <algorithm>
+#include <map>
+#include <mutex>
 #include <numeric>
+#include <tuple>
 #include <vector>
 #include "../../include/qbx.h"
 #include "qbx_device.cuh"
@@ -295,6 +298,23 @@ int configure(qbx_batch* b, int rg, int chunk) {
   return QBX_OK;
 }
 
+// Tuned configurations, cached per (device, p, operators, side, nrhs, real or
+// complex k, and the power-of-two buckets of the largest curve, the total
+// pairs and the curve count): a batch created later with the same key starts
+// from the measured choice instead of the model's.
+typedef std::tuple<int, int, int, int, int, int, int, int, int> TuneKey;
+std::mutex g_tune_mu;
+std::map<TuneKey, std::pair<int, int>> g_tune_cache;
+
+int log2i(double v) { return v < 1.0 ? 0 : (int)std::floor(std::log2(v)); }
+
+TuneKey tune_key(const qbx_batch* b) {
+  double pairs = 0.0;
+  for (const GroupInst& in : b->h_inst) pairs += (double)in.n_ctr * in.n_src;
+  return TuneKey{b->device, b->p, b->ops, b->side, b->nrhs, b->ck ? 1 : 0, log2i(b->max_src), log2i(pairs),
+                 log2i(b->n_inst)};
+}
+
 // partial-sum budget: a quarter of the free device memory
 size_t part_budget(int device) {
   size_t fr = 0, tot = 0;
@@ -411,8 +431,25 @@ int qbx_batch_create(qbx_batch** batch, qbx_plan* plan, int n_inst, const qbx_ge
     destroy(b);
     return bfail(QBX_EINVAL, "p too large for the group kernel");
   }
-  const int chunk = model_chunk(b, num_sms * occ, part_budget(b->device));
-  if (int rc = configure(b, b->rg, chunk)) {
+  int rg = b->rg, chunk = 0;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_cache.find(tune_key(b));
+    if (it != g_tune_cache.end()) {
+      rg = it->second.first;
+      chunk = it->second.second;
+    }
+  }
+  if (chunk > 0) {   // a cached choice, if its partial sums fit
+    std::vector<int> ns;
+    make_items(b->h_inst, chunk, ns);
+    if (part_bytes(b->h_inst, ns, b->ncomp, b->nrhs) > part_budget(b->device)) chunk = 0;
+  }
+  if (chunk == 0) {
+    rg = b->rg;
+    chunk = model_chunk(b, num_sms * occ, part_budget(b->device));
+  }
+  if (int rc = configure(b, rg, chunk)) {
     destroy(b);
     return rc;
   }
@@ -473,6 +510,10 @@ int qbx_batch_tune(qbx_batch* b, void* stream, int* rg_out, int* chunk_out) {
   cudaEventDestroy(e1);
   if (rc) return rc;
   if ((rc = configure(b, best_rg, best_chunk))) return rc;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[tune_key(b)] = std::make_pair(best_rg, best_chunk);
+  }
   if (rg_out) *rg_out = best_rg;
   if (chunk_out) *chunk_out = best_chunk;
   return QBX_OK;

@@ -18,15 +18,23 @@
 
 namespace qbx {
 
+// Phase 2 is a small complex matrix product (centres x sources) x (sources x
+// rhs).  With at most two components it runs on three real products per
+// complex multiply-add (re = T1 - T2, im = T3 - T1 - T2 with T1 = sum a c,
+// T2 = sum b d, T3 = sum (a + b)(c + d)), the sums a + b and c + d formed
+// once per stored value; kernel values and densities then sit in shared
+// memory as three real planes.  Otherwise four FMAs per complex product.
 template <int OPS, typename T, int RG>
 struct GroupSmem {
   static constexpr int kNc = ops_ncomp(OPS);   // raw components: S 1, D 1, grad S 2
   static constexpr bool kD = OPS & OPB_D, kG = OPS & OPB_G;
+  static constexpr bool k3M = kNc <= 2;
+  static constexpr int kVal = k3M ? 24 : 16;   // bytes per stored complex value
   static __host__ __device__ int nslots() { return 1 + ((kD || kG) ? 1 : 0) + (kG ? 1 : 0); }
   static __host__ __device__ size_t bytes(int p) {
     return 4 * kGrpTile * 8 +                                  // x, y, nx, ny
-           (size_t)kGrpTile * kGrpWarps * RG * 16 +             // densities [tile][4 RG]
-           (size_t)kNc * kGrpTile * kGrpCentres * 16 +          // kernel values [comp][tile][centre]
+           (size_t)kGrpTile * kGrpWarps * RG * kVal +           // densities [tile][4 RG]
+           (size_t)kNc * kGrpTile * kGrpCentres * kVal +        // kernel values [comp][tile][centre]
            (size_t)nslots() * (p + 2) * kGrpCentres * sizeof(T) +  // coefficient columns
            16;                                                  // item index
   }
@@ -39,14 +47,24 @@ k_apply_group(GroupArgs a) {
   constexpr bool kS = OPS & OPB_S, kD = OPS & OPB_D, kG = OPS & OPB_G;
   constexpr int kNc = L::kNc;
   constexpr int kRP = kGrpWarps * RG;   // rhs per pass
+  constexpr bool k3M = L::k3M;
+  constexpr int kNW = kGrpTile * kRP, kNK = kNc * kGrpTile * kGrpCentres;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* s_x = reinterpret_cast<double*>(smem_raw);
   double* s_y = s_x + kGrpTile;
   double* s_nx = s_y + kGrpTile;
   double* s_ny = s_nx + kGrpTile;
-  cplx* s_wd = reinterpret_cast<cplx*>(s_ny + kGrpTile);      // [tile][kRP]
-  cplx* s_kv = s_wd + kGrpTile * kRP;                          // [comp][tile][centre]
-  T* slot = reinterpret_cast<T*>(s_kv + kNc * kGrpTile * kGrpCentres);
+  unsigned char* w_raw = reinterpret_cast<unsigned char*>(s_ny + kGrpTile);
+  unsigned char* k_raw = w_raw + (size_t)kNW * L::kVal;
+  cplx* s_wd = reinterpret_cast<cplx*>(w_raw);                 // [tile][kRP]  (4 FMAs)
+  double* s_wa = reinterpret_cast<double*>(w_raw);             // re, im, re + im planes (3M)
+  double* s_wb = s_wa + kNW;
+  double* s_ws = s_wb + kNW;
+  cplx* s_kv = reinterpret_cast<cplx*>(k_raw);                 // [comp][tile][centre]
+  double* s_ka = reinterpret_cast<double*>(k_raw);
+  double* s_kb = s_ka + kNK;
+  double* s_ks = s_kb + kNK;
+  T* slot = reinterpret_cast<T*>(k_raw + (size_t)kNK * L::kVal);
   const int p = a.p;
   const int P2 = (p + 2) * kGrpCentres;
   T* sJ = slot;
@@ -119,10 +137,15 @@ k_apply_group(GroupArgs a) {
 
     for (int r0 = 0; r0 < a.nrhs; r0 += kRP) {
       cplx acc[kNc][RG];
+      double t1[k3M ? kNc : 1][RG], t2[k3M ? kNc : 1][RG], t3[k3M ? kNc : 1][RG];
 #pragma unroll
       for (int q = 0; q < kNc; ++q)
 #pragma unroll
         for (int g = 0; g < RG; ++g) acc[q][g] = cplx{0.0, 0.0};
+#pragma unroll
+      for (int q = 0; q < (k3M ? kNc : 1); ++q)
+#pragma unroll
+        for (int g = 0; g < RG; ++g) t1[q][g] = t2[q][g] = t3[q][g] = 0.0;
 
       for (int base = item.src0; base < item.src1; base += kGrpTile) {
         const int nt = min(kGrpTile, item.src1 - base);
@@ -137,7 +160,14 @@ k_apply_group(GroupArgs a) {
         }
         for (int i = threadIdx.x; i < kGrpTile * kRP; i += blockDim.x) {
           const int s = i / kRP, rr = i - s * kRP;
-          s_wd[i] = (s < nt && r0 + rr < a.nrhs) ? wd[(size_t)(base + s) * a.nrhs + r0 + rr] : cplx{0.0, 0.0};
+          const cplx v = (s < nt && r0 + rr < a.nrhs) ? wd[(size_t)(base + s) * a.nrhs + r0 + rr] : cplx{0.0, 0.0};
+          if constexpr (k3M) {
+            s_wa[i] = v.re;
+            s_wb[i] = v.im;
+            s_ws[i] = v.re + v.im;
+          } else {
+            s_wd[i] = v;
+          }
         }
         __syncthreads();
         // ---- phase 1: kernel values of this warp's sources ----
@@ -151,25 +181,59 @@ k_apply_group(GroupArgs a) {
           cplx GS, K, GA, GB, EX, EY;
           pair_kernels<OPS, T, kGrpCentres>(kw, kk, J0, kneg_j0, colJ, colL, colG, p, dx, dy, nx, ny, ux,
                                             uy, GS, K, GA, GB, EX, EY);
+          auto put = [&](int q, cplx v) {
+            const int idx = (q * kGrpTile + j) * kGrpCentres + lane;
+            if constexpr (k3M) {
+              s_ka[idx] = v.re;
+              s_kb[idx] = v.im;
+              s_ks[idx] = v.re + v.im;
+            } else {
+              s_kv[idx] = v;
+            }
+          };
           int q = 0;
-          if (kS) s_kv[(q++ * kGrpTile + j) * kGrpCentres + lane] = GS;
-          if (kD) s_kv[(q++ * kGrpTile + j) * kGrpCentres + lane] = K;
+          if (kS) put(q++, GS);
+          if (kD) put(q++, K);
           if (kG) {
-            s_kv[(q++ * kGrpTile + j) * kGrpCentres + lane] = GA;
-            s_kv[(q++ * kGrpTile + j) * kGrpCentres + lane] = GB;
+            put(q++, GA);
+            put(q++, GB);
           }
         }
         __syncthreads();
         // ---- phase 2: this warp's rhs group ----
-        for (int j = 0; j < nt; ++j) {
-          const cplx* w = s_wd + j * kRP + warp * RG;
+        if constexpr (k3M) {
+          for (int j = 0; j < nt; ++j) {
+            const int w0 = j * kRP + warp * RG;
 #pragma unroll
-          for (int q = 0; q < kNc; ++q) {
-            const cplx kv = s_kv[(q * kGrpTile + j) * kGrpCentres + lane];
+            for (int q = 0; q < kNc; ++q) {
+              const int idx = (q * kGrpTile + j) * kGrpCentres + lane;
+              const double ka = s_ka[idx], kb = s_kb[idx], ks = s_ks[idx];
 #pragma unroll
-            for (int g = 0; g < RG; ++g) cfma(acc[q][g], w[g], kv);
+              for (int g = 0; g < RG; ++g) {
+                t1[q][g] = fma(ka, s_wa[w0 + g], t1[q][g]);
+                t2[q][g] = fma(kb, s_wb[w0 + g], t2[q][g]);
+                t3[q][g] = fma(ks, s_ws[w0 + g], t3[q][g]);
+              }
+            }
+          }
+        } else {
+          for (int j = 0; j < nt; ++j) {
+            const cplx* w = s_wd + j * kRP + warp * RG;
+#pragma unroll
+            for (int q = 0; q < kNc; ++q) {
+              const cplx kv = s_kv[(q * kGrpTile + j) * kGrpCentres + lane];
+#pragma unroll
+              for (int g = 0; g < RG; ++g) cfma(acc[q][g], w[g], kv);
+            }
           }
         }
+      }
+      if constexpr (k3M) {
+#pragma unroll
+        for (int q = 0; q < kNc; ++q)
+#pragma unroll
+          for (int g = 0; g < RG; ++g)
+            acc[q][g] = cplx{t1[q][g] - t2[q][g], t3[q][g] - t1[q][g] - t2[q][g]};
       }
       // ---- raw sums of this item (grad S already turned into x, y) ----
       if (active) {

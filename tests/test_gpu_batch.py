@@ -132,6 +132,10 @@ def test_batch_tuner_configurations(cuda, nrhs):
     assert rg0 in (2, 8) and chunk0 % 32 == 0 and items0 >= grid0 >= 1
     rg, chunk = batch.tune()
     assert (rg, chunk) == batch.info()[:2]
+    # a batch of the same shape starts from the cached choice
+    again = qbx.Batch(plan, geoms, [k for _, _, k in insts], p, (0, 1), qbx.SIDE_TWO, 0, dens)
+    assert again.info()[:2] == (rg, chunk)
+    again.close()
     out = batch.apply()
     batch.status()
     for i, (c, M, k) in enumerate(insts):
