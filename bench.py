@@ -257,6 +257,8 @@ def run_gpu(args, wl):
             if kernel_ms is not None:
                 kernel_ms[-1] += qbx.qbx_plan_kernel_ms(plan)
 
+    if args.min_waves:
+        qbx.qbx_plan_set_min_waves(plan, args.min_waves)
     qbx.qbx_plan_set_timing(plan, True)   # events around the pair-sum kernel of every call
     for _ in range(args.warmup):
         step(dens)
@@ -519,6 +521,8 @@ def main():
     ap.add_argument("--panels", type=int, default=None,
                     help="profiling only: override the panel count (smaller case for ncu)")
     ap.add_argument("--ops", default=None, help="profiling only: comma list of S,D,GRAD_S")
+    ap.add_argument("--min-waves", type=int, default=None,
+                    help="profiling only: qbx_plan_set_min_waves for the main step")
     ap.add_argument("--batch-curves", type=int, default=None,
                     help="profiling only: the first N curves of the batch")
     ap.add_argument("--batch-only", action="store_true",

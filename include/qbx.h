@@ -112,6 +112,12 @@ int qbx_plan_destroy(qbx_plan *plan);
 int qbx_plan_set_timing(qbx_plan *plan, int on);
 int qbx_plan_kernel_ms(qbx_plan *plan, float *ms);
 
+/* Work decomposition of the plan's applies (no counterpart in the paper):
+ * the source-split choice aims for at least `waves` waves of the kernel's
+ * resident CTAs (1..64; default set at plan creation), so that the block
+ * scheduler can even out CTAs of unequal duration.  Host call. */
+int qbx_plan_set_min_waves(qbx_plan *plan, int waves);
+
 /* Workspace a call needs: for qbx_apply / qbx_far / qbx_form_locals with the
  * given sizes.  n_ctr = number of centres (or far targets) processed, ncoef =
  * coefficients per centre (1 for S/D values, 2 for grad S, 2p+1 for

@@ -27,6 +27,8 @@ struct qbx_plan {
   // optional timing of the pair-sum launches of the last apply
   bool timing = false;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  // waves of resident CTAs the split choice aims for (qbx_plan_set_min_waves)
+  int min_waves = 1;
 };
 
 namespace {
@@ -211,11 +213,13 @@ int host_choose_split(int num_sms, int n_units, int n_src, size_t bytes_per_spli
 }
 
 // Source splits for the fused and group applies: the fewest splits whose
-// items (n_units x ns equal CTAs) fill the waves of the kernel's resident
-// CTAs (occ per SM) to at least 95 %, else the best filling; at least 64
-// sources per split, at most kMaxSplit, and within the workspace.
+// items (n_units x ns equal CTAs) make at least `min_waves` waves of the
+// kernel's resident CTAs (occ per SM) and fill them to at least 95 %, else
+// the best filling; at least 64 sources per split, at most kMaxSplit, and
+// within the workspace.  More waves let the block scheduler even out CTAs
+// whose pairs take different branches.
 int host_choose_split_waves(int num_sms, int occ, int n_units, int n_src, size_t bytes_per_split,
-                            size_t avail) {
+                            size_t avail, int min_waves) {
   if (occ < 1) return host_choose_split(num_sms, n_units, n_src, bytes_per_split, avail);
   const long slots = (long)num_sms * occ;
   long ns_max = std::min<long>(kMaxSplit, std::max(1, n_src / 64));
@@ -223,14 +227,15 @@ int host_choose_split_waves(int num_sms, int occ, int n_units, int n_src, size_t
   if (ns_max < 1) return 0;
   const long units = std::max(n_units, 1);
   long best = 1;
-  double best_fill = -1.0;
+  double best_score = -1.0;
   for (long ns = 1; ns <= ns_max; ++ns) {
     const long items = units * ns;
     const long waves = (items + slots - 1) / slots;
     const double fill = (double)items / (double)(waves * slots);
-    if (fill >= 0.95) return (int)ns;
-    if (fill > best_fill + 1e-12) {
-      best_fill = fill;
+    if (fill >= 0.95 && waves >= min_waves) return (int)ns;
+    const double score = fill + (waves >= min_waves ? 1.0 : 0.0) + 1e-3 * std::min<long>(waves, min_waves);
+    if (score > best_score + 1e-12) {
+      best_score = score;
       best = ns;
     }
   }
@@ -317,6 +322,13 @@ int qbx_plan_set_timing(qbx_plan* p, int on) {
     CK(cudaEventCreate(&p->ev1), "cudaEventCreate");
   }
   p->timing = on != 0;
+  return QBX_OK;
+}
+
+int qbx_plan_set_min_waves(qbx_plan* p, int waves) {
+  if (int rc = check_plan(p)) return rc;
+  if (waves < 1 || waves > 64) return fail(QBX_EINVAL, "min_waves = %d outside [1, 64]", waves);
+  p->min_waves = waves;
   return QBX_OK;
 }
 
@@ -558,7 +570,7 @@ static int apply_impl(qbx_plan* p, const qbx_geom* g, int ops, int side, int lim
   int occ;
   if (group) occ = ck ? group_occupancy_cplx(ops, pp, rg) : group_occupancy_real(ops, pp, rg);
   else occ = ck ? apply_occupancy_cplx(ops, pp, std::min(chunk, nrhs)) : apply_occupancy_real(ops, pp, std::min(chunk, nrhs));
-  const int ns = host_choose_split_waves(p->num_sms, occ, units, g->n_src, per_split, avail);
+  const int ns = host_choose_split_waves(p->num_sms, occ, units, g->n_src, per_split, avail, p->min_waves);
   if (ns < 1) return fail(QBX_ENOMEM, "workspace too small for the apply partial sums");
   if (group ? (ck ? group_smem_cplx(ops, pp, rg) : group_smem_real(ops, pp, rg)) > 220 * 1024
             : apply_smem_bytes(ops, ck, pp, chunk) > 220 * 1024)

@@ -123,7 +123,7 @@ void host_interp_matrix(int q_tgt, int q_src, std::vector<double>& M);
 size_t host_align256(size_t b);
 int host_choose_split(int num_sms, int n_units, int n_src, size_t bytes_per_split, size_t avail);
 int host_choose_split_waves(int num_sms, int occ, int n_units, int n_src, size_t bytes_per_split,
-                            size_t avail);
+                            size_t avail, int min_waves = 1);
 int host_split_len(int n_src, int ns);
 int host_fail(int code, const char* msg);   // sets qbx_last_error(), returns code
 void host_plan_info(const qbx_plan* plan, int* device, int* q_tgt, int* q_src, const double** interp);

@@ -101,6 +101,8 @@ def lib():
             L.qbx_batch_info.argtypes = [_P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I),
                                          ctypes.POINTER(I)]
             L.qbx_batch_info.restype = I
+            L.qbx_plan_set_min_waves.argtypes = [_P, I]
+            L.qbx_plan_set_min_waves.restype = I
             L.qbx_plan_set_timing.argtypes = [_P, I]
             L.qbx_plan_set_timing.restype = I
             L.qbx_plan_kernel_ms.argtypes = [_P, ctypes.POINTER(ctypes.c_float)]
@@ -187,6 +189,10 @@ class Plan:
 
 def qbx_plan_set_timing(plan: Plan, on=True):
     _check(lib().qbx_plan_set_timing(plan.handle, 1 if on else 0))
+
+
+def qbx_plan_set_min_waves(plan: Plan, waves: int):
+    _check(lib().qbx_plan_set_min_waves(plan.handle, int(waves)))
 
 
 def qbx_plan_kernel_ms(plan: Plan) -> float:
