@@ -16,6 +16,7 @@
  *   D coefficients         normal derivative at the source         (Sec. 3.2, eq. graf-coefficient-dlp)
  *   evaluation             local (Bessel) expansion                (Sec. 2, eq. local-exp; Sec. 3.3 step 4c)
  *   target gradient        derivative of the local expansion       (Sec. 3.2)
+ *   R (tangential dipole)  t_s . grad_{x_s} G, no jump             (Sec. 3.2, eq. riesz-def)
  *   jumps / PV / averaging                                          (Sec. 3.2, eqs. dlpjump, dlp-twosided)
  *   source oversampling    interpolate density to a finer grid      (Sec. 3.4.2)
  *   far targets            plain smooth quadrature                 (Sec. 1, Sec. 2)
@@ -42,7 +43,7 @@ typedef double complex cplx;
 #define ORC_PI 3.14159265358979323846264338327950288
 #define ORC_EULER_GAMMA 0.57721566490153286060651209008240243
 
-enum { OP_S = 0, OP_D = 1, OP_GRAD_S = 2 };
+enum { OP_S = 0, OP_D = 1, OP_GRAD_S = 2, OP_R = 3 };
 enum { SIDE_INT = 0, SIDE_EXT = 1, SIDE_TWO = 2 };
 enum { LIMIT_ONE_SIDED = 0, LIMIT_PV = 1 };
 enum { WHAT_VALUE = 0, WHAT_GRAD = 1 };
@@ -403,6 +404,8 @@ int orc_upsample(int M, int q_tgt, int q_src, int nrhs, const double *src_w,
 /*      (Sec. 3.2, eq. graf-coefficient-dlp).  With F_m(y) = H_m(k|y|) e^{i m arg y}, */
 /*      H_l e^{-i l theta} = (-1)^l F_{-l}, and (DLMF 10.6.2 in polar form)     */
 /*      n . grad F_m = (k/2) [ nu F_{m-1} - conj(nu) F_{m+1} ],  nu = n_x + i n_y. */
+/*   R: the same with the unit tangent t = (-n_y, n_x) in place of n          */
+/*      (Sec. 3.2, eq. riesz-def): nu = t_x + i t_y.                           */
 /* alpha is [n_ctr][2p+1][nrhs], index l + p.                                  */
 /* ------------------------------------------------------------------------- */
 static cplx F_m(int m, const cplx *H, double theta)
@@ -432,10 +435,10 @@ int orc_form_locals(int kind, int n_ctr, const double *ctr_x, const double *ctr_
             double rho = hypot(dx, dy);
             double theta = atan2(dy, dx);
             orc_hankel_seq(k * rho, p + 1, H);
-            cplx nu = src_nx[s] + I * src_ny[s];
+            cplx nu = (kind == OP_R) ? -src_ny[s] + I * src_nx[s] : src_nx[s] + I * src_ny[s];
             for (int l = -p; l <= p; ++l) {
                 cplx kern;
-                if (kind == OP_D) {
+                if (kind == OP_D || kind == OP_R) {
                     double sg = (l & 1) ? -1.0 : 1.0;   /* (-1)^l */
                     kern = sg * (k / 2.0) * (nu * F_m(-l - 1, H, theta) - conj(nu) * F_m(-l + 1, H, theta));
                 } else {
@@ -514,6 +517,7 @@ int orc_eval_locals(int n_eval, const double *ex, const double *ey, const int *e
 /*   S:      continuous, no correction                                         */
 /*   D:      PV = lim_{+-} D mu  -/+ mu/2            (eq. dlpjump)             */
 /*   grad S: PV = lim_{+-} grad S sigma +/- n sigma/2                          */
+/*   R:      continuous (the jump is (n . t) sigma / 2 = 0; Sec. 3.2)           */
 /*   two-sided: PV = (lim_+ + lim_-)/2                (eq. dlp-twosided)        */
 /* (+ = exterior side, - = interior side).  Output [n_tgt][nrhs] for S and D,  */
 /* [n_tgt][2][nrhs] for grad S.  If sel != NULL only the n_sel targets sel[i]  */
@@ -554,7 +558,7 @@ int orc_apply(int op, int side, int limit, double kre, double kim, int p,
             ey[i] = tgt_y[t];
             ectr[i] = i;
         }
-        orc_form_locals(op == OP_D ? OP_D : OP_S, n_sel, cx, cy, n_src, src_x, src_y,
+        orc_form_locals(op == OP_GRAD_S ? OP_S : op, n_sel, cx, cy, n_src, src_x, src_y,
                         src_nx, src_ny, wd, nrhs, kre, kim, p, alpha);
         orc_eval_locals(n_sel, ex, ey, ectr, cx, cy, alpha, nrhs, kre, kim, p,
                         op == OP_GRAD_S ? WHAT_GRAD : WHAT_VALUE, val);
@@ -593,6 +597,7 @@ int orc_apply(int op, int side, int limit, double kre, double kim, int p,
 /*   D      = (i/4) sum_s wdens_s n_s . grad_{x_s} H0(k|x - x_s|)              */
 /*          = (i k/4) sum_s wdens_s H1(k d) ((x - x_s) . n_s) / d              */
 /*   grad S = (i/4) sum_s wdens_s grad_x H0(k d) = -(i k/4) sum_s wdens_s H1(k d) (x - x_s)/d */
+/*   R      = as D with the unit tangent t_s = (-n_y, n_x) in place of n_s      */
 /* Output [n][nrhs] or [n][2][nrhs].                                           */
 /* ------------------------------------------------------------------------- */
 int orc_far(int op, int n_far, const double *xy, int n_src,
@@ -615,6 +620,8 @@ int orc_far(int op, int n_far, const double *xy, int n_src,
                     out[(size_t)e * nrhs + r] += (I / 4.0) * wdv * h0;
                 } else if (op == OP_D) {
                     out[(size_t)e * nrhs + r] += (I * k / 4.0) * wdv * h1 * (rx * src_nx[s] + ry * src_ny[s]) / d;
+                } else if (op == OP_R) {   /* t = (-n_y, n_x) in place of n */
+                    out[(size_t)e * nrhs + r] += (I * k / 4.0) * wdv * h1 * (-rx * src_ny[s] + ry * src_nx[s]) / d;
                 } else {
                     out[((size_t)e * 2 + 0) * nrhs + r] += -(I * k / 4.0) * wdv * h1 * rx / d;
                     out[((size_t)e * 2 + 1) * nrhs + r] += -(I * k / 4.0) * wdv * h1 * ry / d;

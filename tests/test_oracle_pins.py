@@ -582,3 +582,45 @@ def test_shape_tangent_circle_radius(m, k):
     dlam = 0.5j * np.pi * (J * H + k * (Jp * H + J * Hp))
     _, du = oracle.apply_s_tangent(cur, radial, edges, 16, 64, INT, k, 12, dens)
     assert relerr(du[:, 0], dlam * dens) < 1e-9
+
+
+# ---------------------------------------------------------------------------
+# R: the tangential source derivative (Sec. 3.2, eq. riesz-def)
+# ---------------------------------------------------------------------------
+OP_R = oracle.OP_R
+
+
+@pytest.mark.parametrize("m,k", [(0, 5.0), (3, 5.0), (5, 3 + 0.4j)])
+def test_r_circle_eigenvalues(m, k):
+    """On a closed curve R sigma = -S[d sigma/ds] (integration by parts along
+    the curve), so on the unit circle R e^{imt} = (pi m/2) J_m(k) H_m(k) e^{imt},
+    on both sides (R has no jump: n . t = 0)."""
+    cur = W.circle(1.0)
+    g = oracle.geometry(cur, cur.edges(32), 16, 64)
+    dens = np.exp(1j * m * g["t_tgt"])
+    lam = 0.5 * np.pi * m * sp.jv(m, k) * sp.hankel1(m, k)
+    for side in (INT, EXT, TWO):
+        u = oracle.apply(g, OP_R, side, PV, k, 12, dens)[:, 0]
+        if m == 0:
+            assert np.abs(u).max() < 1e-12
+        else:
+            assert relerr(u, lam * dens) < (1e-10 if side == INT else 1e-9)
+
+
+def test_r_equals_minus_s_of_arclength_derivative():
+    """R sigma = -S[d sigma/ds] on the starfish, on the surface (one-sided
+    limits from either side) and at off-surface points by plain quadrature."""
+    cur, M, k, p = W.starfish(), 64, 7.0, 12
+    g = oracle.geometry(cur, cur.edges(M), 16, 64)
+    t = g["t_tgt"]
+    sig = W.density_cfg1(t)
+    _, dg = cur(t)
+    dsig = (-3 * np.sin(3 * t) + 0.5j * np.cos(t)) / np.hypot(dg[:, 0], dg[:, 1])
+    for side in (INT, EXT):
+        r = oracle.apply(g, OP_R, side, ONE, k, p, sig)[:, 0]
+        s = oracle.apply(g, OP_S, side, ONE, k, p, dsig)[:, 0]
+        assert relerr(r, -s) < 1e-9
+    xy = np.array([[0.2, 0.1], [2.0, -1.5], [-0.4, 0.5]])
+    rf = oracle.far(g, OP_R, k, oracle.upsample(g, sig), xy)[:, 0]
+    sf = oracle.far(g, OP_S, k, oracle.upsample(g, dsig), xy)[:, 0]
+    assert relerr(rf, -sf) < 1e-10
