@@ -55,7 +55,7 @@ def lib():
             L.orc_hankel01_array.argtypes = [I, P, P, P]
             L.orc_hankel_seq_array.argtypes = [I, P, I, P]
             L.orc_besselj_seq_array.argtypes = [I, P, I, P]
-            L.orc_geometry.argtypes = [I, I, I, P, P, P, P, P, D] + [P] * 15
+            L.orc_geometry.argtypes = [I, I, I, P, P, P, P, P, D, I] + [P] * 15
             L.orc_upsample.argtypes = [I, I, I, I, P, P, P]
             L.orc_form_locals.argtypes = [I, I, P, P, I, P, P, P, P, P, I, D, D, I, P]
             L.orc_eval_locals.argtypes = [I, P, P, P, P, P, P, I, D, D, I, I, P]
@@ -133,9 +133,13 @@ def panel_nodes(t_edges, q):
     return (0.5 * (a + b)[:, None] + 0.5 * (b - a)[:, None] * x[None, :]).reshape(-1)
 
 
-def geometry(curve, t_edges, q_tgt: int, q_src: int, r_factor: float = 0.5):
+RADIUS_H, RADIUS_SQRT_H = 0, 1
+
+
+def geometry(curve, t_edges, q_tgt: int, q_src: int, r_factor: float = 0.5, rule: int = RADIUS_H):
     """Discretise `curve` (callable t -> (gamma [n,2], dgamma [n,2])) on panels
-    with edges t_edges; Sec. 3.3 step 4a geometry and centres."""
+    with edges t_edges; Sec. 3.3 step 4a geometry and centres, with
+    r = r_factor h (rule 0) or r = r_factor sqrt(h) (rule 1, Sec. 3.1)."""
     t_edges = _f64(t_edges)
     M = t_edges.size - 1
     tt = panel_nodes(t_edges, q_tgt)
@@ -148,7 +152,7 @@ def geometry(curve, t_edges, q_tgt: int, q_src: int, r_factor: float = 0.5):
     g["panel_h"] = np.zeros(M)
     g.update({k: np.zeros(2 * n_t) for k in ("ctr_x", "ctr_y", "ctr_r", "ctr_ratio")})
     rc = lib().orc_geometry(M, q_tgt, q_src, _p(t_edges), _p(gt), _p(dgt), _p(gs), _p(dgs),
-                            float(r_factor),
+                            float(r_factor), int(rule),
                             *[_p(g[k]) for k in ("src_x", "src_y", "src_nx", "src_ny", "src_w",
                                                  "tgt_x", "tgt_y", "tgt_nx", "tgt_ny", "tgt_w",
                                                  "panel_h", "ctr_x", "ctr_y", "ctr_r", "ctr_ratio")])

@@ -287,7 +287,9 @@ void orc_besselj_seq_array(int n, const double *zin, int nmax, double *jout)
 /*        curve (Sec. 3.2: n = (t_2, -t_1))                                   */
 /*   w = w^GL (t_{m+1}-t_m)/2 |gamma'|    arc-length quadrature weight         */
 /*   h_m = sum of the panel's source weights (arc length of the panel)        */
-/*   r_m = r_factor h_m (Sec. 3.3 step 3: r_m = h_m/2)                         */
+/*   r_m = r_factor h_m (Sec. 3.3 step 3: r_m = h_m/2), or with rule 1         */
+/*   r_m = r_factor sqrt(h_m): r refined more slowly than h, the classically    */
+/*   convergent choice of the remarks after eq. error_anal (Sec. 3.1)           */
 /*   c   = x - r_m n (interior side), x + r_m n (exterior side)  (step 4a)    */
 /*   ratio = min_s |x_s - c| / r_m  (Graf validity, eq. x-c-closest)          */
 /* Centre arrays have length 2*n_tgt: interior centres first, then exterior.  */
@@ -295,7 +297,7 @@ void orc_besselj_seq_array(int n, const double *zin, int nmax, double *jout)
 int orc_geometry(int M, int q_tgt, int q_src, const double *t_edges,
                  const double *gam_tgt, const double *dgam_tgt,
                  const double *gam_src, const double *dgam_src,
-                 double r_factor,
+                 double r_factor, int rule,
                  double *src_x, double *src_y, double *src_nx, double *src_ny, double *src_w,
                  double *tgt_x, double *tgt_y, double *tgt_nx, double *tgt_ny, double *tgt_w,
                  double *panel_h,
@@ -330,7 +332,7 @@ int orc_geometry(int M, int q_tgt, int q_src, const double *t_edges,
             tgt_nx[t] = dy / sp;
             tgt_ny[t] = -dx / sp;
             tgt_w[t] = wt[i] * half * sp;
-            double r = r_factor * h;
+            double r = rule == 1 ? r_factor * sqrt(h) : r_factor * h;
             ctr_x[t] = tgt_x[t] - r * tgt_nx[t];
             ctr_y[t] = tgt_y[t] - r * tgt_ny[t];
             ctr_r[t] = r;
@@ -717,7 +719,7 @@ int orc_apply_s_tangent(int side, double kre, double kim, int p, int M, int q_tg
     double *d_sx = dbuf, *d_sy = d_sx + nd * nd_s, *d_sw = d_sy + nd * nd_s;
     double *d_cx = d_sw + nd * nd_s, *d_cy = d_cx + nd * 2 * nd_t, *d_h = d_cy + nd * 2 * nd_t;
     (void)spare; (void)spare2;
-    orc_geometry(M, q_tgt, q_src, t_edges, gam_tgt, dgam_tgt, gam_src, dgam_src, r_factor,
+    orc_geometry(M, q_tgt, q_src, t_edges, gam_tgt, dgam_tgt, gam_src, dgam_src, r_factor, 0,
                  src_x, src_y, src_nx, src_ny, src_w, tgt_x, tgt_y, tgt_nx, tgt_ny, tgt_w,
                  panel_h, ctr_x, ctr_y, ctr_r, ctr_ratio);
     double xs[ORC_MAXN], ws[ORC_MAXN];

@@ -624,3 +624,24 @@ def test_r_equals_minus_s_of_arclength_derivative():
     rf = oracle.far(g, OP_R, k, oracle.upsample(g, sig), xy)[:, 0]
     sf = oracle.far(g, OP_S, k, oracle.upsample(g, dsig), xy)[:, 0]
     assert relerr(rf, -sf) < 1e-10
+
+
+def test_sqrt_h_radius_rule_converges_classically():
+    """Sec. 3.1 remarks: with r = h/2 and an unrefined source rule the error
+    stalls at the rule's quadrature floor, while r refined more slowly than h
+    (r = c sqrt(h)) converges.  Unit circle, S e^{3it}, k = 5, p = 10,
+    16-node source rule (no oversampling)."""
+    cur, k, m, p = W.circle(1.0), 5.0, 3, 10
+    lam = 0.5j * np.pi * sp.jv(m, k) * sp.hankel1(m, k)
+
+    def err(M, rule, c):
+        g = oracle.geometry(cur, cur.edges(M), 16, 16, c, rule)
+        if rule == oracle.RADIUS_SQRT_H:
+            assert np.allclose(g["ctr_r"][:g["n_tgt"]], c * np.sqrt(np.repeat(g["panel_h"], 16)), rtol=1e-15)
+        d = np.exp(1j * m * g["t_tgt"])
+        return np.abs(oracle.apply(g, OP_S, INT, ONE, k, p, d)[:, 0] - lam * d).max() / abs(lam)
+    e_h = [err(M, oracle.RADIUS_H, 0.5) for M in (32, 64)]
+    e_s = [err(M, oracle.RADIUS_SQRT_H, 0.3) for M in (16, 32, 64)]
+    assert min(e_h) > 1e-9                      # stalled at the quadrature floor
+    assert e_s[0] > 100 * e_s[1] > 100 * 100 * e_s[2]
+    assert e_s[2] < 1e-12
