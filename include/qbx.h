@@ -62,7 +62,12 @@ enum {
   QBX_ENOMEM = 7           /* workspace too small / allocation failed */
 };
 
-enum { QBX_OP_S = 0, QBX_OP_D = 1, QBX_OP_GRAD_S = 2 };
+/* Operators: S sigma, D mu, grad S sigma (Sec. 1, Sec. 3.2), and R sigma =
+ * integral of t(x') . grad_{x'} G(x, x') sigma(x') ds (the tangential
+ * dipole, Sec. 3.2 eq. riesz-def: continuous across the curve since
+ * n . t = 0).  R is accepted by qbx_apply and qbx_far, not by
+ * qbx_apply_ops, the batch, the adjoints or qbx_apply_static. */
+enum { QBX_OP_S = 0, QBX_OP_D = 1, QBX_OP_GRAD_S = 2, QBX_OP_R = 3 };
 enum { QBX_SIDE_INT = 0, QBX_SIDE_EXT = 1, QBX_SIDE_TWO = 2 };
 enum { QBX_LIMIT_ONE_SIDED = 0, QBX_LIMIT_PV = 1 };
 enum { QBX_VALUE = 0, QBX_GRAD = 1 };

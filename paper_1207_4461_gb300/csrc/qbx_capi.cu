@@ -508,13 +508,27 @@ int qbx_far(qbx_plan* p, const qbx_geom* g, int op, qbx_c64 k, const qbx_c64* wd
             int n_far, const double* x_far, qbx_c64* out, void* stream) {
   if (int rc = check_plan(p)) return rc;
   if (int rc = check_geom(p, g, false)) return rc;
-  if (op != QBX_OP_S && op != QBX_OP_D && op != QBX_OP_GRAD_S) return fail(QBX_EINVAL, "bad op %d", op);
+  if (op != QBX_OP_S && op != QBX_OP_D && op != QBX_OP_GRAD_S && op != QBX_OP_R)
+    return fail(QBX_EINVAL, "bad op %d", op);
   if (int rc = check_k(k)) return rc;
   if (nrhs < 1) return fail(QBX_EINVAL, "nrhs = %d < 1", nrhs);
   if (n_far < 0) return fail(QBX_EINVAL, "n_far < 0");
   if (n_far == 0) return QBX_OK;
   if (!wdens_src || !x_far || !out) return fail(QBX_EINVAL, "NULL array");
   CK(cudaSetDevice(p->device), "cudaSetDevice");
+  if (op == QBX_OP_R) {   // D's quadrature with the source tangents (Sec. 3.2, eq. riesz-def)
+    const size_t tb = align256((size_t)g->n_src * 16);
+    if (p->ws_bytes < tb + 512) return fail(QBX_ENOMEM, "workspace too small for the source tangents");
+    char* base = (char*)align256((size_t)p->ws);
+    double* tx = (double*)base;
+    double* ty = tx + g->n_src;
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(launch_tangents(g->n_src, g->src_nx, g->src_ny, tx, ty, st), "tangents");
+    qbx_geom gt = *g;
+    gt.src_nx = tx;
+    gt.src_ny = ty;
+    return far_impl(p, &gt, QBX_OP_D, k, wdens_src, nrhs, n_far, x_far, out, base + tb, p->ws_bytes - tb - 512, st);
+  }
   void* part = (void*)align256((size_t)p->ws);
   return far_impl(p, g, op, k, wdens_src, nrhs, n_far, x_far, out, part,
                   p->ws_bytes > 256 ? p->ws_bytes - 256 : 0, (cudaStream_t)stream);
@@ -522,9 +536,11 @@ int qbx_far(qbx_plan* p, const qbx_geom* g, int op, qbx_c64 k, const qbx_c64* wd
 
 // On-surface apply of the operator subset `ops` (one pass over the pairs for
 // all of them), plus far targets when a single operator is requested.
+// tangent: the R operator (Sec. 3.2, eq. riesz-def): the D sums with the
+// source tangents in place of the normals, and no jump (ops must be D alone).
 static int apply_impl(qbx_plan* p, const qbx_geom* g, int ops, int side, int limit, qbx_c64 k, int pp,
                       const qbx_c64* const dens[3], int nrhs, qbx_c64* const out[3], int n_far,
-                      const double* x_far, qbx_c64* out_far, void* stream) {
+                      const double* x_far, qbx_c64* out_far, void* stream, bool tangent = false) {
   if (int rc = check_plan(p)) return rc;
   if (int rc = check_geom(p, g, true)) return rc;
   if (ops < 1 || ops > 7) return fail(QBX_EINVAL, "operator set %d is not a non-empty subset of {S, D, grad S}", ops);
@@ -555,7 +571,8 @@ static int apply_impl(qbx_plan* p, const qbx_geom* g, int ops, int side, int lim
     slot_of[o] = s;
   }
   const size_t wd_one = align256((size_t)g->n_src * nrhs * 16);
-  const size_t wd_bytes = wd_one * nd;
+  const size_t tan_bytes = tangent ? align256((size_t)g->n_src * 16) : 0;
+  const size_t wd_bytes = wd_one * nd + tan_bytes;
   if (p->ws_bytes < wd_bytes + 512) return fail(QBX_ENOMEM, "workspace too small (%zu < %zu)", p->ws_bytes, wd_bytes + 512);
   const size_t avail = p->ws_bytes - wd_bytes - 512;
   const size_t per_split = (size_t)nc * ncomp * nrhs * 16;
@@ -582,6 +599,16 @@ static int apply_impl(qbx_plan* p, const qbx_geom* g, int ops, int side, int lim
   for (int s = 0; s < nd; ++s)
     CK(launch_upsample(g->M, g->q_tgt, g->q_src, nrhs, p->d_interp, g->src_w, distinct[s], base + s * wd_one, st),
        "upsample");
+  qbx_geom gtan;
+  if (tangent) {   // the same geometry with the source tangents as "normals"
+    double* tx = (double*)(base + nd * wd_one);
+    double* ty = tx + g->n_src;
+    CK(launch_tangents(g->n_src, g->src_nx, g->src_ny, tx, ty, st), "tangents");
+    gtan = *g;
+    gtan.src_nx = tx;
+    gtan.src_ny = ty;
+    g = &gtan;
+  }
   const void* wd = base;  // far targets (single operator): its oversampled density
   if (p->timing) CK(cudaEventRecord(p->ev0, st), "timing event");
   // a2-a6 fused, per chunk of rhs
@@ -644,7 +671,8 @@ static int apply_impl(qbx_plan* p, const qbx_geom* g, int ops, int side, int lim
   // a7: reduce, i/4, jumps / two-sided average, per operator
   for (int o = 0; o < 3; ++o) {
     if (!(ops >> o & 1)) continue;
-    CK(launch_apply_finish(o, side, limit, g->n_tgt, ns, nc, nrhs, comp0[o], ncomp, part, dens[o], g->tgt_nx,
+    CK(launch_apply_finish(tangent ? QBX_OP_S : o, side, limit, g->n_tgt, ns, nc, nrhs, comp0[o], ncomp, part,
+                           dens[o], g->tgt_nx,
                            g->tgt_ny, out[o], p->d_status, st),
        "apply finish");
   }
@@ -660,9 +688,12 @@ static int apply_impl(qbx_plan* p, const qbx_geom* g, int ops, int side, int lim
 int qbx_apply(qbx_plan* p, const qbx_geom* g, int op, int side, int limit, qbx_c64 k, int pp,
               const qbx_c64* dens_tgt, int nrhs, int n_far, const double* x_far, qbx_c64* out_on,
               qbx_c64* out_far, void* stream) {
-  if (op != QBX_OP_S && op != QBX_OP_D && op != QBX_OP_GRAD_S) return fail(QBX_EINVAL, "bad op %d", op);
+  if (op != QBX_OP_S && op != QBX_OP_D && op != QBX_OP_GRAD_S && op != QBX_OP_R)
+    return fail(QBX_EINVAL, "bad op %d", op);
   const qbx_c64* dens[3] = {dens_tgt, dens_tgt, dens_tgt};
   qbx_c64* out[3] = {out_on, out_on, out_on};
+  if (op == QBX_OP_R)
+    return apply_impl(p, g, 1 << QBX_OP_D, side, limit, k, pp, dens, nrhs, out, n_far, x_far, out_far, stream, true);
   return apply_impl(p, g, 1 << op, side, limit, k, pp, dens, nrhs, out, n_far, x_far, out_far, stream);
 }
 

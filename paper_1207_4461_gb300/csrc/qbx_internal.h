@@ -113,6 +113,7 @@ cudaError_t launch_geometry(int M, int q_tgt, int q_src, const double* t_edges,
 cudaError_t launch_upsample(int M, int q_tgt, int q_src, int nrhs, const double* interp,
                             const double* src_w, const void* dens_tgt, void* wdens,
                             cudaStream_t st);
+cudaError_t launch_tangents(int n, const double* nx, const double* ny, double* tx, double* ty, cudaStream_t st);
 cudaError_t launch_assign(int n, const double* xy, int n_ctr, const double* cx,
                           const double* cy, const double* cr, int* out, cudaStream_t st);
 cudaError_t launch_debug_hankel(const void* z, int n, void* h0, void* h1, cudaStream_t st);

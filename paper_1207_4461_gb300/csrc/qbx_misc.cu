@@ -115,6 +115,21 @@ __global__ void k_upsample(int n_src, int q_tgt, int q_src, int nrhs, const doub
   out[idx] = cplx{w[s] * re, w[s] * im};
 }
 
+// Unit tangents t = (-n_y, n_x) of the source nodes (the R operator of
+// Sec. 3.2, eq. riesz-def, takes the D kernel with t in place of n).
+__global__ void k_tangents(int n, const double* nx, const double* ny, double* tx, double* ty) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  tx[i] = -ny[i];
+  ty[i] = nx[i];
+}
+
+cudaError_t launch_tangents(int n, const double* nx, const double* ny, double* tx, double* ty, cudaStream_t st) {
+  if (n < 1) return cudaSuccess;
+  k_tangents<<<(n + 255) / 256, 256, 0, st>>>(n, nx, ny, tx, ty);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_upsample(int M, int q_tgt, int q_src, int nrhs, const double* interp,
                             const double* src_w, const void* dens_tgt, void* wdens,
                             cudaStream_t st) {

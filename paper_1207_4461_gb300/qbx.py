@@ -19,7 +19,7 @@ import torch
 
 from . import build as _build
 
-OP_S, OP_D, OP_GRAD_S = 0, 1, 2
+OP_S, OP_D, OP_GRAD_S, OP_R = 0, 1, 2, 3
 SIDE_INT, SIDE_EXT, SIDE_TWO = 0, 1, 2
 LIMIT_ONE_SIDED, LIMIT_PV = 0, 1
 VALUE, GRAD = 0, 1

@@ -321,3 +321,21 @@ def test_kernel_timing_events(cuda):
     assert 0.0 < kms <= e0.elapsed_time(e1)
     assert torch.equal(out[qbx.OP_S], ref) or rel(out[qbx.OP_S], ref.cpu().numpy()) < 1e-13
     qbx.qbx_plan_set_timing(plan, False)
+
+
+@pytest.mark.parametrize("side,limit", [(qbx.SIDE_INT, qbx.LIMIT_PV), (qbx.SIDE_EXT, qbx.LIMIT_ONE_SIDED),
+                                        (qbx.SIDE_TWO, qbx.LIMIT_PV)])
+@pytest.mark.parametrize("k,p,nrhs", [(7.0, 10, 1), (4 + 0.6j, 6, 3), (9.0, 8, 20)])
+def test_apply_r_matches_oracle(cuda, side, limit, k, p, nrhs):
+    """The tangential dipole R (Sec. 3.2, eq. riesz-def) on 13 panels (ragged
+    tiles), with far targets through the same call; 20 rhs take the group
+    kernel."""
+    plan, g, go = make(W.starfish(0.2, 3), 13, nrhs=nrhs, p=p)
+    dens = W.complex_gaussian(17, g.n_tgt * nrhs).reshape(g.n_tgt, nrhs)
+    xy = np.array([[0.1, 0.05], [2.5, 0.3], [-1.9, -2.2], [0.0, 1.6]])
+    got, far = qbx.qbx_apply(plan, g, qbx.OP_R, side, limit, k, p, dev(dens), x_far=dev(xy))
+    qbx.qbx_sync_status(plan)
+    assert rel(got, oracle.apply(go, oracle.OP_R, side, limit, k, p, dens)) < TOL
+    assert rel(far, oracle.far(go, oracle.OP_R, k, oracle.upsample(go, dens), xy)) < TOL
+    wd = qbx.qbx_upsample(plan, g, dev(dens))
+    assert rel(qbx.qbx_far(plan, g, qbx.OP_R, k, wd, dev(xy)), far.cpu().numpy()) < 1e-13
