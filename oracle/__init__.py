@@ -25,7 +25,7 @@ _LIB = os.path.join(_BUILD, "libqbx_oracle.so")
 _lock = threading.Lock()
 _lib = None
 
-OP_S, OP_D, OP_GRAD_S, OP_R = 0, 1, 2, 3
+OP_S, OP_D, OP_GRAD_S, OP_R, OP_GRAD_D = 0, 1, 2, 3, 4
 SIDE_INT, SIDE_EXT, SIDE_TWO = 0, 1, 2
 LIMIT_ONE_SIDED, LIMIT_PV = 0, 1
 
@@ -59,7 +59,7 @@ def lib():
             L.orc_upsample.argtypes = [I, I, I, I, P, P, P]
             L.orc_form_locals.argtypes = [I, I, P, P, I, P, P, P, P, P, I, D, D, I, P]
             L.orc_eval_locals.argtypes = [I, P, P, P, P, P, P, I, D, D, I, I, P]
-            L.orc_apply.argtypes = [I, I, I, D, D, I, I, I, I] + [P] * 11 + [P, I, I, P, P]
+            L.orc_apply.argtypes = [I, I, I, D, D, I, I, I, I] + [P] * 12 + [P, I, I, P, P]
             L.orc_far.argtypes = [I, I, P, I, P, P, P, P, P, I, D, D, P]
             L.orc_assign_centres.argtypes = [I, P, I, I, P, P, P, P]
             L.orc_apply_s_tangent.argtypes = [I, D, D, I, I, I, I, P, D] + [P] * 4 + [I] + [P] * 4 + [P, I, P, P]
@@ -235,11 +235,11 @@ def apply(g, op, side, limit, k, p, dens_tgt, sel=None):
     else:
         sel = np.ascontiguousarray(sel, dtype=np.int32)
         n_out, n_sel, selp = sel.size, sel.size, _p(sel)
-    shape = (n_out, 2, nrhs) if op == OP_GRAD_S else (n_out, nrhs)
+    shape = (n_out, 2, nrhs) if op in (OP_GRAD_S, OP_GRAD_D) else (n_out, nrhs)
     out = np.zeros(shape, dtype=np.complex128)
     rc = lib().orc_apply(op, side, limit, k.real, k.imag, p, g["M"], g["q_tgt"], g["q_src"],
                          *[_p(g[n]) for n in ("src_x", "src_y", "src_nx", "src_ny", "src_w",
-                                              "tgt_x", "tgt_y", "tgt_nx", "tgt_ny",
+                                              "tgt_x", "tgt_y", "tgt_nx", "tgt_ny", "tgt_w",
                                               "ctr_x", "ctr_y")],
                          _p(d), nrhs, n_sel, selp, _p(out))
     if rc != 0:

@@ -17,6 +17,8 @@
  *   evaluation             local (Bessel) expansion                (Sec. 2, eq. local-exp; Sec. 3.3 step 4c)
  *   target gradient        derivative of the local expansion       (Sec. 3.2)
  *   R (tangential dipole)  t_s . grad_{x_s} G, no jump             (Sec. 3.2, eq. riesz-def)
+ *   grad D                 target gradient of the D expansion, jump
+ *                          -/+ t dsigma/ds / 2                      (Sec. 3.2, eq. dlpderiv)
  *   jumps / PV / averaging                                          (Sec. 3.2, eqs. dlpjump, dlp-twosided)
  *   source oversampling    interpolate density to a finer grid      (Sec. 3.4.2)
  *   far targets            plain smooth quadrature                 (Sec. 1, Sec. 2)
@@ -43,7 +45,7 @@ typedef double complex cplx;
 #define ORC_PI 3.14159265358979323846264338327950288
 #define ORC_EULER_GAMMA 0.57721566490153286060651209008240243
 
-enum { OP_S = 0, OP_D = 1, OP_GRAD_S = 2, OP_R = 3 };
+enum { OP_S = 0, OP_D = 1, OP_GRAD_S = 2, OP_R = 3, OP_GRAD_D = 4 };
 enum { SIDE_INT = 0, SIDE_EXT = 1, SIDE_TWO = 2 };
 enum { LIMIT_ONE_SIDED = 0, LIMIT_PV = 1 };
 enum { WHAT_VALUE = 0, WHAT_GRAD = 1 };
@@ -512,6 +514,27 @@ int orc_eval_locals(int n_eval, const double *ex, const double *ey, const int *e
     return 0;
 }
 
+/* d sigma/ds at target node t (panel m, node i): derivative of the panel's   */
+/* degree q-1 interpolant at its own node, in barycentric form,               */
+/*   p'(x_i) = sum_{j != i} (lam_j / lam_i) (sigma_j - sigma_i) / (x_i - x_j), */
+/* lam_j = 1 / prod_{k != j} (x_j - x_k), divided by ds/dxi = w_t / w^GL_i.   */
+static cplx dsigma_ds(int q, int t, int nrhs, int r, const cplx *dens, const double *tgt_w)
+{
+    double x[ORC_MAXN], w[ORC_MAXN], lam[ORC_MAXN];
+    orc_gauss_legendre(q, x, w);
+    for (int j = 0; j < q; ++j) {
+        double pr = 1.0;
+        for (int k = 0; k < q; ++k) if (k != j) pr *= (x[j] - x[k]);
+        lam[j] = 1.0 / pr;
+    }
+    int m = t / q, i = t - m * q;
+    const cplx *d = dens + (size_t)m * q * nrhs + r;
+    cplx acc = 0.0;
+    for (int j = 0; j < q; ++j)
+        if (j != i) acc += (lam[j] / lam[i]) * (d[(size_t)j * nrhs] - d[(size_t)i * nrhs]) / (x[i] - x[j]);
+    return acc * w[i] / tgt_w[t];
+}
+
 /* ------------------------------------------------------------------------- */
 /* Full on-surface apply, Sec. 3.3: upsample, coefficients at every centre of  */
 /* the requested side(s), evaluation at the centre's own target, and the jump */
@@ -520,6 +543,10 @@ int orc_eval_locals(int n_eval, const double *ex, const double *ey, const int *e
 /*   D:      PV = lim_{+-} D mu  -/+ mu/2            (eq. dlpjump)             */
 /*   grad S: PV = lim_{+-} grad S sigma +/- n sigma/2                          */
 /*   R:      continuous (the jump is (n . t) sigma / 2 = 0; Sec. 3.2)           */
+/*   grad D: PV = lim_{+-} grad D mu -/+ t dmu/ds / 2  (eq. dlpderiv), with     */
+/*           dmu/ds from the derivative of the panel's interpolant at the node  */
+/*           (barycentric form, Berrut & Trefethen 2004, eq. 9.4) divided by    */
+/*           ds/dxi = w / w^GL                                                  */
 /*   two-sided: PV = (lim_+ + lim_-)/2                (eq. dlp-twosided)        */
 /* (+ = exterior side, - = interior side).  Output [n_tgt][nrhs] for S and D,  */
 /* [n_tgt][2][nrhs] for grad S.  If sel != NULL only the n_sel targets sel[i]  */
@@ -530,12 +557,13 @@ int orc_apply(int op, int side, int limit, double kre, double kim, int p,
               const double *src_x, const double *src_y, const double *src_nx,
               const double *src_ny, const double *src_w,
               const double *tgt_x, const double *tgt_y, const double *tgt_nx,
-              const double *tgt_ny,
+              const double *tgt_ny, const double *tgt_w,
               const double *ctr_x, const double *ctr_y,
               const cplx *dens_tgt, int nrhs, int n_sel, const int *sel, cplx *out)
 {
     int n_tgt = M * q_tgt, n_src = M * q_src, nl = 2 * p + 1;
-    int ncomp = (op == OP_GRAD_S) ? 2 : 1;
+    int grad = (op == OP_GRAD_S || op == OP_GRAD_D);
+    int ncomp = grad ? 2 : 1;
     if (n_sel <= 0 || !sel) n_sel = n_tgt, sel = NULL;
     cplx *wd = malloc(sizeof(cplx) * (size_t)n_src * nrhs);
     cplx *alpha = malloc(sizeof(cplx) * (size_t)n_sel * nl * nrhs);
@@ -560,21 +588,26 @@ int orc_apply(int op, int side, int limit, double kre, double kim, int p,
             ey[i] = tgt_y[t];
             ectr[i] = i;
         }
-        orc_form_locals(op == OP_GRAD_S ? OP_S : op, n_sel, cx, cy, n_src, src_x, src_y,
+        orc_form_locals(op == OP_GRAD_S ? OP_S : (op == OP_GRAD_D ? OP_D : op), n_sel, cx, cy, n_src, src_x, src_y,
                         src_nx, src_ny, wd, nrhs, kre, kim, p, alpha);
         orc_eval_locals(n_sel, ex, ey, ectr, cx, cy, alpha, nrhs, kre, kim, p,
-                        op == OP_GRAD_S ? WHAT_GRAD : WHAT_VALUE, val);
+                        grad ? WHAT_GRAD : WHAT_VALUE, val);
         double sgn = (sd == SIDE_EXT) ? 1.0 : -1.0;    /* +1 exterior, -1 interior */
         for (int i = 0; i < n_sel; ++i) {
             int t = sel ? sel[i] : i;
             for (int r = 0; r < nrhs; ++r) {
                 cplx dens = dens_tgt[(size_t)t * nrhs + r];
-                if (op == OP_GRAD_S) {
+                if (grad) {
                     cplx gx = val[((size_t)i * 2 + 0) * nrhs + r];
                     cplx gy = val[((size_t)i * 2 + 1) * nrhs + r];
-                    if (side != SIDE_TWO && limit == LIMIT_PV) {
+                    if (side != SIDE_TWO && limit == LIMIT_PV && op == OP_GRAD_S) {
                         gx += sgn * 0.5 * tgt_nx[t] * dens;
                         gy += sgn * 0.5 * tgt_ny[t] * dens;
+                    }
+                    if (side != SIDE_TWO && limit == LIMIT_PV && op == OP_GRAD_D) {
+                        cplx ds = dsigma_ds(q_tgt, t, nrhs, r, dens_tgt, tgt_w);
+                        gx -= sgn * 0.5 * (-tgt_ny[t]) * ds;     /* tangent t = (-n_y, n_x) */
+                        gy -= sgn * 0.5 * tgt_nx[t] * ds;
                     }
                     if (side == SIDE_TWO) { gx *= 0.5; gy *= 0.5; }
                     out[((size_t)i * 2 + 0) * nrhs + r] += gx;
