@@ -62,12 +62,16 @@ enum {
   QBX_ENOMEM = 7           /* workspace too small / allocation failed */
 };
 
-/* Operators: S sigma, D mu, grad S sigma (Sec. 1, Sec. 3.2), and R sigma =
+/* Operators: S sigma, D mu, grad S sigma (Sec. 1, Sec. 3.2), R sigma =
  * integral of t(x') . grad_{x'} G(x, x') sigma(x') ds (the tangential
  * dipole, Sec. 3.2 eq. riesz-def: continuous across the curve since
- * n . t = 0).  R is accepted by qbx_apply and qbx_far, not by
- * qbx_apply_ops, the batch, the adjoints or qbx_apply_static. */
-enum { QBX_OP_S = 0, QBX_OP_D = 1, QBX_OP_GRAD_S = 2, QBX_OP_R = 3 };
+ * n . t = 0), and grad D mu, the target gradient of the double layer
+ * (Sec. 3.2, eq. dlpderiv: PV = lim -/+ t dmu/ds / 2, + exterior), output
+ * [n_tgt][2][nrhs] like grad S.  R is accepted by qbx_apply and qbx_far;
+ * grad D by qbx_apply on the surface only (coefficients formed unfused,
+ * a4 + a6); neither by qbx_apply_ops, the batch, the adjoints or
+ * qbx_apply_static. */
+enum { QBX_OP_S = 0, QBX_OP_D = 1, QBX_OP_GRAD_S = 2, QBX_OP_R = 3, QBX_OP_GRAD_D = 4 };
 enum { QBX_SIDE_INT = 0, QBX_SIDE_EXT = 1, QBX_SIDE_TWO = 2 };
 enum { QBX_LIMIT_ONE_SIDED = 0, QBX_LIMIT_PV = 1 };
 enum { QBX_VALUE = 0, QBX_GRAD = 1 };
@@ -148,6 +152,17 @@ int qbx_geometry(qbx_plan *plan, qbx_geom *g, const double *t_edges,
                  const double *gam_tgt, const double *dgam_tgt,
                  const double *gam_src, const double *dgam_src,
                  double r_factor, void *stream);
+
+/* qbx_geometry with a choice of expansion radius: QBX_RADIUS_H gives
+ * r = r_factor * panel_h (as qbx_geometry), QBX_RADIUS_SQRT_H gives
+ * r = r_factor * sqrt(panel_h): r refined more slowly than h, which makes
+ * QBX classically convergent without source oversampling (the remarks after
+ * eq. error_anal, Sec. 3.1).  QBX_EINVAL for another rule. */
+enum { QBX_RADIUS_H = 0, QBX_RADIUS_SQRT_H = 1 };
+int qbx_geometry_rule(qbx_plan *plan, qbx_geom *g, const double *t_edges,
+                      const double *gam_tgt, const double *dgam_tgt,
+                      const double *gam_src, const double *dgam_src,
+                      int rule, double r_factor, void *stream);
 
 /* Source oversampling (Sec. 3.4.2): per panel, polynomial interpolation of
  * dens_tgt [n_tgt][nrhs] from the target to the source nodes, times the source
@@ -259,6 +274,8 @@ int qbx_apply_adjoint(qbx_plan *plan, const qbx_geom *g, int op, int side, int l
  *     qbx_geometry (device);
  *   g_gam_tgt, g_dgam_tgt [n_tgt][2], g_gam_src, g_dgam_src [n_src][2]:
  *     device outputs, overwritten (summed over the right-hand sides).
+ * The geometry must have r = r_factor * panel_h (qbx_geometry, or
+ * QBX_RADIUS_H): the chain through the radius uses dr/dh = r/h.
  * Uses the plan's workspace (qbx_shape_adjoint_workspace_bytes); too small
  * a workspace gives QBX_ENOMEM, bad arguments QBX_EINVAL, nothing launched. */
 int qbx_apply_shape_adjoint(qbx_plan *plan, const qbx_geom *g, int side, qbx_c64 k, int p,

@@ -21,6 +21,7 @@ struct qbx_plan {
   double* d_interp;   // [q_src][q_tgt]
   double* d_wgl_tgt;  // [q_tgt]
   double* d_wgl_src;  // [q_src]
+  double* d_diff;     // [q_tgt][q_tgt] d/dxi of the target-grid interpolant at its nodes
   int* d_status;
   void* ws;
   size_t ws_bytes;
@@ -118,6 +119,26 @@ void interp_matrix(int qt, int qs, std::vector<double>& Mx) {
       double s = 0.0;
       for (int n = 0; n < qt; ++n) s += (2.0 * n + 1.0) * 0.5 * Pt[i * qt + n] * Ps[n];
       Mx[(size_t)j * qt + i] = s * wt[i];
+    }
+  }
+}
+
+// Differentiation at the target nodes through the same Legendre expansion:
+// f'(x_i) = sum_j Dx[i][j] f_j, Dx[i][j] = sum_n (2n+1)/2 w_j P_n(x_j) P_n'(x_i),
+// with P'_{n+1} = P'_{n-1} + (2n+1) P_n.
+void diff_matrix(int q, std::vector<double>& Dx) {
+  std::vector<double> x(q), w(q), P(q * q), dP(q);
+  gl_rule(q, x.data(), w.data());
+  for (int j = 0; j < q; ++j) legendre_all(q, x[j], &P[j * q]);
+  Dx.assign((size_t)q * q, 0.0);
+  for (int i = 0; i < q; ++i) {
+    dP[0] = 0.0;
+    if (q > 1) dP[1] = 1.0;
+    for (int n = 1; n + 1 < q; ++n) dP[n + 1] = dP[n - 1] + (2.0 * n + 1.0) * P[i * q + n];
+    for (int j = 0; j < q; ++j) {
+      double acc = 0.0;
+      for (int n = 0; n < q; ++n) acc += (2.0 * n + 1.0) * 0.5 * P[j * q + n] * dP[n];
+      Dx[(size_t)i * q + j] = acc * w[j];
     }
   }
 }
@@ -274,19 +295,23 @@ int qbx_plan_create(qbx_plan** plan, int device, int q_tgt, int q_src, size_t wo
   CK(cudaSetDevice(device), "cudaSetDevice");
   qbx_plan* p = new qbx_plan();
   memset(p, 0, sizeof(*p));
+  p->min_waves = 1;
   p->device = device;
   p->q_tgt = q_tgt;
   p->q_src = q_src;
   cudaError_t e = cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, device);
-  std::vector<double> Mx, xt(q_tgt), wt(q_tgt), xs(q_src), ws(q_src);
+  std::vector<double> Mx, Dx, xt(q_tgt), wt(q_tgt), xs(q_src), ws(q_src);
   interp_matrix(q_tgt, q_src, Mx);
+  diff_matrix(q_tgt, Dx);
   gl_rule(q_tgt, xt.data(), wt.data());
   gl_rule(q_src, xs.data(), ws.data());
   if (e == cudaSuccess) e = cudaMalloc(&p->d_interp, Mx.size() * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&p->d_wgl_tgt, q_tgt * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&p->d_wgl_src, q_src * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&p->d_status, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&p->d_diff, Dx.size() * sizeof(double));
   if (e == cudaSuccess && workspace_bytes > 0) e = cudaMalloc(&p->ws, workspace_bytes);
+  if (e == cudaSuccess) e = cudaMemcpy(p->d_diff, Dx.data(), Dx.size() * sizeof(double), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(p->d_interp, Mx.data(), Mx.size() * sizeof(double), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(p->d_wgl_tgt, wt.data(), q_tgt * sizeof(double), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(p->d_wgl_src, ws.data(), q_src * sizeof(double), cudaMemcpyHostToDevice);
@@ -309,6 +334,7 @@ int qbx_plan_destroy(qbx_plan* p) {
   cudaFree(p->d_wgl_tgt);
   cudaFree(p->d_wgl_src);
   cudaFree(p->d_status);
+  cudaFree(p->d_diff);
   cudaFree(p->ws);
   delete p;
   return QBX_OK;
@@ -354,9 +380,9 @@ int qbx_sync_status(qbx_plan* p, void* stream) {
   return QBX_OK;
 }
 
-int qbx_geometry(qbx_plan* p, qbx_geom* g, const double* t_edges, const double* gam_tgt,
-                 const double* dgam_tgt, const double* gam_src, const double* dgam_src,
-                 double r_factor, void* stream) {
+int qbx_geometry_rule(qbx_plan* p, qbx_geom* g, const double* t_edges, const double* gam_tgt,
+                      const double* dgam_tgt, const double* gam_src, const double* dgam_src, int rule,
+                      double r_factor, void* stream) {
   if (int rc = check_plan(p)) return rc;
   if (!g) return fail(QBX_EINVAL, "geometry is NULL");
   g->n_tgt = g->M * g->q_tgt;
@@ -365,11 +391,18 @@ int qbx_geometry(qbx_plan* p, qbx_geom* g, const double* t_edges, const double* 
   if (!g->panel_h || !g->ctr_ratio || !g->src_w || !g->tgt_w) return fail(QBX_EINVAL, "geometry: NULL output");
   if (!t_edges || !gam_tgt || !dgam_tgt || !gam_src || !dgam_src) return fail(QBX_EINVAL, "NULL curve samples");
   if (!(r_factor > 0.0) || !isfinite(r_factor)) return fail(QBX_EINVAL, "r_factor must be > 0");
+  if (rule != QBX_RADIUS_H && rule != QBX_RADIUS_SQRT_H) return fail(QBX_EINVAL, "bad radius rule %d", rule);
   CK(cudaSetDevice(p->device), "cudaSetDevice");
   CK(launch_geometry(g->M, g->q_tgt, g->q_src, t_edges, gam_tgt, dgam_tgt, gam_src, dgam_src,
-                     p->d_wgl_tgt, p->d_wgl_src, r_factor, *g, (cudaStream_t)stream),
+                     p->d_wgl_tgt, p->d_wgl_src, r_factor, rule, *g, (cudaStream_t)stream),
      "geometry kernels");
   return QBX_OK;
+}
+
+int qbx_geometry(qbx_plan* p, qbx_geom* g, const double* t_edges, const double* gam_tgt,
+                 const double* dgam_tgt, const double* gam_src, const double* dgam_src,
+                 double r_factor, void* stream) {
+  return qbx_geometry_rule(p, g, t_edges, gam_tgt, dgam_tgt, gam_src, dgam_src, QBX_RADIUS_H, r_factor, stream);
 }
 
 int qbx_upsample(qbx_plan* p, const qbx_geom* g, const qbx_c64* dens_tgt, int nrhs,
@@ -685,11 +718,99 @@ static int apply_impl(qbx_plan* p, const qbx_geom* g, int ops, int side, int lim
   return QBX_OK;
 }
 
+// grad D (Sec. 3.2, eq. dlpderiv): the D coefficients of every centre of the
+// side(s) (a4 unfused), the gradient of each expansion at its target (a6),
+// and the finish with the tangential jump.  Workspace: oversampled density,
+// coefficients, gradients, then the coefficient partial sums.
+static int grad_d_impl(qbx_plan* p, const qbx_geom* g, int side, int limit, qbx_c64 k, int pp,
+                       const qbx_c64* dens, int nrhs, qbx_c64* out, void* stream) {
+  if (int rc = check_plan(p)) return rc;
+  if (int rc = check_geom(p, g, true)) return rc;
+  if (!g->tgt_w) return fail(QBX_EINVAL, "geometry: NULL target weights");
+  if (limit != QBX_LIMIT_ONE_SIDED && limit != QBX_LIMIT_PV) return fail(QBX_EINVAL, "bad limit %d", limit);
+  if (int rc = check_k(k)) return rc;
+  if (int rc = check_p(pp)) return rc;
+  if (nrhs < 1) return fail(QBX_EINVAL, "nrhs = %d < 1", nrhs);
+  if (!dens || !out) return fail(QBX_EINVAL, "NULL density or output");
+  int c0, nc;
+  if (int rc = side_range(side, g->n_tgt, &c0, &nc)) return rc;
+  const int nsides = side == QBX_SIDE_TWO ? 2 : 1;
+  const int side0 = side == QBX_SIDE_EXT ? QBX_SIDE_EXT : QBX_SIDE_INT;
+  const int ncoef = 2 * pp + 1;
+  int nr = nrhs;
+  while (nr > 1 && form_smem_bytes(pp, nr) > 160 * 1024) nr = (nr + 1) / 2;
+  if (form_smem_bytes(pp, nr) > 200 * 1024) return fail(QBX_EINVAL, "p = %d too large", pp);
+  const size_t b_wd = align256((size_t)g->n_src * nrhs * 16);
+  const size_t b_al = align256((size_t)nc * ncoef * nrhs * 16);
+  const size_t b_ev = align256((size_t)nc * 2 * nrhs * 16);
+  const size_t fixed = b_wd + b_al + b_ev + 512;
+  if (p->ws_bytes < fixed) return fail(QBX_ENOMEM, "workspace too small for grad D");
+  const size_t per_split = (size_t)nc * ncoef * nrhs * 16;
+  const int units = (nc + kFormThreads - 1) / kFormThreads;
+  const int ns = choose_split(p, units, g->n_src, per_split, p->ws_bytes - fixed);
+  if (ns < 1) return fail(QBX_ENOMEM, "workspace too small for the grad D partial sums");
+  CK(cudaSetDevice(p->device), "cudaSetDevice");
+  cudaStream_t st = (cudaStream_t)stream;
+  char* base = (char*)align256((size_t)p->ws);
+  void* wd = base;
+  void* alpha = base + b_wd;
+  void* ev = base + b_wd + b_al;
+  void* part = base + b_wd + b_al + b_ev;
+  CK(launch_upsample(g->M, g->q_tgt, g->q_src, nrhs, p->d_interp, g->src_w, dens, wd, st), "upsample");
+  if (p->timing) CK(cudaEventRecord(p->ev0, st), "timing event");
+  FormArgs a{};
+  a.kind = QBX_OP_D;
+  a.p = pp;
+  a.kre = k.re;
+  a.kim = k.im;
+  a.n_ctr = nc;
+  a.cx = g->ctr_x + c0;
+  a.cy = g->ctr_y + c0;
+  a.src = SrcView{g->src_x, g->src_y, g->src_nx, g->src_ny, g->n_src};
+  a.wd = wd;
+  a.nrhs = nrhs;
+  a.nsplit = ns;
+  a.src_per_split = split_len(g->n_src, ns);
+  a.part = part;
+  for (int r0 = 0; r0 < nrhs; r0 += nr) {
+    a.rhs0 = r0;
+    a.nr = std::min(nr, nrhs - r0);
+    CK(launch_form(a, st), "form kernel");
+  }
+  CK(launch_form_finish(nc, ncoef, ns, nrhs, part, alpha, p->d_status, st), "form finish");
+  EvalArgs e{};
+  e.what = QBX_GRAD;
+  e.p = pp;
+  e.kre = k.re;
+  e.kim = k.im;
+  e.n_eval = nc;
+  e.cx = g->ctr_x + c0;
+  e.cy = g->ctr_y + c0;
+  e.n_tgt = g->n_tgt;
+  e.tx = g->tgt_x;
+  e.ty = g->tgt_y;
+  e.alpha = alpha;
+  e.nrhs = nrhs;
+  e.out = ev;
+  e.n_ctr = nc;
+  e.status = p->d_status;
+  CK(launch_eval(e, st), "eval kernel");
+  if (p->timing) CK(cudaEventRecord(p->ev1, st), "timing event");
+  CK(launch_grad_d_finish(g->n_tgt, g->q_tgt, nsides, side0, limit, nrhs, ev, dens, g->tgt_nx, g->tgt_ny,
+                          g->tgt_w, p->d_wgl_tgt, p->d_diff, out, p->d_status, st),
+     "grad D finish");
+  return QBX_OK;
+}
+
 int qbx_apply(qbx_plan* p, const qbx_geom* g, int op, int side, int limit, qbx_c64 k, int pp,
               const qbx_c64* dens_tgt, int nrhs, int n_far, const double* x_far, qbx_c64* out_on,
               qbx_c64* out_far, void* stream) {
-  if (op != QBX_OP_S && op != QBX_OP_D && op != QBX_OP_GRAD_S && op != QBX_OP_R)
+  if (op != QBX_OP_S && op != QBX_OP_D && op != QBX_OP_GRAD_S && op != QBX_OP_R && op != QBX_OP_GRAD_D)
     return fail(QBX_EINVAL, "bad op %d", op);
+  if (op == QBX_OP_GRAD_D) {
+    if (n_far > 0) return fail(QBX_EINVAL, "far targets are not offered with grad D");
+    return grad_d_impl(p, g, side, limit, k, pp, dens_tgt, nrhs, out_on, stream);
+  }
   const qbx_c64* dens[3] = {dens_tgt, dens_tgt, dens_tgt};
   qbx_c64* out[3] = {out_on, out_on, out_on};
   if (op == QBX_OP_R)

@@ -108,11 +108,14 @@ cudaError_t launch_form_finish(int n_ctr, int ncoef, int nsplit, int nrhs, const
 cudaError_t launch_geometry(int M, int q_tgt, int q_src, const double* t_edges,
                             const double* gam_tgt, const double* dgam_tgt,
                             const double* gam_src, const double* dgam_src,
-                            const double* wgl_tgt, const double* wgl_src, double r_factor,
+                            const double* wgl_tgt, const double* wgl_src, double r_factor, int rule,
                             const qbx_geom& g, cudaStream_t st);
 cudaError_t launch_upsample(int M, int q_tgt, int q_src, int nrhs, const double* interp,
                             const double* src_w, const void* dens_tgt, void* wdens,
                             cudaStream_t st);
+cudaError_t launch_grad_d_finish(int n_tgt, int q_tgt, int nsides, int side0, int limit, int nrhs, const void* ev,
+                                 const void* dens, const double* tnx, const double* tny, const double* tw,
+                                 const double* wgl, const double* Dx, void* out, int* status, cudaStream_t st);
 cudaError_t launch_tangents(int n, const double* nx, const double* ny, double* tx, double* ty, cudaStream_t st);
 cudaError_t launch_assign(int n, const double* xy, int n_ctr, const double* cx,
                           const double* cy, const double* cr, int* out, cudaStream_t st);

@@ -38,12 +38,13 @@ __global__ void k_panel_h(int M, int q_src, const double* w, double* h) {
   h[m] = s;
 }
 
-__global__ void k_centres(int n_tgt, int q_tgt, double r_factor, const double* h, const double* tx,
+__global__ void k_centres(int n_tgt, int q_tgt, double r_factor, int rule, const double* h, const double* tx,
                           const double* ty, const double* tnx, const double* tny, double* cx,
                           double* cy, double* cr) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n_tgt) return;
-  const double r = r_factor * h[t / q_tgt];
+  const double hm = h[t / q_tgt];
+  const double r = rule == QBX_RADIUS_SQRT_H ? r_factor * sqrt(hm) : r_factor * hm;
   cx[t] = tx[t] - r * tnx[t];
   cy[t] = ty[t] - r * tny[t];
   cr[t] = r;
@@ -79,7 +80,7 @@ __global__ void k_ratio(int n_ctr, const double* cx, const double* cy, const dou
 cudaError_t launch_geometry(int M, int q_tgt, int q_src, const double* t_edges,
                             const double* gam_tgt, const double* dgam_tgt,
                             const double* gam_src, const double* dgam_src,
-                            const double* wgl_tgt, const double* wgl_src, double r_factor,
+                            const double* wgl_tgt, const double* wgl_src, double r_factor, int rule,
                             const qbx_geom& g, cudaStream_t st) {
   const int n_t = M * q_tgt, n_s = M * q_src;
   k_geom_nodes<<<(n_s + 255) / 256, 256, 0, st>>>(n_s, q_src, t_edges, gam_src, dgam_src, wgl_src,
@@ -87,7 +88,7 @@ cudaError_t launch_geometry(int M, int q_tgt, int q_src, const double* t_edges,
   k_geom_nodes<<<(n_t + 255) / 256, 256, 0, st>>>(n_t, q_tgt, t_edges, gam_tgt, dgam_tgt, wgl_tgt,
                                                  g.tgt_x, g.tgt_y, g.tgt_nx, g.tgt_ny, g.tgt_w);
   k_panel_h<<<(M + 127) / 128, 128, 0, st>>>(M, q_src, g.src_w, g.panel_h);
-  k_centres<<<(n_t + 255) / 256, 256, 0, st>>>(n_t, q_tgt, r_factor, g.panel_h, g.tgt_x, g.tgt_y,
+  k_centres<<<(n_t + 255) / 256, 256, 0, st>>>(n_t, q_tgt, r_factor, rule, g.panel_h, g.tgt_x, g.tgt_y,
                                               g.tgt_nx, g.tgt_ny, g.ctr_x, g.ctr_y, g.ctr_r);
   k_ratio<<<(2 * n_t + 255) / 256, 256, 0, st>>>(2 * n_t, g.ctr_x, g.ctr_y, g.ctr_r, n_s, g.src_x,
                                                 g.src_y, g.ctr_ratio);
@@ -127,6 +128,54 @@ __global__ void k_tangents(int n, const double* nx, const double* ny, double* tx
 cudaError_t launch_tangents(int n, const double* nx, const double* ny, double* tx, double* ty, cudaStream_t st) {
   if (n < 1) return cudaSuccess;
   k_tangents<<<(n + 255) / 256, 256, 0, st>>>(n, nx, ny, tx, ty);
+  return cudaGetLastError();
+}
+
+// grad D finish (Sec. 3.2, eq. dlpderiv): ev [n_ctr][2][nrhs] are the
+// gradients of the D expansions at the targets (interior centres first for
+// two sides).  Two-sided: the average; PV from one side: lim -/+ t dmu/ds / 2
+// (+ exterior), t = (-n_y, n_x), dmu/ds = (sum_j Dx[i][j] mu_j) w^GL_i / w_t.
+__global__ void k_grad_d_finish(int n_tgt, int q_tgt, int nsides, int side0, int limit, int nrhs,
+                                const cplx* ev, const cplx* dens, const double* tnx, const double* tny,
+                                const double* tw, const double* wgl, const double* Dx, cplx* out, int* status) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n_tgt * nrhs) return;
+  const int t = idx / nrhs, r = idx - t * nrhs;
+  cplx gx{0.0, 0.0}, gy{0.0, 0.0};
+  for (int sd = 0; sd < nsides; ++sd) {
+    const size_t row = ((size_t)(sd * n_tgt + t) * 2) * nrhs + r;
+    gx = gx + ev[row];
+    gy = gy + ev[row + nrhs];
+  }
+  if (nsides == 2) {
+    gx = 0.5 * gx;
+    gy = 0.5 * gy;
+  } else if (limit == QBX_LIMIT_PV) {
+    const int m = t / q_tgt, i = t - m * q_tgt;
+    const cplx* d = dens + (size_t)m * q_tgt * nrhs + r;
+    double re = 0.0, im = 0.0;
+    for (int j = 0; j < q_tgt; ++j) {
+      const double c = Dx[i * q_tgt + j];
+      re = fma(c, d[(size_t)j * nrhs].re, re);
+      im = fma(c, d[(size_t)j * nrhs].im, im);
+    }
+    const double f = wgl[i] / tw[t];
+    const cplx ds{re * f, im * f};
+    const double sg = side0 == QBX_SIDE_EXT ? 1.0 : -1.0;
+    gx = gx - (0.5 * sg * -tny[t]) * ds;
+    gy = gy - (0.5 * sg * tnx[t]) * ds;
+  }
+  out[((size_t)t * 2) * nrhs + r] = gx;
+  out[((size_t)t * 2 + 1) * nrhs + r] = gy;
+  if (!(isfinite(gx.re) && isfinite(gx.im) && isfinite(gy.re) && isfinite(gy.im))) atomicOr(status, 1);
+}
+
+cudaError_t launch_grad_d_finish(int n_tgt, int q_tgt, int nsides, int side0, int limit, int nrhs, const void* ev,
+                                 const void* dens, const double* tnx, const double* tny, const double* tw,
+                                 const double* wgl, const double* Dx, void* out, int* status, cudaStream_t st) {
+  const int n = n_tgt * nrhs;
+  k_grad_d_finish<<<(n + 255) / 256, 256, 0, st>>>(n_tgt, q_tgt, nsides, side0, limit, nrhs, (const cplx*)ev,
+                                                   (const cplx*)dens, tnx, tny, tw, wgl, Dx, (cplx*)out, status);
   return cudaGetLastError();
 }
 

@@ -19,7 +19,7 @@ import torch
 
 from . import build as _build
 
-OP_S, OP_D, OP_GRAD_S, OP_R = 0, 1, 2, 3
+OP_S, OP_D, OP_GRAD_S, OP_R, OP_GRAD_D = 0, 1, 2, 3, 4
 SIDE_INT, SIDE_EXT, SIDE_TWO = 0, 1, 2
 LIMIT_ONE_SIDED, LIMIT_PV = 0, 1
 VALUE, GRAD = 0, 1
@@ -101,6 +101,8 @@ def lib():
             L.qbx_batch_info.argtypes = [_P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I),
                                          ctypes.POINTER(I)]
             L.qbx_batch_info.restype = I
+            L.qbx_geometry_rule.argtypes = [_P, G, _P, _P, _P, _P, _P, I, D, _P]
+            L.qbx_geometry_rule.restype = I
             L.qbx_plan_set_min_waves.argtypes = [_P, I]
             L.qbx_plan_set_min_waves.restype = I
             L.qbx_plan_set_timing.argtypes = [_P, I]
@@ -247,7 +249,10 @@ def panel_nodes(t_edges, q):
     return (0.5 * (a + b)[:, None] + 0.5 * (b - a)[:, None] * x[None, :]).reshape(-1)
 
 
-def qbx_geometry(plan: Plan, curve, t_edges, r_factor=0.5) -> Geometry:
+RADIUS_H, RADIUS_SQRT_H = 0, 1
+
+
+def qbx_geometry(plan: Plan, curve, t_edges, r_factor=0.5, rule=RADIUS_H) -> Geometry:
     """Sample `curve` (t -> (gamma [n,2], gamma' [n,2])) at the panels' GL nodes
     and run qbx_geometry on the device."""
     dev = torch.device("cuda", plan.device)
@@ -257,10 +262,11 @@ def qbx_geometry(plan: Plan, curve, t_edges, r_factor=0.5) -> Geometry:
     gt, dgt = curve(t_tgt)
     gs, dgs = curve(t_src)
     up = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device=dev)
-    return qbx_geometry_samples(plan, t_edges, up(gt), up(dgt), up(gs), up(dgs), r_factor)
+    return qbx_geometry_samples(plan, t_edges, up(gt), up(dgt), up(gs), up(dgs), r_factor, rule)
 
 
-def qbx_geometry_samples(plan: Plan, t_edges, gam_tgt, dgam_tgt, gam_src, dgam_src, r_factor=0.5) -> Geometry:
+def qbx_geometry_samples(plan: Plan, t_edges, gam_tgt, dgam_tgt, gam_src, dgam_src, r_factor=0.5,
+                         rule=RADIUS_H) -> Geometry:
     """qbx_geometry from curve samples already on the device: gamma, gamma' at
     the target nodes [n_tgt, 2] and at the source nodes [n_src, 2] (float64,
     at panel_nodes(t_edges, q) of the plan's grids)."""
@@ -277,8 +283,9 @@ def qbx_geometry_samples(plan: Plan, t_edges, gam_tgt, dgam_tgt, gam_src, dgam_s
     g.r_factor = float(r_factor)
     g.t_tgt = panel_nodes(t_edges, plan.q_tgt)
     g.t_src = panel_nodes(t_edges, plan.q_src)
-    _check(lib().qbx_geometry(plan.handle, g.ref(), *[_ptr(a) for a in g.inputs], float(r_factor),
-                              _stream()))
+    _check(lib().qbx_geometry_rule(plan.handle, g.ref(), *[_ptr(a) for a in g.inputs], int(rule),
+                                   float(r_factor), _stream()))
+    g.rule = rule
     return g
 
 
@@ -328,7 +335,7 @@ def qbx_apply(plan: Plan, g: Geometry, op, side, limit, k, p, dens_tgt, x_far=No
     """On-surface apply of S, D or grad S (plus far targets x_far [n,2])."""
     d = _dens2d(dens_tgt, g.n_tgt)
     nrhs = d.shape[1]
-    shape = (g.n_tgt, 2, nrhs) if op == OP_GRAD_S else (g.n_tgt, nrhs)
+    shape = (g.n_tgt, 2, nrhs) if op in (OP_GRAD_S, OP_GRAD_D) else (g.n_tgt, nrhs)
     if out_on is None:
         out_on = torch.empty(shape, dtype=torch.complex128, device=d.device)
     n_far = 0 if x_far is None else x_far.shape[0]
@@ -382,6 +389,8 @@ def qbx_apply_shape_adjoint(plan: Plan, g: Geometry, side, k, p, dens, gout):
     """Gradient of L = Re sum conj(gout) (S dens) with respect to the curve
     samples given to qbx_geometry: returns (d gamma_tgt, d gamma'_tgt,
     d gamma_src, d gamma'_src), [n, 2] float64 each."""
+    if getattr(g, "rule", RADIUS_H) != RADIUS_H:
+        raise ValueError("the shape adjoint needs r = r_factor * h (RADIUS_H)")
     d = _dens2d(dens, g.n_tgt)
     go = _dens2d(gout, g.n_tgt)
     if go.shape != d.shape:
@@ -532,7 +541,7 @@ def qbx_apply_static(g: Geometry, op, side, limit, k, p, dens_tgt, out_on=None):
     the caller's (allocated here by torch when out_on is None)."""
     d = _dens2d(dens_tgt, g.n_tgt)
     nrhs = d.shape[1]
-    shape = (g.n_tgt, 2, nrhs) if op == OP_GRAD_S else (g.n_tgt, nrhs)
+    shape = (g.n_tgt, 2, nrhs) if op in (OP_GRAD_S, OP_GRAD_D) else (g.n_tgt, nrhs)
     if out_on is None:
         out_on = torch.empty(shape, dtype=torch.complex128, device=d.device)
     _check(lib().qbx_apply_static(g.ref(), op, side, limit, _k(k), p, _ptr(d), nrhs, _ptr(out_on), _stream()))

@@ -339,3 +339,35 @@ def test_apply_r_matches_oracle(cuda, side, limit, k, p, nrhs):
     assert rel(far, oracle.far(go, oracle.OP_R, k, oracle.upsample(go, dens), xy)) < TOL
     wd = qbx.qbx_upsample(plan, g, dev(dens))
     assert rel(qbx.qbx_far(plan, g, qbx.OP_R, k, wd, dev(xy)), far.cpu().numpy()) < 1e-13
+
+
+@pytest.mark.parametrize("q_src", [16, 64])
+def test_sqrt_h_radius_rule(cuda, q_src):
+    """r = c sqrt(h) (qbx_geometry_rule): centres and radii as the oracle's,
+    and S, D, grad S on them, with and without source oversampling."""
+    cur, M, k, p, c = W.starfish(0.2, 3), 20, 6.0, 10, 0.3
+    plan = qbx.Plan(16, q_src, n_src=M * q_src, n_ctr=2 * M * 16, ncoef=4, nrhs=2)
+    g = qbx.qbx_geometry(plan, cur, cur.edges(M), c, qbx.RADIUS_SQRT_H)
+    go = oracle.geometry(cur, cur.edges(M), 16, q_src, c, oracle.RADIUS_SQRT_H)
+    for name in ("ctr_x", "ctr_y", "ctr_r"):
+        assert rel(g[name], go[name]) < 1e-14, name
+    dens = W.complex_gaussian(21, g.n_tgt * 2).reshape(g.n_tgt, 2)
+    got = qbx.qbx_apply_ops(plan, g, (0, 1, 2), qbx.SIDE_TWO, 0, k, p, dev(dens))
+    for o in (0, 1, 2):
+        assert rel(got[o], oracle.apply(go, o, qbx.SIDE_TWO, 0, k, p, dens)) < TOL, o
+    with pytest.raises(qbx.QBXError):
+        qbx.qbx_geometry(plan, cur, cur.edges(M), c, 7)
+
+
+@pytest.mark.parametrize("side,limit", [(qbx.SIDE_INT, qbx.LIMIT_PV), (qbx.SIDE_EXT, qbx.LIMIT_PV),
+                                        (qbx.SIDE_EXT, qbx.LIMIT_ONE_SIDED), (qbx.SIDE_TWO, qbx.LIMIT_PV)])
+@pytest.mark.parametrize("k,p,nrhs", [(7.0, 10, 1), (4 + 0.6j, 6, 3)])
+def test_apply_grad_d_matches_oracle(cuda, side, limit, k, p, nrhs):
+    """grad D (Sec. 3.2, eq. dlpderiv) on 13 panels: unfused coefficients,
+    the expansion's gradient at the target, the tangential jump for the PV."""
+    plan, g, go = make(W.starfish(0.2, 3), 13, nrhs=nrhs, p=p)
+    dens = W.complex_gaussian(19, g.n_tgt * nrhs).reshape(g.n_tgt, nrhs)
+    got = qbx.qbx_apply(plan, g, qbx.OP_GRAD_D, side, limit, k, p, dev(dens))
+    qbx.qbx_sync_status(plan)
+    assert got.shape == (g.n_tgt, 2, nrhs)
+    assert rel(got, oracle.apply(go, oracle.OP_GRAD_D, side, limit, k, p, dens)) < TOL
