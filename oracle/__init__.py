@@ -63,6 +63,7 @@ def lib():
             L.orc_far.argtypes = [I, I, P, I, P, P, P, P, P, I, D, D, P]
             L.orc_assign_centres.argtypes = [I, P, I, I, P, P, P, P]
             L.orc_apply_s_tangent.argtypes = [I, D, D, I, I, I, I, P, D] + [P] * 4 + [I] + [P] * 4 + [P, I, P, P]
+            L.orc_apply_local.argtypes = [I, I, I, D, D, I, D, I, I, I] + [P] * 12 + [P, I, I, P, P]
             L.orc_num_threads.restype = I
             _lib = L
     return _lib
@@ -244,6 +245,30 @@ def apply(g, op, side, limit, k, p, dens_tgt, sel=None):
                          _p(d), nrhs, n_sel, selp, _p(out))
     if rc != 0:
         raise MemoryError("orc_apply failed")
+    return out
+
+
+def apply_local(g, op, side, limit, k, p, eta, dens_tgt, sel=None):
+    """Near-only QBX (Sec. 5 remark): source nodes with |x_s - c| < eta r
+    through the expansion at c, the rest by the smooth rule at the target;
+    jumps as apply().  ops S, D, grad S; nrhs <= 64."""
+    d = _dens2d(dens_tgt, g["n_tgt"])
+    nrhs = d.shape[1]
+    k = complex(k)
+    if sel is None:
+        n_out, n_sel, selp = g["n_tgt"], 0, None
+    else:
+        sel = np.ascontiguousarray(sel, dtype=np.int32)
+        n_out, n_sel, selp = sel.size, sel.size, _p(sel)
+    shape = (n_out, 2, nrhs) if op == OP_GRAD_S else (n_out, nrhs)
+    out = np.zeros(shape, dtype=np.complex128)
+    rc = lib().orc_apply_local(op, side, limit, k.real, k.imag, p, float(eta), g["M"], g["q_tgt"], g["q_src"],
+                               *[_p(g[n]) for n in ("src_x", "src_y", "src_nx", "src_ny", "src_w",
+                                                    "tgt_x", "tgt_y", "tgt_nx", "tgt_ny",
+                                                    "ctr_x", "ctr_y", "ctr_r")],
+                               _p(d), nrhs, n_sel, selp, _p(out))
+    if rc != 0:
+        raise ValueError(f"orc_apply_local failed ({rc})")
     return out
 
 

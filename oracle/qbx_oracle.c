@@ -869,6 +869,108 @@ int orc_apply_s_tangent(int side, double kre, double kim, int p, int M, int q_tg
     return fail ? 2 : 0;
 }
 
+/* ------------------------------------------------------------------------- */
+/* Near-only QBX (the optimisation remarked in Sec. 5: direct evaluation for  */
+/* distant interactions, QBX for near ones).  Reading: for the centre c of    */
+/* target x_t, a source node x_s is near when |x_s - c| < eta r_c; near nodes */
+/* go through the local expansion at c (form + evaluate, as orc_apply), the   */
+/* others through the smooth rule at x_t itself (as orc_far).  The jumps of   */
+/* orc_apply follow.  ops S, D, grad S; out as orc_apply.                    */
+/* ------------------------------------------------------------------------- */
+int orc_apply_local(int op, int side, int limit, double kre, double kim, int p, double eta,
+                    int M, int q_tgt, int q_src,
+                    const double *src_x, const double *src_y, const double *src_nx,
+                    const double *src_ny, const double *src_w,
+                    const double *tgt_x, const double *tgt_y, const double *tgt_nx,
+                    const double *tgt_ny,
+                    const double *ctr_x, const double *ctr_y, const double *ctr_r,
+                    const cplx *dens_tgt, int nrhs, int n_sel, const int *sel, cplx *out)
+{
+    int n_tgt = M * q_tgt, n_src = M * q_src, nl = 2 * p + 1;
+    int ncomp = (op == OP_GRAD_S) ? 2 : 1;
+    if (op != OP_S && op != OP_D && op != OP_GRAD_S) return 1;
+    if (n_sel <= 0 || !sel) n_sel = n_tgt, sel = NULL;
+    cplx *wd = malloc(sizeof(cplx) * (size_t)n_src * nrhs);
+    if (!wd) return 2;
+    orc_upsample(M, q_tgt, q_src, nrhs, src_w, dens_tgt, wd);
+    for (size_t i = 0; i < (size_t)n_sel * ncomp * nrhs; ++i) out[i] = 0.0;
+    int s0 = (side == SIDE_TWO) ? SIDE_INT : side;
+    int s1 = (side == SIDE_TWO) ? SIDE_EXT : side;
+    cplx k = kre + I * kim;
+    int fail = 0;
+    for (int sd = s0; sd <= s1; ++sd) {
+        double sgn = (sd == SIDE_EXT) ? 1.0 : -1.0;
+        #pragma omp parallel for schedule(dynamic, 4)
+        for (int i = 0; i < n_sel; ++i) {
+            int t = sel ? sel[i] : i;
+            size_t c = (size_t)sd * n_tgt + t;
+            double cx = ctr_x[c], cy = ctr_y[c], lim = eta * ctr_r[c];
+            /* near sources, compacted */
+            double *nx_ = malloc(sizeof(double) * 4 * (size_t)n_src);
+            cplx *nwd = malloc(sizeof(cplx) * (size_t)n_src * nrhs);
+            cplx *al = malloc(sizeof(cplx) * (size_t)nl * nrhs);
+            cplx val[2 * 64];
+            if (!nx_ || !nwd || !al || nrhs > 64) {
+                free(nx_); free(nwd); free(al);
+                #pragma omp atomic write
+                fail = 1;
+                continue;
+            }
+            double *ny_ = nx_ + n_src, *nnx = ny_ + n_src, *nny = nnx + n_src;
+            int nn = 0;
+            cplx far[2 * 64];
+            for (int q = 0; q < ncomp * nrhs; ++q) far[q] = 0.0;
+            for (int s = 0; s < n_src; ++s) {
+                if (hypot(src_x[s] - cx, src_y[s] - cy) < lim) {
+                    nx_[nn] = src_x[s]; ny_[nn] = src_y[s]; nnx[nn] = src_nx[s]; nny[nn] = src_ny[s];
+                    for (int r = 0; r < nrhs; ++r) nwd[(size_t)nn * nrhs + r] = wd[(size_t)s * nrhs + r];
+                    ++nn;
+                } else {   /* smooth rule at the target */
+                    double rx = tgt_x[t] - src_x[s], ry = tgt_y[t] - src_y[s];
+                    double d = hypot(rx, ry);
+                    cplx h0, h1;
+                    orc_hankel01(k * d, &h0, &h1);
+                    for (int r = 0; r < nrhs; ++r) {
+                        cplx w = wd[(size_t)s * nrhs + r];
+                        if (op == OP_S) far[r] += (I / 4.0) * w * h0;
+                        else if (op == OP_D) far[r] += (I * k / 4.0) * w * h1 * (rx * src_nx[s] + ry * src_ny[s]) / d;
+                        else {
+                            far[r] += -(I * k / 4.0) * w * h1 * rx / d;
+                            far[nrhs + r] += -(I * k / 4.0) * w * h1 * ry / d;
+                        }
+                    }
+                }
+            }
+            double ccx[1] = {cx}, ccy[1] = {cy}, ex[1] = {tgt_x[t]}, ey[1] = {tgt_y[t]};
+            int ec[1] = {0};
+            orc_form_locals(op == OP_D ? OP_D : OP_S, 1, ccx, ccy, nn, nx_, ny_, nnx, nny, nwd, nrhs, kre, kim, p, al);
+            orc_eval_locals(1, ex, ey, ec, ccx, ccy, al, nrhs, kre, kim, p,
+                            op == OP_GRAD_S ? WHAT_GRAD : WHAT_VALUE, val);
+            for (int r = 0; r < nrhs; ++r) {
+                cplx dens = dens_tgt[(size_t)t * nrhs + r];
+                if (op == OP_GRAD_S) {
+                    cplx gx = val[r] + far[r], gy = val[nrhs + r] + far[nrhs + r];
+                    if (side != SIDE_TWO && limit == LIMIT_PV) {
+                        gx += sgn * 0.5 * tgt_nx[t] * dens;
+                        gy += sgn * 0.5 * tgt_ny[t] * dens;
+                    }
+                    if (side == SIDE_TWO) { gx *= 0.5; gy *= 0.5; }
+                    out[((size_t)i * 2 + 0) * nrhs + r] += gx;
+                    out[((size_t)i * 2 + 1) * nrhs + r] += gy;
+                } else {
+                    cplx u = val[r] + far[r];
+                    if (op == OP_D && side != SIDE_TWO && limit == LIMIT_PV) u -= sgn * 0.5 * dens;
+                    if (side == SIDE_TWO) u *= 0.5;
+                    out[(size_t)i * nrhs + r] += u;
+                }
+            }
+            free(nx_); free(nwd); free(al);
+        }
+    }
+    free(wd);
+    return fail ? 2 : 0;
+}
+
 int orc_num_threads(void)
 {
 #ifdef _OPENMP

@@ -708,3 +708,40 @@ def test_grad_d_tangential_jump_and_normal_continuity():
     pv_e = oracle.apply(g, OP_GD, EXT, PV, k, p, mu, sel=sel)[:, :, 0]
     avg = 0.5 * (gm + gp)
     assert np.abs(pv_i - avg).max() < 3e-7 * scale and np.abs(pv_e - avg).max() < 3e-7 * scale
+
+
+# ---------------------------------------------------------------------------
+# Near-only QBX (Sec. 5 remark): QBX for near sources, the smooth rule for
+# the rest
+# ---------------------------------------------------------------------------
+def test_local_qbx_limits_and_agreement():
+    """eta large: every source is near and the result is the global apply;
+    eta = 0: every source goes through the smooth rule at the target (the far
+    quadrature evaluated at the target nodes); in between the difference from
+    the global apply falls like eta^-(p+1) (starfish, 32 panels, p = 12)."""
+    cur, M, k, p = W.starfish(), 32, 7.0, 12
+    g = oracle.geometry(cur, cur.edges(M), 16, 64)
+    d = W.density_cfg1(g["t_tgt"])
+    xy = np.stack([g["tgt_x"], g["tgt_y"]], 1)
+    wd = oracle.upsample(g, d)
+    for op in (OP_S, OP_D, OP_G):
+        full = oracle.apply(g, op, TWO, ONE, k, p, d)
+        assert relerr(oracle.apply_local(g, op, TWO, ONE, k, p, 1e6, d), full) < 1e-14
+        assert relerr(oracle.apply_local(g, op, INT, ONE, k, p, 0.0, d), oracle.far(g, op, k, wd, xy)) < 1e-14
+        e3 = relerr(oracle.apply_local(g, op, TWO, ONE, k, p, 3.0, d), full)
+        e8 = relerr(oracle.apply_local(g, op, TWO, ONE, k, p, 8.0, d), full)
+        assert e3 > 1e-10 and e8 < 5e-12 and e8 < e3 * (3.0 / 8.0) ** 10
+
+
+@pytest.mark.parametrize("m,k", [(3, 5.0), (2, 4 + 0.5j)])
+def test_local_qbx_circle_eigenvalues(m, k):
+    """The near-only variant (eta = 8) keeps the global apply's accuracy on the
+    circle: S e^{imt} = (i pi/2) J_m H_m e^{imt}, D^- = (i pi k/2) J_m H_m'."""
+    cur = W.circle(1.0)
+    g = oracle.geometry(cur, cur.edges(32), 16, 64)
+    dens = np.exp(1j * m * g["t_tgt"])
+    c = 0.5j * np.pi
+    S = oracle.apply_local(g, OP_S, INT, ONE, k, 12, 8.0, dens)[:, 0]
+    Dm = oracle.apply_local(g, OP_D, INT, ONE, k, 12, 8.0, dens)[:, 0]
+    assert relerr(S, c * sp.jv(m, k) * sp.hankel1(m, k) * dens) < 1e-10
+    assert relerr(Dm, c * k * sp.jv(m, k) * sp.h1vp(m, k) * dens) < 1e-10
