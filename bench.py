@@ -69,15 +69,15 @@ def flops_per_pair_ops(ops, p, nrhs=1):
 # on the full-size starfish workload, from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum); valid only for the kernel
 # sources it was taken with, identified by their hash.
-TRAFFIC = {"3107441e03059061": 1.89e6}   # profiles/k_apply_fused_S_D_gradS_starfish_M256_dram.md
+TRAFFIC = {"ef6e20a976f53d3e": 1.63e6}   # profiles/k_apply_fused_S_D_gradS_starfish_M256_dram.md
 KERNEL_SOURCES = ["qbx_apply_impl.cuh", "qbx_device.cuh", "special_tables.h", "qbx_apply_real.cu"]
 GROUP_SOURCES = ["qbx_group_impl.cuh", "qbx_apply_impl.cuh", "qbx_device.cuh", "special_tables.h"]
 # Hardware-counted FP64 operations per (centre, source) pair, 2 DFMA + DMUL +
 # DADD from ncu's smsp__sass_thread_inst_executed_op_{dfma,dmul,dadd}_pred_on
 # counters divided by the pairs of the captured launch, for the kernel
 # sources with the given hash (profiles/*_fp64_counts.md).
-HW_FP64_PER_PAIR = {"3107441e03059061": 572.3}         # fused S + D + grad S, p = 12, one rhs
-HW_FP64_PER_PAIR_GROUP = {"b0837c18d2fe8557": 763.4}   # group kernel, S + D, p = 10, 32 rhs
+HW_FP64_PER_PAIR = {"ef6e20a976f53d3e": 572.3}         # fused S + D + grad S, p = 12, one rhs
+HW_FP64_PER_PAIR_GROUP = {"1057cfa26ed62516": 763.4}   # group kernel, S + D, p = 10, 32 rhs
 
 
 def source_hash(names=KERNEL_SOURCES):
@@ -106,6 +106,22 @@ def kernel_traffic(wl, args):
     if args.separate or args.panels or args.ops:
         return None
     return TRAFFIC.get(kernel_source_hash())
+
+
+def max_over_ranks(x, torch, device, world):
+    """The largest of the ranks' values (the job's time under replicas); x
+    itself for one rank.  One all_reduce(MAX) of a float64 on `device`."""
+    if world <= 1:
+        return x
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world, units_per_rank, ms):
+    """Whole-job throughput: `world` replicas, each `units_per_rank` units in
+    `ms` (the max over ranks)."""
+    return world * units_per_rank / (ms * 1e-3)
 
 
 def env_rank():
@@ -289,12 +305,9 @@ def run_gpu(args, wl):
     steps_ms = [a.elapsed_time(b) for a, b in ev]
     step_ms = sum(steps_ms) / args.steps
     qbx.qbx_sync_status(plan)
-    if world > 1:
-        t = torch.tensor([step_ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        step_ms = float(t.item())
+    step_ms = max_over_ranks(step_ms, torch, dev, world)
     terms_step = len(wl.ops) * wl.terms_per_op()
-    value = world * terms_step / (step_ms * 1e-3)
+    value = job_rate(world, terms_step, step_ms)
 
     # roofline of the dominant kernel (the fused apply): algorithmic flops / duration
     pairs = wl.n_ctr * wl.n_src
@@ -336,8 +349,8 @@ def run_gpu(args, wl):
         e1.record(stream)
         e1.synchronize()
         e2e_ms += e0.elapsed_time(e1)
-    e2e_ms /= args.steps
-    e2e = {"value": world * terms_step / (e2e_ms * 1e-3), "unit": "terms/s",
+    e2e_ms = max_over_ranks(e2e_ms / args.steps, torch, dev, world)
+    e2e = {"value": job_rate(world, terms_step, e2e_ms), "unit": "terms/s",
            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms}
 
     launches = (3 * len(wl.ops)) if args.separate else (2 + len(wl.ops))   # upsample, fused, finish(es)
@@ -348,6 +361,9 @@ def run_gpu(args, wl):
             "gpu_launches": args.steps * launches,
             "targets_per_s": world * len(wl.ops) * wl.n_tgt * wl.nrhs / (step_ms * 1e-3),
             "pairs_per_s": world * len(wl.ops) * pairs / (step_ms * 1e-3)}
+    if rank == 0 and not args.panels and not args.separate:
+        line["near_only"] = run_local_compare(args, qbx, torch, plan, g, codes, wl, dens, outs, flush, stream,
+                                              step_ms)
     if rank == 0 and not args.no_batch and not args.panels:
         line["batched"] = run_batch_compare(args, qbx, torch)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -361,6 +377,31 @@ def run_gpu(args, wl):
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def run_local_compare(args, qbx, torch, plan, g, codes, wl, dens, outs, flush, stream, global_ms, eta=8.0):
+    """Near-only QBX (qbx_apply_local, sources beyond eta r by the smooth rule
+    at the target) on the same step: time per step and the largest relative
+    difference from the global apply's outputs (not the benchmark metric)."""
+    loc = {c: torch.empty_like(outs[c]) for c in outs}
+    for _ in range(2):
+        qbx.qbx_apply_ops(plan, g, codes, qbx.SIDE_TWO, 0, wl.k, wl.p, dens, out=loc, eta=eta)
+    torch.cuda.synchronize()
+    tot = 0.0
+    steps = max(1, min(args.steps, 5))
+    for s in range(steps):
+        flush.fill_(s & 0xFF)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        qbx.qbx_apply_ops(plan, g, codes, qbx.SIDE_TWO, 0, wl.k, wl.p, dens, out=loc, eta=eta)
+        e1.record(stream)
+        e1.synchronize()
+        tot += e0.elapsed_time(e1)
+    ms = tot / steps
+    qbx.qbx_apply_ops(plan, g, codes, qbx.SIDE_TWO, 0, wl.k, wl.p, dens, out=outs)
+    diff = max((torch.abs(loc[c] - outs[c]).max() / torch.abs(outs[c]).max()).item() for c in outs)
+    return {"eta": eta, "ms_per_step": ms, "speedup_vs_global": global_ms / ms, "max_rel_diff_vs_global": diff,
+            "call": "qbx_apply_local (sources with |x_s - c| >= eta r by the smooth rule at the target)"}
 
 
 def run_batch_compare(args, qbx, torch):

@@ -229,6 +229,16 @@ int qbx_apply(qbx_plan *plan, const qbx_geom *g, int op, int side, int limit, qb
 int qbx_apply_ops(qbx_plan *plan, const qbx_geom *g, int ops, int side, int limit, qbx_c64 k, int p,
                   const qbx_c64 *const dens[3], int nrhs, qbx_c64 *const out[3], void *stream);
 
+/* Near-only QBX (the optimisation remarked in Sec. 5: direct evaluation for
+ * distant interactions, QBX for near ones): as qbx_apply_ops, except that a
+ * source node with |x_s - c| >= eta r_c goes through the smooth rule at the
+ * centre's target (as qbx_far) instead of the expansion at c.  The result
+ * differs from qbx_apply_ops by about eta^-(p+1) relative (QBX truncation of
+ * the distant pairs); eta = 8 at p = 12 agrees to ~1e-13.  eta > 0, else
+ * QBX_EINVAL.  Always the fused kernel (no group kernel). */
+int qbx_apply_local(qbx_plan *plan, const qbx_geom *g, int ops, int side, int limit, qbx_c64 k, int p,
+                    double eta, const qbx_c64 *const dens[3], int nrhs, qbx_c64 *const out[3], void *stream);
+
 /* Plain smooth quadrature at off-surface points (Sec. 1, Sec. 2):
  * S = (i/4) sum wdens H0(kd), D = (ik/4) sum wdens H1(kd) (x-x_s).n_s/d,
  * grad S = -(ik/4) sum wdens H1(kd) (x-x_s)/d.  wdens_src [n_src][nrhs],

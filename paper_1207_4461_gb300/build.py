@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libqbx_gb300.so")
-SOURCES = ["qbx_apply_real.cu", "qbx_apply_cplx.cu", "qbx_far.cu", "qbx_misc.cu", "qbx_capi.cu", "qbx_batch.cu",
+SOURCES = ["qbx_apply_real.cu", "qbx_apply_cplx.cu", "qbx_apply_local.cu", "qbx_far.cu", "qbx_misc.cu", "qbx_capi.cu", "qbx_batch.cu",
            "qbx_adjoint.cu", "qbx_gmres.cu", "qbx_shape.cu",
            "qbx_static.cu"]
 HEADERS = ["qbx_device.cuh", "qbx_internal.h", "special_tables.h", "qbx_apply_impl.cuh",

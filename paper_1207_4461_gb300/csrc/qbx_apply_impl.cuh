@@ -239,12 +239,41 @@ __device__ __forceinline__ void pair_kernels(const KW<T>& kw, const T kk, const 
   }
 }
 
+// Near-only QBX (a source far from the centre goes through the smooth rule
+// at the target instead of the expansion): the raw kernel values of one
+// (target, source) pair in the same form as pair_kernels returns them, with
+// (ex, ey) = x_t - x_s, d = |x_t - x_s|:
+//   S: H0(kd);  D: k H1(kd) (e . n_s)/d;
+//   grad S: -k H1(kd) e/d, returned as GA = (grad . e_r)/k = -H1 (e . e_r)/d and
+//   GB = -(grad . e_theta) r/2 = k H1 (e . e_theta) r/(2d), which the
+//   epilogue maps back through k GA e_r - (2/r) GB e_theta.
+template <int OPS, typename T>
+__device__ __forceinline__ void pair_direct(const KW<T>& kw, const T kk, double ex, double ey, double nx, double ny,
+                                            double ux, double uy, double r, cplx& GS, cplx& K, cplx& GA,
+                                            cplx& GB) {
+  constexpr bool kS = OPS & OPB_S, kD = OPS & OPB_D, kG = OPS & OPB_G;
+  const double d2 = fma(ex, ex, ey * ey);
+  double inv, d, yq;
+  kw.geom(d2, inv, d, yq);
+  cplx H0, H1;
+  T twoz;
+  kw.hankel(d, inv, yq, H0, H1, twoz);
+  if (kS) GS = H0;
+  if (kD) K = smul(rmul(kk, fma(ex, nx, ey * ny) * inv), H1);
+  if (kG) {
+    GA = H1 * (-fma(ex, ux, ey * uy) * inv);
+    GB = smul(rmul(kk, 0.5 * r * fma(ex, -uy, ey * ux) * inv), H1);
+  }
+}
+
 // D through sums shared with grad S when both are requested:
 //   D = -k a J0 H1 + 2 k a D1 + (2/rho)(b D2 - a D3),
 //   D1 = sum_{l>=1} J_l cos(l psi) H_{l-1},  D2 = sum l J_l sin(l psi) H_l (= grad S's B / 2),
 //   D3 = sum l J_l cos(l psi) H_l,
 // otherwise by the coefficients e_m with the C_m, V_m recurrences.
-template <int OPS, typename T, int NR>
+// LOCAL: the near-only variant (a separate instance, so that the global
+// apply carries no per-pair test).
+template <int OPS, typename T, int NR, bool LOCAL = false>
 __global__ void __launch_bounds__(kApplyThreads)
 k_apply_fused(ApplyArgs a) {
   using L = ApplySmem<OPS, T, NR>;
@@ -276,6 +305,8 @@ k_apply_fused(ApplyArgs a) {
   const double ir = 1.0 / r;
   ux *= ir;
   uy *= ir;
+  // near-only QBX: sources at |x_s - c| >= eta r take the smooth rule
+  const double lim2 = (!LOCAL || kX || !(a.eta2 > 0.0)) ? INFINITY : a.eta2 * r * r;
   KW<T> kw;
   kw.init(a.kre, a.kim);
   const T kk = kw.kval();
@@ -349,8 +380,12 @@ k_apply_fused(ApplyArgs a) {
         ny = s_ny[j];
       }
       cplx GS, K, GA, GB, EX, EY;
-      pair_kernels<OPS, T, kApplyThreads>(kw, kk, J0, kneg_j0, cJ, cL, cG, p, dx, dy, nx, ny, ux, uy, GS,
-                                           K, GA, GB, EX, EY);
+      if (LOCAL && fma(dx, dx, dy * dy) >= lim2) {   // near-only QBX: a distant source
+        pair_direct<OPS, T>(kw, kk, r * ux - dx, r * uy - dy, nx, ny, ux, uy, r, GS, K, GA, GB);
+      } else {
+        pair_kernels<OPS, T, kApplyThreads>(kw, kk, J0, kneg_j0, cJ, cL, cG, p, dx, dy, nx, ny, ux, uy, GS,
+                                             K, GA, GB, EX, EY);
+      }
       // ---- weighted densities ----
       int slotn = 0;
       if (kS) {
@@ -403,10 +438,10 @@ k_apply_fused(ApplyArgs a) {
   }
 }
 
-template <int OPS, typename T, int NR>
+template <int OPS, typename T, int NR, bool LOCAL>
 static cudaError_t launch_apply_t(const ApplyArgs& a, cudaStream_t st) {
   const size_t smem = ApplySmem<OPS, T, NR>::bytes(a.p);
-  auto kern = k_apply_fused<OPS, T, NR>;
+  auto kern = k_apply_fused<OPS, T, NR, LOCAL>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   dim3 grid((a.n_ctr + kApplyThreads - 1) / kApplyThreads, a.nsplit);
@@ -414,15 +449,16 @@ static cudaError_t launch_apply_t(const ApplyArgs& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-// rhs per pass: single operator up to 8, several operators up to 4
-template <int OPS, typename T>
+// rhs per pass: single operator up to 8, several operators (or the
+// near-only variant) up to 4
+template <int OPS, typename T, bool LOCAL>
 static cudaError_t launch_apply_nr(const ApplyArgs& a, cudaStream_t st) {
-  if (a.nr <= 1) return launch_apply_t<OPS, T, 1>(a, st);
-  if constexpr (multi_op(OPS)) {
-    return launch_apply_t<OPS, T, 4>(a, st);
+  if (a.nr <= 1) return launch_apply_t<OPS, T, 1, LOCAL>(a, st);
+  if constexpr (multi_op(OPS) || LOCAL) {
+    return launch_apply_t<OPS, T, 4, LOCAL>(a, st);
   } else {
-    if (a.nr <= 4) return launch_apply_t<OPS, T, 4>(a, st);
-    return launch_apply_t<OPS, T, 8>(a, st);
+    if (a.nr <= 4) return launch_apply_t<OPS, T, 4, LOCAL>(a, st);
+    return launch_apply_t<OPS, T, 8, LOCAL>(a, st);
   }
 }
 
@@ -442,7 +478,7 @@ static size_t apply_smem_t(int ops, int p, int nr) {
 }
 
 // CTAs of the kernel instance that one SM holds at once.
-template <int OPS, typename T>
+template <int OPS, typename T, bool LOCAL>
 static int occupancy_t(int p, int nr) {
   // (the shared-memory opt-in must be set before the query when above 48 KB)
   auto occ = [](auto kern, size_t smem) {
@@ -451,41 +487,45 @@ static int occupancy_t(int p, int nr) {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, kApplyThreads, smem);
     return n;
   };
-  if (nr <= 1) return occ(k_apply_fused<OPS, T, 1>, ApplySmem<OPS, T, 1>::bytes(p));
-  if constexpr (multi_op(OPS)) {
-    return occ(k_apply_fused<OPS, T, 4>, ApplySmem<OPS, T, 4>::bytes(p));
+  if (nr <= 1) return occ(k_apply_fused<OPS, T, 1, LOCAL>, ApplySmem<OPS, T, 1>::bytes(p));
+  if constexpr (multi_op(OPS) || LOCAL) {
+    return occ(k_apply_fused<OPS, T, 4, LOCAL>, ApplySmem<OPS, T, 4>::bytes(p));
   } else {
-    if (nr <= 4) return occ(k_apply_fused<OPS, T, 4>, ApplySmem<OPS, T, 4>::bytes(p));
-    return occ(k_apply_fused<OPS, T, 8>, ApplySmem<OPS, T, 8>::bytes(p));
+    if (nr <= 4) return occ(k_apply_fused<OPS, T, 4, LOCAL>, ApplySmem<OPS, T, 4>::bytes(p));
+    return occ(k_apply_fused<OPS, T, 8, LOCAL>, ApplySmem<OPS, T, 8>::bytes(p));
   }
 }
 
-template <typename T>
+template <typename T, bool LOCAL = false>
 static int apply_occupancy_t(int ops, int p, int nr) {
   switch (ops) {
-    case OPB_S: return occupancy_t<OPB_S, T>(p, nr);
-    case OPB_D: return occupancy_t<OPB_D, T>(p, nr);
-    case OPB_G: return occupancy_t<OPB_G, T>(p, nr);
-    case OPB_S | OPB_D: return occupancy_t<OPB_S | OPB_D, T>(p, nr);
-    case OPB_S | OPB_G: return occupancy_t<OPB_S | OPB_G, T>(p, nr);
-    case OPB_D | OPB_G: return occupancy_t<OPB_D | OPB_G, T>(p, nr);
-    case OPB_S | OPB_D | OPB_G: return occupancy_t<OPB_S | OPB_D | OPB_G, T>(p, nr);
-    case OPB_G | OPB_X: return occupancy_t<OPB_G | OPB_X, T>(p, nr);
+    case OPB_S: return occupancy_t<OPB_S, T, LOCAL>(p, nr);
+    case OPB_D: return occupancy_t<OPB_D, T, LOCAL>(p, nr);
+    case OPB_G: return occupancy_t<OPB_G, T, LOCAL>(p, nr);
+    case OPB_S | OPB_D: return occupancy_t<OPB_S | OPB_D, T, LOCAL>(p, nr);
+    case OPB_S | OPB_G: return occupancy_t<OPB_S | OPB_G, T, LOCAL>(p, nr);
+    case OPB_D | OPB_G: return occupancy_t<OPB_D | OPB_G, T, LOCAL>(p, nr);
+    case OPB_S | OPB_D | OPB_G: return occupancy_t<OPB_S | OPB_D | OPB_G, T, LOCAL>(p, nr);
+    case OPB_G | OPB_X:
+      if constexpr (!LOCAL) return occupancy_t<OPB_G | OPB_X, T, false>(p, nr);
+      return 0;
     default: return 0;
   }
 }
 
-template <typename T>
+template <typename T, bool LOCAL = false>
 static cudaError_t launch_apply_ops(const ApplyArgs& a, cudaStream_t st) {
   switch (a.ops) {
-    case OPB_S: return launch_apply_nr<OPB_S, T>(a, st);
-    case OPB_D: return launch_apply_nr<OPB_D, T>(a, st);
-    case OPB_G: return launch_apply_nr<OPB_G, T>(a, st);
-    case OPB_S | OPB_D: return launch_apply_nr<OPB_S | OPB_D, T>(a, st);
-    case OPB_S | OPB_G: return launch_apply_nr<OPB_S | OPB_G, T>(a, st);
-    case OPB_D | OPB_G: return launch_apply_nr<OPB_D | OPB_G, T>(a, st);
-    case OPB_S | OPB_D | OPB_G: return launch_apply_nr<OPB_S | OPB_D | OPB_G, T>(a, st);
-    case OPB_G | OPB_X: return launch_apply_nr<OPB_G | OPB_X, T>(a, st);
+    case OPB_S: return launch_apply_nr<OPB_S, T, LOCAL>(a, st);
+    case OPB_D: return launch_apply_nr<OPB_D, T, LOCAL>(a, st);
+    case OPB_G: return launch_apply_nr<OPB_G, T, LOCAL>(a, st);
+    case OPB_S | OPB_D: return launch_apply_nr<OPB_S | OPB_D, T, LOCAL>(a, st);
+    case OPB_S | OPB_G: return launch_apply_nr<OPB_S | OPB_G, T, LOCAL>(a, st);
+    case OPB_D | OPB_G: return launch_apply_nr<OPB_D | OPB_G, T, LOCAL>(a, st);
+    case OPB_S | OPB_D | OPB_G: return launch_apply_nr<OPB_S | OPB_D | OPB_G, T, LOCAL>(a, st);
+    case OPB_G | OPB_X:
+      if constexpr (!LOCAL) return launch_apply_nr<OPB_G | OPB_X, T, false>(a, st);
+      return cudaErrorInvalidValue;
     default: return cudaErrorInvalidValue;
   }
 }

@@ -1,0 +1,18 @@
+// qbx_apply_local.cu -- instances of the near-only variant of the fused
+// apply (sources beyond eta r by the smooth rule at the target), real and
+// complex k, kept apart from the global instances.
+#include "qbx_apply_impl.cuh"
+
+namespace qbx {
+
+cudaError_t launch_apply_fused_local_real(const ApplyArgs& a, cudaStream_t st) {
+  return launch_apply_ops<double, true>(a, st);
+}
+cudaError_t launch_apply_fused_local_cplx(const ApplyArgs& a, cudaStream_t st) {
+  return launch_apply_ops<cplx, true>(a, st);
+}
+int apply_occupancy_local(int ops, bool ck, int p, int nr) {
+  return ck ? apply_occupancy_t<cplx, true>(ops, p, nr) : apply_occupancy_t<double, true>(ops, p, nr);
+}
+
+}  // namespace qbx

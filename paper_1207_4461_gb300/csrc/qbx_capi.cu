@@ -573,7 +573,8 @@ int qbx_far(qbx_plan* p, const qbx_geom* g, int op, qbx_c64 k, const qbx_c64* wd
 // source tangents in place of the normals, and no jump (ops must be D alone).
 static int apply_impl(qbx_plan* p, const qbx_geom* g, int ops, int side, int limit, qbx_c64 k, int pp,
                       const qbx_c64* const dens[3], int nrhs, qbx_c64* const out[3], int n_far,
-                      const double* x_far, qbx_c64* out_far, void* stream, bool tangent = false) {
+                      const double* x_far, qbx_c64* out_far, void* stream, bool tangent = false,
+                      double eta = 0.0) {
   if (int rc = check_plan(p)) return rc;
   if (int rc = check_geom(p, g, true)) return rc;
   if (ops < 1 || ops > 7) return fail(QBX_EINVAL, "operator set %d is not a non-empty subset of {S, D, grad S}", ops);
@@ -612,13 +613,15 @@ static int apply_impl(qbx_plan* p, const qbx_geom* g, int ops, int side, int lim
   // many right-hand sides of one density: the group kernel (kernel values
   // formed once per pair for all rhs); otherwise the fused kernel
   const bool ck = k.im != 0.0;
-  const bool group = nrhs >= 16 && nd == 1 && (ops == 1 || ops == 2 || ops == 3 || ops == 7);
+  const bool group = nrhs >= 16 && nd == 1 && (ops == 1 || ops == 2 || ops == 3 || ops == 7) && !(eta > 0.0);
   const int rg = 8;
   const int units = group ? (nc + kGrpCentres - 1) / kGrpCentres : (nc + kApplyThreads - 1) / kApplyThreads;
-  const int chunk = apply_chunk(ops);
+  const bool local = eta > 0.0;
+  const int chunk = local ? std::min(4, apply_chunk(ops)) : apply_chunk(ops);
   CK(cudaSetDevice(p->device), "cudaSetDevice");
   int occ;
   if (group) occ = ck ? group_occupancy_cplx(ops, pp, rg) : group_occupancy_real(ops, pp, rg);
+  else if (local) occ = apply_occupancy_local(ops, ck, pp, std::min(chunk, nrhs));
   else occ = ck ? apply_occupancy_cplx(ops, pp, std::min(chunk, nrhs)) : apply_occupancy_real(ops, pp, std::min(chunk, nrhs));
   const int ns = host_choose_split_waves(p->num_sms, occ, units, g->n_src, per_split, avail, p->min_waves);
   if (ns < 1) return fail(QBX_ENOMEM, "workspace too small for the apply partial sums");
@@ -662,6 +665,7 @@ static int apply_impl(qbx_plan* p, const qbx_geom* g, int ops, int side, int lim
   a.nsplit = ns;
   a.src_per_split = split_len(g->n_src, ns);
   a.part = part;
+  a.eta2 = eta > 0.0 ? eta * eta : 0.0;
   if (group) {
     GroupArgs ga{};
     ga.ops = ops;
@@ -816,6 +820,13 @@ int qbx_apply(qbx_plan* p, const qbx_geom* g, int op, int side, int limit, qbx_c
   if (op == QBX_OP_R)
     return apply_impl(p, g, 1 << QBX_OP_D, side, limit, k, pp, dens, nrhs, out, n_far, x_far, out_far, stream, true);
   return apply_impl(p, g, 1 << op, side, limit, k, pp, dens, nrhs, out, n_far, x_far, out_far, stream);
+}
+
+int qbx_apply_local(qbx_plan* p, const qbx_geom* g, int ops, int side, int limit, qbx_c64 k, int pp, double eta,
+                    const qbx_c64* const dens[3], int nrhs, qbx_c64* const out[3], void* stream) {
+  if (!dens || !out) return fail(QBX_EINVAL, "NULL density or output table");
+  if (!(eta > 0.0) || !isfinite(eta)) return fail(QBX_EINVAL, "eta must be finite and > 0");
+  return apply_impl(p, g, ops, side, limit, k, pp, dens, nrhs, out, 0, nullptr, nullptr, stream, false, eta);
 }
 
 int qbx_apply_ops(qbx_plan* p, const qbx_geom* g, int ops, int side, int limit, qbx_c64 k, int pp,

@@ -34,10 +34,15 @@ struct ApplyArgs {
   int nrhs, rhs0, nr;     // total rhs, first rhs of this chunk, chunk width
   int nsplit, src_per_split;
   void* part;             // [nsplit][n_ctr][ncomp][nrhs] complex, comps S, D, grad S (x, y)
+  double eta2;            // near-only QBX: if > 0, sources with |x_s - c|^2 >= eta2 r^2 by the
+                          // smooth rule at the target; otherwise (default) all through the expansion
 };
 cudaError_t launch_apply_fused(const ApplyArgs& a, cudaStream_t st);
 cudaError_t launch_apply_fused_real(const ApplyArgs& a, cudaStream_t st);
 cudaError_t launch_apply_fused_cplx(const ApplyArgs& a, cudaStream_t st);
+cudaError_t launch_apply_fused_local_real(const ApplyArgs& a, cudaStream_t st);
+cudaError_t launch_apply_fused_local_cplx(const ApplyArgs& a, cudaStream_t st);
+int apply_occupancy_local(int ops, bool ck, int p, int nr);   // near-only instances
 size_t apply_smem_bytes(int ops, bool ck, int p, int nr);
 size_t apply_smem_bytes_real(int ops, int p, int nr);
 size_t apply_smem_bytes_cplx(int ops, int p, int nr);

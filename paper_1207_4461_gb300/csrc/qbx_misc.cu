@@ -237,6 +237,7 @@ cudaError_t launch_apply_finish(int op, int side, int limit, int n_tgt, int nspl
 
 // Fused apply dispatch: real k (fitted real-argument Hankel path) or complex k.
 cudaError_t launch_apply_fused(const ApplyArgs& a, cudaStream_t st) {
+  if (a.eta2 > 0.0) return a.kim == 0.0 ? launch_apply_fused_local_real(a, st) : launch_apply_fused_local_cplx(a, st);
   return a.kim == 0.0 ? launch_apply_fused_real(a, st) : launch_apply_fused_cplx(a, st);
 }
 

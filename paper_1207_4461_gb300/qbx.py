@@ -101,6 +101,8 @@ def lib():
             L.qbx_batch_info.argtypes = [_P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I),
                                          ctypes.POINTER(I)]
             L.qbx_batch_info.restype = I
+            L.qbx_apply_local.argtypes = [_P, G, I, I, I, c64, I, D, ctypes.POINTER(_P), I, ctypes.POINTER(_P), _P]
+            L.qbx_apply_local.restype = I
             L.qbx_geometry_rule.argtypes = [_P, G, _P, _P, _P, _P, _P, I, D, _P]
             L.qbx_geometry_rule.restype = I
             L.qbx_plan_set_min_waves.argtypes = [_P, I]
@@ -454,9 +456,10 @@ def qbx_solve_exterior_dirichlet(plan: Plan, g: Geometry, k, eta, p, f, tol=1e-1
 OPS_S, OPS_D, OPS_GRAD_S = 1, 2, 4
 
 
-def qbx_apply_ops(plan: Plan, g: Geometry, ops, side, limit, k, p, dens, out=None):
+def qbx_apply_ops(plan: Plan, g: Geometry, ops, side, limit, k, p, dens, out=None, eta=None):
     """Several operators in one pass.  `ops`: iterable of OP_* codes; `dens`:
-    one density tensor for all, or a dict {op: tensor}; returns {op: output}."""
+    one density tensor for all, or a dict {op: tensor}; returns {op: output}.
+    eta > 0: near-only QBX (qbx_apply_local)."""
     ops = sorted(set(ops))
     if not isinstance(dens, dict):
         dens = {o: dens for o in ops}
@@ -472,7 +475,11 @@ def qbx_apply_ops(plan: Plan, g: Geometry, ops, side, limit, k, p, dens, out=Non
     dp = (_P * 3)(*[_ptr(dd[o]) if o in dd else None for o in range(3)])
     op_ = (_P * 3)(*[_ptr(out[o]) if o in out else None for o in range(3)])
     mask = sum(1 << o for o in ops)
-    _check(lib().qbx_apply_ops(plan.handle, g.ref(), mask, side, limit, _k(k), p, dp, nrhs, op_, _stream()))
+    if eta is None:
+        _check(lib().qbx_apply_ops(plan.handle, g.ref(), mask, side, limit, _k(k), p, dp, nrhs, op_, _stream()))
+    else:
+        _check(lib().qbx_apply_local(plan.handle, g.ref(), mask, side, limit, _k(k), p, float(eta), dp, nrhs, op_,
+                                     _stream()))
     return {o: out[o] for o in ops}
 
 

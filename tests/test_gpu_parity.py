@@ -371,3 +371,24 @@ def test_apply_grad_d_matches_oracle(cuda, side, limit, k, p, nrhs):
     qbx.qbx_sync_status(plan)
     assert got.shape == (g.n_tgt, 2, nrhs)
     assert rel(got, oracle.apply(go, oracle.OP_GRAD_D, side, limit, k, p, dens)) < TOL
+
+
+@pytest.mark.parametrize("ops,side,limit,k,eta", [((0, 1, 2), qbx.SIDE_TWO, 0, 7.0, 3.0),
+                                                  ((0,), qbx.SIDE_INT, 1, 3 + 0.5j, 5.0),
+                                                  ((1, 2), qbx.SIDE_EXT, 1, 9.0, 8.0)])
+def test_apply_local_matches_oracle(cuda, ops, side, limit, k, eta):
+    """Near-only QBX (qbx_apply_local): the oracle's near/far split with the
+    same eta; pairs exactly at the boundary may fall on either side, which
+    costs at most eta^-(p+1) of a pair's kernel."""
+    p, nrhs = 10, 2
+    plan, g, go = make(W.starfish(0.2, 3), 24, nrhs=nrhs, p=p)
+    dens = W.complex_gaussian(23, g.n_tgt * nrhs).reshape(g.n_tgt, nrhs)
+    got = qbx.qbx_apply_ops(plan, g, ops, side, limit, k, p, dev(dens), eta=eta)
+    qbx.qbx_sync_status(plan)
+    glob = qbx.qbx_apply_ops(plan, g, ops, side, limit, k, p, dev(dens))
+    for o in ops:
+        assert rel(got[o], oracle.apply_local(go, o, side, limit, k, p, eta, dens)) < TOL, o
+        # and it is not the global apply (every case has distant sources)
+        assert rel(got[o], glob[o].cpu().numpy()) > 1e-14, o
+    with pytest.raises(qbx.QBXError):
+        qbx.qbx_apply_ops(plan, g, ops, side, limit, k, p, dev(dens), eta=-1.0)

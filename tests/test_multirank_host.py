@@ -1,0 +1,61 @@
+"""The multi-rank leg of bench.py on CPU: two gloo ranks (replicas, no data
+path collective) agree on the job time (max over ranks) and the whole-job
+rate; the reference arm does its work on rank 0 only."""
+import os
+import socket
+import sys
+
+import pytest
+import torch
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank, world, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    ms = [80.0, 95.5][rank]
+    job_ms = bench.max_over_ranks(ms, torch, "cpu", world)
+    q.put((rank, job_ms, bench.job_rate(world, 1.0e10, job_ms)))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_agree_on_job_time_and_rate():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    got = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert [g[1] for g in got] == [95.5, 95.5]
+    assert all(abs(g[2] - 2 * 1.0e10 / 0.0955) < 1e-3 for g in got)
+
+
+def test_single_rank_needs_no_process_group():
+    assert bench.max_over_ranks(12.5, torch, "cpu", 1) == 12.5
+    assert bench.job_rate(1, 100.0, 1000.0) == 100.0
+
+
+def test_reference_arm_other_ranks_exit_without_work(monkeypatch, capsys):
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setenv("WORLD_SIZE", "2")
+
+    class A:
+        ref_sample, warmup, steps, gpus, separate = 48, 1, 1, 2, False
+    assert bench.run_reference(A(), None) == 0
+    assert capsys.readouterr().out == ""

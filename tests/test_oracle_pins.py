@@ -745,3 +745,25 @@ def test_local_qbx_circle_eigenvalues(m, k):
     Dm = oracle.apply_local(g, OP_D, INT, ONE, k, 12, 8.0, dens)[:, 0]
     assert relerr(S, c * sp.jv(m, k) * sp.hankel1(m, k) * dens) < 1e-10
     assert relerr(Dm, c * k * sp.jv(m, k) * sp.h1vp(m, k) * dens) < 1e-10
+
+
+def test_oracle_matches_its_frozen_output():
+    """tests/golden/starfish32_k5_p8_int_pv.txt (written by
+    tests/golden/make_golden.py from the oracle): any change of the oracle's
+    arithmetic shows here and must come with a regenerated fixture."""
+    import importlib.util
+    import os
+    here = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+    spec = importlib.util.spec_from_file_location("make_golden", os.path.join(here, "make_golden.py"))
+    mg = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mg)
+    stored = {}
+    for line in open(os.path.join(here, "starfish32_k5_p8_int_pv.txt")):
+        if line.startswith("#"):
+            continue
+        name, t, c, re, im = line.split()
+        stored[(name, int(t), int(c))] = complex(float(re), float(im))
+    got = {(n, t, c): complex(re, im) for n, t, c, re, im in mg.compute()}
+    assert got.keys() == stored.keys()
+    scale = max(abs(v) for v in stored.values())
+    assert max(abs(got[k] - stored[k]) for k in got) <= 1e-13 * scale
