@@ -159,22 +159,22 @@ def main():
     lines.append(f"#define QBX_HK_RED_HI {fmt(hi)}")
     lines.append(f"#define QBX_HK_RED_LO {fmt(lo)}")
     lines.append(f"// worst fitted amplitude error on the check grid: {worst:.2e}")
-    # amplitude table: [NI][4 parts Re B0, Im B0, Re B1, Im B1][DEG+1] plus 1 + mids
+    # amplitude table: [NI][DEG+1][4 parts Re B0, Im B0, Re B1, Im B1] (the four
+    # coefficients of one degree adjacent: two 16-byte loads), plus 1 + mids
     lines.append(f"QBX_HK_GQUAL double qbx_hk_mid1[{NI}] = {{")
     lines.append("  " + ", ".join(fmt(1.0 + tabs[0][i][0]) for i in range(NI)) + "};")
-    lines.append(f"QBX_HK_GQUAL double qbx_hk_amp[{NI}][4][{deg + 1}] = {{")
+    lines.append(f"QBX_HK_GQUAL __align__(16) double qbx_hk_amp[{NI}][{deg + 1}][4] = {{")
     for i in range(NI):
         rows = []
-        for n in (0, 1):
-            for part in (0, 1):
-                rows.append("{" + ", ".join(fmt(c) for c in tabs[n][i][1][part]) + "}")
+        for d in range(deg + 1):
+            rows.append("{" + ", ".join(fmt(tabs[n][i][1][part][d]) for n in (0, 1) for part in (0, 1)) + "}")
         lines.append("  {" + ", ".join(rows) + "},")
     lines.append("};")
     lines.append(f"QBX_HK_CQUAL double qbx_hk_ser[4][{NSER}] = {{")
     for arr in (j0, j1, y0, y1):
         lines.append("  {" + ", ".join(fmt(c) for c in arr) + "},")
     lines.append("};")
-    lines.append(f"QBX_HK_GQUAL double qbx_hk_phase[{NT}][2] = {{")
+    lines.append(f"QBX_HK_GQUAL __align__(16) double qbx_hk_phase[{NT}][2] = {{")
     for j in range(NT):
         a = 2 * mp.pi * j / NT - mp.pi / 4
         lines.append(f"  {{{fmt(mp.cos(a))}, {fmt(mp.sin(a))}}},")

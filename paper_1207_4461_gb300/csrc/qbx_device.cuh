@@ -100,8 +100,8 @@ __device__ __forceinline__ cplx expi_shift(double z) {
   const double t = r * r;
   const double c = fma(fma(1.0 / 24.0, t, -0.5), t, 1.0);
   const double s = fma(r * t, fma(1.0 / 120.0, t, -1.0 / 6.0), r);
-  const double tc = __ldg(&qbx_hk_phase[idx][0]);
-  const double ts = __ldg(&qbx_hk_phase[idx][1]);
+  const double2 tcs = __ldg(reinterpret_cast<const double2*>(&qbx_hk_phase[idx][0]));
+  const double tc = tcs.x, ts = tcs.y;
   return cplx{fma(tc, c, -ts * s), fma(tc, s, ts * c)};
 }
 
@@ -127,17 +127,18 @@ __device__ __forceinline__ void hankel01_real(double z, double invz, double s, c
     int i = (int)((__double2hiint(y) >> (20 - QBX_HK_LOG2_PER_UNIT)) & ((1 << QBX_HK_LOG2_PER_UNIT) - 1));
     i = i < QBX_HK_NI ? i : QBX_HK_NI - 1;   // floor(s * 2^LOG2_PER_UNIT)
     const double u = y - __ldg(&qbx_hk_mid1[i]);
-    const double* A = &qbx_hk_amp[i][0][0];
-    double b0r = __ldg(&A[0 * (QBX_HK_DEG + 1) + QBX_HK_DEG]);
-    double b0i = __ldg(&A[1 * (QBX_HK_DEG + 1) + QBX_HK_DEG]);
-    double b1r = __ldg(&A[2 * (QBX_HK_DEG + 1) + QBX_HK_DEG]);
-    double b1i = __ldg(&A[3 * (QBX_HK_DEG + 1) + QBX_HK_DEG]);
+    // [degree][Re B0, Im B0, Re B1, Im B1]: two 16-byte loads per degree
+    const double2* A = reinterpret_cast<const double2*>(&qbx_hk_amp[i][0][0]);
+    double2 c0 = __ldg(&A[2 * QBX_HK_DEG]), c1 = __ldg(&A[2 * QBX_HK_DEG + 1]);
+    double b0r = c0.x, b0i = c0.y, b1r = c1.x, b1i = c1.y;
 #pragma unroll
     for (int d = QBX_HK_DEG - 1; d >= 0; --d) {
-      b0r = fma(b0r, u, __ldg(&A[0 * (QBX_HK_DEG + 1) + d]));
-      b0i = fma(b0i, u, __ldg(&A[1 * (QBX_HK_DEG + 1) + d]));
-      b1r = fma(b1r, u, __ldg(&A[2 * (QBX_HK_DEG + 1) + d]));
-      b1i = fma(b1i, u, __ldg(&A[3 * (QBX_HK_DEG + 1) + d]));
+      c0 = __ldg(&A[2 * d]);
+      c1 = __ldg(&A[2 * d + 1]);
+      b0r = fma(b0r, u, c0.x);
+      b0i = fma(b0i, u, c0.y);
+      b1r = fma(b1r, u, c1.x);
+      b1i = fma(b1i, u, c1.y);
     }
     const cplx e = expi_shift(z);
     h0 = e * cplx{b0r, b0i};
