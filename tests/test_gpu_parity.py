@@ -392,3 +392,21 @@ def test_apply_local_matches_oracle(cuda, ops, side, limit, k, eta):
         assert rel(got[o], glob[o].cpu().numpy()) > 1e-14, o
     with pytest.raises(qbx.QBXError):
         qbx.qbx_apply_ops(plan, g, ops, side, limit, k, p, dev(dens), eta=-1.0)
+
+
+@pytest.mark.parametrize("k,p,nrhs", [(6.0, 40, 1), (6.0, 40, 20), (3 + 0.4j, 30, 2)])
+def test_maximum_orders(cuda, k, p, nrhs):
+    """The largest orders: p = QBX_MAX_P = 40 (real k; fused kernel and, with
+    20 rhs, the group kernel) and p = 30 for complex k (the fused kernel's
+    coefficient columns of complex J_l fill 208 KB of shared memory), on the
+    32-panel starfish, all three operators in one call."""
+    assert qbx.MAX_P == 40
+    cur = W.starfish()
+    plan, g, go = make(cur, 32, nrhs=nrhs, p=p)
+    dens = W.complex_gaussian(31, g.n_tgt * nrhs).reshape(g.n_tgt, nrhs)
+    got = qbx.qbx_apply_ops(plan, g, (0, 1, 2), qbx.SIDE_INT, qbx.LIMIT_PV, k, p, dev(dens))
+    qbx.qbx_sync_status(plan)
+    for o in (0, 1, 2):
+        assert rel(got[o], oracle.apply(go, o, qbx.SIDE_INT, qbx.LIMIT_PV, k, p, dens)) < TOL, o
+    with pytest.raises(qbx.QBXError):
+        qbx.qbx_apply_ops(plan, g, (0, 1, 2), qbx.SIDE_INT, qbx.LIMIT_PV, k, 41, dev(dens))
