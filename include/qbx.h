@@ -99,7 +99,7 @@ const char *qbx_last_error(void);
 /* Library ABI version (increments on incompatible changes). */
 int qbx_version(void);
 
-/* host.  q-node Gauss-Legendre rule on [-1,1] (the "underlying smooth rule"
+/* host.  q-node Gauss-Legendre rule on [-1,1] (the base smooth rule
  * of Sec. 3.1 / Sec. 4.1).  nodes, weights: host arrays of length q,
  * nodes ascending.  1 <= q <= QBX_MAX_Q, else QBX_EINVAL. */
 int qbx_gauss_legendre(int q, double *nodes, double *weights);

@@ -282,7 +282,7 @@ void orc_besselj_seq_array(int n, const double *zin, int nmax, double *jout)
 }
 
 /* ------------------------------------------------------------------------- */
-/* Geometry (Sec. 3.3, "informal description"; Sec. 4.1 discretisation).     */
+/* Geometry (Sec. 3.3 algorithm outline; Sec. 4.1 discretisation).           */
 /* Panel m spans [t_m, t_{m+1}] of the curve parameter.  The caller samples   */
 /* gamma and gamma' at the q-node Gauss-Legendre points of every panel.       */
 /*   n = (gamma'_y, -gamma'_x)/|gamma'|   outward for a counter-clockwise      */

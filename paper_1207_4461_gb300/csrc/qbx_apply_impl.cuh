@@ -1,5 +1,5 @@
 // qbx_apply_impl.cuh -- the storage-free QBX apply (the G_p kernel of Sec. 2,
-// eq. qbx-kernel; "each source adds its contribution directly", Sec. 3.3),
+// eq. qbx-kernel; every source adding to the target sum without stored coefficients, Sec. 3.3),
 // for any subset of {S, D, grad S} in one pass over the (centre, source)
 // pairs.  Included by qbx_apply_real.cu (real k) and qbx_apply_cplx.cu
 // (complex k), which instantiate it.

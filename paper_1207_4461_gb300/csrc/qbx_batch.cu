@@ -175,7 +175,7 @@ double lpt_makespan(const std::vector<GroupInst>& inst, const std::vector<GroupI
 }
 
 // The source chunk the model prefers: the smallest predicted makespan over
-// chunks 2^j * 32 (and "all sources"), ties to the larger chunk (fewer
+// chunks 2^j * 32 (and all sources), ties to the larger chunk (fewer
 // partial sums), within the partial-sum memory budget.
 int model_chunk(const qbx_batch* b, int slots, size_t budget) {
   std::vector<int> cand{(b->max_src + kGrpTile - 1) / kGrpTile * kGrpTile};

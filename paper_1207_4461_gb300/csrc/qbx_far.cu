@@ -1,5 +1,5 @@
 // qbx_far.cu -- far targets by the plain smooth quadrature rule (a8; Sec. 1,
-// Sec. 2 "high-accuracy region"), partial sums over source splits:
+// Sec. 2: targets where the smooth rule is accurate), partial sums over source splits:
 //   S: sum wd H0(kd);  D: sum wd H1(kd) (x - x_s).n_s / d;  grad S: sum wd H1(kd) (x - x_s)/d
 // (the factors i/4, ik/4, -ik/4 are applied by the finishing kernel).
 #include "qbx_apply_impl.cuh"
