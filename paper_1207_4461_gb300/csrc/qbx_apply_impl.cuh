@@ -293,7 +293,22 @@ k_apply_fused(ApplyArgs a) {
   T* sG = sL + ((kD || kG) ? P2 : 0);        // J_{l-1} - J_{l+1}
 
   const int tid = threadIdx.x;
-  const int c = blockIdx.x * kApplyThreads + tid;
+  // work item (centre block, source split).  With the grids' node counts
+  // given (near_q_tgt > 0), rank r = blockIdx.x / nblk takes for every block
+  // the split at offset 0, +1, -1, +2, ... (mod nsplit) from its home split,
+  // the one holding the sources of the block's own panels: the near-field
+  // items, whose pairs take the slower small-argument Hankel branch, are
+  // dispatched first and the last wave holds uniform far-field items.
+  const int nblk = (a.n_ctr + kApplyThreads - 1) / kApplyThreads;
+  const int cblk = (int)(blockIdx.x % (unsigned)nblk), rank = (int)(blockIdx.x / (unsigned)nblk);
+  int split = rank;
+  if (a.near_q_tgt > 0) {
+    const int tmid = (cblk * kApplyThreads + kApplyThreads / 2) % a.n_tgt;
+    const int home = min(a.nsplit - 1, (tmid / a.near_q_tgt) * a.near_q_src / a.src_per_split);
+    const int off = (rank & 1) ? (rank + 1) / 2 : -(rank / 2);
+    split = ((home + off) % a.nsplit + a.nsplit) % a.nsplit;
+  }
+  const int c = cblk * kApplyThreads + tid;
   const bool active = c < a.n_ctr;
   const int cc = active ? c : a.n_ctr - 1;
 
@@ -335,7 +350,7 @@ k_apply_fused(ApplyArgs a) {
 #pragma unroll
   for (int q = 0; q < NR; ++q) accS[q] = accD[q] = accA[q] = accB[q] = accX[q] = accY[q] = cplx{0.0, 0.0};
 
-  const int s_begin = blockIdx.y * a.src_per_split;
+  const int s_begin = split * a.src_per_split;
   const int s_end = min(a.src.n, s_begin + a.src_per_split);
   const cplx* wdp[3] = {reinterpret_cast<const cplx*>(a.wd[0]), reinterpret_cast<const cplx*>(a.wd[1]),
                         reinterpret_cast<const cplx*>(a.wd[2])};
@@ -417,7 +432,7 @@ k_apply_fused(ApplyArgs a) {
   if (!active) return;
   cplx* part = reinterpret_cast<cplx*>(a.part);
   constexpr int ncomp = ops_ncomp(OPS);
-  const size_t row = ((size_t)blockIdx.y * a.n_ctr + c) * ncomp;
+  const size_t row = ((size_t)split * a.n_ctr + c) * ncomp;
 #pragma unroll
   for (int q = 0; q < NR; ++q) {
     if (q >= a.nr) break;
@@ -444,7 +459,7 @@ static cudaError_t launch_apply_t(const ApplyArgs& a, cudaStream_t st) {
   auto kern = k_apply_fused<OPS, T, NR, LOCAL>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  dim3 grid((a.n_ctr + kApplyThreads - 1) / kApplyThreads, a.nsplit);
+  const unsigned grid = (unsigned)((a.n_ctr + kApplyThreads - 1) / kApplyThreads) * (unsigned)a.nsplit;
   kern<<<grid, kApplyThreads, smem, st>>>(a);
   return cudaGetLastError();
 }

@@ -623,7 +623,10 @@ static int apply_impl(qbx_plan* p, const qbx_geom* g, int ops, int side, int lim
   if (group) occ = ck ? group_occupancy_cplx(ops, pp, rg) : group_occupancy_real(ops, pp, rg);
   else if (local) occ = apply_occupancy_local(ops, ck, pp, std::min(chunk, nrhs));
   else occ = ck ? apply_occupancy_cplx(ops, pp, std::min(chunk, nrhs)) : apply_occupancy_real(ops, pp, std::min(chunk, nrhs));
-  const int ns = host_choose_split_waves(p->num_sms, occ, units, g->n_src, per_split, avail, p->min_waves);
+  // the near-only variant's items differ more in cost (distant pairs take the
+  // short direct path): four waves let the near-field items spread out
+  const int waves = local ? std::max(p->min_waves, 4) : p->min_waves;
+  const int ns = host_choose_split_waves(p->num_sms, occ, units, g->n_src, per_split, avail, waves);
   if (ns < 1) return fail(QBX_ENOMEM, "workspace too small for the apply partial sums");
   if (group ? (ck ? group_smem_cplx(ops, pp, rg) : group_smem_real(ops, pp, rg)) > 220 * 1024
             : apply_smem_bytes(ops, ck, pp, chunk) > 220 * 1024)
@@ -666,6 +669,8 @@ static int apply_impl(qbx_plan* p, const qbx_geom* g, int ops, int side, int lim
   a.src_per_split = split_len(g->n_src, ns);
   a.part = part;
   a.eta2 = eta > 0.0 ? eta * eta : 0.0;
+  a.near_q_tgt = g->q_tgt;   // near-field items first
+  a.near_q_src = g->q_src;
   if (group) {
     GroupArgs ga{};
     ga.ops = ops;

@@ -36,6 +36,7 @@ struct ApplyArgs {
   void* part;             // [nsplit][n_ctr][ncomp][nrhs] complex, comps S, D, grad S (x, y)
   double eta2;            // near-only QBX: if > 0, sources with |x_s - c|^2 >= eta2 r^2 by the
                           // smooth rule at the target; otherwise (default) all through the expansion
+  int near_q_tgt, near_q_src;   // > 0: near-field items first (node counts per panel); 0: plain order
 };
 cudaError_t launch_apply_fused(const ApplyArgs& a, cudaStream_t st);
 cudaError_t launch_apply_fused_real(const ApplyArgs& a, cudaStream_t st);
