@@ -374,7 +374,13 @@ def run_gpu(args, wl):
         line["batched"] = run_batch_compare(args, qbx, torch)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         terms, dt, cores = oracle_sample(wl, args.cpu_sample)
+        import oracle
+        oracle.set_num_threads(1)   # the same oracle on one core, smaller sample
+        terms1, dt1, _ = oracle_sample(wl, max(8, args.cpu_sample // 24))
+        oracle.set_num_threads(cores)
         line["cpu_baseline"] = {"value": terms / dt, "unit": "terms/s", "cores": cores, "kind": "oracle",
+                                "single_core_value": terms1 / dt1,
+                                "single_core_sample": f"{max(8, args.cpu_sample // 24)} targets, {dt1:.1f} s",
                                 "sample": f"{args.cpu_sample} of {wl.n_tgt} targets, both sides, S, D and "
                                           f"grad S, all {wl.n_src} sources; CPU: {cpu_model()}",
                                 "seconds": dt}

@@ -65,6 +65,7 @@ def lib():
             L.orc_apply_s_tangent.argtypes = [I, D, D, I, I, I, I, P, D] + [P] * 4 + [I] + [P] * 4 + [P, I, P, P]
             L.orc_apply_local.argtypes = [I, I, I, D, D, I, D, I, I, I] + [P] * 12 + [P, I, I, P, P]
             L.orc_num_threads.restype = I
+            L.orc_set_num_threads.argtypes = [I]
             _lib = L
     return _lib
 
@@ -336,3 +337,8 @@ def apply_s_tangent(curve, pert, t_edges, q_tgt: int, q_src: int, side, k, p, de
     if rc != 0:
         raise ValueError(f"orc_apply_s_tangent failed ({rc})")
     return u, (du if isinstance(pert, (list, tuple)) else du[0])
+
+
+def set_num_threads(n: int):
+    """OpenMP threads of the oracle's parallel loops (results do not depend on it)."""
+    lib().orc_set_num_threads(int(n))

@@ -971,6 +971,16 @@ int orc_apply_local(int op, int side, int limit, double kre, double kim, int p, 
     return fail ? 2 : 0;
 }
 
+void orc_set_num_threads(int n)
+{
+#ifdef _OPENMP
+    extern void omp_set_num_threads(int);
+    omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 int orc_num_threads(void)
 {
 #ifdef _OPENMP
