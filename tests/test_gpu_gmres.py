@@ -66,3 +66,30 @@ def test_gmres_point_source_field_outside(cuda):
     ref = 0.25j * sp.hankel1(0, k * np.hypot(xy[:, 0] - x0[0], xy[:, 1] - x0[1]))
     # the oracle's dense solve of the same system reproduces the field to 7e-11
     assert np.abs(u - ref).max() / np.abs(ref).max() < 1e-7
+
+
+def test_gmres_full_size_teardrop(cuda):
+    """The scattering solve at full size: the paper's teardrop with 1008
+    panels and 8 dyadic levels on each side of the corner (1024 panels,
+    16384 targets, 65536 sources), k = 30, p = 14, eta = k, four of the 64
+    plane waves; GMRES to 1e-10, then the residual recomputed by the oracle
+    at 16 sampled targets."""
+    k, p = 30.0, 14
+    cur = W.teardrop()
+    edges = W.dyadic_edges(1008, 8)
+    M = len(edges) - 1
+    assert M == 1024
+    plan = qbx.Plan(16, 64, n_src=M * 64, n_ctr=2 * M * 16, ncoef=2, nrhs=4)
+    g = qbx.qbx_geometry(plan, cur, edges)
+    ang = 2 * np.pi * np.array([0, 16, 33, 50]) / 64
+    tx, ty = g["tgt_x"].cpu().numpy(), g["tgt_y"].cpu().numpy()
+    f = -np.exp(1j * k * (tx[:, None] * np.cos(ang)[None, :] + ty[:, None] * np.sin(ang)[None, :]))
+    mu, its, res = qbx.qbx_solve_exterior_dirichlet(plan, g, k, k, p, dev(f), tol=1e-10, restart=60, maxiter=300)
+    assert np.all(res <= 1e-10) and its < 100
+    go = oracle.geometry(cur, edges, 16, 64)
+    sel = np.arange(7, g.n_tgt, 1024)
+    mu_h = mu.cpu().numpy()
+    S = oracle.apply(go, oracle.OP_S, oracle.SIDE_TWO, 0, k, p, mu_h, sel=sel)
+    D = oracle.apply(go, oracle.OP_D, oracle.SIDE_TWO, 0, k, p, mu_h, sel=sel)
+    r = 0.5 * mu_h[sel] + D - 1j * k * S - f[sel]
+    assert np.abs(r).max() / np.abs(f).max() < 1e-8
