@@ -336,6 +336,23 @@ int qbx_vec_orth_update(int n, int nrhs, int nv, const qbx_c64 *V, const qbx_c64
 int qbx_vec_scale_cols(int n, int nrhs, const double *a, const qbx_c64 *in, qbx_c64 *out, void *stream);
 int qbx_vec_combine(int n, int nrhs, int nv, const qbx_c64 *V, const qbx_c64 *y, qbx_c64 *x, void *stream);
 
+/* The assembled Nystrom matrix of the same combined-field operator (Sec. 4.2;
+ * Sec. 3.3 notes the discrete operator may be stored as a matrix): A~ =
+ * W^{1/2} (1/2 I + D - i eta S) W^{-1/2} with D and S the two-sided
+ * averages and W the target weights, n_tgt x n_tgt complex, written
+ * column-major into A (entry (t, t') at A[t' n_tgt + t]; 16 n_tgt^2 bytes,
+ * caller-owned device memory).  Row t holds, for both centres of target t,
+ * the truncated Graf sums against every source node carried back to the
+ * target grid by the per-panel interpolation.  q_tgt <= 16.  Async on
+ * stream.  qbx_solve_exterior_dirichlet_assembled then runs the same GMRES
+ * with one ZGEMM (cuBLAS) per iteration for all right-hand sides; k, eta
+ * and p are those the matrix was assembled with. */
+int qbx_assemble_cfie(qbx_plan *plan, const qbx_geom *g, qbx_c64 k, qbx_c64 eta, int p, qbx_c64 *A,
+                      void *stream);
+int qbx_solve_exterior_dirichlet_assembled(qbx_plan *plan, const qbx_geom *g, const qbx_c64 *A,
+                                           const qbx_c64 *f, int nrhs, double tol, int restart, int maxiter,
+                                           qbx_c64 *mu, int *iters, double *resid, void *stream);
+
 /* Batched apply: many curves, each with its own panels, wavenumber and nrhs
  * densities, in one persistent launch run as a CUDA graph (the paper's cost
  * remark, Sec. 5: the work is O(N N_t) per curve; many small curves would

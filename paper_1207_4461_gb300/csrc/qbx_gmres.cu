@@ -184,6 +184,7 @@ int qbx_vec_combine(int n, int nrhs, int nv, const qbx_c64* V, const qbx_c64* y,
 // the device; the (m+1) x m Hessenberg columns come to the host, where
 // Givens rotations update the residual estimates |g_{j+1}|.
 // ---------------------------------------------------------------------------
+#include <cublas_v2.h>
 #include <complex>
 #include <vector>
 
@@ -198,9 +199,11 @@ struct Dev {
 
 }  // namespace
 
-extern "C" int qbx_solve_exterior_dirichlet(qbx_plan* plan, const qbx_geom* g, qbx_c64 k, qbx_c64 eta, int p,
-                                            const qbx_c64* f, int nrhs, double tol, int restart, int maxiter,
-                                            qbx_c64* mu, int* iters, double* resid, void* stream) {
+// Adense: the sqrt-weighted matrix from qbx_assemble_cfie (column-major), or
+// NULL for matrix-free matvecs through qbx_apply_ops.
+static int solve_impl(qbx_plan* plan, const qbx_geom* g, qbx_c64 k, qbx_c64 eta, int p, const qbx_c64* Adense,
+                      const qbx_c64* f, int nrhs, double tol, int restart, int maxiter, qbx_c64* mu, int* iters,
+                      double* resid, void* stream) {
   if (!plan || !g || !f || !mu || nrhs < 1 || restart < 1 || maxiter < 1 || !(tol > 0.0))
     return gfail(QBX_EINVAL, "bad arguments to qbx_solve_exterior_dirichlet");
   const int n = g->n_tgt;
@@ -226,9 +229,29 @@ extern "C" int qbx_solve_exterior_dirichlet(qbx_plan* plan, const qbx_geom* g, q
   if ((rc = qbx_vec_scale_sqrtw(n, nrhs, g->tgt_w, f, (qbx_c64*)F.p, 0, stream))) return rc;
   if ((rc = qbx_vec_scale_sqrtw(n, nrhs, g->tgt_w, mu, (qbx_c64*)X.p, 0, stream))) return rc;
   const int ops = QBX_OPS_S | QBX_OPS_D;
-  // y = A~ x~ : density x~/sqrt(w), S and D two-sided in one pass, combine
+  struct Blas {
+    cublasHandle_t h = nullptr;
+    ~Blas() {
+      if (h) cublasDestroy(h);
+    }
+  } blas;
+  if (Adense) {
+    if (cublasCreate(&blas.h) != CUBLAS_STATUS_SUCCESS) return gfail(QBX_ECUDA, "cublasCreate failed");
+    if (cublasSetStream(blas.h, st) != CUBLAS_STATUS_SUCCESS) return gfail(QBX_ECUDA, "cublasSetStream failed");
+  }
+  // y = A~ x~ : density x~/sqrt(w), S and D two-sided in one pass, combine;
+  // or one ZGEMM with the assembled A~ (row-major [n][nrhs] vectors are the
+  // column-major nrhs x n matrices X^T, Y^T = X^T A~^T)
   auto matvec = [&](const qbx_c64* xs, qbx_c64* y) -> int {
     int r;
+    if (Adense) {
+      const cuDoubleComplex one = make_cuDoubleComplex(1.0, 0.0), zero = make_cuDoubleComplex(0.0, 0.0);
+      cublasStatus_t cs = cublasZgemm(blas.h, CUBLAS_OP_N, CUBLAS_OP_T, nrhs, n, n, &one,
+                                      reinterpret_cast<const cuDoubleComplex*>(xs), nrhs,
+                                      reinterpret_cast<const cuDoubleComplex*>(Adense), n, &zero,
+                                      reinterpret_cast<cuDoubleComplex*>(y), nrhs);
+      return cs == CUBLAS_STATUS_SUCCESS ? QBX_OK : gfail(QBX_ECUDA, "cublasZgemm failed");
+    }
     if ((r = qbx_vec_scale_sqrtw(n, nrhs, g->tgt_w, xs, (qbx_c64*)DEN.p, 1, stream))) return r;
     const qbx_c64* dens[3] = {(qbx_c64*)DEN.p, (qbx_c64*)DEN.p, nullptr};
     qbx_c64* outs[3] = {(qbx_c64*)SM.p, (qbx_c64*)DM.p, nullptr};
@@ -357,4 +380,19 @@ extern "C" int qbx_solve_exterior_dirichlet(qbx_plan* plan, const qbx_geom* g, q
     for (int r = 0; r < nrhs; ++r) resid[r] = rel[r];
   if (!done) return gfail(QBX_ENOCONV, "GMRES did not reach the tolerance within maxiter iterations");
   return QBX_OK;
+}
+
+extern "C" int qbx_solve_exterior_dirichlet(qbx_plan* plan, const qbx_geom* g, qbx_c64 k, qbx_c64 eta, int p,
+                                            const qbx_c64* f, int nrhs, double tol, int restart, int maxiter,
+                                            qbx_c64* mu, int* iters, double* resid, void* stream) {
+  return solve_impl(plan, g, k, eta, p, nullptr, f, nrhs, tol, restart, maxiter, mu, iters, resid, stream);
+}
+
+extern "C" int qbx_solve_exterior_dirichlet_assembled(qbx_plan* plan, const qbx_geom* g, const qbx_c64* A,
+                                                      const qbx_c64* f, int nrhs, double tol, int restart,
+                                                      int maxiter, qbx_c64* mu, int* iters, double* resid,
+                                                      void* stream) {
+  if (!A) return gfail(QBX_EINVAL, "NULL matrix");
+  return solve_impl(plan, g, qbx_c64{1.0, 0.0}, qbx_c64{0.0, 0.0}, 0, A, f, nrhs, tol, restart, maxiter, mu, iters,
+                    resid, stream);
 }

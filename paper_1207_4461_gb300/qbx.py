@@ -101,6 +101,11 @@ def lib():
             L.qbx_batch_info.argtypes = [_P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I),
                                          ctypes.POINTER(I)]
             L.qbx_batch_info.restype = I
+            L.qbx_assemble_cfie.argtypes = [_P, G, c64, c64, I, _P, _P]
+            L.qbx_assemble_cfie.restype = I
+            L.qbx_solve_exterior_dirichlet_assembled.argtypes = [_P, G, _P, _P, I, D, I, I, _P,
+                                                                 ctypes.POINTER(I), ctypes.POINTER(D), _P]
+            L.qbx_solve_exterior_dirichlet_assembled.restype = I
             L.qbx_apply_local.argtypes = [_P, G, I, I, I, c64, I, D, ctypes.POINTER(_P), I, ctypes.POINTER(_P), _P]
             L.qbx_apply_local.restype = I
             L.qbx_geometry_rule.argtypes = [_P, G, _P, _P, _P, _P, _P, I, D, _P]
@@ -437,17 +442,32 @@ def apply_s_shape_autograd(plan: Plan, t_edges, gam_tgt, dgam_tgt, gam_src, dgam
     return QBXShapeS.apply(dens, gam_tgt, dgam_tgt, gam_src, dgam_src, plan, t_edges, side, k, p, r_factor)
 
 
+def qbx_assemble_cfie(plan: Plan, g: Geometry, k, eta, p):
+    """The sqrt-weighted Nystrom matrix of 1/2 + D - i eta S (two-sided), as a
+    [n][n] tensor holding A~ column-major: tensor[t', t] = A~[t, t']."""
+    n = g.n_tgt
+    A = torch.empty((n, n), dtype=torch.complex128, device=torch.device("cuda", plan.device))
+    _check(lib().qbx_assemble_cfie(plan.handle, g.ref(), _k(k), _k(eta), p, _ptr(A), _stream()))
+    return A
+
+
 def qbx_solve_exterior_dirichlet(plan: Plan, g: Geometry, k, eta, p, f, tol=1e-10, restart=40, maxiter=200,
-                                 mu0=None, raise_on_noconv=True):
+                                 mu0=None, raise_on_noconv=True, A=None):
     """GMRES for (1/2 + D - i eta S) mu = f (two-sided D and S, sqrt-weight
-    unknowns).  Returns (mu, matvecs, relative residuals)."""
+    unknowns).  Returns (mu, matvecs, relative residuals).  With A (from
+    qbx_assemble_cfie with the same k, eta, p) every matvec is one ZGEMM."""
     ff = _dens2d(f, g.n_tgt)
     nrhs = ff.shape[1]
     mu = torch.zeros_like(ff) if mu0 is None else _dens2d(mu0, g.n_tgt).clone()
     it = ctypes.c_int(0)
     res = (ctypes.c_double * nrhs)()
-    rc = lib().qbx_solve_exterior_dirichlet(plan.handle, g.ref(), _k(k), _k(eta), p, _ptr(ff), nrhs, float(tol),
-                                            restart, maxiter, _ptr(mu), ctypes.byref(it), res, _stream())
+    if A is None:
+        rc = lib().qbx_solve_exterior_dirichlet(plan.handle, g.ref(), _k(k), _k(eta), p, _ptr(ff), nrhs, float(tol),
+                                                restart, maxiter, _ptr(mu), ctypes.byref(it), res, _stream())
+    else:
+        rc = lib().qbx_solve_exterior_dirichlet_assembled(plan.handle, g.ref(), _ptr(A), _ptr(ff), nrhs, float(tol),
+                                                          restart, maxiter, _ptr(mu), ctypes.byref(it), res,
+                                                          _stream())
     if rc != 0 and (raise_on_noconv or rc != 5):
         _check(rc)
     return mu, it.value, np.array(res[:])
