@@ -69,15 +69,15 @@ def flops_per_pair_ops(ops, p, nrhs=1):
 # on the full-size starfish workload, from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum); valid only for the kernel
 # sources it was taken with, identified by their hash.
-TRAFFIC = {"865b551b69dcf885": 1.61e6}   # profiles/k_apply_fused_S_D_gradS_starfish_M256_dram.md
+TRAFFIC = {"e98e9246b2d913fb": 1.73e6}   # profiles/k_apply_fused_S_D_gradS_starfish_M256_dram.md
 KERNEL_SOURCES = ["qbx_apply_impl.cuh", "qbx_device.cuh", "special_tables.h", "qbx_apply_real.cu"]
 GROUP_SOURCES = ["qbx_group_impl.cuh", "qbx_apply_impl.cuh", "qbx_device.cuh", "special_tables.h"]
 # Hardware-counted FP64 operations per (centre, source) pair, 2 DFMA + DMUL +
 # DADD from ncu's smsp__sass_thread_inst_executed_op_{dfma,dmul,dadd}_pred_on
 # counters divided by the pairs of the captured launch, for the kernel
 # sources with the given hash (profiles/*_fp64_counts.md).
-HW_FP64_PER_PAIR = {"865b551b69dcf885": 572.3}         # fused S + D + grad S, p = 12, one rhs
-HW_FP64_PER_PAIR_GROUP = {"2c6c65ada89a83cd": 763.4}   # group kernel, S + D, p = 10, 32 rhs
+HW_FP64_PER_PAIR = {"e98e9246b2d913fb": 572.3}         # fused S + D + grad S, p = 12, one rhs
+HW_FP64_PER_PAIR_GROUP = {"954b24ff2e9df65a": 763.4}   # group kernel, S + D, p = 10, 32 rhs
 
 
 def source_hash(names=KERNEL_SOURCES):
@@ -570,7 +570,7 @@ def run_solve(args):
             "assembled": {"assembly_s": asm_ms * 1e-3, "solve_s": asm_solve_ms * 1e-3, "matvecs": its_a,
                           "max_resid": float(np.max(res_a)), "max_rel_diff_vs_matrix_free": mu_diff,
                           "matrix_bytes": 16 * g.n_tgt * g.n_tgt,
-                          "call": "qbx_assemble_cfie + qbx_solve_exterior_dirichlet_assembled (cuBLAS ZGEMM)"},
+                          "call": "qbx_assemble_cfie + qbx_solve_exterior_dirichlet_assembled (cuBLAS ZGEMM3M)"},
             "oracle_sample": f"targets {sel.tolist()}, rhs {cols}",
             "clocks": clk}
     print(json.dumps(line))

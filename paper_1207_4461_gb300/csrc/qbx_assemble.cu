@@ -3,7 +3,7 @@
 // a matrix, Sec. 3.3): A = 1/2 I + D - i eta S with D and S two-sided
 // averages, in the sqrt-weight unknowns of Sec. 4.2,
 //   At[t][t'] = sqrt(w_t) A[t][t'] / sqrt(w_t'),
-// and the GMRES solve whose matvecs are then one complex GEMM (cuBLAS ZGEMM)
+// and the GMRES solve whose matvecs are then one complex GEMM (cuBLAS ZGEMM3M)
 // for all right-hand sides.
 //
 // Row t of A collects, for both centres of target t (interior, exterior;
