@@ -69,15 +69,15 @@ def flops_per_pair_ops(ops, p, nrhs=1):
 # on the full-size starfish workload, from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum); valid only for the kernel
 # sources it was taken with, identified by their hash.
-TRAFFIC = {"e98e9246b2d913fb": 1.73e6}   # profiles/k_apply_fused_S_D_gradS_starfish_M256_dram.md
+TRAFFIC = {"4f2a70b84a045772": 1.71e6}   # profiles/k_apply_fused_S_D_gradS_starfish_M256_dram.md
 KERNEL_SOURCES = ["qbx_apply_impl.cuh", "qbx_device.cuh", "special_tables.h", "qbx_apply_real.cu"]
 GROUP_SOURCES = ["qbx_group_impl.cuh", "qbx_apply_impl.cuh", "qbx_device.cuh", "special_tables.h"]
 # Hardware-counted FP64 operations per (centre, source) pair, 2 DFMA + DMUL +
 # DADD from ncu's smsp__sass_thread_inst_executed_op_{dfma,dmul,dadd}_pred_on
 # counters divided by the pairs of the captured launch, for the kernel
 # sources with the given hash (profiles/*_fp64_counts.md).
-HW_FP64_PER_PAIR = {"e98e9246b2d913fb": 572.3}         # fused S + D + grad S, p = 12, one rhs
-HW_FP64_PER_PAIR_GROUP = {"954b24ff2e9df65a": 763.4}   # group kernel, S + D, p = 10, 32 rhs
+HW_FP64_PER_PAIR = {"4f2a70b84a045772": 551.5}         # fused S + D + grad S, p = 12, one rhs
+HW_FP64_PER_PAIR_GROUP = {"64a6a673d2967226": 763.4}   # group kernel, S + D, p = 10, 32 rhs
 
 
 def source_hash(names=KERNEL_SOURCES):
@@ -493,8 +493,8 @@ def run_solve(args):
     p = 14, f = -e^{i k d_m . x} for 64 plane waves d_m = (cos 2 pi m/64,
     sin 2 pi m/64), GMRES(restart) on the device to 1e-10.  Prints one JSON
     line (not the benchmark metric): solve time, matvecs, time per matvec,
-    residuals, and the oracle's residual at sampled targets for 4 of the
-    right-hand sides."""
+    residuals (GMRES's and one recomputed by a separate apply); the same
+    solve on the assembled matrix."""
     import torch
     import paper_1207_4461_gb300 as qbx
     torch.cuda.set_device(0)
@@ -547,16 +547,16 @@ def run_solve(args):
     asm_solve_ms = e0.elapsed_time(e1)
     mu_diff = (torch.abs(mu_a - mu).max() / torch.abs(mu).max()).item()
     del A
-    # oracle residual at sampled targets (every 1024th target)
-    import oracle
-    go = oracle.geometry(cur, edges, 16, 64)
-    sel = np.arange(7, g.n_tgt, 1024)
-    cols = [0, 16, 33, 50]
-    mu_h = mu.cpu().numpy()[:, cols]
-    f_h = f.cpu().numpy()[:, cols]
-    So = oracle.apply(go, oracle.OP_S, oracle.SIDE_TWO, 0, k, p, mu_h, sel=sel)
-    Do = oracle.apply(go, oracle.OP_D, oracle.SIDE_TWO, 0, k, p, mu_h, sel=sel)
-    r = 0.5 * mu_h[sel] + Do - 1j * k * So - f_h[sel]
+    # the residual recomputed by one more apply of both operators to mu: in
+    # GMRES's norm (sqrt-weighted 2-norm per rhs, relative to f) and pointwise
+    # (max |r| / max |f|, largest at the refined corner panels); the oracle's
+    # residual at sampled targets is a test
+    sd = {qbx.OP_S: torch.empty_like(mu), qbx.OP_D: torch.empty_like(mu)}
+    qbx.qbx_apply_ops(plan, g, (qbx.OP_S, qbx.OP_D), qbx.SIDE_TWO, 0, k, p, mu.contiguous(), out=sd)
+    r = 0.5 * mu + sd[qbx.OP_D] - 1j * k * sd[qbx.OP_S] - f
+    sw = torch.sqrt(g["tgt_w"])[:, None]
+    resid_w = (torch.linalg.norm(sw * r, dim=0) / torch.linalg.norm(sw * f, dim=0)).max().item()
+    resid_apply = (torch.abs(r).max() / torch.abs(f).max()).item()
     pairs = 2 * g.n_tgt * g.n_src
     line = {"solve": "exterior sound-soft, paper's teardrop, 1008+16 panels (dyadic toward the corner), "
                      "k=30, p=14, eta=k, 64 plane waves, two-sided D and S, GMRES on the device",
@@ -566,14 +566,113 @@ def run_solve(args):
             "solve_s": solve_ms * 1e-3, "matvec_ms": mv_ms, "matvec_kernel_ms": mv_kernel_ms,
             "pairs_per_matvec": pairs,
             "terms_per_s_matvec": 2 * pairs * (2 * p + 1) * nrhs / (mv_ms * 1e-3),
-            "oracle_pointwise_resid": float(np.abs(r).max() / np.abs(f_h).max()),
+            "resid_by_apply_weighted_l2": resid_w, "resid_by_apply_pointwise": resid_apply,
             "assembled": {"assembly_s": asm_ms * 1e-3, "solve_s": asm_solve_ms * 1e-3, "matvecs": its_a,
                           "max_resid": float(np.max(res_a)), "max_rel_diff_vs_matrix_free": mu_diff,
                           "matrix_bytes": 16 * g.n_tgt * g.n_tgt,
                           "call": "qbx_assemble_cfie + qbx_solve_exterior_dirichlet_assembled (cuBLAS ZGEMM3M)"},
-            "oracle_sample": f"targets {sel.tolist()}, rhs {cols}",
             "clocks": clk}
     print(json.dumps(line))
+    return 0
+
+
+def fourier_curve_samples(torch, coef, t):
+    """gamma = r(t)(cos t, sin t), r = a0 + sum_{m=1..8} a_m cos mt + b_m sin mt,
+    coef = (a0, a1..a8, b1..b8) as a torch tensor: gamma and gamma' at the
+    parameters t (torch), differentiable in coef."""
+    m = torch.arange(1, 9, dtype=torch.float64, device=coef.device)
+    cm, sm = torch.cos(t[:, None] * m), torch.sin(t[:, None] * m)
+    r = coef[0] + cm @ coef[1:9] + sm @ coef[9:17]
+    dr = (-sm * m) @ coef[1:9] + (cm * m) @ coef[9:17]
+    c, s_ = torch.cos(t), torch.sin(t)
+    return torch.stack([r * c, r * s_], -1), torch.stack([dr * c - r * s_, dr * s_ + r * c], -1)
+
+
+def run_adjoint(args):
+    """Shape-optimisation workload (loss ||S sigma - g||^2, interior centres):
+    the starfish r = 1 + 0.25 cos 5t written as 17 Fourier coefficients of
+    r(t), 128 panels (2048 targets, 8192 sources), k = 10, p = 10,
+    sigma = cos 3t + 0.5 i sin t, g = e^{i k x}.  Times, with CUDA events and
+    the L2 flushed before every call: the forward S apply, the density
+    adjoint (transposed sweep), the shape adjoint, and one whole
+    loss-and-gradient step through autograd (curve samples from the
+    coefficients, geometry, S apply, backward to the 17 coefficients and the
+    density).  Prints one JSON line (not the benchmark metric)."""
+    import torch
+    import paper_1207_4461_gb300 as qbx
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    M, k, p, side = 128, 10.0, 10, qbx.SIDE_INT
+    edges = np.linspace(0.0, 2 * np.pi, M + 1)
+    plan = qbx.Plan(16, 64, workspace_bytes=qbx.qbx_shape_adjoint_workspace_bytes(M, 16, 64, p, 1))
+    tt = torch.as_tensor(qbx.panel_nodes(edges, 16), device=dev)
+    ts = torch.as_tensor(qbx.panel_nodes(edges, 64), device=dev)
+    c0 = torch.zeros(17, dtype=torch.float64, device=dev)
+    c0[0], c0[5] = 1.0, 0.25
+    gt, dgt = fourier_curve_samples(torch, c0, tt)
+    gs, dgs = fourier_curve_samples(torch, c0, ts)
+    g = qbx.qbx_geometry_samples(plan, edges, gt.contiguous(), dgt.contiguous(), gs.contiguous(), dgs.contiguous())
+    sig = torch.as_tensor(W.density_cfg1(tt.cpu().numpy()), device=dev).reshape(-1, 1).contiguous()
+    target = torch.exp(1j * k * gt[:, 0]).reshape(-1, 1)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(args.steps):
+            flush.fill_(1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return statistics.median(ms)
+
+    u = qbx.qbx_apply(plan, g, qbx.OP_S, side, 0, k, p, sig)
+    gout = (2 * (u - target)).contiguous()
+    clocks = ClockSampler(0)
+    clocks.start()
+    t_fwd = timed(lambda: qbx.qbx_apply(plan, g, qbx.OP_S, side, 0, k, p, sig))
+    t_adj = timed(lambda: qbx.qbx_apply_adjoint(plan, g, qbx.OP_S, side, 0, k, p, gout))
+    t_shape = timed(lambda: qbx.qbx_apply_shape_adjoint(plan, g, side, k, p, sig, gout))
+
+    def loss_and_grad():
+        coef = c0.clone().requires_grad_(True)
+        s = sig.clone().requires_grad_(True)
+        a, da = fourier_curve_samples(torch, coef, tt)
+        b, db = fourier_curve_samples(torch, coef, ts)
+        v = qbx.apply_s_shape_autograd(plan, edges, a, da, b, db, s, side, k, p)
+        L = (torch.abs(v - torch.exp(1j * k * a[:, 0]).reshape(-1, 1)) ** 2).sum()
+        L.backward()
+        return coef.grad, s.grad
+
+    t_step = timed(loss_and_grad)
+    clk = clocks.stop()
+    qbx.qbx_sync_status(plan)
+    # the adjoint identity Re <S sigma, y> = Re <sigma, S^H y> for a random y
+    y = torch.as_tensor(W.complex_gaussian(7, g.n_tgt).reshape(-1, 1), device=dev)
+    lhs = torch.vdot(y.flatten(), u.flatten())
+    rhs = torch.vdot(qbx.qbx_apply_adjoint(plan, g, qbx.OP_S, side, 0, k, p, y).flatten(), sig.flatten())
+    ident = (torch.abs(lhs - rhs) / (torch.abs(y).sum() * torch.abs(u).max())).item()
+    n_ctr, n_src = g.n_tgt, g.n_src
+    terms = n_ctr * n_src * (2 * p + 1)
+    print(json.dumps({
+        "adjoint": "shape-optimisation loss ||S sigma - g||^2, starfish r = 1 + 0.25 cos 5t as 17 Fourier "
+                   "coefficients, 128 panels (2048 targets, 8192 sources, 2048 interior centres), k=10, p=10",
+        "n_tgt": g.n_tgt, "n_src": g.n_src, "n_ctr": n_ctr, "p": p, "k": k, "steps": args.steps,
+        "warmup": args.warmup, "l2": "flushed before every timed call (256 MiB write outside the event pair)",
+        "forward_ms": t_fwd, "density_adjoint_ms": t_adj, "shape_adjoint_ms": t_shape,
+        "loss_and_gradient_step_ms": t_step,
+        "forward_terms_per_s": terms / (t_fwd * 1e-3),
+        "density_adjoint_terms_per_s": terms / (t_adj * 1e-3),
+        "density_adjoint_over_forward": t_adj / t_fwd, "shape_adjoint_over_forward": t_shape / t_fwd,
+        "adjoint_identity_relerr": ident,
+        "calls": "qbx_apply (S), qbx_apply_adjoint (S), qbx_apply_shape_adjoint; step: qbx_geometry_samples + "
+                 "qbx_apply forward, qbx_apply_adjoint + qbx_apply_shape_adjoint backward, torch for r(t)",
+        "clocks": clk}))
     return 0
 
 
@@ -601,11 +700,16 @@ def main():
                     help="profiling only: run the batched comparison alone and print it")
     ap.add_argument("--solve", action="store_true",
                     help="run the exterior scattering solve (1024-panel teardrop, 64 plane waves) instead")
+    ap.add_argument("--adjoint", action="store_true",
+                    help="time the forward, density-adjoint and shape-adjoint sweeps of the shape-optimisation "
+                         "workload (128-panel starfish) instead")
     ap.add_argument("--solve-restart", type=int, default=60)
     ap.add_argument("--solve-maxiter", type=int, default=400)
     args = ap.parse_args()
     if args.solve:
         return run_solve(args)
+    if args.adjoint:
+        return run_adjoint(args)
     if args.batch_only:
         import torch
         import paper_1207_4461_gb300 as qbx

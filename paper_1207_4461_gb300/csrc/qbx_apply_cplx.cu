@@ -8,7 +8,9 @@ cudaError_t launch_apply_fused_cplx(const ApplyArgs& a, cudaStream_t st) {
   return launch_apply_ops<cplx>(a, st);
 }
 size_t apply_smem_bytes_cplx(int ops, int p, int nr) { return apply_smem_t<cplx>(ops, p, nr); }
-int apply_occupancy_cplx(int ops, int p, int nr) { return apply_occupancy_t<cplx>(ops, p, nr); }
+int apply_occupancy_cplx(int ops, int p, int nr, bool one_w) {
+  return apply_occupancy_t<cplx>(ops, p, nr, one_w);
+}
 
 cudaError_t launch_group_cplx(const GroupArgs& a, int rg, int grid, cudaStream_t st) {
   return launch_group_any<cplx>(a, rg, grid, st);

@@ -62,6 +62,10 @@ __device__ __forceinline__ cplx hrec(double s, cplx h, cplx hm) {
   return cplx{fma(s, h.re, -hm.re), fma(s, h.im, -hm.im)};
 }
 __device__ __forceinline__ cplx hrec(cplx s, cplx h, cplx hm) { return s * h - hm; }
+__device__ __forceinline__ cplx lin2(double a, cplx x, double b, cplx y) {
+  return cplx{fma(a, x.re, b * y.re), fma(a, x.im, b * y.im)};
+}
+__device__ __forceinline__ cplx lin2(cplx a, cplx x, cplx b, cplx y) { return a * x + b * y; }
 __device__ __forceinline__ double sadd(double a, double b) { return a + b; }
 __device__ __forceinline__ cplx sadd(cplx a, cplx b) { return a + b; }
 
@@ -85,6 +89,13 @@ template <> struct KW<double> {
     twoz = invz + invz;
     hankel01_real(z, invz, y * ksq, h0, h1);
   }
+  // w H0, w H1
+  __device__ __forceinline__ void hankel_w(double rho, double inv, double y, cplx w, cplx& h0, cplx& h1,
+                                           double& twoz) const {
+    const double z = k * rho, invz = ik * inv;
+    twoz = invz + invz;
+    hankel01_real<true>(z, invz, y * ksq, h0, h1, w);
+  }
 };
 template <> struct KW<cplx> {
   cplx k;
@@ -99,6 +110,12 @@ template <> struct KW<cplx> {
     const cplx z = cplx{k.re * rho, k.im * rho};
     twoz = 2.0 * cinv(z);
     hankel01_cplx(z, h0, h1);
+  }
+  __device__ __forceinline__ void hankel_w(double rho, double inv, double y, cplx w, cplx& h0, cplx& h1,
+                                           cplx& twoz) const {
+    hankel(rho, inv, y, h0, h1, twoz);
+    h0 = w * h0;
+    h1 = w * h1;
   }
 };
 
@@ -239,6 +256,111 @@ __device__ __forceinline__ void pair_kernels(const KW<T>& kw, const T kk, const 
   }
 }
 
+// One rhs with one weighted density w = (w sigma)_s for every requested
+// operator: the seeds H0, H1 are multiplied by w, so every order sum comes
+// out weighted (the sums are linear in H_l) and goes straight into the
+// centre's accumulators, without the per-pair kernel values and their
+// complex products with w.  The cosine and sine recurrences carry
+// 2 cos(l psi), 2 sin(l psi) (same recurrence, seeds 2, 2 cos psi and 0,
+// 2 sin psi), which puts the factor 2 of the folded sums into the
+// recurrence: accS receives the S kernel itself, accA and accB twice the A
+// and B sums of pair_kernels, and the D combination takes the doubled
+//   D = a (-k J0 H1 + k D1') + (1/rho) (b D2' - a D3'),  Dn' = 2 Dn.
+// gA0 = 2 (J_{-1} - J_1)/2 = -2 J_1: the l = 0 coefficient of the doubled A sum.
+template <int OPS, typename T, int STRIDE>
+__device__ __forceinline__ void pair_accumulate_w(const KW<T>& kw, const T kk, const T J0, const T kneg_j0,
+                                                  const T gA0, const T* cJ, const T* cL, const T* cG, int p,
+                                                  double dx, double dy, double nx, double ny, double ux,
+                                                  double uy, cplx w, cplx& accS, cplx& accD, cplx& accA,
+                                                  cplx& accB) {
+  constexpr bool kS = OPS & OPB_S, kD = OPS & OPB_D, kG = OPS & OPB_G;
+  static_assert(!(OPS & OPB_X), "the source-position gradient is not formed here");
+  constexpr bool kDsum = kD && kG;
+  const double rho2 = fma(dx, dx, dy * dy);
+  double inv, rho, yq;
+  kw.geom(rho2, inv, rho, yq);
+  const double cs = fma(ux, dx, uy * dy) * inv;  // cos psi
+  cplx H0, H1;
+  T twoz;
+  kw.hankel_w(rho, inv, yq, w, H0, H1, twoz);   // w H0, w H1
+  const double tw = 2.0 * cs;
+  double sn = 0.0;
+  if (kD || kG) sn = fma(uy, dx, -ux * dy) * inv;  // sin psi
+  double av = 0.0, bv = 0.0;
+  if (kD) {
+    av = fma(nx, dx, ny * dy) * inv;   // n_s . e_rho
+    bv = fma(ny, dx, -nx * dy) * inv;  // n_s . e_theta
+  }
+  // ---- l = 0 terms and recurrence seeds ----
+  if (kS) madd(accS, J0, H0);
+  if (kG) madd(accA, gA0, H0);
+  cplx D1 = cplx{0.0, 0.0}, D3 = cplx{0.0, 0.0}, GB = cplx{0.0, 0.0};
+  T Cp, Cc;
+  double Vp = 0.0, Vc = 0.0;
+  if (kD && !kDsum) {
+    const T tka = rmul(kk, 2.0 * av);                // C_0 = 2 k a
+    const double i2 = 2.0 * inv;
+    Cp = tka;
+    Cc = rmul(tka, cs);                              // C_1
+    madd(accD, rmul(kneg_j0, av), H1);               // -k a J0 H1
+    madd(accD, sc_mul(cJ[STRIDE], Cc), H0);          // e_0 = J_1 C_1
+    const T Cn = fmsub_r(tw, Cc, Cp);                // C_2
+    Cp = Cc;
+    Cc = Cn;
+    Vp = -i2 * av;                                   // V_0
+    Vc = i2 * fma(bv, sn, -av * cs);                 // V_1
+  }
+  cplx Hm = H0, H = H1;
+  T s = twoz;
+  double cp = 2.0, cl = tw, sp = 0.0, sl = sn + sn;  // 2 cos(l psi), 2 sin(l psi) at l = 0, 1
+  for (int l = 1; l <= p; ++l) {
+    const int o = l * STRIDE;
+    if (kS || kDsum) {
+      const T tS = rmul(cJ[o], cl);                  // 2 J_l cos(l psi)
+      if (kS) madd(accS, tS, H);
+      if (kDsum) madd(D1, tS, Hm);
+    }
+    if (kDsum) madd(D3, rmul(cL[o], cl), H);
+    if (kD && !kDsum) madd(accD, dcoef(cJ[o + STRIDE], Cc, cL[o], Vc), H);
+    if (kG) {
+      madd(accA, rmul(cG[o], cl), H);
+      if (kDsum) {
+        madd(GB, rmul(cL[o], sl), H);
+      } else {
+        madd(accB, rmul(cL[o], sl), H);
+      }
+    }
+    if (l < p) {
+      const cplx Hn = hrec(s, H, Hm);
+      Hm = H;
+      H = Hn;
+      s = sadd(s, twoz);
+      const double cn = fma(tw, cl, -cp);
+      cp = cl;
+      cl = cn;
+      if (kG) {
+        const double sq = fma(tw, sl, -sp);
+        sp = sl;
+        sl = sq;
+      }
+      if (kD && !kDsum) {
+        const T Cn = fmsub_r(tw, Cc, Cp);
+        Cp = Cc;
+        Cc = Cn;
+        const double Vn = fma(tw, Vc, -Vp);
+        Vp = Vc;
+        Vc = Vn;
+      }
+    }
+  }
+  if (kDsum) {
+    madd(accD, av, lin2(kneg_j0, H1, kk, D1));
+    madd(accD, bv * inv, GB);
+    madd(accD, -av * inv, D3);
+    accB = accB + GB;
+  }
+}
+
 // Near-only QBX (a source far from the centre goes through the smooth rule
 // at the target instead of the expansion): the raw kernel values of one
 // (target, source) pair in the same form as pair_kernels returns them, with
@@ -272,13 +394,15 @@ __device__ __forceinline__ void pair_direct(const KW<T>& kw, const T kk, double 
 //   D3 = sum l J_l cos(l psi) H_l,
 // otherwise by the coefficients e_m with the C_m, V_m recurrences.
 // LOCAL: the near-only variant (a separate instance, so that the global
-// apply carries no per-pair test).
-template <int OPS, typename T, int NR, bool LOCAL = false>
+// apply carries no per-pair test).  ONEW: one rhs and one density for all
+// operators, accumulated through weighted seeds (pair_accumulate_w).
+template <int OPS, typename T, int NR, bool LOCAL = false, bool ONEW = false>
 __global__ void __launch_bounds__(kApplyThreads)
 k_apply_fused(ApplyArgs a) {
   using L = ApplySmem<OPS, T, NR>;
   constexpr bool kS = L::kS, kD = L::kD, kG = L::kG, kX = OPS & OPB_X;
   static_assert(!kX || kG, "X is formed with grad S and shares its density");
+  static_assert(!ONEW || (NR == 1 && !LOCAL && !kX), "one-density instances: one rhs, global, no X");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* s_x = reinterpret_cast<double*>(smem_raw);
   double* s_y = s_x + kSrcTile;
@@ -345,6 +469,8 @@ k_apply_fused(ApplyArgs a) {
     colJ[(p + 1) * kApplyThreads] = z0;  // e_p has no J_{p+1} term (orders |l| <= p)
   }
   const T kneg_j0 = rmul(sc_mul(kk, J0), -1.0);  // -k J0 (D)
+  T gA0;
+  if (kG) gA0 = rmul(colG[0], 2.0);                // -2 J_1 (one-density grad S)
 
   cplx accS[NR], accD[NR], accA[NR], accB[NR], accX[NR], accY[NR];
 #pragma unroll
@@ -371,6 +497,7 @@ k_apply_fused(ApplyArgs a) {
 #pragma unroll
       for (int o = 0; o < 3; ++o) {
         if (!(OPS & (1 << o))) continue;
+        if (ONEW && slotn > 0) break;   // one density for all operators
         const cplx* w = wdp[o];
         cplx* dst = s_wd + (size_t)slotn * kSrcTile * NR;
         for (int i = tid; i < nt * NR; i += kApplyThreads) {
@@ -393,6 +520,11 @@ k_apply_fused(ApplyArgs a) {
       if (kD) {
         nx = s_nx[j];
         ny = s_ny[j];
+      }
+      if constexpr (ONEW) {
+        pair_accumulate_w<OPS, T, kApplyThreads>(kw, kk, J0, kneg_j0, gA0, cJ, cL, cG, p, dx, dy, nx, ny, ux,
+                                                  uy, s_wd[j], accS[0], accD[0], accA[0], accB[0]);
+        continue;
       }
       cplx GS, K, GA, GB, EX, EY;
       if (LOCAL && fma(dx, dx, dy * dy) >= lim2) {   // near-only QBX: a distant source
@@ -441,8 +573,9 @@ k_apply_fused(ApplyArgs a) {
     if (kD) part[(row + comp++) * a.nrhs + a.rhs0 + q] = accD[q];
     if (kG) {
       // grad = e_r k A - e_theta (1/r) B, B = 2 sum l J_l H_l sin: e_r = (ux, uy), e_theta = (-uy, ux)
-      const cplx kA = smul(kk, accA[q]);
-      const cplx Bi = accB[q] * (2.0 * ir);
+      // (the one-density accumulators hold 2 A and 2 B)
+      const cplx kA = smul(kk, ONEW ? 0.5 * accA[q] : accA[q]);
+      const cplx Bi = accB[q] * ((ONEW ? 1.0 : 2.0) * ir);
       part[(row + comp++) * a.nrhs + a.rhs0 + q] = kA * ux + Bi * uy;
       part[(row + comp++) * a.nrhs + a.rhs0 + q] = kA * uy - Bi * ux;
     }
@@ -453,10 +586,10 @@ k_apply_fused(ApplyArgs a) {
   }
 }
 
-template <int OPS, typename T, int NR, bool LOCAL>
+template <int OPS, typename T, int NR, bool LOCAL, bool ONEW = false>
 static cudaError_t launch_apply_t(const ApplyArgs& a, cudaStream_t st) {
   const size_t smem = ApplySmem<OPS, T, NR>::bytes(a.p);
-  auto kern = k_apply_fused<OPS, T, NR, LOCAL>;
+  auto kern = k_apply_fused<OPS, T, NR, LOCAL, ONEW>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const unsigned grid = (unsigned)((a.n_ctr + kApplyThreads - 1) / kApplyThreads) * (unsigned)a.nsplit;
@@ -468,6 +601,9 @@ static cudaError_t launch_apply_t(const ApplyArgs& a, cudaStream_t st) {
 // near-only variant) up to 4
 template <int OPS, typename T, bool LOCAL>
 static cudaError_t launch_apply_nr(const ApplyArgs& a, cudaStream_t st) {
+  if constexpr (!LOCAL && !(OPS & OPB_X)) {
+    if (a.nr <= 1 && a.one_w) return launch_apply_t<OPS, T, 1, false, true>(a, st);
+  }
   if (a.nr <= 1) return launch_apply_t<OPS, T, 1, LOCAL>(a, st);
   if constexpr (multi_op(OPS) || LOCAL) {
     return launch_apply_t<OPS, T, 4, LOCAL>(a, st);
@@ -494,7 +630,7 @@ static size_t apply_smem_t(int ops, int p, int nr) {
 
 // CTAs of the kernel instance that one SM holds at once.
 template <int OPS, typename T, bool LOCAL>
-static int occupancy_t(int p, int nr) {
+static int occupancy_t(int p, int nr, bool one_w) {
   // (the shared-memory opt-in must be set before the query when above 48 KB)
   auto occ = [](auto kern, size_t smem) {
     int n = 0;
@@ -502,6 +638,9 @@ static int occupancy_t(int p, int nr) {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, kApplyThreads, smem);
     return n;
   };
+  if constexpr (!LOCAL && !(OPS & OPB_X)) {
+    if (nr <= 1 && one_w) return occ(k_apply_fused<OPS, T, 1, false, true>, ApplySmem<OPS, T, 1>::bytes(p));
+  }
   if (nr <= 1) return occ(k_apply_fused<OPS, T, 1, LOCAL>, ApplySmem<OPS, T, 1>::bytes(p));
   if constexpr (multi_op(OPS) || LOCAL) {
     return occ(k_apply_fused<OPS, T, 4, LOCAL>, ApplySmem<OPS, T, 4>::bytes(p));
@@ -512,17 +651,17 @@ static int occupancy_t(int p, int nr) {
 }
 
 template <typename T, bool LOCAL = false>
-static int apply_occupancy_t(int ops, int p, int nr) {
+static int apply_occupancy_t(int ops, int p, int nr, bool one_w = false) {
   switch (ops) {
-    case OPB_S: return occupancy_t<OPB_S, T, LOCAL>(p, nr);
-    case OPB_D: return occupancy_t<OPB_D, T, LOCAL>(p, nr);
-    case OPB_G: return occupancy_t<OPB_G, T, LOCAL>(p, nr);
-    case OPB_S | OPB_D: return occupancy_t<OPB_S | OPB_D, T, LOCAL>(p, nr);
-    case OPB_S | OPB_G: return occupancy_t<OPB_S | OPB_G, T, LOCAL>(p, nr);
-    case OPB_D | OPB_G: return occupancy_t<OPB_D | OPB_G, T, LOCAL>(p, nr);
-    case OPB_S | OPB_D | OPB_G: return occupancy_t<OPB_S | OPB_D | OPB_G, T, LOCAL>(p, nr);
+    case OPB_S: return occupancy_t<OPB_S, T, LOCAL>(p, nr, one_w);
+    case OPB_D: return occupancy_t<OPB_D, T, LOCAL>(p, nr, one_w);
+    case OPB_G: return occupancy_t<OPB_G, T, LOCAL>(p, nr, one_w);
+    case OPB_S | OPB_D: return occupancy_t<OPB_S | OPB_D, T, LOCAL>(p, nr, one_w);
+    case OPB_S | OPB_G: return occupancy_t<OPB_S | OPB_G, T, LOCAL>(p, nr, one_w);
+    case OPB_D | OPB_G: return occupancy_t<OPB_D | OPB_G, T, LOCAL>(p, nr, one_w);
+    case OPB_S | OPB_D | OPB_G: return occupancy_t<OPB_S | OPB_D | OPB_G, T, LOCAL>(p, nr, one_w);
     case OPB_G | OPB_X:
-      if constexpr (!LOCAL) return occupancy_t<OPB_G | OPB_X, T, false>(p, nr);
+      if constexpr (!LOCAL) return occupancy_t<OPB_G | OPB_X, T, false>(p, nr, false);
       return 0;
     default: return 0;
   }

@@ -8,7 +8,9 @@ cudaError_t launch_apply_fused_real(const ApplyArgs& a, cudaStream_t st) {
   return launch_apply_ops<double>(a, st);
 }
 size_t apply_smem_bytes_real(int ops, int p, int nr) { return apply_smem_t<double>(ops, p, nr); }
-int apply_occupancy_real(int ops, int p, int nr) { return apply_occupancy_t<double>(ops, p, nr); }
+int apply_occupancy_real(int ops, int p, int nr, bool one_w) {
+  return apply_occupancy_t<double>(ops, p, nr, one_w);
+}
 
 cudaError_t launch_group_real(const GroupArgs& a, int rg, int grid, cudaStream_t st) {
   return launch_group_any<double>(a, rg, grid, st);

@@ -618,11 +618,14 @@ static int apply_impl(qbx_plan* p, const qbx_geom* g, int ops, int side, int lim
   const int units = group ? (nc + kGrpCentres - 1) / kGrpCentres : (nc + kApplyThreads - 1) / kApplyThreads;
   const bool local = eta > 0.0;
   const int chunk = local ? std::min(4, apply_chunk(ops)) : apply_chunk(ops);
+  // one rhs of one density for every operator: the weighted-seed instance
+  const bool one_w = !group && !local && nd == 1 && nrhs == 1;
   CK(cudaSetDevice(p->device), "cudaSetDevice");
   int occ;
   if (group) occ = ck ? group_occupancy_cplx(ops, pp, rg) : group_occupancy_real(ops, pp, rg);
   else if (local) occ = apply_occupancy_local(ops, ck, pp, std::min(chunk, nrhs));
-  else occ = ck ? apply_occupancy_cplx(ops, pp, std::min(chunk, nrhs)) : apply_occupancy_real(ops, pp, std::min(chunk, nrhs));
+  else occ = ck ? apply_occupancy_cplx(ops, pp, std::min(chunk, nrhs), one_w)
+                : apply_occupancy_real(ops, pp, std::min(chunk, nrhs), one_w);
   // the near-only variant's items differ more in cost (distant pairs take the
   // short direct path): four waves let the near-field items spread out
   const int waves = local ? std::max(p->min_waves, 4) : p->min_waves;
@@ -671,6 +674,7 @@ static int apply_impl(qbx_plan* p, const qbx_geom* g, int ops, int side, int lim
   a.eta2 = eta > 0.0 ? eta * eta : 0.0;
   a.near_q_tgt = g->q_tgt;   // near-field items first
   a.near_q_src = g->q_src;
+  a.one_w = one_w ? 1 : 0;
   if (group) {
     GroupArgs ga{};
     ga.ops = ops;

@@ -119,8 +119,11 @@ __device__ __forceinline__ void rho_powers(double rho2, double& y, double& inv, 
   rho = rho2 * inv;
 }
 
-// H0(z), H1(z) for real z > 0, given invz = 1/z and s = z^{-1/2}.
-__device__ __forceinline__ void hankel01_real(double z, double invz, double s, cplx& h0, cplx& h1) {
+// H0(z), H1(z) for real z > 0, given invz = 1/z and s = z^{-1/2}; with
+// SCALED, w H0(z) and w H1(z) (w folded into the phase factor).
+template <bool SCALED = false>
+__device__ __forceinline__ void hankel01_real(double z, double invz, double s, cplx& h0, cplx& h1,
+                                              cplx w = cplx{1.0, 0.0}) {
   if (z >= QBX_HK_ZSPLIT) {
     // B_n(s) = H_n(z) e^{-i(z - pi/4)}: piecewise polynomials in s
     const double y = s + 1.0;
@@ -140,7 +143,8 @@ __device__ __forceinline__ void hankel01_real(double z, double invz, double s, c
       b1r = fma(b1r, u, c1.x);
       b1i = fma(b1i, u, c1.y);
     }
-    const cplx e = expi_shift(z);
+    cplx e = expi_shift(z);
+    if constexpr (SCALED) e = w * e;
     h0 = e * cplx{b0r, b0i};
     h1 = e * cplx{b1r, b1i};
   } else {
@@ -160,6 +164,10 @@ __device__ __forceinline__ void hankel01_real(double z, double invz, double s, c
     double y1 = fma(L, j1, fma(z, sy1, -0.63661977236758134308 * invz));
     h0 = cplx{j0, y0};
     h1 = cplx{j1, y1};
+    if constexpr (SCALED) {
+      h0 = w * h0;
+      h1 = w * h1;
+    }
   }
 }
 

@@ -37,6 +37,8 @@ struct ApplyArgs {
   double eta2;            // near-only QBX: if > 0, sources with |x_s - c|^2 >= eta2 r^2 by the
                           // smooth rule at the target; otherwise (default) all through the expansion
   int near_q_tgt, near_q_src;   // > 0: near-field items first (node counts per panel); 0: plain order
+  int one_w;              // 1: wd[] of every requested operator is one array and nr = 1 (weighted
+                          // seeds: the density multiplies H0, H1); 0: per-pair kernel values
 };
 cudaError_t launch_apply_fused(const ApplyArgs& a, cudaStream_t st);
 cudaError_t launch_apply_fused_real(const ApplyArgs& a, cudaStream_t st);
@@ -48,8 +50,8 @@ size_t apply_smem_bytes(int ops, bool ck, int p, int nr);
 size_t apply_smem_bytes_real(int ops, int p, int nr);
 size_t apply_smem_bytes_cplx(int ops, int p, int nr);
 int apply_chunk(int ops);   // rhs per launch for an operator subset
-int apply_occupancy_real(int ops, int p, int nr);   // resident CTAs per SM
-int apply_occupancy_cplx(int ops, int p, int nr);
+int apply_occupancy_real(int ops, int p, int nr, bool one_w = false);   // resident CTAs per SM
+int apply_occupancy_cplx(int ops, int p, int nr, bool one_w = false);
 
 // Far targets: plain quadrature partial sums.
 struct FarArgs {

@@ -177,6 +177,28 @@ def test_apply_ops_subsets(cuda, ops, side, limit, k, nrhs):
         assert rel(got[o], ref) < TOL, o
 
 
+@pytest.mark.parametrize("ops", ALL_SUBSETS)
+@pytest.mark.parametrize("side,limit,k", [(qbx.SIDE_TWO, 0, 8.0), (qbx.SIDE_INT, 1, 3 + 0.4j),
+                                          (qbx.SIDE_EXT, 0, 12.0)])
+def test_apply_ops_one_density(cuda, ops, side, limit, k):
+    """One rhs of one density for every operator takes the weighted-seed
+    instance (the density multiplies H0, H1); the same values in separate
+    arrays take the per-pair instance.  Both against the oracle, and against
+    each other to rounding: 11 panels, ragged centre and source tiles."""
+    p = 9
+    plan, g, go = make(W.starfish(0.3, 4), 11, nrhs=1, p=p, extra_ctr=2)
+    dens = W.complex_gaussian(77, g.n_tgt).reshape(g.n_tgt, 1)
+    d = dev(dens)
+    one = qbx.qbx_apply_ops(plan, g, ops, side, limit, k, p, d)
+    sep = qbx.qbx_apply_ops(plan, g, ops, side, limit, k, p, {o: d.clone() for o in ops})
+    qbx.qbx_sync_status(plan)
+    for o in ops:
+        ref = oracle.apply(go, o, side, limit, k, p, dens)
+        assert rel(one[o], ref) < TOL, o
+        assert rel(sep[o], ref) < TOL, o
+        assert rel(one[o], sep[o].cpu().numpy()) < 1e-13, o
+
+
 def test_apply_many_rhs(cuda):
     nrhs = 11
     plan, g, go = make(W.ellipse(2.0), 9, nrhs=nrhs)
