@@ -24,6 +24,7 @@ The series coefficients are written out as exact rationals rounded to double.
 Phase: e^{i(z - pi/4)} uses a table of e^{i(2 pi j/NT - pi/4)}, j < NT, and a
 short Taylor polynomial of e^{i r}, |r| <= pi/NT, after Cody-Waite reduction
 of z by 2 pi/NT (two-part split of the step, high part with 30 significant bits).
+The polynomial (cos to r^4, sin to r^5) leaves r^6/720 < 8e-17 at NT = 512.
 """
 import mpmath as mp
 import numpy as np
@@ -34,7 +35,7 @@ Z_SPLIT = 2.0          # series below, amplitude fits above
 NI_PER_UNIT = 128      # intervals per unit of s (a power of two)
 NI = int(mp.ceil(NI_PER_UNIT / mp.sqrt(Z_SPLIT)))   # intervals covering s in [0, Z_SPLIT^-1/2]
 MAX_ERR = 3.5e-16      # absolute; |B_n| <= 0.6 on the range
-NT = 1024              # phase table size
+NT = 512               # phase table size (8 KB: with the amplitude table it stays in L1)
 NSER = 14              # series terms (t <= 1: 1/(13!)^2 ~ 2.6e-20)
 
 

@@ -128,12 +128,13 @@ __host__ __device__ constexpr int ops_ncomp(int m) {
 }
 
 // Shared memory layout (bytes): source tile x, y [, nx, ny] ; densities
-// [nops][tile][NR] ; per-centre coefficient slots [(p+2)][kApplyThreads] of
-// type T: slot J (J_l), slot L (l J_l; with D or grad S), slot G
-// (J_{l-1} - J_{l+1}; with grad S).
-template <int OPS, typename T, int NR>
+// [nops][tile][NR] (one slot for the one-density instances) ; per-centre
+// coefficient columns of type T, kApplyThreads wide: J (J_l, l = 0..p+1),
+// then with D or grad S  L (l J_l, l = 0..p), then with grad S
+// G (J_{l-1} - J_{l+1}, l = 0..p).
+template <int OPS, typename T, int NR, bool ONEW = false>
 struct ApplySmem {
-  static constexpr int kNops = popc3(OPS);   // density slots (X shares grad S's)
+  static constexpr int kNops = ONEW ? 1 : popc3(OPS);   // density slots (X shares grad S's)
   static constexpr bool kS = OPS & OPB_S, kD = OPS & OPB_D, kG = OPS & OPB_G;
   static constexpr int kGeo = kD ? 4 : 2;
   static __host__ __device__ size_t tile_bytes() {
@@ -141,7 +142,7 @@ struct ApplySmem {
   }
   static __host__ __device__ int nslots() { return 1 + ((kD || kG) ? 1 : 0) + (kG ? 1 : 0); }
   static __host__ __device__ size_t bytes(int p) {
-    return tile_bytes() + (size_t)nslots() * (p + 2) * kApplyThreads * sizeof(T);
+    return tile_bytes() + (size_t)((p + 2) + (nslots() - 1) * (p + 1)) * kApplyThreads * sizeof(T);
   }
 };
 
@@ -388,6 +389,28 @@ __device__ __forceinline__ void pair_direct(const KW<T>& kw, const T kk, double 
   }
 }
 
+// pair_direct for the one-density instances: w H0(kd), w H1(kd) and the
+// raw kernels added straight into the accumulators (A and B doubled, as in
+// pair_accumulate_w).
+template <int OPS, typename T>
+__device__ __forceinline__ void pair_direct_w(const KW<T>& kw, const T kk, double ex, double ey, double nx,
+                                              double ny, double ux, double uy, double r, cplx w, cplx& accS,
+                                              cplx& accD, cplx& accA, cplx& accB) {
+  constexpr bool kS = OPS & OPB_S, kD = OPS & OPB_D, kG = OPS & OPB_G;
+  const double d2 = fma(ex, ex, ey * ey);
+  double inv, d, yq;
+  kw.geom(d2, inv, d, yq);
+  cplx H0, H1;
+  T twoz;
+  kw.hankel_w(d, inv, yq, w, H0, H1, twoz);
+  if (kS) accS = accS + H0;
+  if (kD) madd(accD, rmul(kk, fma(ex, nx, ey * ny) * inv), H1);
+  if (kG) {
+    madd(accA, -2.0 * fma(ex, ux, ey * uy) * inv, H1);
+    madd(accB, rmul(kk, r * fma(ex, -uy, ey * ux) * inv), H1);
+  }
+}
+
 // D through sums shared with grad S when both are requested:
 //   D = -k a J0 H1 + 2 k a D1 + (2/rho)(b D2 - a D3),
 //   D1 = sum_{l>=1} J_l cos(l psi) H_{l-1},  D2 = sum l J_l sin(l psi) H_l (= grad S's B / 2),
@@ -395,14 +418,15 @@ __device__ __forceinline__ void pair_direct(const KW<T>& kw, const T kk, double 
 // otherwise by the coefficients e_m with the C_m, V_m recurrences.
 // LOCAL: the near-only variant (a separate instance, so that the global
 // apply carries no per-pair test).  ONEW: one rhs and one density for all
-// operators, accumulated through weighted seeds (pair_accumulate_w).
+// operators, accumulated through weighted seeds (pair_accumulate_w,
+// pair_direct_w).
 template <int OPS, typename T, int NR, bool LOCAL = false, bool ONEW = false>
 __global__ void __launch_bounds__(kApplyThreads)
 k_apply_fused(ApplyArgs a) {
-  using L = ApplySmem<OPS, T, NR>;
+  using L = ApplySmem<OPS, T, NR, ONEW>;
   constexpr bool kS = L::kS, kD = L::kD, kG = L::kG, kX = OPS & OPB_X;
   static_assert(!kX || kG, "X is formed with grad S and shares its density");
-  static_assert(!ONEW || (NR == 1 && !LOCAL && !kX), "one-density instances: one rhs, global, no X");
+  static_assert(!ONEW || (NR == 1 && !kX), "one-density instances: one rhs, no X");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* s_x = reinterpret_cast<double*>(smem_raw);
   double* s_y = s_x + kSrcTile;
@@ -411,10 +435,9 @@ k_apply_fused(ApplyArgs a) {
   cplx* s_wd = reinterpret_cast<cplx*>(smem_raw + (size_t)L::kGeo * kSrcTile * 8);  // [nops][tile][NR]
   T* slot = reinterpret_cast<T*>(smem_raw + L::tile_bytes());
   const int p = a.p;
-  const int P2 = (p + 2) * kApplyThreads;
-  T* sJ = slot;                              // J_l
-  T* sL = slot + P2;                         // l J_l
-  T* sG = sL + ((kD || kG) ? P2 : 0);        // J_{l-1} - J_{l+1}
+  T* sJ = slot;                                                   // J_l, p + 2 rows
+  T* sL = slot + (p + 2) * kApplyThreads;                         // l J_l, p + 1 rows
+  T* sG = sL + ((kD || kG) ? (p + 1) * kApplyThreads : 0);        // J_{l-1} - J_{l+1}, p + 1 rows
 
   const int tid = threadIdx.x;
   // work item (centre block, source split).  With the grids' node counts
@@ -522,8 +545,13 @@ k_apply_fused(ApplyArgs a) {
         ny = s_ny[j];
       }
       if constexpr (ONEW) {
-        pair_accumulate_w<OPS, T, kApplyThreads>(kw, kk, J0, kneg_j0, gA0, cJ, cL, cG, p, dx, dy, nx, ny, ux,
-                                                  uy, s_wd[j], accS[0], accD[0], accA[0], accB[0]);
+        if (LOCAL && fma(dx, dx, dy * dy) >= lim2) {   // near-only QBX: a distant source
+          pair_direct_w<OPS, T>(kw, kk, r * ux - dx, r * uy - dy, nx, ny, ux, uy, r, s_wd[j], accS[0], accD[0],
+                                accA[0], accB[0]);
+        } else {
+          pair_accumulate_w<OPS, T, kApplyThreads>(kw, kk, J0, kneg_j0, gA0, cJ, cL, cG, p, dx, dy, nx, ny, ux,
+                                                    uy, s_wd[j], accS[0], accD[0], accA[0], accB[0]);
+        }
         continue;
       }
       cplx GS, K, GA, GB, EX, EY;
@@ -586,12 +614,45 @@ k_apply_fused(ApplyArgs a) {
   }
 }
 
+// Percentage of the largest shared-memory carve-out (228 KB) that holds n
+// CTAs of smem bytes each (plus the 1 KB the driver reserves per CTA),
+// rounded up; 0 when nothing is to be set.
+static inline int carveout_percent(int n, size_t smem) {
+  if (n < 1) return 0;
+  const size_t need = (size_t)n * (smem + 1024), full = (size_t)228 * 1024;
+  if (need >= full) return 0;
+  return (int)((need * 100 + full - 1) / full);
+}
+
+// Resident CTAs per SM of a one-density instance under the largest
+// carve-out (the preference a previous launch left is reset first).
+template <typename K>
+static cudaError_t onew_occupancy(K kern, size_t smem, int* n) {
+  *n = 0;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, kern, kApplyThreads, smem);
+  return e;
+}
+
 template <int OPS, typename T, int NR, bool LOCAL, bool ONEW = false>
 static cudaError_t launch_apply_t(const ApplyArgs& a, cudaStream_t st) {
-  const size_t smem = ApplySmem<OPS, T, NR>::bytes(a.p);
+  const size_t smem = ApplySmem<OPS, T, NR, ONEW>::bytes(a.p);
   auto kern = k_apply_fused<OPS, T, NR, LOCAL, ONEW>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
+  if constexpr (ONEW) {
+    // the smallest shared-memory carve-out that holds the resident CTAs,
+    // which leaves the rest of the SM's 256 KB to L1 (the Hankel tables)
+    int n = 0;
+    e = onew_occupancy(kern, smem, &n);
+    if (e != cudaSuccess) return e;
+    const int pct = carveout_percent(n, smem);
+    if (pct > 0) {
+      e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+      if (e != cudaSuccess) return e;
+    }
+  }
   const unsigned grid = (unsigned)((a.n_ctr + kApplyThreads - 1) / kApplyThreads) * (unsigned)a.nsplit;
   kern<<<grid, kApplyThreads, smem, st>>>(a);
   return cudaGetLastError();
@@ -601,8 +662,8 @@ static cudaError_t launch_apply_t(const ApplyArgs& a, cudaStream_t st) {
 // near-only variant) up to 4
 template <int OPS, typename T, bool LOCAL>
 static cudaError_t launch_apply_nr(const ApplyArgs& a, cudaStream_t st) {
-  if constexpr (!LOCAL && !(OPS & OPB_X)) {
-    if (a.nr <= 1 && a.one_w) return launch_apply_t<OPS, T, 1, false, true>(a, st);
+  if constexpr (!(OPS & OPB_X)) {
+    if (a.nr <= 1 && a.one_w) return launch_apply_t<OPS, T, 1, LOCAL, true>(a, st);
   }
   if (a.nr <= 1) return launch_apply_t<OPS, T, 1, LOCAL>(a, st);
   if constexpr (multi_op(OPS) || LOCAL) {
@@ -638,8 +699,12 @@ static int occupancy_t(int p, int nr, bool one_w) {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, kApplyThreads, smem);
     return n;
   };
-  if constexpr (!LOCAL && !(OPS & OPB_X)) {
-    if (nr <= 1 && one_w) return occ(k_apply_fused<OPS, T, 1, false, true>, ApplySmem<OPS, T, 1>::bytes(p));
+  if constexpr (!(OPS & OPB_X)) {
+    if (nr <= 1 && one_w) {
+      int n = 0;
+      onew_occupancy(k_apply_fused<OPS, T, 1, LOCAL, true>, ApplySmem<OPS, T, 1, true>::bytes(p), &n);
+      return n;
+    }
   }
   if (nr <= 1) return occ(k_apply_fused<OPS, T, 1, LOCAL>, ApplySmem<OPS, T, 1>::bytes(p));
   if constexpr (multi_op(OPS) || LOCAL) {

@@ -11,8 +11,8 @@ cudaError_t launch_apply_fused_local_real(const ApplyArgs& a, cudaStream_t st) {
 cudaError_t launch_apply_fused_local_cplx(const ApplyArgs& a, cudaStream_t st) {
   return launch_apply_ops<cplx, true>(a, st);
 }
-int apply_occupancy_local(int ops, bool ck, int p, int nr) {
-  return ck ? apply_occupancy_t<cplx, true>(ops, p, nr) : apply_occupancy_t<double, true>(ops, p, nr);
+int apply_occupancy_local(int ops, bool ck, int p, int nr, bool one_w) {
+  return ck ? apply_occupancy_t<cplx, true>(ops, p, nr, one_w) : apply_occupancy_t<double, true>(ops, p, nr, one_w);
 }
 
 }  // namespace qbx

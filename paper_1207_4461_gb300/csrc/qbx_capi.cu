@@ -619,11 +619,11 @@ static int apply_impl(qbx_plan* p, const qbx_geom* g, int ops, int side, int lim
   const bool local = eta > 0.0;
   const int chunk = local ? std::min(4, apply_chunk(ops)) : apply_chunk(ops);
   // one rhs of one density for every operator: the weighted-seed instance
-  const bool one_w = !group && !local && nd == 1 && nrhs == 1;
+  const bool one_w = !group && nd == 1 && nrhs == 1;
   CK(cudaSetDevice(p->device), "cudaSetDevice");
   int occ;
   if (group) occ = ck ? group_occupancy_cplx(ops, pp, rg) : group_occupancy_real(ops, pp, rg);
-  else if (local) occ = apply_occupancy_local(ops, ck, pp, std::min(chunk, nrhs));
+  else if (local) occ = apply_occupancy_local(ops, ck, pp, std::min(chunk, nrhs), one_w);
   else occ = ck ? apply_occupancy_cplx(ops, pp, std::min(chunk, nrhs), one_w)
                 : apply_occupancy_real(ops, pp, std::min(chunk, nrhs), one_w);
   // the near-only variant's items differ more in cost (distant pairs take the

@@ -45,7 +45,7 @@ cudaError_t launch_apply_fused_real(const ApplyArgs& a, cudaStream_t st);
 cudaError_t launch_apply_fused_cplx(const ApplyArgs& a, cudaStream_t st);
 cudaError_t launch_apply_fused_local_real(const ApplyArgs& a, cudaStream_t st);
 cudaError_t launch_apply_fused_local_cplx(const ApplyArgs& a, cudaStream_t st);
-int apply_occupancy_local(int ops, bool ck, int p, int nr);   // near-only instances
+int apply_occupancy_local(int ops, bool ck, int p, int nr, bool one_w = false);   // near-only instances
 size_t apply_smem_bytes(int ops, bool ck, int p, int nr);
 size_t apply_smem_bytes_real(int ops, int p, int nr);
 size_t apply_smem_bytes_cplx(int ops, int p, int nr);

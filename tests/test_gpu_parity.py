@@ -416,11 +416,29 @@ def test_apply_local_matches_oracle(cuda, ops, side, limit, k, eta):
         qbx.qbx_apply_ops(plan, g, ops, side, limit, k, p, dev(dens), eta=-1.0)
 
 
+@pytest.mark.parametrize("ops", [(0, 1, 2), (0,), (1, 2), (0, 1)])
+@pytest.mark.parametrize("side,limit,k,eta", [(qbx.SIDE_TWO, 0, 7.0, 3.0), (qbx.SIDE_INT, 1, 3 + 0.5j, 5.0)])
+def test_apply_local_one_density(cuda, ops, side, limit, k, eta):
+    """Near-only QBX with one rhs of one density (weighted seeds for the
+    expansion pairs and the direct pairs) against the oracle and against the
+    same values in separate arrays (per-pair kernel values)."""
+    p = 10
+    plan, g, go = make(W.starfish(0.2, 3), 24, nrhs=1, p=p, extra_ctr=2)
+    dens = W.complex_gaussian(29, g.n_tgt).reshape(g.n_tgt, 1)
+    d = dev(dens)
+    one = qbx.qbx_apply_ops(plan, g, ops, side, limit, k, p, d, eta=eta)
+    sep = qbx.qbx_apply_ops(plan, g, ops, side, limit, k, p, {o: d.clone() for o in ops}, eta=eta)
+    qbx.qbx_sync_status(plan)
+    for o in ops:
+        assert rel(one[o], oracle.apply_local(go, o, side, limit, k, p, eta, dens)) < TOL, o
+        assert rel(one[o], sep[o].cpu().numpy()) < 1e-13, o
+
+
 @pytest.mark.parametrize("k,p,nrhs", [(6.0, 40, 1), (6.0, 40, 20), (3 + 0.4j, 30, 2)])
 def test_maximum_orders(cuda, k, p, nrhs):
     """The largest orders: p = QBX_MAX_P = 40 (real k; fused kernel and, with
     20 rhs, the group kernel) and p = 30 for complex k (the fused kernel's
-    coefficient columns of complex J_l fill 208 KB of shared memory), on the
+    coefficient columns of complex J_l fill most of the shared memory), on the
     32-panel starfish, all three operators in one call."""
     assert qbx.MAX_P == 40
     cur = W.starfish()
