@@ -77,7 +77,7 @@ GROUP_SOURCES = ["qbx_group_impl.cuh", "qbx_apply_impl.cuh", "qbx_device.cuh", "
 # counters divided by the pairs of the captured launch, for the kernel
 # sources with the given hash (profiles/*_fp64_counts.md).
 HW_FP64_PER_PAIR = {"084480a055477089": 551.5}         # fused S + D + grad S, p = 12, one rhs
-HW_FP64_PER_PAIR_GROUP = {"64a6a673d2967226": 763.4}   # group kernel, S + D, p = 10, 32 rhs
+HW_FP64_PER_PAIR_GROUP = {"4105582d9e3560d6": 763.4}   # group kernel, S + D, p = 10, 32 rhs
 
 
 def source_hash(names=KERNEL_SOURCES):
@@ -538,13 +538,17 @@ def run_solve(args):
     e1.record()
     e1.synchronize()
     asm_ms = e0.elapsed_time(e1)
-    e0.record()
-    mu_a, its_a, res_a = qbx.qbx_solve_exterior_dirichlet(plan, g, k, k, p, f, tol=1e-10,
-                                                         restart=args.solve_restart, maxiter=args.solve_maxiter,
-                                                         raise_on_noconv=False, A=A)
-    e1.record()
-    e1.synchronize()
-    asm_solve_ms = e0.elapsed_time(e1)
+    # twice: the first call also creates the plan's cuBLAS handle
+    asm_ms_calls = []
+    for _ in range(2):
+        e0.record()
+        mu_a, its_a, res_a = qbx.qbx_solve_exterior_dirichlet(plan, g, k, k, p, f, tol=1e-10,
+                                                             restart=args.solve_restart, maxiter=args.solve_maxiter,
+                                                             raise_on_noconv=False, A=A)
+        e1.record()
+        e1.synchronize()
+        asm_ms_calls.append(e0.elapsed_time(e1))
+    asm_solve_ms = asm_ms_calls[-1]
     mu_diff = (torch.abs(mu_a - mu).max() / torch.abs(mu).max()).item()
     del A
     # the residual recomputed by one more apply of both operators to mu: in
@@ -567,7 +571,8 @@ def run_solve(args):
             "pairs_per_matvec": pairs,
             "terms_per_s_matvec": 2 * pairs * (2 * p + 1) * nrhs / (mv_ms * 1e-3),
             "resid_by_apply_weighted_l2": resid_w, "resid_by_apply_pointwise": resid_apply,
-            "assembled": {"assembly_s": asm_ms * 1e-3, "solve_s": asm_solve_ms * 1e-3, "matvecs": its_a,
+            "assembled": {"assembly_s": asm_ms * 1e-3, "solve_s": asm_solve_ms * 1e-3,
+                          "first_solve_call_s": asm_ms_calls[0] * 1e-3, "matvecs": its_a,
                           "max_resid": float(np.max(res_a)), "max_rel_diff_vs_matrix_free": mu_diff,
                           "matrix_bytes": 16 * g.n_tgt * g.n_tgt,
                           "call": "qbx_assemble_cfie + qbx_solve_exterior_dirichlet_assembled (cuBLAS ZGEMM3M)"},

@@ -320,8 +320,8 @@ int qbx_solve_exterior_dirichlet(qbx_plan *plan, const qbx_geom *g, qbx_c64 k, q
  * [n][nrhs] complex device arrays; bases [nv][n][nrhs].
  *   qbx_vec_scale_sqrtw: out = in * sqrt(w) (inverse = 0) or in / sqrt(w).
  *   qbx_cfie_combine: y = sqrt(w) (xden/2 + dmu - i eta smu).
- *   qbx_vec_dots: out[j][r] = sum_i conj(V_j[i][r]) w[i][r], j < nv (fixed
- *     reduction order); work needs qbx_vec_dots_work_bytes(nrhs, nv) bytes.
+ *   qbx_vec_dots: out[j][r] = sum_i conj(V_j[i][r]) w[i][r], j < nv <= 65535
+ *     (fixed reduction order); work needs qbx_vec_dots_work_bytes(nrhs, nv) bytes.
  *   qbx_vec_orth_update: w -= sum_j V_j h[j][r].
  *   qbx_vec_scale_cols: out[i][r] = a[r] in[i][r] (a: device [nrhs] real).
  *   qbx_vec_combine: x += sum_j V_j y[j][r]. */

@@ -1,6 +1,7 @@
 // qbx_capi.cu -- host side of the C ABI declared in include/qbx.h: plans,
 // the Gauss-Legendre rule, the per-panel interpolation matrix, argument
 // checks and the launch sequence of each call.
+#include <cublas_v2.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdarg.h>
@@ -30,6 +31,8 @@ struct qbx_plan {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   // waves of resident CTAs the split choice aims for (qbx_plan_set_min_waves)
   int min_waves = 1;
+  // cuBLAS handle of the assembled-matrix solve, created on first use
+  cublasHandle_t blas = nullptr;
 };
 
 namespace {
@@ -216,6 +219,16 @@ void host_plan_info(const qbx_plan* plan, int* device, int* q_tgt, int* q_src, c
   *interp = plan->d_interp;
 }
 
+void* host_plan_blas(qbx_plan* plan) {
+  if (!plan->blas) {
+    if (cudaSetDevice(plan->device) != cudaSuccess) return nullptr;
+    cublasHandle_t h = nullptr;
+    if (cublasCreate(&h) != CUBLAS_STATUS_SUCCESS) return nullptr;
+    plan->blas = h;
+  }
+  return plan->blas;
+}
+
 size_t host_align256(size_t b) { return align256(b); }
 
 // Number of source splits: fill about two waves of 4 CTAs per SM, bounded by
@@ -330,6 +343,7 @@ int qbx_plan_destroy(qbx_plan* p) {
   cudaSetDevice(p->device);
   if (p->ev0) cudaEventDestroy(p->ev0);
   if (p->ev1) cudaEventDestroy(p->ev1);
+  if (p->blas) cublasDestroy(p->blas);
   cudaFree(p->d_interp);
   cudaFree(p->d_wgl_tgt);
   cudaFree(p->d_wgl_src);

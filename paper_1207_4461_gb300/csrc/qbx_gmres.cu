@@ -40,26 +40,34 @@ __global__ void k_cfie_combine(int n, int nrhs, const double* w, const cplx* xde
   y[idx] = sw * v;
 }
 
-// partial dots: part[b][j][r] = sum_{i in block b's range} conj(V_j[i][r]) w[i][r], j < nv
+// partial dots: part[b][j][r] = sum_{i in block b's range} conj(V_j[i][r]) w[i][r],
+// grid (kRedBlocks, nv): block (b, j) takes row range b of vector j.  Lanes
+// own right-hand sides (rows of [n][nrhs] are read whole and coalesced):
+// thread t takes rhs r0 + t % R and every S-th row of the range,
+// S = blockDim / R; the S partial sums of each r are then added in a fixed
+// order, so the result does not depend on timing.
 __global__ void k_dots_pass1(int n, int nrhs, int nv, const cplx* V, const cplx* w, cplx* part) {
   extern __shared__ cplx sred[];
+  const int j = blockIdx.y;
   const int per = (n + gridDim.x - 1) / gridDim.x;
   const int i0 = blockIdx.x * per, i1 = min(n, i0 + per);
-  for (int jr = 0; jr < nv * nrhs; ++jr) {
-    const int j = jr / nrhs, r = jr - j * nrhs;
+  const int R = min(nrhs, (int)blockDim.x), S = blockDim.x / R;
+  const int rr = threadIdx.x % R, sub = threadIdx.x / R;
+  const cplx* Vj = V + (size_t)j * n * nrhs;
+  for (int r0 = 0; r0 < nrhs; r0 += R) {
+    const int r = r0 + rr;
     cplx acc{0.0, 0.0};
-    for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-      const cplx a = V[((size_t)j * n + i) * nrhs + r];
-      const cplx b = w[(size_t)i * nrhs + r];
-      acc = acc + conj(a) * b;
+    if (sub < S && r < nrhs) {
+#pragma unroll 4
+      for (int i = i0 + sub; i < i1; i += S) acc = acc + conj(Vj[(size_t)i * nrhs + r]) * w[(size_t)i * nrhs + r];
     }
     sred[threadIdx.x] = acc;
     __syncthreads();
-    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-      if (threadIdx.x < s) sred[threadIdx.x] = sred[threadIdx.x] + sred[threadIdx.x + s];
-      __syncthreads();
+    if (sub == 0 && r < nrhs) {
+      cplx tot = sred[rr];
+      for (int q = 1; q < S; ++q) tot = tot + sred[q * R + rr];
+      part[((size_t)blockIdx.x * nv + j) * nrhs + r] = tot;
     }
-    if (threadIdx.x == 0) part[((size_t)blockIdx.x * nv + j) * nrhs + r] = sred[0];
     __syncthreads();
   }
 }
@@ -140,9 +148,10 @@ int qbx_cfie_combine(int n, int nrhs, const double* w, const qbx_c64* xden, cons
 
 int qbx_vec_dots(int n, int nrhs, int nv, const qbx_c64* V, const qbx_c64* w, qbx_c64* work, qbx_c64* out,
                  void* stream) {
-  if (n < 1 || nrhs < 1 || nv < 1 || !V || !w || !work || !out) return gfail(QBX_EINVAL, "bad arguments to qbx_vec_dots");
+  if (n < 1 || nrhs < 1 || nv < 1 || nv > 65535 || !V || !w || !work || !out)
+    return gfail(QBX_EINVAL, "bad arguments to qbx_vec_dots");
   cudaStream_t st = (cudaStream_t)stream;
-  k_dots_pass1<<<kRedBlocks, kRedThreads, kRedThreads * sizeof(cplx), st>>>(n, nrhs, nv, (const cplx*)V,
+  k_dots_pass1<<<dim3(kRedBlocks, nv), kRedThreads, kRedThreads * sizeof(cplx), st>>>(n, nrhs, nv, (const cplx*)V,
                                                                             (const cplx*)w, (cplx*)work);
   k_dots_pass2<<<blocks((long)nv * nrhs), 256, 0, st>>>(kRedBlocks, nrhs, nv, (const cplx*)work, (cplx*)out);
   cudaError_t e = cudaGetLastError();
@@ -229,15 +238,11 @@ static int solve_impl(qbx_plan* plan, const qbx_geom* g, qbx_c64 k, qbx_c64 eta,
   if ((rc = qbx_vec_scale_sqrtw(n, nrhs, g->tgt_w, f, (qbx_c64*)F.p, 0, stream))) return rc;
   if ((rc = qbx_vec_scale_sqrtw(n, nrhs, g->tgt_w, mu, (qbx_c64*)X.p, 0, stream))) return rc;
   const int ops = QBX_OPS_S | QBX_OPS_D;
-  struct Blas {
-    cublasHandle_t h = nullptr;
-    ~Blas() {
-      if (h) cublasDestroy(h);
-    }
-  } blas;
+  cublasHandle_t blas = nullptr;   // the plan's handle (kept for later solves)
   if (Adense) {
-    if (cublasCreate(&blas.h) != CUBLAS_STATUS_SUCCESS) return gfail(QBX_ECUDA, "cublasCreate failed");
-    if (cublasSetStream(blas.h, st) != CUBLAS_STATUS_SUCCESS) return gfail(QBX_ECUDA, "cublasSetStream failed");
+    blas = (cublasHandle_t)host_plan_blas(plan);
+    if (!blas) return gfail(QBX_ECUDA, "cublasCreate failed");
+    if (cublasSetStream(blas, st) != CUBLAS_STATUS_SUCCESS) return gfail(QBX_ECUDA, "cublasSetStream failed");
   }
   // y = A~ x~ : density x~/sqrt(w), S and D two-sided in one pass, combine;
   // or one complex GEMM with the assembled A~ (row-major [n][nrhs] vectors are
@@ -248,7 +253,7 @@ static int solve_impl(qbx_plan* plan, const qbx_geom* g, qbx_c64 k, qbx_c64 eta,
     int r;
     if (Adense) {
       const cuDoubleComplex one = make_cuDoubleComplex(1.0, 0.0), zero = make_cuDoubleComplex(0.0, 0.0);
-      cublasStatus_t cs = cublasZgemm3m(blas.h, CUBLAS_OP_N, CUBLAS_OP_T, nrhs, n, n, &one,
+      cublasStatus_t cs = cublasZgemm3m(blas, CUBLAS_OP_N, CUBLAS_OP_T, nrhs, n, n, &one,
                                         reinterpret_cast<const cuDoubleComplex*>(xs), nrhs,
                                         reinterpret_cast<const cuDoubleComplex*>(Adense), n, &zero,
                                         reinterpret_cast<cuDoubleComplex*>(y), nrhs);

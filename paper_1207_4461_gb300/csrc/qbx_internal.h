@@ -139,6 +139,8 @@ int host_choose_split_waves(int num_sms, int occ, int n_units, int n_src, size_t
 int host_split_len(int n_src, int ns);
 int host_fail(int code, const char* msg);   // sets qbx_last_error(), returns code
 void host_plan_info(const qbx_plan* plan, int* device, int* q_tgt, int* q_src, const double** interp);
+// The plan's cuBLAS handle (a cublasHandle_t), created on first use; NULL on failure.
+void* host_plan_blas(qbx_plan* plan);
 
 }  // namespace qbx
 

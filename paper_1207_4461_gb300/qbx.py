@@ -119,6 +119,14 @@ def lib():
             L.qbx_shape_adjoint_workspace_bytes.restype = ctypes.c_size_t
             L.qbx_apply_static.argtypes = [G, I, I, I, c64, I, _P, I, _P, _P]
             L.qbx_apply_static.restype = I
+            L.qbx_vec_dots.argtypes = [I, I, I, _P, _P, _P, _P, _P]
+            L.qbx_vec_dots.restype = I
+            L.qbx_vec_dots_work_bytes.argtypes = [I, I]
+            L.qbx_vec_dots_work_bytes.restype = Z
+            L.qbx_vec_orth_update.argtypes = [I, I, I, _P, _P, _P, _P]
+            L.qbx_vec_orth_update.restype = I
+            L.qbx_vec_combine.argtypes = [I, I, I, _P, _P, _P, _P]
+            L.qbx_vec_combine.restype = I
             L.qbx_debug_hankel01.argtypes = [_P, I, _P, _P, _P]
             L.qbx_debug_besselj.argtypes = [_P, I, I, _P, _P]
             for name in ("qbx_gauss_legendre", "qbx_plan_create", "qbx_plan_destroy", "qbx_sync_status",
@@ -474,6 +482,35 @@ def qbx_solve_exterior_dirichlet(plan: Plan, g: Geometry, k, eta, p, f, tol=1e-1
 
 
 OPS_S, OPS_D, OPS_GRAD_S = 1, 2, 4
+
+
+def qbx_vec_dots(V, w):
+    """out[j][r] = sum_i conj(V[j][i][r]) w[i][r] for the Krylov vectors V
+    [nv][n][nrhs] and w [n][nrhs] (complex128 on the device), in a fixed
+    reduction order: the GMRES inner products, one per basis vector and
+    right-hand side."""
+    nv, n, nrhs = V.shape
+    if tuple(w.shape) != (n, nrhs):
+        raise ValueError("w must be [n][nrhs] like the rows of V")
+    V, w = V.contiguous(), w.contiguous()
+    work = torch.empty(int(lib().qbx_vec_dots_work_bytes(nrhs, nv)), dtype=torch.uint8, device=V.device)
+    out = torch.empty((nv, nrhs), dtype=torch.complex128, device=V.device)
+    _check(lib().qbx_vec_dots(n, nrhs, nv, _ptr(V), _ptr(w), _ptr(work), _ptr(out), _stream()))
+    return out
+
+
+def qbx_vec_orth_update(V, h, w):
+    """w -= sum_j V[j] h[j] (per right-hand side), in place."""
+    nv, n, nrhs = V.shape
+    _check(lib().qbx_vec_orth_update(n, nrhs, nv, _ptr(V.contiguous()), _ptr(h.contiguous()), _ptr(w), _stream()))
+    return w
+
+
+def qbx_vec_combine(V, y, x):
+    """x += sum_j V[j] y[j] (per right-hand side), in place."""
+    nv, n, nrhs = V.shape
+    _check(lib().qbx_vec_combine(n, nrhs, nv, _ptr(V.contiguous()), _ptr(y.contiguous()), _ptr(x), _stream()))
+    return x
 
 
 def qbx_apply_ops(plan: Plan, g: Geometry, ops, side, limit, k, p, dens, out=None, eta=None):

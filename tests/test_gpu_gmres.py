@@ -137,3 +137,22 @@ def test_assembled_solve_matches_matrix_free(cuda):
     r = 0.5 * mu_a + D - 1j * eta * S - f
     sw = np.sqrt(go["tgt_w"])[:, None]
     assert np.all(np.linalg.norm(sw * r, axis=0) / np.linalg.norm(sw * f, axis=0) <= 5e-11)
+
+
+@pytest.mark.parametrize("n,nrhs,nv", [(1000, 1, 3), (16391, 64, 41), (777, 3, 1), (300, 300, 2), (5, 100, 4)])
+def test_krylov_vector_kernels(cuda, n, nrhs, nv):
+    """The GMRES vector kernels against torch: the inner products of every
+    basis vector with w per right-hand side (fixed-order reduction, so two
+    calls agree bit for bit), the orthogonalisation update and the solution
+    update, at ragged sizes and rhs counts below, at and above a block."""
+    g = torch.Generator(device="cpu").manual_seed(n + nrhs + nv)
+    V = torch.randn((nv, n, nrhs), dtype=torch.complex128, generator=g).cuda()
+    w = torch.randn((n, nrhs), dtype=torch.complex128, generator=g).cuda()
+    h = qbx.qbx_vec_dots(V, w)
+    ref = torch.einsum("jir,ir->jr", V.conj(), w)
+    assert (h - ref).abs().max().item() <= 1e-13 * n ** 0.5 * ref.abs().max().item() + 1e-300
+    assert torch.equal(h, qbx.qbx_vec_dots(V, w))
+    w2 = qbx.qbx_vec_orth_update(V, h, w.clone())
+    assert (w2 - (w - torch.einsum("jir,jr->ir", V, h))).abs().max().item() <= 1e-12 * w.abs().max().item() * nv
+    x = qbx.qbx_vec_combine(V, h, w.clone())
+    assert (x - (w + torch.einsum("jir,jr->ir", V, h))).abs().max().item() <= 1e-12 * w.abs().max().item() * nv
