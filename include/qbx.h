@@ -23,7 +23,11 @@
  *  - Density arrays have a right-hand-side axis: [n][nrhs].
  *  - Every compute call is asynchronous on `stream` (a cudaStream_t passed as
  *    void*, NULL = legacy default stream) and allocates nothing; only
- *    qbx_plan_create allocates (its workspace).
+ *    qbx_plan_create (its workspace), qbx_batch_create (the batch's arrays)
+ *    and the GMRES solves (their Krylov bases; the assembled solve also
+ *    creates the plan's cuBLAS handle on first use) allocate.
+ *  - A plan is not thread-safe: calls on one plan from several host threads
+ *    must be serialised by the caller.
  *  - Return value: QBX_OK or an error code; qbx_last_error() gives a
  *    thread-local message.  Argument errors are detected on the host before
  *    anything is launched.  Device-side conditions (non-finite values in the
@@ -345,8 +349,10 @@ int qbx_vec_combine(int n, int nrhs, int nv, const qbx_c64 *V, const qbx_c64 *y,
  * the truncated Graf sums against every source node carried back to the
  * target grid by the per-panel interpolation.  q_tgt <= 16.  Async on
  * stream.  qbx_solve_exterior_dirichlet_assembled then runs the same GMRES
- * with one ZGEMM (cuBLAS) per iteration for all right-hand sides; k, eta
- * and p are those the matrix was assembled with. */
+ * with one complex GEMM (cuBLAS ZGEMM3M) per iteration for all right-hand
+ * sides; k, eta and p are those the matrix was assembled with.  Its first
+ * call on a plan creates the plan's cuBLAS handle (freed by
+ * qbx_plan_destroy). */
 int qbx_assemble_cfie(qbx_plan *plan, const qbx_geom *g, qbx_c64 k, qbx_c64 eta, int p, qbx_c64 *A,
                       void *stream);
 int qbx_solve_exterior_dirichlet_assembled(qbx_plan *plan, const qbx_geom *g, const qbx_c64 *A,
