@@ -681,6 +681,72 @@ def run_adjoint(args):
     return 0
 
 
+def run_variants(args):
+    """The operator variants on the full-size starfish workload (256 panels,
+    4096 targets, 16384 sources, both sides, k = 20, p = 12, one CN(0,1)
+    density): the tangential dipole R (D's sums with the source tangents),
+    grad D (coefficients formed, then the expansion's gradient at each
+    target), S + D + grad S on centres at r = c sqrt(h) (c = 0.08, about the
+    h/2 radius at this panel size), and near-only S + D + grad S (eta = 8),
+    beside the global S + D + grad S step.  CUDA events per call, L2 flushed
+    before every timed call.  Prints one JSON line (not the benchmark
+    metric)."""
+    import torch
+    import paper_1207_4461_gb300 as qbx
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    wl = W.cfg2()
+    plan = qbx.Plan(wl.q_tgt, wl.q_src, n_src=wl.n_src, n_ctr=wl.n_ctr, ncoef=2 * wl.p + 1, nrhs=1)
+    g = qbx.qbx_geometry(plan, wl.curve, wl.curve.edges(wl.M))
+    g_sq = qbx.qbx_geometry(plan, wl.curve, wl.curve.edges(wl.M), 0.08, qbx.RADIUS_SQRT_H)
+    dens = torch.as_tensor(wl.dens(g.t_tgt), device=dev).contiguous()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    ops3 = (qbx.OP_S, qbx.OP_D, qbx.OP_GRAD_S)
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(args.steps):
+            flush.fill_(1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return statistics.median(ms)
+
+    clocks = ClockSampler(0)
+    clocks.start()
+    t = {
+        "S+D+grad S": timed(lambda: qbx.qbx_apply_ops(plan, g, ops3, qbx.SIDE_TWO, 0, wl.k, wl.p, dens)),
+        "R": timed(lambda: qbx.qbx_apply(plan, g, qbx.OP_R, qbx.SIDE_TWO, 0, wl.k, wl.p, dens)),
+        "grad D (PV)": timed(lambda: qbx.qbx_apply(plan, g, qbx.OP_GRAD_D, qbx.SIDE_TWO, qbx.LIMIT_PV, wl.k, wl.p,
+                                                 dens)),
+        "S+D+grad S, r = 0.08 sqrt(h)": timed(lambda: qbx.qbx_apply_ops(plan, g_sq, ops3, qbx.SIDE_TWO, 0, wl.k,
+                                                                        wl.p, dens)),
+        "S+D+grad S, near-only eta = 8": timed(lambda: qbx.qbx_apply_ops(plan, g, ops3, qbx.SIDE_TWO, 0, wl.k, wl.p,
+                                                                         dens, eta=8.0)),
+    }
+    clk = clocks.stop()
+    qbx.qbx_sync_status(plan)
+    pairs = wl.n_ctr * wl.n_src
+    per_op_terms = pairs * (2 * wl.p + 1)
+    nops = {"S+D+grad S": 3, "R": 1, "grad D (PV)": 1, "S+D+grad S, r = 0.08 sqrt(h)": 3,
+            "S+D+grad S, near-only eta = 8": 3}
+    print(json.dumps({
+        "variants": "starfish r=1+0.25cos5t, 256 panels (4096 targets, 16384 sources, 8192 centres), k=20, p=12, "
+                    "one CN(0,1) density (seed 2)",
+        "steps": args.steps, "warmup": args.warmup,
+        "l2": "flushed before every timed call (256 MiB write outside the event pair)",
+        "ms": t,
+        "terms_per_s": {name: nops[name] * per_op_terms / (ms * 1e-3) for name, ms in t.items()},
+        "clocks": clk}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -705,6 +771,9 @@ def main():
                     help="profiling only: run the batched comparison alone and print it")
     ap.add_argument("--solve", action="store_true",
                     help="run the exterior scattering solve (1024-panel teardrop, 64 plane waves) instead")
+    ap.add_argument("--variants", action="store_true",
+                    help="time the R, grad D, r = c sqrt(h) and near-only variants on the full-size workload "
+                         "instead")
     ap.add_argument("--adjoint", action="store_true",
                     help="time the forward, density-adjoint and shape-adjoint sweeps of the shape-optimisation "
                          "workload (128-panel starfish) instead")
@@ -715,6 +784,8 @@ def main():
         return run_solve(args)
     if args.adjoint:
         return run_adjoint(args)
+    if args.variants:
+        return run_variants(args)
     if args.batch_only:
         import torch
         import paper_1207_4461_gb300 as qbx

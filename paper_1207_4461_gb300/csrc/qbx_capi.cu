@@ -763,6 +763,59 @@ static int grad_d_impl(qbx_plan* p, const qbx_geom* g, int side, int limit, qbx_
   if (int rc = side_range(side, g->n_tgt, &c0, &nc)) return rc;
   const int nsides = side == QBX_SIDE_TWO ? 2 : 1;
   const int side0 = side == QBX_SIDE_EXT ? QBX_SIDE_EXT : QBX_SIDE_INT;
+  const bool ck = k.im != 0.0;
+  if (pp >= 1 && nrhs <= 3 && grad_d_fused_smem(ck, pp) <= 200 * 1024) {
+    // storage-free sums, one rhs per pass (few rhs: each pass costs a full sweep)
+    const size_t b_wd = align256((size_t)g->n_src * nrhs * 16);
+    const size_t b_ev = align256((size_t)nc * 2 * nrhs * 16);
+    const size_t fixed = b_wd + b_ev + 512;
+    if (p->ws_bytes < fixed) return fail(QBX_ENOMEM, "workspace too small for grad D");
+    const size_t per_split = (size_t)nc * 2 * nrhs * 16;
+    const int units = (nc + kApplyThreads - 1) / kApplyThreads;
+    CK(cudaSetDevice(p->device), "cudaSetDevice");
+    const int occ = grad_d_fused_occupancy(ck, pp);
+    const int ns = host_choose_split_waves(p->num_sms, occ, units, g->n_src, per_split, p->ws_bytes - fixed,
+                                           p->min_waves);
+    if (ns < 1) return fail(QBX_ENOMEM, "workspace too small for the grad D partial sums");
+    cudaStream_t st = (cudaStream_t)stream;
+    char* base = (char*)align256((size_t)p->ws);
+    void* wd = base;
+    void* ev = base + b_wd;
+    void* part = base + b_wd + b_ev;
+    CK(launch_upsample(g->M, g->q_tgt, g->q_src, nrhs, p->d_interp, g->src_w, dens, wd, st), "upsample");
+    if (p->timing) CK(cudaEventRecord(p->ev0, st), "timing event");
+    ApplyArgs a{};
+    a.p = pp;
+    a.kre = k.re;
+    a.kim = k.im;
+    a.n_ctr = nc;
+    a.cx = g->ctr_x + c0;
+    a.cy = g->ctr_y + c0;
+    a.n_tgt = g->n_tgt;
+    a.tx = g->tgt_x;
+    a.ty = g->tgt_y;
+    a.src = SrcView{g->src_x, g->src_y, g->src_nx, g->src_ny, g->n_src};
+    a.wd[0] = a.wd[1] = a.wd[2] = wd;
+    a.nrhs = nrhs;
+    a.nr = 1;
+    a.nsplit = ns;
+    a.src_per_split = split_len(g->n_src, ns);
+    a.part = part;
+    a.near_q_tgt = g->q_tgt;
+    a.near_q_src = g->q_src;
+    for (int r = 0; r < nrhs; ++r) {
+      a.rhs0 = r;
+      CK(launch_grad_d_fused(a, st), "grad D kernel");
+    }
+    CK(launch_form_finish(nc, 2, ns, nrhs, part, ev, p->d_status, st), "grad D reduction");
+    if (p->timing) CK(cudaEventRecord(p->ev1, st), "timing event");
+    CK(launch_grad_d_finish(g->n_tgt, g->q_tgt, nsides, side0, limit, nrhs, ev, dens, g->tgt_nx, g->tgt_ny,
+                            g->tgt_w, p->d_wgl_tgt, p->d_diff, out, p->d_status, st),
+       "grad D finish");
+    return QBX_OK;
+  }
+  // otherwise: the D coefficients formed and stored, then the expansion's
+  // gradient at each target
   const int ncoef = 2 * pp + 1;
   int nr = nrhs;
   while (nr > 1 && form_smem_bytes(pp, nr) > 160 * 1024) nr = (nr + 1) / 2;

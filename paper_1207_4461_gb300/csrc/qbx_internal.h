@@ -46,6 +46,12 @@ cudaError_t launch_apply_fused_cplx(const ApplyArgs& a, cudaStream_t st);
 cudaError_t launch_apply_fused_local_real(const ApplyArgs& a, cudaStream_t st);
 cudaError_t launch_apply_fused_local_cplx(const ApplyArgs& a, cudaStream_t st);
 int apply_occupancy_local(int ops, bool ck, int p, int nr, bool one_w = false);   // near-only instances
+// Storage-free grad D (one rhs per launch, a.rhs0; a.wd[0] the weighted
+// density): partial sums [nsplit][n_ctr][2][nrhs] of the expansion gradient
+// without the factor i/4.
+cudaError_t launch_grad_d_fused(const ApplyArgs& a, cudaStream_t st);
+size_t grad_d_fused_smem(bool ck, int p);
+int grad_d_fused_occupancy(bool ck, int p);
 size_t apply_smem_bytes(int ops, bool ck, int p, int nr);
 size_t apply_smem_bytes_real(int ops, int p, int nr);
 size_t apply_smem_bytes_cplx(int ops, int p, int nr);

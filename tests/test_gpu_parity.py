@@ -383,16 +383,32 @@ def test_sqrt_h_radius_rule(cuda, q_src):
 
 @pytest.mark.parametrize("side,limit", [(qbx.SIDE_INT, qbx.LIMIT_PV), (qbx.SIDE_EXT, qbx.LIMIT_PV),
                                         (qbx.SIDE_EXT, qbx.LIMIT_ONE_SIDED), (qbx.SIDE_TWO, qbx.LIMIT_PV)])
-@pytest.mark.parametrize("k,p,nrhs", [(7.0, 10, 1), (4 + 0.6j, 6, 3)])
+@pytest.mark.parametrize("k,p,nrhs", [(7.0, 10, 1), (4 + 0.6j, 6, 3), (5.0, 1, 2), (6.0, 0, 1), (8.0, 9, 5)])
 def test_apply_grad_d_matches_oracle(cuda, side, limit, k, p, nrhs):
-    """grad D (Sec. 3.2, eq. dlpderiv) on 13 panels: unfused coefficients,
-    the expansion's gradient at the target, the tangential jump for the PV."""
+    """grad D (Sec. 3.2, eq. dlpderiv) on 13 panels, the tangential jump for
+    the PV: storage-free sums for 1-3 rhs and p >= 1 (p = 1: no interior
+    orders, only the edge orders), stored coefficients and the expansion's
+    gradient otherwise (p = 0, 5 rhs)."""
     plan, g, go = make(W.starfish(0.2, 3), 13, nrhs=nrhs, p=p)
     dens = W.complex_gaussian(19, g.n_tgt * nrhs).reshape(g.n_tgt, nrhs)
     got = qbx.qbx_apply(plan, g, qbx.OP_GRAD_D, side, limit, k, p, dev(dens))
     qbx.qbx_sync_status(plan)
     assert got.shape == (g.n_tgt, 2, nrhs)
     assert rel(got, oracle.apply(go, oracle.OP_GRAD_D, side, limit, k, p, dens)) < TOL
+
+
+@pytest.mark.parametrize("k,p", [(7.0, 10), (3 + 0.5j, 8), (9.0, 2)])
+def test_grad_d_fused_matches_stored_coefficients(cuda, k, p):
+    """The storage-free grad D (one rhs) and the stored-coefficient path (the
+    same density in 4 columns) agree to rounding on every target, both
+    sides."""
+    plan, g, go = make(W.starfish(0.2, 3), 17, nrhs=4, p=p)
+    dens = W.complex_gaussian(37, g.n_tgt).reshape(g.n_tgt, 1)
+    one = qbx.qbx_apply(plan, g, qbx.OP_GRAD_D, qbx.SIDE_TWO, qbx.LIMIT_PV, k, p, dev(dens))
+    four = qbx.qbx_apply(plan, g, qbx.OP_GRAD_D, qbx.SIDE_TWO, qbx.LIMIT_PV, k, p, dev(np.repeat(dens, 4, axis=1)))
+    qbx.qbx_sync_status(plan)
+    assert rel(one[:, :, 0], four[:, :, 0].cpu().numpy()) < 1e-12
+    assert rel(one[:, :, 0], four[:, :, 3].cpu().numpy()) < 1e-12
 
 
 @pytest.mark.parametrize("ops,side,limit,k,eta", [((0, 1, 2), qbx.SIDE_TWO, 0, 7.0, 3.0),
