@@ -498,12 +498,25 @@ def run_solve(args):
     import torch
     import paper_1207_4461_gb300 as qbx
     torch.cuda.set_device(0)
-    k, p, nrhs, m_base, levels = 30.0, 14, 64, 1008, 8
+    k, p, nrhs, m_base, levels = 30.0, 14, 64, args.solve_base, 8
     cur = W.teardrop()
     edges = W.dyadic_edges(m_base, levels)
     M = len(edges) - 1
     plan = qbx.Plan(16, 64, n_src=64 * M, n_ctr=32 * M, ncoef=2, nrhs=nrhs)
     g = qbx.qbx_geometry(plan, cur, edges)
+    if args.assemble_only:   # the assembly kernel alone (profiling), after one warm-up call
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        A = qbx.qbx_assemble_cfie(plan, g, k, k, p)
+        torch.cuda.synchronize()
+        e0.record()
+        A = qbx.qbx_assemble_cfie(plan, g, k, k, p)
+        e1.record()
+        e1.synchronize()
+        qbx.qbx_sync_status(plan)
+        print(json.dumps({"assemble": f"teardrop, {m_base}+{2 * levels} panels, k=30, p=14", "n_tgt": g.n_tgt,
+                          "n_src": g.n_src, "ms": e0.elapsed_time(e1),
+                          "pairs": 2 * g.n_tgt * g.n_src}))
+        return 0
     tx, ty = g["tgt_x"], g["tgt_y"]
     ang = 2 * math.pi * torch.arange(nrhs, dtype=torch.float64, device="cuda") / nrhs
     f = -torch.exp(1j * k * (tx[:, None] * torch.cos(ang)[None, :] + ty[:, None] * torch.sin(ang)[None, :]))
@@ -562,7 +575,7 @@ def run_solve(args):
     resid_w = (torch.linalg.norm(sw * r, dim=0) / torch.linalg.norm(sw * f, dim=0)).max().item()
     resid_apply = (torch.abs(r).max() / torch.abs(f).max()).item()
     pairs = 2 * g.n_tgt * g.n_src
-    line = {"solve": "exterior sound-soft, paper's teardrop, 1008+16 panels (dyadic toward the corner), "
+    line = {"solve": f"exterior sound-soft, paper's teardrop, {m_base}+16 panels (dyadic toward the corner), "
                      "k=30, p=14, eta=k, 64 plane waves, two-sided D and S, GMRES on the device",
             "n_tgt": g.n_tgt, "n_src": g.n_src, "n_ctr": 2 * g.n_tgt, "nrhs": nrhs,
             "restart": args.solve_restart, "tol": 1e-10, "matvecs": its,
@@ -696,6 +709,8 @@ def run_variants(args):
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
     wl = W.cfg2()
+    if args.panels:
+        wl.M = args.panels
     plan = qbx.Plan(wl.q_tgt, wl.q_src, n_src=wl.n_src, n_ctr=wl.n_ctr, ncoef=2 * wl.p + 1, nrhs=1)
     g = qbx.qbx_geometry(plan, wl.curve, wl.curve.edges(wl.M))
     g_sq = qbx.qbx_geometry(plan, wl.curve, wl.curve.edges(wl.M), 0.08, qbx.RADIUS_SQRT_H)
@@ -737,8 +752,8 @@ def run_variants(args):
     nops = {"S+D+grad S": 3, "R": 1, "grad D (PV)": 1, "S+D+grad S, r = 0.08 sqrt(h)": 3,
             "S+D+grad S, near-only eta = 8": 3}
     print(json.dumps({
-        "variants": "starfish r=1+0.25cos5t, 256 panels (4096 targets, 16384 sources, 8192 centres), k=20, p=12, "
-                    "one CN(0,1) density (seed 2)",
+        "variants": f"starfish r=1+0.25cos5t, {wl.M} panels ({wl.n_tgt} targets, {wl.n_src} sources, "
+                    f"{wl.n_ctr} centres), k=20, p=12, one CN(0,1) density (seed 2)",
         "steps": args.steps, "warmup": args.warmup,
         "l2": "flushed before every timed call (256 MiB write outside the event pair)",
         "ms": t,
@@ -777,6 +792,10 @@ def main():
     ap.add_argument("--adjoint", action="store_true",
                     help="time the forward, density-adjoint and shape-adjoint sweeps of the shape-optimisation "
                          "workload (128-panel starfish) instead")
+    ap.add_argument("--solve-base", type=int, default=1008,
+                    help="panels equispaced in t before the 2 x 8 corner bisections (profiling: smaller)")
+    ap.add_argument("--assemble-only", action="store_true",
+                    help="profiling only: with --solve, time the matrix assembly alone")
     ap.add_argument("--solve-restart", type=int, default=60)
     ap.add_argument("--solve-maxiter", type=int, default=400)
     args = ap.parse_args()
