@@ -177,9 +177,10 @@ extern "C" int qbx_assemble_cfie(qbx_plan* plan, const qbx_geom* g, qbx_c64 k, q
   const bool ck = k.im != 0.0;
   const size_t smem = ck ? asm_smem<cplx>(p, q_src, q_tgt) : asm_smem<double>(p, q_src, q_tgt);
   if (smem > 200 * 1024) return afail(QBX_EINVAL, "p too large");
-  // panel groups: about four CTAs per SM slot in all
+  // panel groups: about 8192 CTAs in all (some 18 waves of the resident
+  // CTAs), so that the last, partly filled wave costs little
   const unsigned gx = (unsigned)((g->n_tgt + kAsmLanes - 1) / kAsmLanes);
-  const unsigned gy = (unsigned)std::max(1, std::min((g->M + kAsmWarps - 1) / kAsmWarps, (int)((2048 + gx - 1) / gx)));
+  const unsigned gy = (unsigned)std::max(1, std::min((g->M + kAsmWarps - 1) / kAsmWarps, (int)((8192 + gx - 1) / gx)));
   const dim3 grid(gx, gy);
   cudaStream_t st = (cudaStream_t)stream;
   if (ck) {
