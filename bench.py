@@ -698,10 +698,11 @@ def run_variants(args):
     """The operator variants on the full-size starfish workload (256 panels,
     4096 targets, 16384 sources, both sides, k = 20, p = 12, one CN(0,1)
     density): the tangential dipole R (D's sums with the source tangents),
-    grad D (coefficients formed, then the expansion's gradient at each
-    target), S + D + grad S on centres at r = c sqrt(h) (c = 0.08, about the
-    h/2 radius at this panel size), and near-only S + D + grad S (eta = 8),
-    beside the global S + D + grad S step.  CUDA events per call, L2 flushed
+    grad D (storage-free), S + D + grad S on centres at r = c sqrt(h)
+    (c = 0.08, about the h/2 radius at this panel size), and near-only
+    S + D + grad S (eta = 8), beside the global S + D + grad S step; then
+    S + D + grad S for 32 right-hand sides (the group kernel), global and
+    near-only.  CUDA events per call, L2 flushed
     before every timed call.  Prints one JSON line (not the benchmark
     metric)."""
     import torch
@@ -745,12 +746,21 @@ def run_variants(args):
         "S+D+grad S, near-only eta = 8": timed(lambda: qbx.qbx_apply_ops(plan, g, ops3, qbx.SIDE_TWO, 0, wl.k, wl.p,
                                                                          dens, eta=8.0)),
     }
+    # 32 rhs of one density: the group kernel, global and near-only
+    plan32 = qbx.Plan(wl.q_tgt, wl.q_src, n_src=wl.n_src, n_ctr=wl.n_ctr, ncoef=4, nrhs=32)
+    g32 = qbx.qbx_geometry(plan32, wl.curve, wl.curve.edges(wl.M))
+    d32 = torch.as_tensor(W.complex_gaussian(5, g32.n_tgt * 32).reshape(g32.n_tgt, 32), device=dev)
+    t["S+D+grad S, 32 rhs"] = timed(lambda: qbx.qbx_apply_ops(plan32, g32, ops3, qbx.SIDE_TWO, 0, wl.k, wl.p, d32))
+    t["S+D+grad S, 32 rhs, near-only eta = 8"] = timed(
+        lambda: qbx.qbx_apply_ops(plan32, g32, ops3, qbx.SIDE_TWO, 0, wl.k, wl.p, d32, eta=8.0))
+    qbx.qbx_sync_status(plan32)
     clk = clocks.stop()
     qbx.qbx_sync_status(plan)
     pairs = wl.n_ctr * wl.n_src
     per_op_terms = pairs * (2 * wl.p + 1)
     nops = {"S+D+grad S": 3, "R": 1, "grad D (PV)": 1, "S+D+grad S, r = 0.08 sqrt(h)": 3,
-            "S+D+grad S, near-only eta = 8": 3}
+            "S+D+grad S, near-only eta = 8": 3, "S+D+grad S, 32 rhs": 3 * 32,
+            "S+D+grad S, 32 rhs, near-only eta = 8": 3 * 32}
     print(json.dumps({
         "variants": f"starfish r=1+0.25cos5t, {wl.M} panels ({wl.n_tgt} targets, {wl.n_src} sources, "
                     f"{wl.n_ctr} centres), k=20, p=12, one CN(0,1) density (seed 2)",

@@ -239,7 +239,8 @@ int qbx_apply_ops(qbx_plan *plan, const qbx_geom *g, int ops, int side, int limi
  * centre's target (as qbx_far) instead of the expansion at c.  The result
  * differs from qbx_apply_ops by about eta^-(p+1) relative (QBX truncation of
  * the distant pairs); eta = 8 at p = 12 agrees to ~1e-13.  eta > 0, else
- * QBX_EINVAL.  Always the fused kernel (no group kernel). */
+ * QBX_EINVAL.  Kernels as qbx_apply_ops: the group kernel for >= 16 rhs of
+ * one density (S, D, S + D or all three), the fused kernel otherwise. */
 int qbx_apply_local(qbx_plan *plan, const qbx_geom *g, int ops, int side, int limit, qbx_c64 k, int p,
                     double eta, const qbx_c64 *const dens[3], int nrhs, qbx_c64 *const out[3], void *stream);
 

@@ -1,7 +1,7 @@
 // qbx_apply_local.cu -- instances of the near-only variant of the fused
-// apply (sources beyond eta r by the smooth rule at the target), real and
-// complex k, kept apart from the global instances.
-#include "qbx_apply_impl.cuh"
+// apply and of the group kernel (sources beyond eta r by the smooth rule at
+// the target), real and complex k, kept apart from the global instances.
+#include "qbx_group_impl.cuh"
 
 namespace qbx {
 
@@ -13,6 +13,13 @@ cudaError_t launch_apply_fused_local_cplx(const ApplyArgs& a, cudaStream_t st) {
 }
 int apply_occupancy_local(int ops, bool ck, int p, int nr, bool one_w) {
   return ck ? apply_occupancy_t<cplx, true>(ops, p, nr, one_w) : apply_occupancy_t<double, true>(ops, p, nr, one_w);
+}
+
+cudaError_t launch_group_local(const GroupArgs& a, bool ck, int rg, int grid, cudaStream_t st) {
+  return ck ? launch_group_any<cplx, true>(a, rg, grid, st) : launch_group_any<double, true>(a, rg, grid, st);
+}
+int group_occupancy_local(int ops, bool ck, int p, int rg) {
+  return ck ? group_occupancy_any<cplx, true>(ops, p, rg) : group_occupancy_any<double, true>(ops, p, rg);
 }
 
 }  // namespace qbx

@@ -627,7 +627,7 @@ static int apply_impl(qbx_plan* p, const qbx_geom* g, int ops, int side, int lim
   // many right-hand sides of one density: the group kernel (kernel values
   // formed once per pair for all rhs); otherwise the fused kernel
   const bool ck = k.im != 0.0;
-  const bool group = nrhs >= 16 && nd == 1 && (ops == 1 || ops == 2 || ops == 3 || ops == 7) && !(eta > 0.0);
+  const bool group = nrhs >= 16 && nd == 1 && (ops == 1 || ops == 2 || ops == 3 || ops == 7);
   const int rg = 8;
   const int units = group ? (nc + kGrpCentres - 1) / kGrpCentres : (nc + kApplyThreads - 1) / kApplyThreads;
   const bool local = eta > 0.0;
@@ -636,7 +636,8 @@ static int apply_impl(qbx_plan* p, const qbx_geom* g, int ops, int side, int lim
   const bool one_w = !group && nd == 1 && nrhs == 1;
   CK(cudaSetDevice(p->device), "cudaSetDevice");
   int occ;
-  if (group) occ = ck ? group_occupancy_cplx(ops, pp, rg) : group_occupancy_real(ops, pp, rg);
+  if (group && local) occ = group_occupancy_local(ops, ck, pp, rg);
+  else if (group) occ = ck ? group_occupancy_cplx(ops, pp, rg) : group_occupancy_real(ops, pp, rg);
   else if (local) occ = apply_occupancy_local(ops, ck, pp, std::min(chunk, nrhs), one_w);
   else occ = ck ? apply_occupancy_cplx(ops, pp, std::min(chunk, nrhs), one_w)
                 : apply_occupancy_real(ops, pp, std::min(chunk, nrhs), one_w);
@@ -719,7 +720,11 @@ static int apply_impl(qbx_plan* p, const qbx_geom* g, int ops, int side, int lim
     ga.st_units = units;
     ga.st_nsplit = ns;
     ga.st_split_len = split_len(g->n_src, ns);
-    CK(ck ? launch_group_cplx(ga, rg, units * ns, st) : launch_group_real(ga, rg, units * ns, st), "group kernel");
+    ga.eta2 = a.eta2;
+    if (local)
+      CK(launch_group_local(ga, ck, rg, units * ns, st), "group kernel (near-only)");
+    else
+      CK(ck ? launch_group_cplx(ga, rg, units * ns, st) : launch_group_real(ga, rg, units * ns, st), "group kernel");
   } else {
     for (int r0 = 0; r0 < nrhs; r0 += chunk) {
       a.rhs0 = r0;

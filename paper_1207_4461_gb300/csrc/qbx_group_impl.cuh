@@ -40,7 +40,9 @@ struct GroupSmem {
   }
 };
 
-template <int OPS, typename T, int RG>
+// LOCAL: near-only QBX (sources at |x_s - c| >= eta r by the smooth rule at
+// the target, pair_direct), a separate instance.
+template <int OPS, typename T, int RG, bool LOCAL = false>
 __global__ void __launch_bounds__(kGrpCentres * kGrpWarps)
 k_apply_group(GroupArgs a) {
   using L = GroupSmem<OPS, T, RG>;
@@ -116,6 +118,7 @@ k_apply_group(GroupArgs a) {
     const double ir = 1.0 / r;
     ux *= ir;
     uy *= ir;
+    const double lim2 = LOCAL ? a.eta2 * r * r : INFINITY;
     KW<T> kw;
     kw.init(in.kre, in.kim);
     const T kk = kw.kval();
@@ -187,8 +190,12 @@ k_apply_group(GroupArgs a) {
             ny = s_ny[j];
           }
           cplx GS, K, GA, GB, EX, EY;
-          pair_kernels<OPS, T, kGrpCentres>(kw, kk, J0, kneg_j0, colJ, colL, colG, p, dx, dy, nx, ny, ux,
-                                            uy, GS, K, GA, GB, EX, EY);
+          if (LOCAL && fma(dx, dx, dy * dy) >= lim2) {   // near-only QBX: a distant source
+            pair_direct<OPS, T>(kw, kk, r * ux - dx, r * uy - dy, nx, ny, ux, uy, r, GS, K, GA, GB);
+          } else {
+            pair_kernels<OPS, T, kGrpCentres>(kw, kk, J0, kneg_j0, colJ, colL, colG, p, dx, dy, nx, ny, ux,
+                                              uy, GS, K, GA, GB, EX, EY);
+          }
           auto put = [&](int q, cplx v) {
             const int idx = (q * kGrpTile + j) * kGrpCentres + lane;
             if constexpr (k3M) {
@@ -273,10 +280,10 @@ k_apply_group(GroupArgs a) {
   }
 }
 
-template <int OPS, typename T, int RG>
+template <int OPS, typename T, int RG, bool LOCAL = false>
 static cudaError_t launch_group_t(const GroupArgs& a, int grid, cudaStream_t st) {
   const size_t smem = GroupSmem<OPS, T, RG>::bytes(a.p);
-  auto kern = k_apply_group<OPS, T, RG>;
+  auto kern = k_apply_group<OPS, T, RG, LOCAL>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   kern<<<grid, kGrpCentres * kGrpWarps, smem, st>>>(a);
@@ -292,10 +299,10 @@ static cudaError_t launch_group_t(const GroupArgs& a, int grid, cudaStream_t st)
     default: break;                                                      \
   }
 
-template <typename T>
+template <typename T, bool LOCAL = false>
 static cudaError_t launch_group_any(const GroupArgs& a, int rg, int grid, cudaStream_t st) {
   const int ops = a.ops;
-#define X(O, TT, R) return launch_group_t<O, TT, R>(a, grid, st)
+#define X(O, TT, R) return launch_group_t<O, TT, R, LOCAL>(a, grid, st)
   if (rg == 8) {
     QBX_GROUP_OPS(X, T, 8)
   } else {
@@ -305,14 +312,14 @@ static cudaError_t launch_group_any(const GroupArgs& a, int rg, int grid, cudaSt
   return cudaErrorInvalidValue;
 }
 
-template <typename T>
+template <typename T, bool LOCAL = false>
 static int group_occupancy_any(int ops, int p, int rg) {
   int n = 0;
-#define X(O, TT, R)                                                                                 \
-  cudaFuncSetAttribute(k_apply_group<O, TT, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,        \
-                       (int)GroupSmem<O, TT, R>::bytes(p));                                         \
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_apply_group<O, TT, R>, kGrpCentres * kGrpWarps, \
-                                                GroupSmem<O, TT, R>::bytes(p));                     \
+#define X(O, TT, R)                                                                                         \
+  cudaFuncSetAttribute(k_apply_group<O, TT, R, LOCAL>, cudaFuncAttributeMaxDynamicSharedMemorySize,        \
+                       (int)GroupSmem<O, TT, R>::bytes(p));                                                 \
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_apply_group<O, TT, R, LOCAL>, kGrpCentres * kGrpWarps, \
+                                                GroupSmem<O, TT, R>::bytes(p));                             \
   return n
   if (rg == 8) {
     QBX_GROUP_OPS(X, T, 8)

@@ -411,14 +411,17 @@ def test_grad_d_fused_matches_stored_coefficients(cuda, k, p):
     assert rel(one[:, :, 0], four[:, :, 3].cpu().numpy()) < 1e-12
 
 
-@pytest.mark.parametrize("ops,side,limit,k,eta", [((0, 1, 2), qbx.SIDE_TWO, 0, 7.0, 3.0),
-                                                  ((0,), qbx.SIDE_INT, 1, 3 + 0.5j, 5.0),
-                                                  ((1, 2), qbx.SIDE_EXT, 1, 9.0, 8.0)])
-def test_apply_local_matches_oracle(cuda, ops, side, limit, k, eta):
+@pytest.mark.parametrize("ops,side,limit,k,eta,nrhs", [((0, 1, 2), qbx.SIDE_TWO, 0, 7.0, 3.0, 2),
+                                                       ((0,), qbx.SIDE_INT, 1, 3 + 0.5j, 5.0, 2),
+                                                       ((1, 2), qbx.SIDE_EXT, 1, 9.0, 8.0, 2),
+                                                       ((0, 1, 2), qbx.SIDE_TWO, 1, 7.0, 3.0, 17),
+                                                       ((0, 1), qbx.SIDE_INT, 0, 3 + 0.5j, 4.0, 16)])
+def test_apply_local_matches_oracle(cuda, ops, side, limit, k, eta, nrhs):
     """Near-only QBX (qbx_apply_local): the oracle's near/far split with the
     same eta; pairs exactly at the boundary may fall on either side, which
-    costs at most eta^-(p+1) of a pair's kernel."""
-    p, nrhs = 10, 2
+    costs at most eta^-(p+1) of a pair's kernel.  16 and 17 rhs of one
+    density take the group kernel."""
+    p = 10
     plan, g, go = make(W.starfish(0.2, 3), 24, nrhs=nrhs, p=p)
     dens = W.complex_gaussian(23, g.n_tgt * nrhs).reshape(g.n_tgt, nrhs)
     got = qbx.qbx_apply_ops(plan, g, ops, side, limit, k, p, dev(dens), eta=eta)
