@@ -77,7 +77,7 @@ GROUP_SOURCES = ["qbx_group_impl.cuh", "qbx_apply_impl.cuh", "qbx_device.cuh", "
 # counters divided by the pairs of the captured launch, for the kernel
 # sources with the given hash (profiles/*_fp64_counts.md).
 HW_FP64_PER_PAIR = {"084480a055477089": 551.5}         # fused S + D + grad S, p = 12, one rhs
-HW_FP64_PER_PAIR_GROUP = {"4105582d9e3560d6": 763.4}   # group kernel, S + D, p = 10, 32 rhs
+HW_FP64_PER_PAIR_GROUP = {"f5e81dff23b7c1a3": 763.4}   # group kernel, S + D, p = 10, 32 rhs
 
 
 def source_hash(names=KERNEL_SOURCES):
@@ -701,6 +701,7 @@ def run_variants(args):
     grad D (storage-free), S + D + grad S on centres at r = c sqrt(h)
     (c = 0.08, about the h/2 radius at this panel size), and near-only
     S + D + grad S (eta = 8), beside the global S + D + grad S step; then
+    S, D and grad S through stored coefficients (form, then evaluate), and
     S + D + grad S for 32 right-hand sides (the group kernel), global and
     near-only.  CUDA events per call, L2 flushed
     before every timed call.  Prints one JSON line (not the benchmark
@@ -746,6 +747,19 @@ def run_variants(args):
         "S+D+grad S, near-only eta = 8": timed(lambda: qbx.qbx_apply_ops(plan, g, ops3, qbx.SIDE_TWO, 0, wl.k, wl.p,
                                                                          dens, eta=8.0)),
     }
+    # the same three operators through stored coefficients (Sec. 3.3 as
+    # written: form alpha for S and for D, then evaluate S, D and grad S;
+    # raw expansion values, without the finishing step)
+    KS, KD = qbx.OP_S, qbx.OP_D
+
+    def stored():
+        wdn = qbx.qbx_upsample(plan, g, dens)
+        a_s = qbx.qbx_form_locals(plan, g, KS, qbx.SIDE_TWO, wl.k, wl.p, wdn)
+        a_d = qbx.qbx_form_locals(plan, g, KD, qbx.SIDE_TWO, wl.k, wl.p, wdn)
+        qbx.qbx_eval_locals(plan, g, qbx.SIDE_TWO, wl.k, wl.p, a_s, qbx.VALUE)
+        qbx.qbx_eval_locals(plan, g, qbx.SIDE_TWO, wl.k, wl.p, a_d, qbx.VALUE)
+        qbx.qbx_eval_locals(plan, g, qbx.SIDE_TWO, wl.k, wl.p, a_s, qbx.GRAD)
+    t["S, D, grad S via stored coefficients (form + eval)"] = timed(stored)
     # 32 rhs of one density: the group kernel, global and near-only
     plan32 = qbx.Plan(wl.q_tgt, wl.q_src, n_src=wl.n_src, n_ctr=wl.n_ctr, ncoef=4, nrhs=32)
     g32 = qbx.qbx_geometry(plan32, wl.curve, wl.curve.edges(wl.M))
@@ -760,6 +774,7 @@ def run_variants(args):
     per_op_terms = pairs * (2 * wl.p + 1)
     nops = {"S+D+grad S": 3, "R": 1, "grad D (PV)": 1, "S+D+grad S, r = 0.08 sqrt(h)": 3,
             "S+D+grad S, near-only eta = 8": 3, "S+D+grad S, 32 rhs": 3 * 32,
+            "S, D, grad S via stored coefficients (form + eval)": 3,
             "S+D+grad S, 32 rhs, near-only eta = 8": 3 * 32}
     print(json.dumps({
         "variants": f"starfish r=1+0.25cos5t, {wl.M} panels ({wl.n_tgt} targets, {wl.n_src} sources, "
