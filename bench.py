@@ -77,7 +77,7 @@ GROUP_SOURCES = ["qbx_group_impl.cuh", "qbx_apply_impl.cuh", "qbx_device.cuh", "
 # counters divided by the pairs of the captured launch, for the kernel
 # sources with the given hash (profiles/*_fp64_counts.md).
 HW_FP64_PER_PAIR = {"084480a055477089": 551.5}         # fused S + D + grad S, p = 12, one rhs
-HW_FP64_PER_PAIR_GROUP = {"f5e81dff23b7c1a3": 763.4}   # group kernel, S + D, p = 10, 32 rhs
+HW_FP64_PER_PAIR_GROUP = {"c12d07e4ebe97dd4": 763.4}   # group kernel, S + D, p = 10, 32 rhs
 
 
 def source_hash(names=KERNEL_SOURCES):
@@ -462,6 +462,11 @@ def run_batch_compare(args, qbx, torch):
     batch.status()
     ms_inst = timed(per_instance, steps)
     qbx.qbx_sync_status(plan)
+    # the same batch with near-only QBX (eta = 8), then back to the global apply
+    batch.set_eta(8.0)
+    ms_near = timed(batch.apply, 1)
+    batch.set_eta(0.0)
+    batch.status()
     pairs = sum(g.n_tgt * g.n_src for g in geoms)
     terms = pairs * (2 * bw.p + 1) * bw.nrhs * 2
     fpp = flops_per_pair_ops(["S", "D"], bw.p, bw.nrhs)
@@ -474,6 +479,7 @@ def run_batch_compare(args, qbx, torch):
             "batched_terms_per_s": terms / (ms_batch * 1e-3),
             "per_instance_terms_per_s": terms / (ms_inst * 1e-3),
             "speedup": ms_inst / ms_batch,
+            "near_only_batched_ms": ms_near,
             "items": {"model": dict(zip(("rhs_per_warp", "src_chunk", "items", "ctas"), model_cfg)),
                       "tuned": dict(zip(("rhs_per_warp", "src_chunk", "items", "ctas"), tuned_cfg)),
                       "tune_s": t_tune},

@@ -395,6 +395,13 @@ int qbx_batch_status(qbx_batch *batch, void *stream);
  * sources, the total pairs and the curve count); qbx_batch_create starts
  * from a cached choice when one matches. */
 int qbx_batch_tune(qbx_batch *batch, void *stream, int *rg, int *chunk);
+/* Near-only QBX for the whole batch (as qbx_apply_local, Sec. 5 remark):
+ * eta > 0 sends every source node with |x_s - c| >= eta r_c through the
+ * smooth rule at the centre's target instead of the expansion; eta = 0
+ * restores the global apply.  Rebuilds the batch's graph with its current
+ * configuration (host call, synchronous); eta < 0 or not finite:
+ * QBX_EINVAL.  qbx_batch_tune measures the mode that is set. */
+int qbx_batch_set_eta(qbx_batch *batch, double eta);
 /* The batch's current configuration: rhs per warp group, sources per item,
  * work items, persistent CTAs.  Host, no device work. */
 int qbx_batch_info(const qbx_batch *batch, int *rg, int *chunk, int *n_items, int *grid);

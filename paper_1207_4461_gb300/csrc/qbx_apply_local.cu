@@ -21,5 +21,8 @@ cudaError_t launch_group_local(const GroupArgs& a, bool ck, int rg, int grid, cu
 int group_occupancy_local(int ops, bool ck, int p, int rg) {
   return ck ? group_occupancy_any<cplx, true>(ops, p, rg) : group_occupancy_any<double, true>(ops, p, rg);
 }
+const void* group_ptr_local(int ops, bool ck, int rg) {
+  return ck ? group_ptr_any<cplx, true>(ops, rg) : group_ptr_any<double, true>(ops, rg);
+}
 
 }  // namespace qbx

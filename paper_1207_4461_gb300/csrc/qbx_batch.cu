@@ -23,6 +23,7 @@ struct qbx_batch {
   bool ck = false;
   int n_items = 0, grid = 0, max_src = 0, max_tgt = 0, num_sms = 0;
   int chunk = 0;                    // sources per work item (multiple of 32)
+  double eta2 = 0.0;                // near-only QBX when > 0 (qbx_batch_set_eta)
   size_t part_cap = 0;              // bytes allocated for the partial sums
   std::vector<qbx::GroupInst> h_inst;
   GroupInst* d_inst = nullptr;
@@ -231,7 +232,9 @@ int configure(qbx_batch* b, int rg, int chunk) {
   b->n_items = (int)items.size();
   b->rg = rg;
   b->chunk = chunk;
-  const int occ = b->ck ? group_occupancy_cplx(b->ops, b->p, rg) : group_occupancy_real(b->ops, b->p, rg);
+  const bool local = b->eta2 > 0.0;
+  const int occ = local ? group_occupancy_local(b->ops, b->ck, b->p, rg)
+                        : (b->ck ? group_occupancy_cplx(b->ops, b->p, rg) : group_occupancy_real(b->ops, b->p, rg));
   const size_t gsmem = b->ck ? group_smem_cplx(b->ops, b->p, rg) : group_smem_real(b->ops, b->p, rg);
   if (occ < 1 || gsmem > 220 * 1024) return bfail(QBX_EINVAL, "p too large for the group kernel");
   b->grid = std::min(b->n_items, b->num_sms * occ);
@@ -247,7 +250,9 @@ int configure(qbx_batch* b, int rg, int chunk) {
   ga.n_items = b->n_items;
   ga.items = b->d_items;
   ga.counter = b->d_counter;
-  const void* gk = b->ck ? group_ptr_cplx(b->ops, rg) : group_ptr_real(b->ops, rg);
+  ga.eta2 = b->eta2;
+  const void* gk = local ? group_ptr_local(b->ops, b->ck, rg)
+                         : (b->ck ? group_ptr_cplx(b->ops, rg) : group_ptr_real(b->ops, rg));
   if (!gk) return bfail(QBX_EINVAL, "no group kernel for this operator set");
   e = cudaFuncSetAttribute(gk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsmem);
   if (e == cudaSuccess) e = cudaGraphCreate(&b->graph, 0);
@@ -299,10 +304,10 @@ int configure(qbx_batch* b, int rg, int chunk) {
 }
 
 // Tuned configurations, cached per (device, p, operators, side, nrhs, real or
-// complex k, and the power-of-two buckets of the largest curve, the total
-// pairs and the curve count): a batch created later with the same key starts
-// from the measured choice instead of the model's.
-typedef std::tuple<int, int, int, int, int, int, int, int, int> TuneKey;
+// complex k, global or near-only, and the power-of-two buckets of the largest
+// curve, the total pairs and the curve count): a batch created later with the
+// same key starts from the measured choice instead of the model's.
+typedef std::tuple<int, int, int, int, int, int, int, int, int, int> TuneKey;
 std::mutex g_tune_mu;
 std::map<TuneKey, std::pair<int, int>> g_tune_cache;
 
@@ -311,8 +316,8 @@ int log2i(double v) { return v < 1.0 ? 0 : (int)std::floor(std::log2(v)); }
 TuneKey tune_key(const qbx_batch* b) {
   double pairs = 0.0;
   for (const GroupInst& in : b->h_inst) pairs += (double)in.n_ctr * in.n_src;
-  return TuneKey{b->device, b->p, b->ops, b->side, b->nrhs, b->ck ? 1 : 0, log2i(b->max_src), log2i(pairs),
-                 log2i(b->n_inst)};
+  return TuneKey{b->device, b->p, b->ops, b->side, b->nrhs, b->ck ? 1 : 0, b->eta2 > 0.0 ? 1 : 0,
+                 log2i(b->max_src), log2i(pairs), log2i(b->n_inst)};
 }
 
 // partial-sum budget: a quarter of the free device memory
@@ -517,6 +522,13 @@ int qbx_batch_tune(qbx_batch* b, void* stream, int* rg_out, int* chunk_out) {
   if (rg_out) *rg_out = best_rg;
   if (chunk_out) *chunk_out = best_chunk;
   return QBX_OK;
+}
+
+int qbx_batch_set_eta(qbx_batch* b, double eta) {
+  if (!b) return bfail(QBX_EINVAL, "NULL batch");
+  if (!(eta >= 0.0) || !isfinite(eta)) return bfail(QBX_EINVAL, "eta must be finite and >= 0");
+  b->eta2 = eta * eta;
+  return configure(b, b->rg, b->chunk);
 }
 
 int qbx_batch_info(const qbx_batch* b, int* rg, int* chunk, int* n_items, int* grid) {

@@ -330,9 +330,9 @@ static int group_occupancy_any(int ops, int p, int rg) {
   return 0;
 }
 
-template <typename T>
+template <typename T, bool LOCAL = false>
 static const void* group_ptr_any(int ops, int rg) {
-#define X(O, TT, R) return (const void*)k_apply_group<O, TT, R>
+#define X(O, TT, R) return (const void*)k_apply_group<O, TT, R, LOCAL>
   if (rg == 8) {
     QBX_GROUP_OPS(X, T, 8)
   } else {

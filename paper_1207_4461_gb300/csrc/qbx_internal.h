@@ -183,8 +183,8 @@ struct GroupArgs {
   const GroupItem* items;         // dynamic mode: item list (longest first)
   int* counter;                   // dynamic mode: next item (zeroed before launch)
   int st_units, st_nsplit, st_split_len;   // static mode (items == nullptr): one instance
-  double eta2;                    // near-only QBX (static mode, > 0): sources with |x_s - c|^2 >= eta2 r^2
-                                  // by the smooth rule at the target; 0: all through the expansion
+  double eta2;                    // near-only QBX (> 0): sources with |x_s - c|^2 >= eta2 r^2 by the
+                                  // smooth rule at the target; 0: all through the expansion
 };
 cudaError_t launch_group_real(const GroupArgs& a, int rg, int grid, cudaStream_t st);
 cudaError_t launch_group_cplx(const GroupArgs& a, int rg, int grid, cudaStream_t st);
@@ -197,6 +197,7 @@ const void* group_ptr_cplx(int ops, int rg);
 // near-only instances of the group kernel (GroupArgs::eta2 > 0)
 cudaError_t launch_group_local(const GroupArgs& a, bool ck, int rg, int grid, cudaStream_t st);
 int group_occupancy_local(int ops, bool ck, int p, int rg);
+const void* group_ptr_local(int ops, bool ck, int rg);
 
 }  // namespace qbx
 

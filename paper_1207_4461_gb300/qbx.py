@@ -101,6 +101,8 @@ def lib():
             L.qbx_batch_info.argtypes = [_P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I),
                                          ctypes.POINTER(I)]
             L.qbx_batch_info.restype = I
+            L.qbx_batch_set_eta.argtypes = [_P, D]
+            L.qbx_batch_set_eta.restype = I
             L.qbx_assemble_cfie.argtypes = [_P, G, c64, c64, I, _P, _P]
             L.qbx_assemble_cfie.restype = I
             L.qbx_solve_exterior_dirichlet_assembled.argtypes = [_P, G, _P, _P, I, D, I, I, _P,
@@ -577,6 +579,11 @@ class Batch:
         rg, ch = ctypes.c_int(0), ctypes.c_int(0)
         _check(lib().qbx_batch_tune(self.handle, _stream(), ctypes.byref(rg), ctypes.byref(ch)))
         return rg.value, ch.value
+
+    def set_eta(self, eta):
+        """qbx_batch_set_eta: near-only QBX with this eta (> 0), or the global
+        apply (0)."""
+        _check(lib().qbx_batch_set_eta(self.handle, float(eta)))
 
     def info(self):
         """(rhs per warp group, sources per item, items, persistent CTAs)."""

@@ -69,6 +69,33 @@ def test_batch_matches_oracle(cuda, ops, ks, side, limit):
             assert rel(out[i][o], ref) < TOL, (i, o)
 
 
+@pytest.mark.parametrize("ops,side,limit,eta", [((0, 1), qbx.SIDE_INT, 0, 3.0), ((0, 1, 2), qbx.SIDE_TWO, 1, 5.0)])
+def test_batch_near_only_matches_oracle(cuda, ops, side, limit, eta):
+    """qbx_batch_set_eta: the batch's near-only apply against the oracle's
+    near-only apply for every curve, then back to the global apply (eta 0)
+    against the oracle's global apply."""
+    ks, Ms = (5.0, 3 + 0.4j, 9.0, 12.0), (2, 7, 12, 5)
+    nrhs, p = 3, 8
+    insts, bw = small_batch(ks, Ms, nrhs)
+    plan = qbx.Plan(16, 64, n_src=64 * max(Ms), n_ctr=2 * 16 * max(Ms), ncoef=4, nrhs=nrhs)
+    geoms = [qbx.qbx_geometry(plan, c, c.edges(M)) for c, M, _ in insts]
+    dens = [dev(bw.dens(i, g.n_tgt)) for i, g in enumerate(geoms)]
+    batch = qbx.Batch(plan, geoms, list(ks), p, ops, side, limit, dens)
+    batch.set_eta(eta)
+    near = [{o: t.clone() for o, t in d.items()} for d in batch.apply()]
+    batch.set_eta(0.0)
+    glob = batch.apply()
+    batch.status()
+    for i, (c, M, k) in enumerate(insts):
+        go = oracle.geometry(c, c.edges(M), 16, 64)
+        d = bw.dens(i, go["n_tgt"])
+        for o in ops:
+            assert rel(near[i][o], oracle.apply_local(go, o, side, limit, k, p, eta, d)) < TOL, (i, o)
+            assert rel(glob[i][o], oracle.apply(go, o, side, limit, k, p, d)) < TOL, (i, o)
+    with pytest.raises(qbx.QBXError):
+        batch.set_eta(-1.0)
+
+
 def test_batch_reads_current_densities(cuda):
     """Densities are bound at creation; each apply reads their current values."""
     insts, bw = small_batch((4.0, 9.0), (4, 6), 3)
