@@ -33,6 +33,19 @@ namespace qbx {
 
 enum { OPB_S = 1, OPB_D = 2, OPB_G = 4, OPB_X = 8 };
 
+// Near-field-first work order: rank r of a launch takes, for the centre
+// block whose middle target is tmid, the source split at offset 0, +1, -1,
+// +2, ... (mod nsplit) from the block's home split (the one holding the
+// sources of the block's own panels; q_tgt, q_src nodes per panel), so the
+// items whose pairs take the slower small-argument Hankel branch run first
+// and the last wave holds uniform far-field items.
+__device__ __forceinline__ int near_first_split(int rank, int tmid, int q_tgt, int q_src, int split_len,
+                                                int nsplit) {
+  const int home = min(nsplit - 1, (tmid / q_tgt) * q_src / split_len);
+  const int off = (rank & 1) ? (rank + 1) / 2 : -(rank / 2);
+  return ((home + off) % nsplit + nsplit) % nsplit;
+}
+
 // ---- scalar helpers for T = double (real k) or cplx (complex k) ----------
 __device__ __forceinline__ void madd(cplx& acc, double e, cplx h) {
   acc.re = fma(e, h.re, acc.re);
@@ -440,21 +453,13 @@ k_apply_fused(ApplyArgs a) {
   T* sG = sL + ((kD || kG) ? (p + 1) * kApplyThreads : 0);        // J_{l-1} - J_{l+1}, p + 1 rows
 
   const int tid = threadIdx.x;
-  // work item (centre block, source split).  With the grids' node counts
-  // given (near_q_tgt > 0), rank r = blockIdx.x / nblk takes for every block
-  // the split at offset 0, +1, -1, +2, ... (mod nsplit) from its home split,
-  // the one holding the sources of the block's own panels: the near-field
-  // items, whose pairs take the slower small-argument Hankel branch, are
-  // dispatched first and the last wave holds uniform far-field items.
+  // work item (centre block, source split): rank r = blockIdx.x / nblk;
+  // near-field splits first when the grids' node counts are given
   const int nblk = (a.n_ctr + kApplyThreads - 1) / kApplyThreads;
   const int cblk = (int)(blockIdx.x % (unsigned)nblk), rank = (int)(blockIdx.x / (unsigned)nblk);
-  int split = rank;
-  if (a.near_q_tgt > 0) {
-    const int tmid = (cblk * kApplyThreads + kApplyThreads / 2) % a.n_tgt;
-    const int home = min(a.nsplit - 1, (tmid / a.near_q_tgt) * a.near_q_src / a.src_per_split);
-    const int off = (rank & 1) ? (rank + 1) / 2 : -(rank / 2);
-    split = ((home + off) % a.nsplit + a.nsplit) % a.nsplit;
-  }
+  const int split = a.near_q_tgt > 0 ? near_first_split(rank, (cblk * kApplyThreads + kApplyThreads / 2) % a.n_tgt,
+                                                        a.near_q_tgt, a.near_q_src, a.src_per_split, a.nsplit)
+                                     : rank;
   const int c = cblk * kApplyThreads + tid;
   const bool active = c < a.n_ctr;
   const int cc = active ? c : a.n_ctr - 1;

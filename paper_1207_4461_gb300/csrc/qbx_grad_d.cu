@@ -60,13 +60,9 @@ __global__ void __launch_bounds__(kGdThreads) k_grad_d_fused(ApplyArgs a) {
   // work item (centre block, source split), near-field splits first
   const int nblk = (a.n_ctr + kGdThreads - 1) / kGdThreads;
   const int cblk = (int)(blockIdx.x % (unsigned)nblk), rank = (int)(blockIdx.x / (unsigned)nblk);
-  int split = rank;
-  if (a.near_q_tgt > 0) {
-    const int tmid = (cblk * kGdThreads + kGdThreads / 2) % a.n_tgt;
-    const int home = min(a.nsplit - 1, (tmid / a.near_q_tgt) * a.near_q_src / a.src_per_split);
-    const int off = (rank & 1) ? (rank + 1) / 2 : -(rank / 2);
-    split = ((home + off) % a.nsplit + a.nsplit) % a.nsplit;
-  }
+  const int split = a.near_q_tgt > 0 ? near_first_split(rank, (cblk * kGdThreads + kGdThreads / 2) % a.n_tgt,
+                                                        a.near_q_tgt, a.near_q_src, a.src_per_split, a.nsplit)
+                                     : rank;
   const int c = cblk * kGdThreads + tid;
   const bool active = c < a.n_ctr;
   const int cc = active ? c : a.n_ctr - 1;

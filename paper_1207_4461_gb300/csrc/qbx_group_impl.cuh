@@ -91,17 +91,14 @@ k_apply_group(GroupArgs a) {
     if (dynamic) {
       item = a.items[it];
     } else {
-      // rank r of the launch takes, for every 32-centre unit, the split at
-      // offset 0, +1, -1, +2, ... from the unit's home split (the one holding
-      // its own panels' sources): near-field items first, as the fused apply
+      // rank r of the launch takes the 32-centre units' splits near-field
+      // first, as the fused apply
       item.inst = 0;
       const int unit = it % a.st_units, rank = it / a.st_units;
       const int q_t = a.inst0.n_tgt / a.inst0.M, q_s = a.inst0.n_src / a.inst0.M;
-      const int tmid = (unit * kGrpCentres + kGrpCentres / 2) % a.inst0.n_tgt;
-      const int home = min(a.st_nsplit - 1, (tmid / q_t) * q_s / a.st_split_len);
-      const int off = (rank & 1) ? (rank + 1) / 2 : -(rank / 2);
       item.ctr0 = unit * kGrpCentres;
-      item.split = ((home + off) % a.st_nsplit + a.st_nsplit) % a.st_nsplit;
+      item.split = near_first_split(rank, (unit * kGrpCentres + kGrpCentres / 2) % a.inst0.n_tgt, q_t, q_s,
+                                    a.st_split_len, a.st_nsplit);
       item.src0 = item.split * a.st_split_len;
       item.src1 = min(a.inst0.n_src, item.src0 + a.st_split_len);
     }
