@@ -69,15 +69,15 @@ def flops_per_pair_ops(ops, p, nrhs=1):
 # on the full-size starfish workload, from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum); valid only for the kernel
 # sources it was taken with, identified by their hash.
-TRAFFIC = {"f7b3875ba227d9ed": 1.60e6}   # profiles/k_apply_fused_S_D_gradS_starfish_M256_dram.md
+TRAFFIC = {"b9f91757dba0af26": 1.70e6}   # profiles/k_apply_fused_S_D_gradS_starfish_M256_dram.md
 KERNEL_SOURCES = ["qbx_apply_impl.cuh", "qbx_device.cuh", "special_tables.h", "qbx_apply_real.cu"]
 GROUP_SOURCES = ["qbx_group_impl.cuh", "qbx_apply_impl.cuh", "qbx_device.cuh", "special_tables.h"]
 # Hardware-counted FP64 operations per (centre, source) pair, 2 DFMA + DMUL +
 # DADD from ncu's smsp__sass_thread_inst_executed_op_{dfma,dmul,dadd}_pred_on
 # counters divided by the pairs of the captured launch, for the kernel
 # sources with the given hash (profiles/*_fp64_counts.md).
-HW_FP64_PER_PAIR = {"f7b3875ba227d9ed": 551.5}         # fused S + D + grad S, p = 12, one rhs
-HW_FP64_PER_PAIR_GROUP = {"b989ec74a7ddd62e": 763.4}   # group kernel, S + D, p = 10, 32 rhs
+HW_FP64_PER_PAIR = {"b9f91757dba0af26": 543.7}         # fused S + D + grad S, p = 12, one rhs
+HW_FP64_PER_PAIR_GROUP = {"61c06a417da0aabe": 756.0}   # group kernel, S + D, p = 10, 32 rhs
 
 
 def source_hash(names=KERNEL_SOURCES):

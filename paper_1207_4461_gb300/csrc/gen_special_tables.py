@@ -32,7 +32,7 @@ import numpy as np
 mp.mp.dps = 40
 
 Z_SPLIT = 2.0          # series below, amplitude fits above
-NI_PER_UNIT = 128      # intervals per unit of s (a power of two)
+NI_PER_UNIT = 256      # intervals per unit of s (a power of two)
 NI = int(mp.ceil(NI_PER_UNIT / mp.sqrt(Z_SPLIT)))   # intervals covering s in [0, Z_SPLIT^-1/2]
 MAX_ERR = 3.5e-16      # absolute; |B_n| <= 0.6 on the range
 NT = 512               # phase table size (8 KB: with the amplitude table it stays in L1)

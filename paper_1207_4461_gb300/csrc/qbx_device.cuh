@@ -7,7 +7,7 @@
 //   z <  2 : ascending series in (z/2)^2 (DLMF 10.2.2, 10.8.1) with log(z/2)
 //   z >= 2 : H_n = e^{i(z - pi/4)} B_n(s), s = z^{-1/2}, where
 //            B_n = sqrt(2/pi) s e^{-i n pi/2} (P_n + i Q_n) (DLMF 10.17.3) is a
-//            degree-5 polynomial on each of 91 intervals of s, and
+//            degree-4 polynomial on each of 182 intervals of s, and
 //            e^{i(z - pi/4)} comes from a 512-entry table + Taylor after
 //            Cody-Waite reduction.
 // Complex argument (Im z > 0): series for |z| <= 6, Miller's backward
