@@ -69,15 +69,15 @@ def flops_per_pair_ops(ops, p, nrhs=1):
 # on the full-size starfish workload, from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum); valid only for the kernel
 # sources it was taken with, identified by their hash.
-TRAFFIC = {"b9f91757dba0af26": 1.70e6}   # profiles/k_apply_fused_S_D_gradS_starfish_M256_dram.md
+TRAFFIC = {"f7a1a26ef612288b": 1.66e6}   # profiles/k_apply_fused_S_D_gradS_starfish_M256_dram.md
 KERNEL_SOURCES = ["qbx_apply_impl.cuh", "qbx_device.cuh", "special_tables.h", "qbx_apply_real.cu"]
 GROUP_SOURCES = ["qbx_group_impl.cuh", "qbx_apply_impl.cuh", "qbx_device.cuh", "special_tables.h"]
 # Hardware-counted FP64 operations per (centre, source) pair, 2 DFMA + DMUL +
 # DADD from ncu's smsp__sass_thread_inst_executed_op_{dfma,dmul,dadd}_pred_on
 # counters divided by the pairs of the captured launch, for the kernel
 # sources with the given hash (profiles/*_fp64_counts.md).
-HW_FP64_PER_PAIR = {"b9f91757dba0af26": 543.7}         # fused S + D + grad S, p = 12, one rhs
-HW_FP64_PER_PAIR_GROUP = {"61c06a417da0aabe": 756.0}   # group kernel, S + D, p = 10, 32 rhs
+HW_FP64_PER_PAIR = {"f7a1a26ef612288b": 543.7}         # fused S + D + grad S, p = 12, one rhs
+HW_FP64_PER_PAIR_GROUP = {"c0efa2290bd63732": 756.0}   # group kernel, S + D, p = 10, 32 rhs
 
 
 def source_hash(names=KERNEL_SOURCES):
@@ -109,7 +109,7 @@ def hw_roofline(ops_per_pair, pairs, seconds):
 
 
 def kernel_traffic(wl, args):
-    if args.separate or args.panels or args.ops:
+    if args.separate or args.panels or args.ops or args.k:
         return None
     return TRAFFIC.get(kernel_source_hash())
 
@@ -237,7 +237,8 @@ def config_dict(wl, args):
     return {"workload": f"starfish r=1+0.25cos5t, M={wl.M} panels x {wl.q_tgt} targets "
                         f"({wl.n_tgt}), {wl.n_src} sources (4x), k={wl.k:g}, p={wl.p}, "
                         f"two-sided centres ({wl.n_ctr}), ops S+D+gradS, CN(0,1) density seed {wl.seed}",
-            "n_tgt": wl.n_tgt, "n_src": wl.n_src, "n_ctr": wl.n_ctr, "k": wl.k, "p": wl.p,
+            "n_tgt": wl.n_tgt, "n_src": wl.n_src, "n_ctr": wl.n_ctr,
+            "k": wl.k if isinstance(wl.k, float) else str(wl.k), "p": wl.p,
             "nrhs": wl.nrhs, "terms_per_step": len(wl.ops) * wl.terms_per_op(),
             "l2": "flushed between timed steps (256 MiB write outside the event pair)",
             "parallelism": "replicas" if args.gpus > 1 else "single",
@@ -330,7 +331,7 @@ def run_gpu(args, wl):
                 "timing": "CUDA events recorded by the library around the kernel launch(es) of every "
                           "timed call, on the launching stream",
                 "flops_per_pair": fpp, "peak_basis": "152 SMs x 4 FP64 flop/clk x 2.07 GHz"}
-    if not (args.separate or args.panels or args.ops):
+    if not (args.separate or args.panels or args.ops or args.k):
         roofline["hw"] = hw_roofline(HW_FP64_PER_PAIR.get(kernel_source_hash()), pairs, kern_ms * 1e-3)
 
     # ---- end to end through the public API with host buffers (pinned)
@@ -707,9 +708,9 @@ def run_variants(args):
     grad D (storage-free), S + D + grad S on centres at r = c sqrt(h)
     (c = 0.08, about the h/2 radius at this panel size), and near-only
     S + D + grad S (eta = 8), beside the global S + D + grad S step; then
-    S, D and grad S through stored coefficients (form, then evaluate), and
-    S + D + grad S for 32 right-hand sides (the group kernel), global and
-    near-only.  CUDA events per call, L2 flushed
+    S, D and grad S through stored coefficients (form, then evaluate),
+    S + D + grad S at the complex wavenumber 20 + 1i, and S + D + grad S for
+    32 right-hand sides (the group kernel), global and near-only.  CUDA events per call, L2 flushed
     before every timed call.  Prints one JSON line (not the benchmark
     metric)."""
     import torch
@@ -766,6 +767,9 @@ def run_variants(args):
         qbx.qbx_eval_locals(plan, g, qbx.SIDE_TWO, wl.k, wl.p, a_d, qbx.VALUE)
         qbx.qbx_eval_locals(plan, g, qbx.SIDE_TWO, wl.k, wl.p, a_s, qbx.GRAD)
     t["S, D, grad S via stored coefficients (form + eval)"] = timed(stored)
+    # complex wavenumber (absorbing medium): the amplitude table of the ray z = k rho
+    kc = complex(wl.k, 1.0)
+    t["S+D+grad S, k = 20 + 1i"] = timed(lambda: qbx.qbx_apply_ops(plan, g, ops3, qbx.SIDE_TWO, 0, kc, wl.p, dens))
     # 32 rhs of one density: the group kernel, global and near-only
     plan32 = qbx.Plan(wl.q_tgt, wl.q_src, n_src=wl.n_src, n_ctr=wl.n_ctr, ncoef=4, nrhs=32)
     g32 = qbx.qbx_geometry(plan32, wl.curve, wl.curve.edges(wl.M))
@@ -780,7 +784,7 @@ def run_variants(args):
     per_op_terms = pairs * (2 * wl.p + 1)
     nops = {"S+D+grad S": 3, "R": 1, "grad D (PV)": 1, "S+D+grad S, r = 0.08 sqrt(h)": 3,
             "S+D+grad S, near-only eta = 8": 3, "S+D+grad S, 32 rhs": 3 * 32,
-            "S, D, grad S via stored coefficients (form + eval)": 3,
+            "S, D, grad S via stored coefficients (form + eval)": 3, "S+D+grad S, k = 20 + 1i": 3,
             "S+D+grad S, 32 rhs, near-only eta = 8": 3 * 32}
     print(json.dumps({
         "variants": f"starfish r=1+0.25cos5t, {wl.M} panels ({wl.n_tgt} targets, {wl.n_src} sources, "
@@ -809,6 +813,7 @@ def main():
     ap.add_argument("--panels", type=int, default=None,
                     help="profiling only: override the panel count (smaller case for ncu)")
     ap.add_argument("--ops", default=None, help="profiling only: comma list of S,D,GRAD_S")
+    ap.add_argument("--k", default=None, help="profiling only: override the wavenumber (complex: e.g. 20+1j)")
     ap.add_argument("--min-waves", type=int, default=None,
                     help="profiling only: qbx_plan_set_min_waves for the main step")
     ap.add_argument("--batch-curves", type=int, default=None,
@@ -847,6 +852,8 @@ def main():
         wl.M = args.panels
     if args.ops:
         wl.ops = tuple(args.ops.split(","))
+    if args.k:
+        wl.k = complex(args.k) if "j" in args.k else float(args.k)
     if args.impl == "reference":
         return run_reference(args, wl)
     return run_gpu(args, wl)

@@ -442,6 +442,12 @@ int qbx_apply_static(const qbx_geom *g, int op, int side, int limit, qbx_c64 k, 
  * Im z == 0), and J_0..J_nmax (Miller) at z[n].  For tests. */
 int qbx_debug_hankel01(const qbx_c64 *z, int n, qbx_c64 *h0, qbx_c64 *h1, void *stream);
 int qbx_debug_besselj(const qbx_c64 *z, int n, int nmax, qbx_c64 *j, void *stream);
+/* H0, H1 at z = k rho[i] (rho > 0, n values) as the pair kernels evaluate
+ * them for this k: for Im k > 0 through the plan's amplitude table of the ray
+ * z = k rho (fitted once per k) where |z| >= 2, the direct evaluation
+ * otherwise; for real k the direct complex-argument evaluation.  For tests. */
+int qbx_debug_hankel01_ray(qbx_plan *plan, qbx_c64 k, const double *rho, int n, qbx_c64 *h0, qbx_c64 *h1,
+                           void *stream);
 
 #ifdef __cplusplus
 }

@@ -87,7 +87,7 @@ __device__ __forceinline__ cplx sadd(cplx a, cplx b) { return a + b; }
 template <typename T> struct KW;
 template <> struct KW<double> {
   double k, ik, ksq;  // k, 1/k, k^{-1/2}
-  __device__ __forceinline__ void init(double kre, double) {
+  __device__ __forceinline__ void init(double kre, double, const double* = nullptr) {
     k = kre;
     ik = 1.0 / kre;
     ksq = rsqrt(kre);
@@ -110,25 +110,59 @@ template <> struct KW<double> {
     hankel01_real<true>(z, invz, y * ksq, h0, h1, w);
   }
 };
+// Complex k.  With a ray table (tab: the amplitudes B_n along z = k rho, made
+// for this k by launch_hk_table), |z| >= 2 takes the fitted amplitudes times
+// e^{i(Re k rho - pi/4)} e^{-Im k rho}; |z| < 2, or no table, the series /
+// Miller / asymptotic evaluation of hankel01_cplx.
 template <> struct KW<cplx> {
-  cplx k;
-  __device__ __forceinline__ void init(double kre, double kim) { k = cplx{kre, kim}; }
+  cplx k, c2;                 // k, 2 conj(k) / |k|^2 (2/z = c2 / rho)
+  double kisq;                // |k|^{-1/2}
+  const double* tab;
+  __device__ __forceinline__ void init(double kre, double kim, const double* t = nullptr) {
+    k = cplx{kre, kim};
+    const double a2 = kre * kre + kim * kim;
+    c2 = cplx{2.0 * kre / a2, -2.0 * kim / a2};
+    kisq = rsqrt(sqrt(a2));
+    tab = t;
+  }
   __device__ __forceinline__ cplx kval() const { return k; }
   __device__ __forceinline__ void geom(double rho2, double& inv, double& rho, double& y) const {
-    inv = rsqrt(rho2);
-    rho = rho2 * inv;
-    y = 0.0;
+    if (tab) {
+      rho_powers(rho2, y, inv, rho);
+    } else {
+      inv = rsqrt(rho2);
+      rho = rho2 * inv;
+      y = 0.0;
+    }
   }
-  __device__ __forceinline__ void hankel(double rho, double, double, cplx& h0, cplx& h1, cplx& twoz) const {
+  template <bool SCALED>
+  __device__ __forceinline__ void hk(double rho, double inv, double y, cplx w, cplx& h0, cplx& h1,
+                                     cplx& twoz) const {
+    const double s = y * kisq;   // |z|^{-1/2}
+    if (tab && s <= QBX_HK_S_MAX) {
+      cplx B0, B1;
+      hk_amp_eval(tab, s, B0, B1);
+      cplx e = exp(-k.im * rho) * expi_shift(k.re * rho);
+      if constexpr (SCALED) e = w * e;
+      h0 = e * B0;
+      h1 = e * B1;
+      twoz = c2 * inv;
+      return;
+    }
     const cplx z = cplx{k.re * rho, k.im * rho};
     twoz = 2.0 * cinv(z);
     hankel01_cplx(z, h0, h1);
+    if constexpr (SCALED) {
+      h0 = w * h0;
+      h1 = w * h1;
+    }
+  }
+  __device__ __forceinline__ void hankel(double rho, double inv, double y, cplx& h0, cplx& h1, cplx& twoz) const {
+    hk<false>(rho, inv, y, cplx{1.0, 0.0}, h0, h1, twoz);
   }
   __device__ __forceinline__ void hankel_w(double rho, double inv, double y, cplx w, cplx& h0, cplx& h1,
                                            cplx& twoz) const {
-    hankel(rho, inv, y, h0, h1, twoz);
-    h0 = w * h0;
-    h1 = w * h1;
+    hk<true>(rho, inv, y, w, h0, h1, twoz);
   }
 };
 
@@ -475,7 +509,7 @@ k_apply_fused(ApplyArgs a) {
   // near-only QBX: sources at |x_s - c| >= eta r take the smooth rule
   const double lim2 = (!LOCAL || kX || !(a.eta2 > 0.0)) ? INFINITY : a.eta2 * r * r;
   KW<T> kw;
-  kw.init(a.kre, a.kim);
+  kw.init(a.kre, a.kim, a.hk_tab);
   const T kk = kw.kval();
   T* colJ = sJ + tid;
   T* colL = sL + tid;

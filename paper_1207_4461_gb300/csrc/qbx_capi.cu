@@ -33,6 +33,10 @@ struct qbx_plan {
   int min_waves = 1;
   // cuBLAS handle of the assembled-matrix solve, created on first use
   cublasHandle_t blas = nullptr;
+  // H0/H1 amplitude table of the ray z = k rho for the last complex k
+  // (tab_kim = 0: none made yet)
+  double* d_hk_tab;
+  double tab_kre, tab_kim;
 };
 
 namespace {
@@ -229,6 +233,20 @@ void* host_plan_blas(qbx_plan* plan) {
   return plan->blas;
 }
 
+// The plan's amplitude table for complex k (made on `st` when k changes;
+// later calls on the plan's streams see it in stream order), or null for real k.
+const double* host_plan_hk_table(qbx_plan* plan, qbx_c64 k, cudaStream_t st, cudaError_t* err) {
+  *err = cudaSuccess;
+  if (k.im == 0.0) return nullptr;
+  if (plan->tab_kre != k.re || plan->tab_kim != k.im) {
+    *err = launch_hk_table(k.re, k.im, plan->d_hk_tab, st);
+    if (*err != cudaSuccess) return nullptr;
+    plan->tab_kre = k.re;
+    plan->tab_kim = k.im;
+  }
+  return plan->d_hk_tab;
+}
+
 size_t host_align256(size_t b) { return align256(b); }
 
 // Number of source splits: fill about two waves of 4 CTAs per SM, bounded by
@@ -323,6 +341,7 @@ int qbx_plan_create(qbx_plan** plan, int device, int q_tgt, int q_src, size_t wo
   if (e == cudaSuccess) e = cudaMalloc(&p->d_wgl_src, q_src * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&p->d_status, sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&p->d_diff, Dx.size() * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&p->d_hk_tab, (size_t)hk_table_doubles() * sizeof(double));
   if (e == cudaSuccess && workspace_bytes > 0) e = cudaMalloc(&p->ws, workspace_bytes);
   if (e == cudaSuccess) e = cudaMemcpy(p->d_diff, Dx.data(), Dx.size() * sizeof(double), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(p->d_interp, Mx.data(), Mx.size() * sizeof(double), cudaMemcpyHostToDevice);
@@ -349,6 +368,7 @@ int qbx_plan_destroy(qbx_plan* p) {
   cudaFree(p->d_wgl_src);
   cudaFree(p->d_status);
   cudaFree(p->d_diff);
+  cudaFree(p->d_hk_tab);
   cudaFree(p->ws);
   delete p;
   return QBX_OK;
@@ -690,6 +710,11 @@ static int apply_impl(qbx_plan* p, const qbx_geom* g, int ops, int side, int lim
   a.near_q_tgt = g->q_tgt;   // near-field items first
   a.near_q_src = g->q_src;
   a.one_w = one_w ? 1 : 0;
+  {
+    cudaError_t te;
+    a.hk_tab = host_plan_hk_table(p, k, st, &te);
+    CK(te, "complex-k amplitude table");
+  }
   if (group) {
     GroupArgs ga{};
     ga.ops = ops;
@@ -808,6 +833,11 @@ static int grad_d_impl(qbx_plan* p, const qbx_geom* g, int side, int limit, qbx_
     a.part = part;
     a.near_q_tgt = g->q_tgt;
     a.near_q_src = g->q_src;
+    {
+      cudaError_t te;
+      a.hk_tab = host_plan_hk_table(p, k, st, &te);
+      CK(te, "complex-k amplitude table");
+    }
     for (int r = 0; r < nrhs; ++r) {
       a.rhs0 = r;
       CK(launch_grad_d_fused(a, st), "grad D kernel");
@@ -936,6 +966,22 @@ int qbx_debug_hankel01(const qbx_c64* z, int n, qbx_c64* h0, qbx_c64* h1, void* 
   if (n == 0) return QBX_OK;
   if (!z || !h0 || !h1) return fail(QBX_EINVAL, "NULL array");
   CK(launch_debug_hankel(z, n, h0, h1, (cudaStream_t)stream), "debug hankel");
+  return QBX_OK;
+}
+
+int qbx_debug_hankel01_ray(qbx_plan* p, qbx_c64 k, const double* rho, int n, qbx_c64* h0, qbx_c64* h1,
+                           void* stream) {
+  if (int rc = check_plan(p)) return rc;
+  if (int rc = check_k(k)) return rc;
+  if (n < 0) return fail(QBX_EINVAL, "n < 0");
+  if (n == 0) return QBX_OK;
+  if (!rho || !h0 || !h1) return fail(QBX_EINVAL, "NULL array");
+  CK(cudaSetDevice(p->device), "cudaSetDevice");
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t te;
+  const double* tab = host_plan_hk_table(p, k, st, &te);
+  CK(te, "complex-k amplitude table");
+  CK(launch_debug_hankel_ray(k.re, k.im, tab, rho, n, h0, h1, st), "debug hankel (ray)");
   return QBX_OK;
 }
 

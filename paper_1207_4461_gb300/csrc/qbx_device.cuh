@@ -119,6 +119,33 @@ __device__ __forceinline__ void rho_powers(double rho2, double& y, double& inv, 
   rho = rho2 * inv;
 }
 
+// The modulated amplitudes B_n(s) = H_n(z) e^{-i(z - pi/4)}, n = 0, 1, at
+// s = |z|^{-1/2} <= QBX_HK_S_MAX from a table laid out as qbx_hk_amp
+// ([interval][degree][Re B0, Im B0, Re B1, Im B1], intervals of width
+// 2^-QBX_HK_LOG2_PER_UNIT in s, polynomials in u = s - mid): the real-axis
+// fits, or a table made for one complex k (z = k rho on its ray).
+__device__ __forceinline__ void hk_amp_eval(const double* __restrict__ tab, double s, cplx& B0, cplx& B1) {
+  const double y = s + 1.0;
+  int i = (int)((__double2hiint(y) >> (20 - QBX_HK_LOG2_PER_UNIT)) & ((1 << QBX_HK_LOG2_PER_UNIT) - 1));
+  i = i < QBX_HK_NI ? i : QBX_HK_NI - 1;   // floor(s * 2^LOG2_PER_UNIT)
+  const double u = y - __ldg(&qbx_hk_mid1[i]);
+  // two 16-byte loads per degree
+  const double2* A = reinterpret_cast<const double2*>(tab + (size_t)i * (QBX_HK_DEG + 1) * 4);
+  double2 c0 = __ldg(&A[2 * QBX_HK_DEG]), c1 = __ldg(&A[2 * QBX_HK_DEG + 1]);
+  double b0r = c0.x, b0i = c0.y, b1r = c1.x, b1i = c1.y;
+#pragma unroll
+  for (int d = QBX_HK_DEG - 1; d >= 0; --d) {
+    c0 = __ldg(&A[2 * d]);
+    c1 = __ldg(&A[2 * d + 1]);
+    b0r = fma(b0r, u, c0.x);
+    b0i = fma(b0i, u, c0.y);
+    b1r = fma(b1r, u, c1.x);
+    b1i = fma(b1i, u, c1.y);
+  }
+  B0 = cplx{b0r, b0i};
+  B1 = cplx{b1r, b1i};
+}
+
 // H0(z), H1(z) for real z > 0, given invz = 1/z and s = z^{-1/2}; with
 // SCALED, w H0(z) and w H1(z) (w folded into the phase factor).
 template <bool SCALED = false>
@@ -126,27 +153,12 @@ __device__ __forceinline__ void hankel01_real(double z, double invz, double s, c
                                               cplx w = cplx{1.0, 0.0}) {
   if (z >= QBX_HK_ZSPLIT) {
     // B_n(s) = H_n(z) e^{-i(z - pi/4)}: piecewise polynomials in s
-    const double y = s + 1.0;
-    int i = (int)((__double2hiint(y) >> (20 - QBX_HK_LOG2_PER_UNIT)) & ((1 << QBX_HK_LOG2_PER_UNIT) - 1));
-    i = i < QBX_HK_NI ? i : QBX_HK_NI - 1;   // floor(s * 2^LOG2_PER_UNIT)
-    const double u = y - __ldg(&qbx_hk_mid1[i]);
-    // [degree][Re B0, Im B0, Re B1, Im B1]: two 16-byte loads per degree
-    const double2* A = reinterpret_cast<const double2*>(&qbx_hk_amp[i][0][0]);
-    double2 c0 = __ldg(&A[2 * QBX_HK_DEG]), c1 = __ldg(&A[2 * QBX_HK_DEG + 1]);
-    double b0r = c0.x, b0i = c0.y, b1r = c1.x, b1i = c1.y;
-#pragma unroll
-    for (int d = QBX_HK_DEG - 1; d >= 0; --d) {
-      c0 = __ldg(&A[2 * d]);
-      c1 = __ldg(&A[2 * d + 1]);
-      b0r = fma(b0r, u, c0.x);
-      b0i = fma(b0i, u, c0.y);
-      b1r = fma(b1r, u, c1.x);
-      b1i = fma(b1i, u, c1.y);
-    }
+    cplx B0, B1;
+    hk_amp_eval(&qbx_hk_amp[0][0][0], s, B0, B1);
     cplx e = expi_shift(z);
     if constexpr (SCALED) e = w * e;
-    h0 = e * cplx{b0r, b0i};
-    h1 = e * cplx{b1r, b1i};
+    h0 = e * B0;
+    h1 = e * B1;
   } else {
     double t = 0.25 * z * z;
     double sj0 = qbx_hk_ser[0][QBX_HK_NSER - 1], sj1 = qbx_hk_ser[1][QBX_HK_NSER - 1];
@@ -264,8 +276,11 @@ __host__ __device__ inline void jy01_miller_c(cplx z, cplx& j0, cplx& j1, cplx& 
        1.27323954473516268615 * sY1;
 }
 
-// DLMF 10.17.5 with the series truncated at its smallest term (|z| > 20).
-__host__ __device__ inline cplx hankel_asym_c(cplx z, int nu) {
+// DLMF 10.17.5 with the series truncated at its smallest term (|z| > 20):
+// the modulated amplitude H_nu(z) e^{-i(z - pi/4)} = (2/(pi z))^{1/2}
+// e^{-i nu pi/2} sum_k i^k a_k(nu) / z^k (no exponential: finite for any
+// Im z >= 0), and H_nu itself.
+__host__ __device__ inline cplx hankel_amp_asym_c(cplx z, int nu) {
   double mu = 4.0 * nu * nu;
   cplx iz = cinv(z);
   cplx sum{1.0, 0.0}, term{1.0, 0.0};
@@ -280,9 +295,13 @@ __host__ __device__ inline cplx hankel_asym_c(cplx z, int nu) {
     prev = mag;
     if (mag < 1e-18) break;
   }
-  cplx w = z - cplx{nu * 1.57079632679489661923 + 0.78539816339744830962, 0.0};
   cplx pre = csqrt_(0.63661977236758134308 * iz);
-  return pre * cexp_(mul_i(w)) * sum;
+  if (nu & 1) pre = cplx{pre.im, -pre.re};   // e^{-i pi/2}
+  return pre * sum;
+}
+
+__host__ __device__ inline cplx hankel_asym_c(cplx z, int nu) {
+  return hankel_amp_asym_c(z, nu) * cexp_(mul_i(z - cplx{0.78539816339744830962, 0.0}));
 }
 
 __host__ __device__ inline void hankel01_cplx(cplx z, cplx& h0, cplx& h1) {

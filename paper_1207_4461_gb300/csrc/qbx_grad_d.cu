@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(kGdThreads) k_grad_d_fused(ApplyArgs a) {
   ux /= r;
   uy /= r;
   KW<T> kw;
-  kw.init(a.kre, a.kim);
+  kw.init(a.kre, a.kim, a.hk_tab);
   const T kk = kw.kval();
   T* colJ = sJ + tid;
   T* colC = sC + tid;

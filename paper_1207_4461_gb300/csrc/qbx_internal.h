@@ -39,7 +39,15 @@ struct ApplyArgs {
   int near_q_tgt, near_q_src;   // > 0: near-field items first (node counts per panel); 0: plain order
   int one_w;              // 1: wd[] of every requested operator is one array and nr = 1 (weighted
                           // seeds: the density multiplies H0, H1); 0: per-pair kernel values
+  const double* hk_tab;   // complex k: the amplitude table of this k's ray (launch_hk_table), or null
 };
+// Amplitudes B_n = H_n(z) e^{-i(z - pi/4)}, n = 0, 1, along the ray z = k rho
+// (|z| >= 2) as piecewise polynomials in s = |z|^{-1/2}, in the layout of the
+// real-axis table (hk_table_doubles() doubles), for Im k > 0.
+int hk_table_doubles();
+cudaError_t launch_hk_table(double kre, double kim, double* tab, cudaStream_t st);
+cudaError_t launch_debug_hankel_ray(double kre, double kim, const double* tab, const double* rho, int n, void* h0,
+                                    void* h1, cudaStream_t st);
 cudaError_t launch_apply_fused(const ApplyArgs& a, cudaStream_t st);
 cudaError_t launch_apply_fused_real(const ApplyArgs& a, cudaStream_t st);
 cudaError_t launch_apply_fused_cplx(const ApplyArgs& a, cudaStream_t st);

@@ -131,6 +131,8 @@ def lib():
             L.qbx_vec_combine.restype = I
             L.qbx_debug_hankel01.argtypes = [_P, I, _P, _P, _P]
             L.qbx_debug_besselj.argtypes = [_P, I, I, _P, _P]
+            L.qbx_debug_hankel01_ray.argtypes = [_P, c64, _P, I, _P, _P, _P]
+            L.qbx_debug_hankel01_ray.restype = I
             for name in ("qbx_gauss_legendre", "qbx_plan_create", "qbx_plan_destroy", "qbx_sync_status",
                          "qbx_geometry", "qbx_upsample", "qbx_form_locals", "qbx_eval_locals", "qbx_apply",
                          "qbx_far", "qbx_assign_centres", "qbx_debug_hankel01", "qbx_debug_besselj"):
@@ -642,6 +644,16 @@ def qbx_debug_hankel01(z):
     h0 = torch.empty_like(z)
     h1 = torch.empty_like(z)
     _check(lib().qbx_debug_hankel01(_ptr(z), z.numel(), _ptr(h0), _ptr(h1), _stream()))
+    return h0, h1
+
+
+def qbx_debug_hankel01_ray(plan: Plan, k, rho):
+    """(H0, H1) at z = k rho as the pair kernels evaluate them for this k
+    (complex k: the plan's amplitude table of the ray where |z| >= 2)."""
+    rho = rho.contiguous()
+    h0 = torch.empty(rho.shape, dtype=torch.complex128, device=rho.device)
+    h1 = torch.empty_like(h0)
+    _check(lib().qbx_debug_hankel01_ray(plan.handle, _k(k), _ptr(rho), rho.numel(), _ptr(h0), _ptr(h1), _stream()))
     return h0, h1
 
 

@@ -64,6 +64,33 @@ def test_device_hankel_complex(cuda):
     assert np.all(np.abs(h1.cpu().numpy() - r1) <= tol * np.abs(r1))
 
 
+@pytest.mark.parametrize("k", [20 + 1j, 5 + 0.5j, 8 + 2j, 40 + 0.05j, 3 + 0.1j])
+def test_device_hankel_complex_ray(cuda, k):
+    """Complex k: H0, H1 at z = k rho through the amplitude table fitted for
+    this k's ray (|z| >= 2; the series below), rho from 1e-3 to 3, against
+    scipy.  The table's node values have the accuracy of the direct
+    complex evaluation (which loses ~e^{2 Im z} to cancellation for
+    |z| <= 20); above |z| = 20 they come from the asymptotic amplitude."""
+    plan = qbx.Plan(16, 64, workspace_bytes=1 << 12)
+    rho = np.concatenate([np.logspace(-3, np.log10(3.0), 3000), 2.0 / abs(k) * np.array([0.999, 1.0, 1.001])])
+    h0, h1 = qbx.qbx_debug_hankel01_ray(plan, k, dev(rho))
+    z = k * rho
+    r0, r1 = sp.hankel1(0, z), sp.hankel1(1, z)
+    imz = np.minimum(z.imag, 20.0 * np.sin(np.angle(k)))
+    tol = 6e-14 * np.exp(2 * imz) * np.maximum(1.0, np.abs(z) / 8)
+    e0 = np.abs(h0.cpu().numpy() - r0) / np.abs(r0)
+    e1 = np.abs(h1.cpu().numpy() - r1) / np.abs(r1)
+    assert np.all(e0 <= tol), (e0 / tol).max()
+    assert np.all(e1 <= tol), (e1 / tol).max()
+    # a second k on the same plan remakes the table
+    k2 = k.real + 2j * k.imag
+    g0, _ = qbx.qbx_debug_hankel01_ray(plan, k2, dev(rho))
+    r2 = sp.hankel1(0, k2 * rho)
+    imz2 = np.minimum((k2 * rho).imag, 20.0 * np.sin(np.angle(k2)))
+    assert np.all(np.abs(g0.cpu().numpy() - r2) / np.abs(r2)
+                  <= 6e-14 * np.exp(2 * imz2) * np.maximum(1.0, np.abs(k2 * rho) / 8))
+
+
 def test_device_besselj(cuda):
     z = np.concatenate([np.linspace(1e-4, 12, 500), np.linspace(0.05, 6, 60) + 0.4j])
     nmax = 20
