@@ -777,6 +777,8 @@ def run_variants(args):
     t["S+D+grad S, 32 rhs"] = timed(lambda: qbx.qbx_apply_ops(plan32, g32, ops3, qbx.SIDE_TWO, 0, wl.k, wl.p, d32))
     t["S+D+grad S, 32 rhs, near-only eta = 8"] = timed(
         lambda: qbx.qbx_apply_ops(plan32, g32, ops3, qbx.SIDE_TWO, 0, wl.k, wl.p, d32, eta=8.0))
+    t["S+D+grad S, 32 rhs, k = 20 + 1i"] = timed(
+        lambda: qbx.qbx_apply_ops(plan32, g32, ops3, qbx.SIDE_TWO, 0, kc, wl.p, d32))
     qbx.qbx_sync_status(plan32)
     clk = clocks.stop()
     qbx.qbx_sync_status(plan)
@@ -785,7 +787,7 @@ def run_variants(args):
     nops = {"S+D+grad S": 3, "R": 1, "grad D (PV)": 1, "S+D+grad S, r = 0.08 sqrt(h)": 3,
             "S+D+grad S, near-only eta = 8": 3, "S+D+grad S, 32 rhs": 3 * 32,
             "S, D, grad S via stored coefficients (form + eval)": 3, "S+D+grad S, k = 20 + 1i": 3,
-            "S+D+grad S, 32 rhs, near-only eta = 8": 3 * 32}
+            "S+D+grad S, 32 rhs, near-only eta = 8": 3 * 32, "S+D+grad S, 32 rhs, k = 20 + 1i": 3 * 32}
     print(json.dumps({
         "variants": f"starfish r=1+0.25cos5t, {wl.M} panels ({wl.n_tgt} targets, {wl.n_src} sources, "
                     f"{wl.n_ctr} centres), k=20, p=12, one CN(0,1) density (seed 2)",

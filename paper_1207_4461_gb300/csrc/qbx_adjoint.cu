@@ -144,6 +144,8 @@ extern "C" int qbx_apply_adjoint(qbx_plan* plan, const qbx_geom* g, int op, int 
   a.nsplit = ns;
   a.ctr_per_split = (nc + ns - 1) / ns;
   a.part = part;
+  a.hk_tab = host_plan_hk_table(plan, k, st, &e);
+  if (e != cudaSuccess) return acuda(e, "complex-k amplitude table");
   e = ck ? launch_adjoint_cplx(a, st) : launch_adjoint_real(a, st);
   if (e != cudaSuccess) return acuda(e, "adjoint kernel");
   k_adj_reduce<<<(g->n_src * nrhs + 255) / 256, 256, 0, st>>>(g->n_src, ns, nrhs, g->src_w, (const cplx*)part,

@@ -26,7 +26,7 @@ __global__ void k_coef_columns(AdjArgs a) {
   const int P2 = a.p + 2;
   T* col = reinterpret_cast<T*>(a.coef) + (size_t)c * ns * P2;
   KW<T> kw;
-  kw.init(a.kre, a.kim);
+  kw.init(a.kre, a.kim, a.hk_tab);
   const T kk = kw.kval();
   const double cx = a.cx[c], cy = a.cy[c];
   const int t = c % a.n_tgt;
@@ -99,7 +99,7 @@ k_adjoint(AdjArgs a) {
     sny = a.sny[ss];
   }
   KW<T> kw;
-  kw.init(a.kre, a.kim);
+  kw.init(a.kre, a.kim, a.hk_tab);
   const T kk = kw.kval();
   const cplx* gin = reinterpret_cast<const cplx*>(a.gc);
   const T* coef = reinterpret_cast<const T*>(a.coef);

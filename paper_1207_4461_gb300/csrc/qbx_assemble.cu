@@ -40,6 +40,7 @@ struct AsmArgs {
   const double *sx, *sy, *snx, *sny, *sw;
   const double* P;     // [q_src][q_tgt]
   cplx* out;           // [n_tgt][n_tgt] column-major
+  const double* hk_tab;   // complex k: the amplitude table of this k's ray, or null
 };
 
 template <typename T>
@@ -62,7 +63,7 @@ __global__ void __launch_bounds__(kAsmLanes * kAsmWarps) k_assemble_cfie(AsmArgs
   ux /= r;
   uy /= r;
   KW<T> kw;
-  kw.init(a.kre, a.kim);
+  kw.init(a.kre, a.kim, a.hk_tab);
   const T kk = kw.kval();
   if (warp == 0) {
     besselj_seq<T>(rmul(kk, r), p + 1, sJ + lane, kAsmLanes);
@@ -183,6 +184,8 @@ extern "C" int qbx_assemble_cfie(qbx_plan* plan, const qbx_geom* g, qbx_c64 k, q
   const unsigned gy = (unsigned)std::max(1, std::min((g->M + kAsmWarps - 1) / kAsmWarps, (int)((8192 + gx - 1) / gx)));
   const dim3 grid(gx, gy);
   cudaStream_t st = (cudaStream_t)stream;
+  a.hk_tab = host_plan_hk_table(plan, k, st, &e);
+  if (e != cudaSuccess) return acuda(e, "complex-k amplitude table");
   if (ck) {
     e = cudaFuncSetAttribute(k_assemble_cfie<cplx>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess) k_assemble_cfie<cplx><<<grid, kAsmLanes * kAsmWarps, smem, st>>>(a);

@@ -24,6 +24,7 @@ struct qbx_batch {
   int n_items = 0, grid = 0, max_src = 0, max_tgt = 0, num_sms = 0;
   int chunk = 0;                    // sources per work item (multiple of 32)
   double eta2 = 0.0;                // near-only QBX when > 0 (qbx_batch_set_eta)
+  double* d_hk = nullptr;           // amplitude tables of the complex-k curves' rays
   size_t part_cap = 0;              // bytes allocated for the partial sums
   std::vector<qbx::GroupInst> h_inst;
   GroupInst* d_inst = nullptr;
@@ -127,6 +128,7 @@ void destroy(qbx_batch* b) {
   cudaFree(b->d_status);
   cudaFree(b->d_wd);
   cudaFree(b->d_part);
+  cudaFree(b->d_hk);
   delete b;
 }
 
@@ -420,7 +422,10 @@ int qbx_batch_create(qbx_batch** batch, qbx_plan* plan, int n_inst, const qbx_ge
   b->num_sms = num_sms;
   b->h_inst = inst;
   // ---- device memory: instance table, densities, counter, status ----
+  int n_ck = 0;
+  for (int i = 0; i < n_inst; ++i) n_ck += inst[i].kim != 0.0 ? 1 : 0;
   e = cudaMalloc(&b->d_wd, wd_total);
+  if (e == cudaSuccess && n_ck > 0) e = cudaMalloc(&b->d_hk, (size_t)n_ck * hk_table_doubles() * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&b->d_inst, sizeof(GroupInst) * n_inst);
   if (e == cudaSuccess) e = cudaMalloc(&b->d_counter, sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&b->d_status, sizeof(int));
@@ -430,6 +435,24 @@ int qbx_batch_create(qbx_batch** batch, qbx_plan* plan, int n_inst, const qbx_ge
     return bcuda(e, "allocation");
   }
   for (int i = 0; i < n_inst; ++i) b->h_inst[i].wd = static_cast<char*>(b->d_wd) + wd_off[i];
+  // complex k: each curve's amplitude table (the k of a curve is fixed for the batch's life)
+  for (int i = 0, j = 0; i < n_inst; ++i) {
+    GroupInst& in = b->h_inst[i];
+    in.hk_tab = nullptr;
+    if (in.kim == 0.0) continue;
+    double* t = b->d_hk + (size_t)(j++) * hk_table_doubles();
+    e = launch_hk_table(in.kre, in.kim, t, 0);
+    if (e != cudaSuccess) {
+      destroy(b);
+      return bcuda(e, "complex-k amplitude tables");
+    }
+    in.hk_tab = t;
+  }
+  e = cudaStreamSynchronize(0);   // made before any apply, on whatever stream it runs
+  if (e != cudaSuccess) {
+    destroy(b);
+    return bcuda(e, "complex-k amplitude tables");
+  }
   // ---- items: the source chunk the makespan model prefers ----
   const int occ = b->ck ? group_occupancy_cplx(ops, p, b->rg) : group_occupancy_real(ops, p, b->rg);
   if (occ < 1) {

@@ -742,6 +742,7 @@ static int apply_impl(qbx_plan* p, const qbx_geom* g, int ops, int side, int lim
     in.tny = g->tgt_ny;
     in.wd = base;
     in.part = part;
+    in.hk_tab = a.hk_tab;
     ga.st_units = units;
     ga.st_nsplit = ns;
     ga.st_split_len = split_len(g->n_src, ns);

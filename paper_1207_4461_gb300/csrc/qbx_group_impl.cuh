@@ -117,7 +117,7 @@ k_apply_group(GroupArgs a) {
     uy *= ir;
     const double lim2 = LOCAL ? a.eta2 * r * r : INFINITY;
     KW<T> kw;
-    kw.init(in.kre, in.kim);
+    kw.init(in.kre, in.kim, in.hk_tab);
     const T kk = kw.kval();
     T* colJ = sJ + lane;
     T* colL = sL + lane;

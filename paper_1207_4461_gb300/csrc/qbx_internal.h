@@ -177,6 +177,7 @@ struct GroupInst {
   const void* dens;               // [n_tgt][nrhs] density on the target grid (jump terms)
   void* part;                     // [nsplit][n_ctr][ncomp][nrhs] raw sums
   void* out[3];                   // per operator (S, D, grad S) outputs, for the finish
+  const double* hk_tab;           // complex k: the amplitude table of this curve's k, or null
 };
 // A work item: 32 centres from ctr0 of instance inst, sources [src0, src1),
 // partial-sum slot `split`.
@@ -223,9 +224,13 @@ struct AdjArgs {
   double* cgeo;          // [n_ctr][3] target direction and 1/r (workspace)
   int nsplit, ctr_per_split;
   void* part;            // [nsplit][n_src][1][nrhs]
+  const double* hk_tab;  // complex k: the amplitude table of this k's ray, or null
 };
 cudaError_t launch_adjoint_real(const AdjArgs& a, cudaStream_t st);
 cudaError_t launch_adjoint_cplx(const AdjArgs& a, cudaStream_t st);
 void host_plan_workspace(const qbx_plan* plan, void** ws, size_t* bytes, int* num_sms, int** status);
+// The plan's amplitude table for complex k (made on st when k changes), or
+// null for real k.
+const double* host_plan_hk_table(qbx_plan* plan, qbx_c64 k, cudaStream_t st, cudaError_t* err);
 
 }  // namespace qbx

@@ -270,6 +270,8 @@ extern "C" int qbx_apply_shape_adjoint(qbx_plan* plan, const qbx_geom* g, int si
   a.nsplit = ns_fwd;
   a.src_per_split = host_split_len(n_src, ns_fwd);
   a.part = base + L.fpart;
+  a.hk_tab = host_plan_hk_table(plan, k, st, &e);
+  if (e != cudaSuccess) return scuda(e, "complex-k amplitude table");
   for (int r0 = 0; r0 < nrhs; r0 += chunk) {
     a.rhs0 = r0;
     a.nr = std::min(chunk, nrhs - r0);
@@ -304,6 +306,7 @@ extern "C" int qbx_apply_shape_adjoint(qbx_plan* plan, const qbx_geom* g, int si
   b.nsplit = ns_adj;
   b.ctr_per_split = (nc + ns_adj - 1) / ns_adj;
   b.part = base + L.apart;
+  b.hk_tab = a.hk_tab;
   e = ck ? launch_adjoint_cplx(b, st) : launch_adjoint_real(b, st);
   if (e != cudaSuccess) return scuda(e, "transposed sweep");
   // chain rule to the curve samples
