@@ -77,7 +77,7 @@ GROUP_SOURCES = ["qbx_group_impl.cuh", "qbx_apply_impl.cuh", "qbx_device.cuh", "
 # counters divided by the pairs of the captured launch, for the kernel
 # sources with the given hash (profiles/*_fp64_counts.md).
 HW_FP64_PER_PAIR = {"f7a1a26ef612288b": 543.7}         # fused S + D + grad S, p = 12, one rhs
-HW_FP64_PER_PAIR_GROUP = {"c0efa2290bd63732": 756.0}   # group kernel, S + D, p = 10, 32 rhs
+HW_FP64_PER_PAIR_GROUP = {"3bbdcb2bf613f81f": 756.0}   # group kernel, S + D, p = 10, 32 rhs
 
 
 def source_hash(names=KERNEL_SOURCES):
