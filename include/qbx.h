@@ -26,8 +26,9 @@
  *    qbx_plan_create (its workspace), qbx_batch_create (the batch's arrays)
  *    and the GMRES solves (their Krylov bases; the assembled solve also
  *    creates the plan's cuBLAS handle on first use) allocate.
- *  - A plan is not thread-safe: calls on one plan from several host threads
- *    must be serialised by the caller.
+ *  - A plan is not thread-safe: calls on one plan from several host threads,
+ *    or on several streams at once, must be serialised by the caller (they
+ *    share the plan's workspace and its complex-k amplitude table).
  *  - Return value: QBX_OK or an error code; qbx_last_error() gives a
  *    thread-local message.  Argument errors are detected on the host before
  *    anything is launched.  Device-side conditions (non-finite values in the
