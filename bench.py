@@ -78,6 +78,11 @@ GROUP_SOURCES = ["qbx_group_impl.cuh", "qbx_apply_impl.cuh", "qbx_device.cuh", "
 # sources with the given hash (profiles/*_fp64_counts.md).
 HW_FP64_PER_PAIR = {"f7a1a26ef612288b": 543.7}         # fused S + D + grad S, p = 12, one rhs
 HW_FP64_PER_PAIR_GROUP = {"3bbdcb2bf613f81f": 756.0}   # group kernel, S + D, p = 10, 32 rhs
+# sm__pipe_fp64_cycles_active (of peak) over the active and the elapsed
+# cycles, from the same captures (fused: 128-panel starfish, one wave;
+# group: the first 4 curves of the batch)
+HW_FP64_PIPE = {"f7a1a26ef612288b": (0.922, 0.891)}
+HW_FP64_PIPE_GROUP = {"3bbdcb2bf613f81f": (0.949, 0.926)}
 
 
 def source_hash(names=KERNEL_SOURCES):
@@ -99,13 +104,17 @@ def kernel_source_hash():
     return source_hash(KERNEL_SOURCES)
 
 
-def hw_roofline(ops_per_pair, pairs, seconds):
+def hw_roofline(ops_per_pair, pairs, seconds, pipe=None):
     if ops_per_pair is None:
         return None
     a = pairs * ops_per_pair / seconds / 1e9
-    return {"fp64_ops_per_pair": ops_per_pair, "achieved": a, "frac": a / FP64_PEAK_GFLOPS,
-            "unit": "GFLOP/s", "source": "ncu FP64 instruction counters (2 DFMA + DMUL + DADD) of the same "
-                                         "kernel sources, per pair, x pairs / measured kernel time"}
+    out = {"fp64_ops_per_pair": ops_per_pair, "achieved": a, "frac": a / FP64_PEAK_GFLOPS,
+           "unit": "GFLOP/s", "source": "ncu FP64 instruction counters (2 DFMA + DMUL + DADD) of the same "
+                                        "kernel sources, per pair, x pairs / measured kernel time"}
+    if pipe is not None:
+        out["fp64_pipe_busy"] = {"of_active_cycles": pipe[0], "of_elapsed_cycles": pipe[1],
+                                 "source": "ncu sm__pipe_fp64_cycles_active of the same kernel sources"}
+    return out
 
 
 def kernel_traffic(wl, args):
@@ -332,7 +341,8 @@ def run_gpu(args, wl):
                           "timed call, on the launching stream",
                 "flops_per_pair": fpp, "peak_basis": "152 SMs x 4 FP64 flop/clk x 2.07 GHz"}
     if not (args.separate or args.panels or args.ops or args.k):
-        roofline["hw"] = hw_roofline(HW_FP64_PER_PAIR.get(kernel_source_hash()), pairs, kern_ms * 1e-3)
+        roofline["hw"] = hw_roofline(HW_FP64_PER_PAIR.get(kernel_source_hash()), pairs, kern_ms * 1e-3,
+                                     HW_FP64_PIPE.get(kernel_source_hash()))
 
     # ---- end to end through the public API with host buffers (pinned)
     h_dens = torch.from_numpy(dens_np).pin_memory()
@@ -489,7 +499,8 @@ def run_batch_compare(args, qbx, torch):
                          "kernel": "k_apply_group (persistent, longest-first items, CUDA graph)",
                          "timing": "whole graph (oversampling, group kernel, finishing) per apply",
                          "hw": None if args.batch_curves else hw_roofline(
-                             HW_FP64_PER_PAIR_GROUP.get(source_hash(GROUP_SOURCES)), pairs, ms_batch * 1e-3)}}
+                             HW_FP64_PER_PAIR_GROUP.get(source_hash(GROUP_SOURCES)), pairs, ms_batch * 1e-3,
+                             HW_FP64_PIPE_GROUP.get(source_hash(GROUP_SOURCES)))}}
 
 
 def run_solve(args):
