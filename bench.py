@@ -69,20 +69,20 @@ def flops_per_pair_ops(ops, p, nrhs=1):
 # on the full-size starfish workload, from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum); valid only for the kernel
 # sources it was taken with, identified by their hash.
-TRAFFIC = {"f7a1a26ef612288b": 1.66e6}   # profiles/k_apply_fused_S_D_gradS_starfish_M256_dram.md
+TRAFFIC = {"7e064da1b8dcfcd2": 1.61e6}   # profiles/k_apply_fused_S_D_gradS_starfish_M256_dram.md
 KERNEL_SOURCES = ["qbx_apply_impl.cuh", "qbx_device.cuh", "special_tables.h", "qbx_apply_real.cu"]
 GROUP_SOURCES = ["qbx_group_impl.cuh", "qbx_apply_impl.cuh", "qbx_device.cuh", "special_tables.h"]
 # Hardware-counted FP64 operations per (centre, source) pair, 2 DFMA + DMUL +
 # DADD from ncu's smsp__sass_thread_inst_executed_op_{dfma,dmul,dadd}_pred_on
 # counters divided by the pairs of the captured launch, for the kernel
 # sources with the given hash (profiles/*_fp64_counts.md).
-HW_FP64_PER_PAIR = {"f7a1a26ef612288b": 543.7}         # fused S + D + grad S, p = 12, one rhs
-HW_FP64_PER_PAIR_GROUP = {"3bbdcb2bf613f81f": 756.0}   # group kernel, S + D, p = 10, 32 rhs
+HW_FP64_PER_PAIR = {"7e064da1b8dcfcd2": 543.7}         # fused S + D + grad S, p = 12, one rhs
+HW_FP64_PER_PAIR_GROUP = {"58788bd53b242af9": 756.0}   # group kernel, S + D, p = 10, 32 rhs
 # sm__pipe_fp64_cycles_active (of peak) over the active and the elapsed
 # cycles, from the same captures (fused: 128-panel starfish, one wave;
 # group: the first 4 curves of the batch)
-HW_FP64_PIPE = {"f7a1a26ef612288b": (0.922, 0.891)}
-HW_FP64_PIPE_GROUP = {"3bbdcb2bf613f81f": (0.949, 0.926)}
+HW_FP64_PIPE = {"7e064da1b8dcfcd2": (0.922, 0.891)}
+HW_FP64_PIPE_GROUP = {"58788bd53b242af9": (0.949, 0.925)}
 
 
 def source_hash(names=KERNEL_SOURCES):

@@ -112,8 +112,9 @@ template <> struct KW<double> {
 };
 // Complex k.  With a ray table (tab: the amplitudes B_n along z = k rho, made
 // for this k by launch_hk_table), |z| >= 2 takes the fitted amplitudes times
-// e^{i(Re k rho - pi/4)} e^{-Im k rho}; |z| < 2, or no table, the series /
-// Miller / asymptotic evaluation of hankel01_cplx.
+// e^{i(Re k rho - pi/4)} e^{-Im k rho} and |z| < 2 the tabulated series
+// (hankel01_cplx_small); without a table, the series / Miller / asymptotic
+// evaluation of hankel01_cplx.
 template <> struct KW<cplx> {
   cplx k, c2;                 // k, 2 conj(k) / |k|^2 (2/z = c2 / rho)
   double kisq;                // |k|^{-1/2}
@@ -151,7 +152,11 @@ template <> struct KW<cplx> {
     }
     const cplx z = cplx{k.re * rho, k.im * rho};
     twoz = 2.0 * cinv(z);
-    hankel01_cplx(z, h0, h1);
+    if (tab) {
+      hankel01_cplx_small(z, h0, h1);   // |z| < 2
+    } else {
+      hankel01_cplx(z, h0, h1);
+    }
     if constexpr (SCALED) {
       h0 = w * h0;
       h1 = w * h1;

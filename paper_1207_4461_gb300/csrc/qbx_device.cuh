@@ -304,6 +304,30 @@ __host__ __device__ inline cplx hankel_asym_c(cplx z, int nu) {
   return hankel_amp_asym_c(z, nu) * cexp_(mul_i(z - cplx{0.78539816339744830962, 0.0}));
 }
 
+// H0, H1 for complex z with |z| < 2 (t = z^2/4, |t| < 1): the ascending
+// series of the real path (DLMF 10.2.2, 10.8.1) with its coefficient table
+// qbx_hk_ser, by Horner in complex arithmetic.
+__device__ __forceinline__ void hankel01_cplx_small(cplx z, cplx& h0, cplx& h1) {
+  const cplx t = 0.25 * (z * z);
+  auto horner = [&](int row) {
+    double re = qbx_hk_ser[row][QBX_HK_NSER - 1], im = 0.0;
+#pragma unroll
+    for (int m = QBX_HK_NSER - 2; m >= 0; --m) {
+      const double nre = fma(re, t.re, fma(-im, t.im, qbx_hk_ser[row][m]));
+      im = fma(re, t.im, im * t.re);
+      re = nre;
+    }
+    return cplx{re, im};
+  };
+  const cplx sj0 = horner(0), sj1 = horner(1), sy0 = horner(2), sy1 = horner(3);
+  const cplx L = 0.63661977236758134308 * clog_(0.5 * z);   // (2/pi) ln(z/2)
+  const cplx j0 = sj0, j1 = 0.5 * (z * sj1);
+  const cplx y0 = L * j0 + sy0;
+  const cplx y1 = L * j1 + z * sy1 - 0.63661977236758134308 * cinv(z);
+  h0 = j0 + mul_i(y0);
+  h1 = j1 + mul_i(y1);
+}
+
 __host__ __device__ inline void hankel01_cplx(cplx z, cplx& h0, cplx& h1) {
   double az = cabs_(z);
   if (az > 20.0) {
