@@ -496,3 +496,41 @@ def test_maximum_orders(cuda, k, p, nrhs):
         assert rel(got[o], oracle.apply(go, o, qbx.SIDE_INT, qbx.LIMIT_PV, k, p, dens)) < TOL, o
     with pytest.raises(qbx.QBXError):
         qbx.qbx_apply_ops(plan, g, (0, 1, 2), qbx.SIDE_INT, qbx.LIMIT_PV, k, 41, dev(dens))
+
+
+def _random_cases(n, seed=20240607):
+    rng = np.random.default_rng(seed)
+    subsets = [(0,), (1,), (2,), (0, 1), (0, 2), (1, 2), (0, 1, 2)]
+    cases = []
+    for _ in range(n):
+        ops = subsets[rng.integers(len(subsets))]
+        side = int(rng.integers(3))
+        limit = int(rng.integers(2))
+        kr = float(rng.uniform(1.0, 15.0))
+        k = complex(kr, float(rng.uniform(0.05, 1.5))) if rng.random() < 0.5 else kr
+        p = int(rng.integers(1, 13))
+        nrhs = int(rng.choice([1, 1, 2, 5, 17]))
+        eta = float(rng.uniform(2.5, 8.0)) if rng.random() < 0.3 else None
+        M = int(rng.integers(10, 19))
+        cases.append((ops, side, limit, k, p, nrhs, eta, M))
+    return cases
+
+
+@pytest.mark.parametrize("case", _random_cases(16))
+def test_random_combinations(cuda, case):
+    """Seeded random combinations of operator subset, side, limit, real or
+    complex k, order, rhs count (1: weighted seeds; 17: group kernel),
+    near-only eta and panel count against the oracle: the paths exercised
+    together (complex-k tables with near-only, the group kernel, one
+    density for several operators)."""
+    ops, side, limit, k, p, nrhs, eta, M = case
+    sides = (qbx.SIDE_INT, qbx.SIDE_EXT, qbx.SIDE_TWO)
+    side = sides[side]
+    plan, g, go = make(W.starfish(0.2, 3), M, nrhs=nrhs, p=p)
+    dens = W.complex_gaussian(M + p, g.n_tgt * nrhs).reshape(g.n_tgt, nrhs)
+    got = qbx.qbx_apply_ops(plan, g, ops, side, limit, k, p, dev(dens), eta=eta)
+    qbx.qbx_sync_status(plan)
+    for o in ops:
+        ref = (oracle.apply_local(go, o, side, limit, k, p, eta, dens) if eta is not None
+               else oracle.apply(go, o, side, limit, k, p, dens))
+        assert rel(got[o], ref) < TOL, (case, o)
