@@ -516,7 +516,7 @@ def _random_cases(n, seed=20240607):
     return cases
 
 
-@pytest.mark.parametrize("case", _random_cases(16))
+@pytest.mark.parametrize("case", _random_cases(40))
 def test_random_combinations(cuda, case):
     """Seeded random combinations of operator subset, side, limit, real or
     complex k, order, rhs count (1: weighted seeds; 17: group kernel),
@@ -534,3 +534,25 @@ def test_random_combinations(cuda, case):
         ref = (oracle.apply_local(go, o, side, limit, k, p, eta, dens) if eta is not None
                else oracle.apply(go, o, side, limit, k, p, dens))
         assert rel(got[o], ref) < TOL, (case, o)
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_random_r_and_grad_d(cuda, seed):
+    """Seeded random cases of R and grad D (qbx_apply): side, limit, real or
+    complex k, order, rhs count (1-3: storage-free grad D; 4-5: stored
+    coefficients), panel count, against the oracle."""
+    rng = np.random.default_rng(1000 + seed)
+    op = (qbx.OP_R, qbx.OP_GRAD_D)[seed % 2]
+    side = (qbx.SIDE_INT, qbx.SIDE_EXT, qbx.SIDE_TWO)[int(rng.integers(3))]
+    limit = int(rng.integers(2))
+    kr = float(rng.uniform(1.0, 12.0))
+    k = complex(kr, float(rng.uniform(0.05, 1.0))) if rng.random() < 0.5 else kr
+    p = int(rng.integers(1, 12))
+    nrhs = int(rng.integers(1, 6))
+    M = int(rng.integers(10, 17))
+    plan, g, go = make(W.starfish(0.2, 3), M, nrhs=nrhs, p=p)
+    dens = W.complex_gaussian(seed + 7, g.n_tgt * nrhs).reshape(g.n_tgt, nrhs)
+    got = qbx.qbx_apply(plan, g, op, side, limit, k, p, dev(dens))
+    qbx.qbx_sync_status(plan)
+    oop = oracle.OP_R if op == qbx.OP_R else oracle.OP_GRAD_D
+    assert rel(got, oracle.apply(go, oop, side, limit, k, p, dens)) < TOL, (op, side, limit, k, p, nrhs, M)
