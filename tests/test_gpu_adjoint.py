@@ -85,3 +85,36 @@ def test_autograd_loss_gradient_vs_central_differences(cuda):
             # torch's convention: grad = dL/dRe + i dL/dIm
             an = grad[j, 0].real.item() if unit == 1.0 else grad[j, 0].imag.item()
             assert abs(fd - an) <= floor + 1e-8 * abs(an), (j, unit, fd, an, floor)
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_random_adjoint_inner_product(cuda, seed):
+    """Seeded random cases: operator S or D, side, limit, real or complex k,
+    order, rhs count (1-20), panel count: <A s, g> = <s, A^H g> with the
+    forward apply and the transposed sweep of the library, and A^H g against
+    the oracle's operator matrix at the smaller sizes."""
+    rng = np.random.default_rng(500 + seed)
+    op = (qbx.OP_S, qbx.OP_D)[seed % 2]
+    side = (qbx.SIDE_INT, qbx.SIDE_EXT, qbx.SIDE_TWO)[int(rng.integers(3))]
+    limit = int(rng.integers(2))
+    kr = float(rng.uniform(1.0, 12.0))
+    k = complex(kr, float(rng.uniform(0.05, 1.0))) if rng.random() < 0.5 else kr
+    p = int(rng.integers(1, 11))
+    nrhs = int(rng.choice([1, 2, 5, 20]))
+    M = int(rng.integers(4, 9))
+    cur = W.starfish(0.2, 3)
+    plan = qbx.Plan(16, 64, n_src=M * 64, n_ctr=2 * M * 16, ncoef=2 * p + 1, nrhs=nrhs)
+    g = qbx.qbx_geometry(plan, cur, cur.edges(M))
+    s = W.complex_gaussian(seed + 1, g.n_tgt * nrhs).reshape(g.n_tgt, nrhs)
+    gg = W.complex_gaussian(seed + 2, g.n_tgt * nrhs).reshape(g.n_tgt, nrhs)
+    As = qbx.qbx_apply(plan, g, op, side, limit, k, p, dev(s))
+    Ahg = qbx.qbx_apply_adjoint(plan, g, op, side, limit, k, p, dev(gg))
+    qbx.qbx_sync_status(plan)
+    lhs = (As.conj() * dev(gg)).sum(0)
+    rhs = (dev(s).conj() * Ahg).sum(0)
+    scale = (torch.abs(As) * torch.abs(dev(gg))).sum(0)
+    assert (torch.abs(lhs - rhs) / scale).max().item() < 1e-13, (op, side, limit, k, p, nrhs, M)
+    go = oracle.geometry(cur, cur.edges(M), 16, 64)
+    A = oracle.matrix(go, op, side, limit, k, p)
+    ref = A.conj().T @ gg
+    assert np.abs(Ahg.cpu().numpy() - ref).max() / np.abs(ref).max() < 1e-11, (op, side, limit, k, p, nrhs, M)

@@ -171,3 +171,43 @@ def test_batch_tuner_configurations(cuda, nrhs):
         for o in (0, 1):
             ref = oracle.apply(go, o, qbx.SIDE_TWO, 0, k, p, d)
             assert rel(out[i][o], ref) < TOL, (i, o, rg, chunk)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_random_batches(cuda, seed):
+    """Seeded random batches: 3-5 curves of 14-20 panels, per-curve real or
+    complex k, operator set, side, limit, rhs count, order, and near-only
+    (eta) or global, every curve against the oracle.  (Fewer panels put
+    sources inside the centres' disks on these wavy curves, r = h/2 being
+    large against their features; the Graf sums then amplify rounding by
+    (r/rho)^l and parity is not defined there, so the cases keep every
+    centre's ratio min |x_s - c| / r above 0.8.)"""
+    rng = np.random.default_rng(900 + seed)
+    n = int(rng.integers(3, 6))
+    Ms = tuple(int(m) for m in rng.integers(14, 21, n))
+    ks = tuple(complex(float(rng.uniform(1, 15)), float(rng.uniform(0.05, 1.0))) if rng.random() < 0.4
+               else float(rng.uniform(1, 15)) for _ in range(n))
+    ops = [(0,), (1,), (0, 1), (0, 1, 2)][int(rng.integers(4))]
+    side = (qbx.SIDE_INT, qbx.SIDE_EXT, qbx.SIDE_TWO)[int(rng.integers(3))]
+    limit = int(rng.integers(2))
+    nrhs = int(rng.choice([1, 3, 8]))
+    p = int(rng.integers(2, 11))
+    eta = float(rng.uniform(3.0, 8.0)) if rng.random() < 0.5 else 0.0
+    insts, bw = small_batch(ks, Ms, nrhs, seed=11 + seed)
+    plan = qbx.Plan(16, 64, n_src=64 * max(Ms), n_ctr=2 * 16 * max(Ms), ncoef=4, nrhs=nrhs)
+    geoms = [qbx.qbx_geometry(plan, c, c.edges(M)) for c, M, _ in insts]
+    for g in geoms:   # every centre admissible
+        assert g["ctr_ratio"].min().item() > 0.8
+    dens = [dev(bw.dens(i, g.n_tgt)) for i, g in enumerate(geoms)]
+    batch = qbx.Batch(plan, geoms, list(ks), p, ops, side, limit, dens)
+    if eta > 0:
+        batch.set_eta(eta)
+    out = batch.apply()
+    batch.status()
+    for i, (c, M, k) in enumerate(insts):
+        go = oracle.geometry(c, c.edges(M), 16, 64)
+        d = bw.dens(i, go["n_tgt"])
+        for o in ops:
+            ref = (oracle.apply_local(go, o, side, limit, k, p, eta, d) if eta > 0
+                   else oracle.apply(go, o, side, limit, k, p, d))
+            assert rel(out[i][o], ref) < TOL, (seed, i, o)
