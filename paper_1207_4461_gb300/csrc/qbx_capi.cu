@@ -562,6 +562,11 @@ static int far_impl(qbx_plan* p, const qbx_geom* g, int op, qbx_c64 k, const qbx
   a.nsplit = ns;
   a.src_per_split = split_len(g->n_src, ns);
   a.part = part;
+  {
+    cudaError_t te;
+    a.hk_tab = host_plan_hk_table(p, k, st, &te);
+    CK(te, "complex-k amplitude table");
+  }
   for (int r0 = 0; r0 < nrhs; r0 += 8) {
     a.rhs0 = r0;
     a.nr = std::min(8, nrhs - r0);

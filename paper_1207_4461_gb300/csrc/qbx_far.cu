@@ -17,7 +17,7 @@ k_far(FarArgs a) {
   const int ee = active ? e : a.n_far - 1;
   const double x = a.xy[2 * ee], y = a.xy[2 * ee + 1];
   KW<T> kw;
-  kw.init(a.kre, a.kim);
+  kw.init(a.kre, a.kim, a.hk_tab);
   cplx acc[NR], accb[NR];
 #pragma unroll
   for (int r2 = 0; r2 < NR; ++r2) acc[r2] = accb[r2] = cplx{0.0, 0.0};

@@ -78,6 +78,7 @@ struct FarArgs {
   int nrhs, rhs0, nr;
   int nsplit, src_per_split;
   void* part;             // [nsplit][n_far][ncomp][nrhs]
+  const double* hk_tab;   // complex k: the amplitude table of this k's ray, or null
 };
 cudaError_t launch_far(const FarArgs& a, cudaStream_t st);
 
