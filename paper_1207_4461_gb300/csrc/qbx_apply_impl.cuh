@@ -659,7 +659,7 @@ k_apply_fused(ApplyArgs a) {
 }
 
 // Percentage of the largest shared-memory carve-out (228 KB) that holds n
-// CTAs of smem bytes each (plus the 1 KB the driver reserves per CTA),
+// CTAs of smem bytes each (plus the 1 KB CUDA reserves per CTA),
 // rounded up; 0 when nothing is to be set.
 static inline int carveout_percent(int n, size_t smem) {
   if (n < 1) return 0;
