@@ -59,3 +59,30 @@ def test_reference_arm_other_ranks_exit_without_work(monkeypatch, capsys):
         ref_sample, warmup, steps, gpus, separate = 48, 1, 1, 2, False
     assert bench.run_reference(A(), None) == 0
     assert capsys.readouterr().out == ""
+
+
+def test_bench_json_parts_serialise_for_real_and_complex_k():
+    """The bench line's host-side parts: the workload description for a real
+    and a complex wavenumber (the profiling override), and the counted-flop
+    roofline with the FP64 pipe figures, all JSON-serialisable; the counted
+    rate is pairs x flops per pair / time over the stated peak."""
+    import json
+    import workloads as W
+
+    class A:
+        separate = False
+        gpus = 1
+
+    for k in (20.0, complex("20+1j")):
+        wl = W.cfg2()
+        wl.k = k
+        cfg = bench.config_dict(wl, A())
+        json.dumps(cfg)
+        assert cfg["terms_per_step"] == 3 * wl.n_ctr * wl.n_src * (2 * wl.p + 1)
+        assert ("20+1j" in cfg["workload"]) == isinstance(k, complex)
+    hw = bench.hw_roofline(500.0, 10**8, 0.05, (0.9, 0.85))
+    json.dumps(hw)
+    assert abs(hw["achieved"] - 500.0 * 1e8 / 0.05 / 1e9) < 1e-9
+    assert abs(hw["frac"] - hw["achieved"] / bench.FP64_PEAK_GFLOPS) < 1e-12
+    assert hw["fp64_pipe_busy"]["of_elapsed_cycles"] == 0.85
+    assert bench.hw_roofline(None, 1, 1.0) is None
