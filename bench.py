@@ -432,6 +432,9 @@ def run_batch_compare(args, qbx, torch):
     S and D): one batched launch (CUDA graph) against one qbx_apply_ops call
     per curve.  Returns the figures for the JSON line."""
     bw = W.cfg3()
+    if args.batch_small:
+        # many small curves: each per-curve launch fills a small part of the GPU
+        bw = W.BatchWorkload("fourier-batch-256-small", 256, 10, 32, 4, m_lo=16, m_hi=48)
     insts = bw.instances()
     if args.batch_curves:
         insts = insts[:args.batch_curves]
@@ -483,8 +486,8 @@ def run_batch_compare(args, qbx, torch):
     fpp = flops_per_pair_ops(["S", "D"], bw.p, bw.nrhs)
     achieved = pairs * fpp / (ms_batch * 1e-3) / 1e9
     return {"workload": f"{len(insts)} random Fourier curves r=1+sum_{{m<=8}}(a_m cos mt+b_m sin mt), "
-                        "a,b~U(-0.04,0.04), M~U{16..512} x 16 targets, 4x sources, k~U(1,40), p=10, "
-                        "32 CN(0,1) densities, interior, S and D (seed 3)",
+                        f"a,b~U(-0.04,0.04), M~U{{{bw.m_lo}..{bw.m_hi}}} x 16 targets, 4x sources, k~U(1,40), "
+                        f"p=10, 32 CN(0,1) densities, interior, S and D (seed {bw.seed})",
             "pairs": pairs, "terms_per_step": terms, "steps": steps,
             "batched_ms": ms_batch, "per_instance_ms": ms_inst,
             "batched_terms_per_s": terms / (ms_batch * 1e-3),
@@ -831,6 +834,8 @@ def main():
                     help="profiling only: qbx_plan_set_min_waves for the main step")
     ap.add_argument("--batch-curves", type=int, default=None,
                     help="profiling only: the first N curves of the batch")
+    ap.add_argument("--batch-small", action="store_true",
+                    help="with --batch-only: 256 small curves (16..48 panels) instead of the 64-curve workload")
     ap.add_argument("--batch-only", action="store_true",
                     help="profiling only: run the batched comparison alone and print it")
     ap.add_argument("--solve", action="store_true",
