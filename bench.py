@@ -794,6 +794,15 @@ def run_variants(args):
     t["S+D+grad S, 32 rhs, k = 20 + 1i"] = timed(
         lambda: qbx.qbx_apply_ops(plan32, g32, ops3, qbx.SIDE_TWO, 0, kc, wl.p, d32))
     qbx.qbx_sync_status(plan32)
+    # near-only accuracy against speed: eta sweep (largest relative difference from the global apply)
+    glob = qbx.qbx_apply_ops(plan, g, ops3, qbx.SIDE_TWO, 0, wl.k, wl.p, dens)
+    glob = {o: v.clone() for o, v in glob.items()}
+    eta_sweep = {}
+    for eta in (3.0, 5.0, 8.0, 12.0):
+        ms = timed(lambda: qbx.qbx_apply_ops(plan, g, ops3, qbx.SIDE_TWO, 0, wl.k, wl.p, dens, eta=eta))
+        loc = qbx.qbx_apply_ops(plan, g, ops3, qbx.SIDE_TWO, 0, wl.k, wl.p, dens, eta=eta)
+        diff = max((torch.abs(loc[o] - glob[o]).max() / torch.abs(glob[o]).max()).item() for o in ops3)
+        eta_sweep[f"{eta:g}"] = {"ms": ms, "max_rel_diff_vs_global": diff}
     clk = clocks.stop()
     qbx.qbx_sync_status(plan)
     pairs = wl.n_ctr * wl.n_src
@@ -809,6 +818,7 @@ def run_variants(args):
         "l2": "flushed before every timed call (256 MiB write outside the event pair)",
         "ms": t,
         "terms_per_s": {name: nops[name] * per_op_terms / (ms * 1e-3) for name, ms in t.items()},
+        "near_only_eta_sweep": eta_sweep,
         "clocks": clk}))
     return 0
 
