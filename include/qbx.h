@@ -375,10 +375,11 @@ int qbx_solve_exterior_dirichlet_assembled(qbx_plan *plan, const qbx_geom *g, co
  * at most `chunk` of its sources (equal ranges per curve; the ranges' partial
  * sums are added in a fixed order), taken longest first by persistent CTAs
  * through an atomic counter; no CTA ever waits for another.
- * qbx_batch_create allocates the batch's device memory, picks the chunk
- * with the smallest predicted makespan of that schedule (a model of the
- * persistent grid), and builds and instantiates the graph (synchronous);
- * qbx_batch_apply launches the graph on `stream`. */
+ * qbx_batch_create allocates the batch's device memory (with, for every
+ * curve of complex k, the H0/H1 amplitude table of its ray z = k rho), picks
+ * the chunk with the smallest predicted makespan of that schedule (a model
+ * of the persistent grid), and builds and instantiates the graph
+ * (synchronous); qbx_batch_apply launches the graph on `stream`. */
 typedef struct qbx_batch qbx_batch;
 int qbx_batch_create(qbx_batch **batch, qbx_plan *plan, int n_inst, const qbx_geom *geoms,
                      const qbx_c64 *k, int p, int ops, int side, int limit, int nrhs,
