@@ -113,7 +113,10 @@ int qbx_gauss_legendre(int q, double *nodes, double *weights);
  * uploads the per-panel interpolation matrix from the target to the source
  * nodes (Sec. 3.4.2), a device status word, and allocates `workspace_bytes`
  * of device workspace used by the split-source reductions (see
- * qbx_workspace_bytes).  *plan receives the handle.  Host call, synchronous. */
+ * qbx_workspace_bytes) and a 29 KB buffer for the H0/H1 amplitude table of
+ * the ray z = k rho, which calls with a complex k fill (on their stream)
+ * when k differs from the last one.  *plan receives the handle.  Host call,
+ * synchronous. */
 int qbx_plan_create(qbx_plan **plan, int device, int q_tgt, int q_src, size_t workspace_bytes);
 int qbx_plan_destroy(qbx_plan *plan);
 
