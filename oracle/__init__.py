@@ -63,6 +63,7 @@ def lib():
             L.orc_far.argtypes = [I, I, P, I, P, P, P, P, P, I, D, D, P]
             L.orc_assign_centres.argtypes = [I, P, I, I, P, P, P, P]
             L.orc_apply_s_tangent.argtypes = [I, D, D, I, I, I, I, P, D] + [P] * 4 + [I] + [P] * 4 + [P, I, P, P]
+            L.orc_apply_d_tangent.argtypes = [I, I, D, D, I, I, I, I, P, D] + [P] * 4 + [I] + [P] * 4 + [P, I, P, P]
             L.orc_apply_local.argtypes = [I, I, I, D, D, I, D, I, I, I] + [P] * 12 + [P, I, I, P, P]
             L.orc_num_threads.restype = I
             L.orc_set_num_threads.argtypes = [I]
@@ -336,6 +337,37 @@ def apply_s_tangent(curve, pert, t_edges, q_tgt: int, q_src: int, side, k, p, de
                                    _p(d), nrhs, _p(u), _p(du))
     if rc != 0:
         raise ValueError(f"orc_apply_s_tangent failed ({rc})")
+    return u, (du if isinstance(pert, (list, tuple)) else du[0])
+
+
+def apply_d_tangent(curve, pert, t_edges, q_tgt: int, q_src: int, side, limit, k, p, dens_tgt,
+                    r_factor: float = 0.5):
+    """Shape derivative of the on-surface D apply (limit ONE_SIDED or PV),
+    forward mode, as apply_s_tangent: the D coefficients (eq.
+    graf-coefficient-dlp) differentiated through the source positions,
+    normals and weights and the centres; the PV jump does not move."""
+    t_edges = _f64(t_edges)
+    M = t_edges.size - 1
+    tt = panel_nodes(t_edges, q_tgt)
+    ts = panel_nodes(t_edges, q_src)
+    gt, dgt = (_f64(a) for a in curve(tt))
+    gs, dgs = (_f64(a) for a in curve(ts))
+    perts = list(pert) if isinstance(pert, (list, tuple)) else [pert]
+    nd = len(perts)
+    pgt = _f64(np.stack([_f64(q(tt)[0]) for q in perts]))
+    pdgt = _f64(np.stack([_f64(q(tt)[1]) for q in perts]))
+    pgs = _f64(np.stack([_f64(q(ts)[0]) for q in perts]))
+    pdgs = _f64(np.stack([_f64(q(ts)[1]) for q in perts]))
+    d = _dens2d(dens_tgt, M * q_tgt)
+    nrhs = d.shape[1]
+    k = complex(k)
+    u = np.zeros((M * q_tgt, nrhs), dtype=np.complex128)
+    du = np.zeros((nd, M * q_tgt, nrhs), dtype=np.complex128)
+    rc = lib().orc_apply_d_tangent(side, limit, k.real, k.imag, p, M, q_tgt, q_src, _p(t_edges), float(r_factor),
+                                   _p(gt), _p(dgt), _p(gs), _p(dgs), nd, _p(pgt), _p(pdgt), _p(pgs), _p(pdgs),
+                                   _p(d), nrhs, _p(u), _p(du))
+    if rc != 0:
+        raise ValueError(f"orc_apply_d_tangent failed ({rc})")
     return u, (du if isinstance(pert, (list, tuple)) else du[0])
 
 

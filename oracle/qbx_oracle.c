@@ -870,6 +870,181 @@ int orc_apply_s_tangent(int side, double kre, double kim, int p, int M, int q_tg
 }
 
 /* ------------------------------------------------------------------------- */
+/* Shape derivative of the on-surface D apply, forward mode, as               */
+/* orc_apply_s_tangent: the D coefficients of orc_form_locals,                */
+/*   alpha^D_l = (i/4) sum_s wdens_s (-1)^l (k/2) [nu F_{-l-1} - conj(nu) F_{-l+1}], */
+/* differentiated through the source position (rho, theta of x_s - c), the    */
+/* source normal nu = n_x + i n_y (n = (gamma'_y, -gamma'_x)/|gamma'|), the   */
+/* weight and the centre, with dF_m = (k H_m' drho + i m H_m dtheta) e^{i m theta}, */
+/* H_m' = (H_{m-1} - H_{m+1})/2; then the evaluation as for S.  The PV jump   */
+/* -+ mu/2 (limit PV, one side) does not move with the curve.                 */
+/* ------------------------------------------------------------------------- */
+static cplx dF_m(int m, const cplx *H, double theta, cplx k, double drho, double dth)
+{
+    cplx hm = Z_signed(m, H);
+    cplx hd = (Z_signed(m - 1, H) - Z_signed(m + 1, H)) / 2.0;
+    return (k * hd * drho + I * (double)m * hm * dth) * cexp(I * (double)m * theta);
+}
+
+int orc_apply_d_tangent(int side, int limit, double kre, double kim, int p, int M, int q_tgt, int q_src,
+                        const double *t_edges, double r_factor,
+                        const double *gam_tgt, const double *dgam_tgt,
+                        const double *gam_src, const double *dgam_src, int ndir,
+                        const double *pg_tgt, const double *pdg_tgt,
+                        const double *pg_src, const double *pdg_src,
+                        const cplx *dens_tgt, int nrhs, cplx *u, cplx *du)
+{
+    if (p < 0 || p + 3 >= ORC_MAXN || q_tgt < 1 || q_src < 1 || q_tgt > ORC_MAXN || q_src > ORC_MAXN ||
+        M < 1 || nrhs < 1 || ndir < 1)
+        return 1;
+    cplx k = kre + I * kim;
+    int n_tgt = M * q_tgt, n_src = M * q_src, nl = 2 * p + 1;
+    size_t nd_s = (size_t)n_src, nd_t = (size_t)n_tgt, nd = (size_t)ndir;
+    double *buf = malloc(sizeof(double) * (7 * nd_s + 17 * nd_t + (size_t)M));
+    double *dbuf = malloc(sizeof(double) * nd * (5 * nd_s + 4 * nd_t + (size_t)M));
+    cplx *psig = malloc(sizeof(cplx) * nd_s * nrhs);
+    cplx *wd = malloc(sizeof(cplx) * nd_s * nrhs);
+    if (!buf || !dbuf || !psig || !wd) { free(buf); free(dbuf); free(psig); free(wd); return 2; }
+    double *src_x = buf, *src_y = src_x + nd_s, *src_nx = src_y + nd_s, *src_ny = src_nx + nd_s;
+    double *src_w = src_ny + nd_s, *ones = src_w + nd_s;
+    double *tgt_x = ones + 2 * nd_s, *tgt_y = tgt_x + nd_t, *tgt_nx = tgt_y + nd_t, *tgt_ny = tgt_nx + nd_t;
+    double *tgt_w = tgt_ny + nd_t;
+    double *ctr_x = tgt_w + nd_t, *ctr_y = ctr_x + 2 * nd_t, *ctr_r = ctr_y + 2 * nd_t;
+    double *ctr_ratio = ctr_r + 2 * nd_t;
+    double *panel_h = ctr_ratio + 6 * nd_t;
+    /* per direction: d_sx, d_sy, d_sw, d_snx, d_sny [n_src]; d_cx, d_cy [2 n_tgt]; d_h [M] */
+    double *d_sx = dbuf, *d_sy = d_sx + nd * nd_s, *d_sw = d_sy + nd * nd_s;
+    double *d_snx = d_sw + nd * nd_s, *d_sny = d_snx + nd * nd_s;
+    double *d_cx = d_sny + nd * nd_s, *d_cy = d_cx + nd * 2 * nd_t, *d_h = d_cy + nd * 2 * nd_t;
+    orc_geometry(M, q_tgt, q_src, t_edges, gam_tgt, dgam_tgt, gam_src, dgam_src, r_factor, 0,
+                 src_x, src_y, src_nx, src_ny, src_w, tgt_x, tgt_y, tgt_nx, tgt_ny, tgt_w,
+                 panel_h, ctr_x, ctr_y, ctr_r, ctr_ratio);
+    double xs[ORC_MAXN], ws[ORC_MAXN];
+    orc_gauss_legendre(q_src, xs, ws);
+    for (int s = 0; s < n_src; ++s) ones[s] = 1.0;
+    for (int d = 0; d < ndir; ++d) {
+        const double *pgs = pg_src + (size_t)d * 2 * nd_s, *pdgs = pdg_src + (size_t)d * 2 * nd_s;
+        const double *pgt = pg_tgt + (size_t)d * 2 * nd_t, *pdgt = pdg_tgt + (size_t)d * 2 * nd_t;
+        double *dsx = d_sx + d * nd_s, *dsy = d_sy + d * nd_s, *dsw = d_sw + d * nd_s;
+        double *dsnx = d_snx + d * nd_s, *dsny = d_sny + d * nd_s;
+        double *dcx = d_cx + d * 2 * nd_t, *dcy = d_cy + d * 2 * nd_t, *dh = d_h + (size_t)d * M;
+        /* tangents of the source nodes, normals, weights and panel lengths */
+        for (int m = 0; m < M; ++m) {
+            double half = 0.5 * (t_edges[m + 1] - t_edges[m]), acc = 0.0;
+            for (int j = 0; j < q_src; ++j) {
+                int s = m * q_src + j;
+                double vx = dgam_src[2 * s], vy = dgam_src[2 * s + 1];
+                double sp = sqrt(vx * vx + vy * vy);
+                double px = pdgs[2 * s], py = pdgs[2 * s + 1];
+                double tp = (vx * px + vy * py) / sp;   /* tau . pdg */
+                dsw[s] = ws[j] * half * tp;
+                acc += dsw[s];
+                dsx[s] = pgs[2 * s];
+                dsy[s] = pgs[2 * s + 1];
+                dsnx[s] = (py - src_nx[s] * tp) / sp;
+                dsny[s] = (-px - src_ny[s] * tp) / sp;
+            }
+            dh[m] = acc;
+        }
+        /* tangents of the centres */
+        for (int t = 0; t < n_tgt; ++t) {
+            int m = t / q_tgt;
+            double vx = dgam_tgt[2 * t], vy = dgam_tgt[2 * t + 1];
+            double sp = sqrt(vx * vx + vy * vy);
+            double px = pdgt[2 * t], py = pdgt[2 * t + 1];
+            double tp = (vx * px + vy * py) / sp;
+            double dnx = (py - tgt_nx[t] * tp) / sp, dny = (-px - tgt_ny[t] * tp) / sp;
+            double r = ctr_r[t], dr = r_factor * dh[m];
+            double ox = dr * tgt_nx[t] + r * dnx, oy = dr * tgt_ny[t] + r * dny;
+            dcx[t] = pgt[2 * t] - ox;
+            dcy[t] = pgt[2 * t + 1] - oy;
+            dcx[n_tgt + t] = pgt[2 * t] + ox;
+            dcy[n_tgt + t] = pgt[2 * t + 1] + oy;
+        }
+    }
+    orc_upsample(M, q_tgt, q_src, nrhs, ones, dens_tgt, psig);     /* P mu */
+    for (size_t i = 0; i < nd_s * nrhs; ++i) wd[i] = src_w[i / nrhs] * psig[i];
+    for (size_t i = 0; i < nd_t * nrhs; ++i) u[i] = 0.0;
+    for (size_t i = 0; i < nd * nd_t * nrhs; ++i) du[i] = 0.0;
+    int s0 = (side == SIDE_TWO) ? SIDE_INT : side;
+    int s1 = (side == SIDE_TWO) ? SIDE_EXT : side;
+    double wgt = (side == SIDE_TWO) ? 0.5 : 1.0;
+    int fail = 0;
+    for (int sd = s0; sd <= s1; ++sd) {
+        #pragma omp parallel for schedule(dynamic, 4)
+        for (int t = 0; t < n_tgt; ++t) {
+            cplx H[ORC_MAXN], J[ORC_MAXN];
+            cplx *al = malloc(sizeof(cplx) * (1 + nd) * (size_t)nl * nrhs);
+            if (!al) {
+                #pragma omp atomic write
+                fail = 1;
+                continue;
+            }
+            cplx *dal = al + (size_t)nl * nrhs;             /* [ndir][nl][nrhs] */
+            for (size_t i = 0; i < (1 + nd) * (size_t)nl * nrhs; ++i) al[i] = 0.0;
+            int c = sd * n_tgt + t;
+            double cx = ctr_x[c], cy = ctr_y[c];
+            for (int s = 0; s < n_src; ++s) {
+                double dx = src_x[s] - cx, dy = src_y[s] - cy;
+                double rho = hypot(dx, dy), th = atan2(dy, dx);
+                orc_hankel_seq(k * rho, p + 2, H);
+                cplx nu = src_nx[s] + I * src_ny[s];
+                for (int l = -p; l <= p; ++l) {
+                    double sg = (l & 1) ? -1.0 : 1.0;   /* (-1)^l */
+                    cplx fa = F_m(-l - 1, H, th), fb = F_m(-l + 1, H, th);
+                    cplx kern = sg * (k / 2.0) * (nu * fa - conj(nu) * fb);
+                    for (int r = 0; r < nrhs; ++r)
+                        al[(size_t)(l + p) * nrhs + r] += (I / 4.0) * wd[(size_t)s * nrhs + r] * kern;
+                    for (int d = 0; d < ndir; ++d) {
+                        double ddx = d_sx[d * nd_s + s] - d_cx[d * 2 * nd_t + c];
+                        double ddy = d_sy[d * nd_s + s] - d_cy[d * 2 * nd_t + c];
+                        double drho = (dx * ddx + dy * ddy) / rho;
+                        double dth = (dx * ddy - dy * ddx) / (rho * rho);
+                        cplx dnu = d_snx[d * nd_s + s] + I * d_sny[d * nd_s + s];
+                        cplx dfa = dF_m(-l - 1, H, th, k, drho, dth), dfb = dF_m(-l + 1, H, th, k, drho, dth);
+                        cplx dkern = sg * (k / 2.0) * (dnu * fa + nu * dfa - conj(dnu) * fb - conj(nu) * dfb);
+                        for (int r = 0; r < nrhs; ++r) {
+                            size_t sr = (size_t)s * nrhs + r;
+                            cplx dwd = d_sw[d * nd_s + s] * psig[sr];
+                            dal[((size_t)d * nl + (l + p)) * nrhs + r] += (I / 4.0) * (dwd * kern + wd[sr] * dkern);
+                        }
+                    }
+                }
+            }
+            double ex = tgt_x[t] - cx, ey = tgt_y[t] - cy;
+            double rt = hypot(ex, ey), tht = atan2(ey, ex);
+            orc_besselj_seq(k * rt, p + 1, J);
+            for (int l = -p; l <= p; ++l) {
+                cplx jl = Z_signed(l, J);
+                cplx jd = (Z_signed(l - 1, J) - Z_signed(l + 1, J)) / 2.0;
+                cplx e = cexp(I * (double)l * tht);
+                for (int r = 0; r < nrhs; ++r)
+                    u[(size_t)t * nrhs + r] += wgt * al[(size_t)(l + p) * nrhs + r] * jl * e;
+                for (int d = 0; d < ndir; ++d) {
+                    const double *pgt = pg_tgt + (size_t)d * 2 * nd_t;
+                    double dex = pgt[2 * t] - d_cx[d * 2 * nd_t + c], dey = pgt[2 * t + 1] - d_cy[d * 2 * nd_t + c];
+                    double drt = (ex * dex + ey * dey) / rt;
+                    double dtht = (ex * dey - ey * dex) / (rt * rt);
+                    cplx dfac = (k * jd * drt + I * (double)l * jl * dtht) * e;
+                    for (int r = 0; r < nrhs; ++r) {
+                        cplx a = al[(size_t)(l + p) * nrhs + r], da = dal[((size_t)d * nl + (l + p)) * nrhs + r];
+                        du[((size_t)d * nd_t + t) * nrhs + r] += wgt * (da * jl * e + a * dfac);
+                    }
+                }
+            }
+            free(al);
+        }
+    }
+    /* PV, one side: u = lim - sg mu / 2 (sg = +1 exterior, -1 interior); no derivative */
+    if (side != SIDE_TWO && limit == LIMIT_PV) {
+        double sg = (side == SIDE_EXT) ? 1.0 : -1.0;
+        for (size_t i = 0; i < nd_t * nrhs; ++i) u[i] -= sg * 0.5 * dens_tgt[i];
+    }
+    free(buf); free(dbuf); free(psig); free(wd);
+    return fail ? 2 : 0;
+}
+
+/* ------------------------------------------------------------------------- */
 /* Near-only QBX (the optimisation remarked in Sec. 5: direct evaluation for  */
 /* distant interactions, QBX for near ones).  Reading: for the centre c of    */
 /* target x_t, a source node x_s is near when |x_s - c| < eta r_c; near nodes */

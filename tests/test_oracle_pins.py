@@ -564,6 +564,54 @@ def test_shape_tangent_scaling_identity():
         assert relerr(du, u + k * dk) < 1e-8
 
 
+@pytest.mark.parametrize("side,limit,k,pert", [(INT, ONE, 5.0, ("cos", 3)), (EXT, PV, 3 + 0.5j, ("sin", 2)),
+                                               (TWO, ONE, 7.0, ("cos", 0)), (INT, PV, 6.0, ("sin", 5))])
+def test_d_shape_tangent_vs_central_differences(side, limit, k, pert):
+    """The forward-mode derivative of D (through source positions, normals,
+    weights and centres) against central differences (h = 1e-6) of the
+    oracle's own D apply on moved curves: starfish, 12 panels, p = 8; the
+    bound is the differences' own error (rounding ~1e-16/h amplified by the
+    sums)."""
+    cur, M, p, h = W.starfish(), 12, 8, 1e-6
+    pf = _fourier_pert(pert[1], pert[0])
+    edges = cur.edges(M)
+    dens = W.density_cfg1(oracle.panel_nodes(edges, 16))
+    u, du = oracle.apply_d_tangent(cur, pf, edges, 16, 64, side, limit, k, p, dens)
+    up = oracle.apply(oracle.geometry(_moved(cur, pf, h), edges, 16, 64), OP_D, side, limit, k, p, dens)
+    um = oracle.apply(oracle.geometry(_moved(cur, pf, -h), edges, 16, 64), OP_D, side, limit, k, p, dens)
+    u0 = oracle.apply(oracle.geometry(cur, edges, 16, 64), OP_D, side, limit, k, p, dens)
+    assert relerr(u, u0) < 1e-14
+    assert relerr(du, (up - um) / (2 * h)) < 1e-8
+
+
+def test_d_shape_tangent_rigid_motions_and_scaling():
+    """D is invariant under translations and rotations of the curve (only
+    differences of positions, polar angles and the normals' angles to them
+    enter), so the derivative along a rigid motion vanishes; scaling the
+    curve by lambda gives the discrete D at lambda k (kernel times arc length
+    is dimensionless), so along gamma -> gamma the derivative is k du/dk."""
+    cur, M, p, k, h = W.starfish(), 10, 8, 5.0, 1e-5
+    edges = cur.edges(M)
+    dens = W.density_cfg1(oracle.panel_nodes(edges, 16))
+    g = oracle.geometry(cur, edges, 16, 64)
+
+    def shift(t):
+        n = np.asarray(t).size
+        return np.tile([0.3, -0.7], (n, 1)), np.zeros((n, 2))
+
+    def rot(t):
+        gg, dg = cur(t)
+        return np.stack([-gg[:, 1], gg[:, 0]], -1), np.stack([-dg[:, 1], dg[:, 0]], -1)
+    for side, limit in ((INT, ONE), (EXT, PV), (TWO, ONE)):
+        u, dus = oracle.apply_d_tangent(cur, [shift, rot, lambda t: cur(t)], edges, 16, 64, side, limit, k, p,
+                                        dens)
+        assert np.abs(dus[0]).max() < 1e-13 * np.abs(u).max()
+        assert np.abs(dus[1]).max() < 1e-11 * np.abs(u).max()
+        dk = (oracle.apply(g, OP_D, side, limit, k + h, p, dens) -
+              oracle.apply(g, OP_D, side, limit, k - h, p, dens)) / (2 * h)
+        assert relerr(dus[2], k * dk) < 1e-8
+
+
 @pytest.mark.parametrize("m,k", [(0, 5.0), (3, 5.0), (2, 4 + 0.5j)])
 def test_shape_tangent_circle_radius(m, k):
     """Unit circle, sigma = e^{imt}: S sigma = lambda(R) e^{imt} with
