@@ -432,15 +432,31 @@ int qbx_batch_destroy(qbx_batch *batch);
  * ncomp = 2 for grad S, fail with QBX_ENOMEM and a message naming the limit.
  *
  * The first call on each device (the current device) looks up the device
- * addresses of the fixed arrays and clears a status word; the first call for
- * a new (q_tgt, q_src) pair uploads that pair's interpolation matrix with a
- * synchronous copy.  Make those first calls before any stream capture.
- * Every call shares the one scratch array, which keeps the last call's
- * contents: calls that overlap on the GPU (several streams or threads on the
- * same device) race and must be serialised by the caller. */
+ * addresses of the fixed arrays and clears a status word on `stream`.  A call
+ * whose (q_tgt, q_src) pair differs from the previous call's on that device
+ * drains `stream` (cudaStreamSynchronize: earlier calls on it still read the
+ * old matrix), uploads the pair's interpolation matrix on `stream` and drains
+ * it again, so it returns only when the GPU has caught up.  A call with
+ * Im k > 0 whose k differs from the previous complex k on that device
+ * makes the amplitude table of k's ray in a fourth fixed array, on `stream`.
+ * Make the first call, and any call that changes the grid pair, before a
+ * stream capture.
+ * Every call shares the one scratch array (and the matrix and the table),
+ * which keeps the last call's contents: calls that overlap on the GPU
+ * (several streams or threads on the same device) race and must be
+ * serialised by the caller; calls in order on one stream do not.
+ *
+ * Device-side errors (a non-finite result) set the status word, which
+ * qbx_apply_static_status reads. */
 #define QBX_STATIC_SCRATCH_BYTES (32u << 20)
 int qbx_apply_static(const qbx_geom *g, int op, int side, int limit, qbx_c64 k, int p,
                      const qbx_c64 *dens_tgt, int nrhs, qbx_c64 *out_on, void *stream);
+/* The status word of qbx_apply_static on the current device: read and
+ * cleared in the order of `stream` (after the calls queued on it), then
+ * `stream` is synchronised.  QBX_ENONFINITE if a kernel of any call since the
+ * last read produced a non-finite value, QBX_OK otherwise (also before the
+ * first call on the device).  Allocates nothing. */
+int qbx_apply_static_status(void *stream);
 
 /* Diagnostics of the device special functions used by the kernels: H0, H1
  * at z[n] (complex, Im z >= 0, z != 0; the real-argument path is taken when

@@ -121,6 +121,8 @@ def lib():
             L.qbx_shape_adjoint_workspace_bytes.restype = ctypes.c_size_t
             L.qbx_apply_static.argtypes = [G, I, I, I, c64, I, _P, I, _P, _P]
             L.qbx_apply_static.restype = I
+            L.qbx_apply_static_status.argtypes = [_P]
+            L.qbx_apply_static_status.restype = I
             L.qbx_vec_dots.argtypes = [I, I, I, _P, _P, _P, _P, _P]
             L.qbx_vec_dots.restype = I
             L.qbx_vec_dots_work_bytes.argtypes = [I, I]
@@ -619,6 +621,12 @@ def qbx_apply_static(g: Geometry, op, side, limit, k, p, dens_tgt, out_on=None):
         out_on = torch.empty(shape, dtype=torch.complex128, device=d.device)
     _check(lib().qbx_apply_static(g.ref(), op, side, limit, _k(k), p, _ptr(d), nrhs, _ptr(out_on), _stream()))
     return out_on
+
+
+def qbx_apply_static_status():
+    """Read and clear qbx_apply_static's device status word (raises
+    QBXError(QBX_ENONFINITE) if a kernel produced a non-finite value)."""
+    _check(lib().qbx_apply_static_status(_stream()))
 
 
 def qbx_far(plan: Plan, g: Geometry, op, k, wdens_src, x_far):
