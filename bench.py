@@ -83,6 +83,10 @@ HW_FP64_PER_PAIR_GROUP = {"58788bd53b242af9": 756.0}   # group kernel, S + D, p 
 # group: the first 4 curves of the batch)
 HW_FP64_PIPE = {"7e064da1b8dcfcd2": (0.922, 0.891)}
 HW_FP64_PIPE_GROUP = {"58788bd53b242af9": (0.949, 0.925)}
+# the fused S + D + grad S apply at the complex wavenumber 20 + 1i (same
+# capture set-up: 128-panel starfish, p = 12, one rhs)
+HW_FP64_PER_PAIR_CPLX = {}
+HW_FP64_PIPE_CPLX = {}
 
 
 def source_hash(names=KERNEL_SOURCES):
@@ -334,15 +338,24 @@ def run_gpu(args, wl):
         fpp = flops_per_pair_ops(list(wl.ops), wl.p, wl.nrhs)
         kname = "k_apply_fused, operators " + "+".join(wl.ops) + " in one pass"
     achieved = pairs * fpp / (kern_ms * 1e-3) / 1e9
-    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
-                "frac": achieved / FP64_PEAK_GFLOPS, "traffic": kernel_traffic(wl, args),
+    hw = None
+    if not (args.separate or args.panels or args.ops or args.k):
+        hw = hw_roofline(HW_FP64_PER_PAIR.get(kernel_source_hash()), pairs, kern_ms * 1e-3,
+                         HW_FP64_PIPE.get(kernel_source_hash()))
+    # headline: hardware-counted FP64 flops (2 DFMA + DMUL + DADD per pair from
+    # ncu, for these kernel sources) per second against the FP64 peak; the
+    # algorithmic model beside it; the model alone when no count matches
+    roofline = {"bound": "alu", "achieved": hw["achieved"] if hw else achieved, "peak": FP64_PEAK_GFLOPS,
+                "unit": "GFLOP/s", "frac": hw["frac"] if hw else achieved / FP64_PEAK_GFLOPS,
+                "basis": "ncu-counted FP64 flops per pair" if hw else "algorithmic flop model per pair",
+                "traffic": kernel_traffic(wl, args),
                 "kernel": kname, "kernel_ms": kern_ms,
                 "timing": "CUDA events recorded by the library around the kernel launch(es) of every "
                           "timed call, on the launching stream",
-                "flops_per_pair": fpp, "peak_basis": "152 SMs x 4 FP64 flop/clk x 2.07 GHz"}
-    if not (args.separate or args.panels or args.ops or args.k):
-        roofline["hw"] = hw_roofline(HW_FP64_PER_PAIR.get(kernel_source_hash()), pairs, kern_ms * 1e-3,
-                                     HW_FP64_PIPE.get(kernel_source_hash()))
+                "flops_per_pair": hw["fp64_ops_per_pair"] if hw else fpp,
+                "peak_basis": "152 SMs x 4 FP64 flop/clk x 2.07 GHz",
+                "model": {"flops_per_pair": fpp, "achieved": achieved, "frac": achieved / FP64_PEAK_GFLOPS},
+                "hw": hw}
 
     # ---- end to end through the public API with host buffers (pinned)
     h_dens = torch.from_numpy(dens_np).pin_memory()
@@ -381,8 +394,11 @@ def run_gpu(args, wl):
     if rank == 0 and not args.panels and not args.separate:
         line["near_only"] = run_local_compare(args, qbx, torch, plan, g, codes, wl, dens, outs, flush, stream,
                                               step_ms)
+    if rank == 0 and not args.panels and not args.separate and not args.k and not args.ops:
+        line["complex_k"] = run_complex_k(args, qbx, torch, plan, g, codes, wl, dens, outs, flush, stream)
     if rank == 0 and not args.no_batch and not args.panels:
-        line["batched"] = run_batch_compare(args, qbx, torch)
+        line["batched"] = run_batch_compare(args, qbx, torch, small=False)
+        line["batched_small"] = run_batch_compare(args, qbx, torch, small=True)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         terms, dt, cores = oracle_sample(wl, args.cpu_sample)
         import oracle
@@ -427,14 +443,61 @@ def run_local_compare(args, qbx, torch, plan, g, codes, wl, dens, outs, flush, s
             "call": "qbx_apply_local (sources with |x_s - c| >= eta r by the smooth rule at the target)"}
 
 
-def run_batch_compare(args, qbx, torch):
-    """64 random curves (16..512 panels, k in (1, 40), p = 10, 32 densities,
-    S and D): one batched launch (CUDA graph) against one qbx_apply_ops call
-    per curve.  Returns the figures for the JSON line."""
-    bw = W.cfg3()
-    if args.batch_small:
-        # many small curves: each per-curve launch fills a small part of the GPU
-        bw = W.BatchWorkload("fourier-batch-256-small", 256, 10, 32, 4, m_lo=16, m_hi=48)
+def batch_workload(small):
+    """The batched comparison's workloads: the 64 random curves of 16..512
+    panels, or 256 small ones (16..48 panels), where every per-curve launch
+    fills a small part of the GPU."""
+    if small:
+        return W.BatchWorkload("fourier-batch-256-small", 256, 10, 32, 4, m_lo=16, m_hi=48)
+    return W.cfg3()
+
+
+def spread(xs):
+    xs = sorted(xs)
+    n = len(xs)
+    med = xs[n // 2] if n % 2 else 0.5 * (xs[n // 2 - 1] + xs[n // 2])
+    return {"median": med, "min": xs[0], "max": xs[-1], "samples": n}
+
+
+def run_complex_k(args, qbx, torch, plan, g, codes, wl, dens, outs, flush, stream, k=20.0 + 1.0j):
+    """The same step at the complex wavenumber k = 20 + 1i (Im k > 0: complex
+    J_l, complex recurrences, H0 and H1 from the amplitude table of the ray
+    z = k rho): time per step, kernel time and the counted-flop roofline (not
+    the benchmark metric)."""
+    out = {c: torch.empty_like(outs[c]) for c in outs}
+    for _ in range(2):
+        qbx.qbx_apply_ops(plan, g, codes, qbx.SIDE_TWO, 0, k, wl.p, dens, out=out)
+    torch.cuda.synchronize()
+    qbx.qbx_sync_status(plan)
+    steps = max(3, min(args.steps, 5))
+    tot, kern = 0.0, 0.0
+    for s in range(steps):
+        flush.fill_(s & 0xFF)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        qbx.qbx_apply_ops(plan, g, codes, qbx.SIDE_TWO, 0, k, wl.p, dens, out=out)
+        e1.record(stream)
+        e1.synchronize()
+        tot += e0.elapsed_time(e1)
+        kern += qbx.qbx_plan_kernel_ms(plan)
+    qbx.qbx_sync_status(plan)
+    ms, kms = tot / steps, kern / steps
+    pairs = wl.n_ctr * wl.n_src
+    terms = len(wl.ops) * wl.terms_per_op()
+    return {"k": str(k), "ms_per_step": ms, "kernel_ms": kms, "terms_per_s": terms / (ms * 1e-3), "steps": steps,
+            "roofline_hw": hw_roofline(HW_FP64_PER_PAIR_CPLX.get(kernel_source_hash()), pairs, kms * 1e-3,
+                                       HW_FP64_PIPE_CPLX.get(kernel_source_hash())),
+            "parity": "tests/test_gpu_parity.py::test_apply_full_size_complex_k (the oracle at 256 targets, "
+                      "both sides, S, D and grad S, <= 1e-11 per output array)"}
+
+
+def run_batch_compare(args, qbx, torch, small=None):
+    """Many random curves (p = 10, 32 densities, S and D): one batched launch
+    (CUDA graph) against one qbx_apply_ops call per curve, the two arms
+    alternating step by step (>= 10 timed steps each, L2 flushed before every
+    step), reported as median, min and max.  Returns the figures for the JSON
+    line."""
+    bw = batch_workload(args.batch_small if small is None else small)
     insts = bw.instances()
     if args.batch_curves:
         insts = insts[:args.batch_curves]
@@ -457,39 +520,51 @@ def run_batch_compare(args, qbx, torch):
         for i, g in enumerate(geoms):
             qbx.qbx_apply_ops(plan, g, (qbx.OP_S, qbx.OP_D), qbx.SIDE_INT, 0, ks[i], bw.p, dens[i], out=outs[i])
 
-    def timed(fn, steps):
+    def one(fn, s):
+        flush.fill_(s & 0xFF)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
         fn()
-        torch.cuda.synchronize()
-        tot = 0.0
-        for s in range(steps):
-            flush.fill_(s & 0xFF)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            fn()
-            e1.record(stream)
-            e1.synchronize()
-            tot += e0.elapsed_time(e1)
-        return tot / steps
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1)
 
-    steps = max(1, min(args.steps, 3))
-    ms_batch = timed(batch.apply, steps)
+    batch.apply()
+    per_instance()
+    torch.cuda.synchronize()
+    steps = max(10, args.batch_steps)
+    t_batch, t_inst = [], []
+    for s in range(steps):   # alternate the arms so that drifts of the clock hit both
+        if s % 2 == 0:
+            t_batch.append(one(batch.apply, 2 * s))
+            t_inst.append(one(per_instance, 2 * s + 1))
+        else:
+            t_inst.append(one(per_instance, 2 * s))
+            t_batch.append(one(batch.apply, 2 * s + 1))
     batch.status()
-    ms_inst = timed(per_instance, steps)
     qbx.qbx_sync_status(plan)
+    sb, si = spread(t_batch), spread(t_inst)
+    ms_batch, ms_inst = sb["median"], si["median"]
     # the same batch with near-only QBX (eta = 8), then back to the global apply
     batch.set_eta(8.0)
-    ms_near = timed(batch.apply, 1)
+    batch.apply()
+    ms_near = one(batch.apply, 0)
     batch.set_eta(0.0)
     batch.status()
     pairs = sum(g.n_tgt * g.n_src for g in geoms)
     terms = pairs * (2 * bw.p + 1) * bw.nrhs * 2
     fpp = flops_per_pair_ops(["S", "D"], bw.p, bw.nrhs)
     achieved = pairs * fpp / (ms_batch * 1e-3) / 1e9
+    full64 = not args.batch_curves and bw.n_inst == 64
     return {"workload": f"{len(insts)} random Fourier curves r=1+sum_{{m<=8}}(a_m cos mt+b_m sin mt), "
                         f"a,b~U(-0.04,0.04), M~U{{{bw.m_lo}..{bw.m_hi}}} x 16 targets, 4x sources, k~U(1,40), "
                         f"p=10, 32 CN(0,1) densities, interior, S and D (seed {bw.seed})",
             "pairs": pairs, "terms_per_step": terms, "steps": steps,
+            "timing": "arms alternating step by step, CUDA events on the launching stream, L2 flushed before "
+                      "each step; medians",
             "batched_ms": ms_batch, "per_instance_ms": ms_inst,
+            "batched_ms_spread": sb, "per_instance_ms_spread": si,
+            "ranges_overlap": not (sb["max"] < si["min"] or si["max"] < sb["min"]),
             "batched_terms_per_s": terms / (ms_batch * 1e-3),
             "per_instance_terms_per_s": terms / (ms_inst * 1e-3),
             "speedup": ms_inst / ms_batch,
@@ -501,7 +576,7 @@ def run_batch_compare(args, qbx, torch):
                          "frac": achieved / FP64_PEAK_GFLOPS, "flops_per_pair": fpp,
                          "kernel": "k_apply_group (persistent, longest-first items, CUDA graph)",
                          "timing": "whole graph (oversampling, group kernel, finishing) per apply",
-                         "hw": None if args.batch_curves else hw_roofline(
+                         "hw": None if not full64 else hw_roofline(
                              HW_FP64_PER_PAIR_GROUP.get(source_hash(GROUP_SOURCES)), pairs, ms_batch * 1e-3,
                              HW_FP64_PIPE_GROUP.get(source_hash(GROUP_SOURCES)))}}
 
@@ -842,6 +917,7 @@ def main():
     ap.add_argument("--k", default=None, help="profiling only: override the wavenumber (complex: e.g. 20+1j)")
     ap.add_argument("--min-waves", type=int, default=None,
                     help="profiling only: qbx_plan_set_min_waves for the main step")
+    ap.add_argument("--batch-steps", type=int, default=10, help="timed steps per arm of the batched comparison (>= 10)")
     ap.add_argument("--batch-curves", type=int, default=None,
                     help="profiling only: the first N curves of the batch")
     ap.add_argument("--batch-small", action="store_true",

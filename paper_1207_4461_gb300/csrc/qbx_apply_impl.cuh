@@ -57,6 +57,17 @@ __device__ __forceinline__ void madd(cplx& acc, cplx e, cplx h) {
   acc.im = fma(e.re, h.im, acc.im);
   acc.im = fma(e.im, h.re, acc.im);
 }
+// acc -= e h
+__device__ __forceinline__ void msub(cplx& acc, double e, cplx h) {
+  acc.re = fma(-e, h.re, acc.re);
+  acc.im = fma(-e, h.im, acc.im);
+}
+__device__ __forceinline__ void msub(cplx& acc, cplx e, cplx h) {
+  acc.re = fma(-e.re, h.re, acc.re);
+  acc.re = fma(e.im, h.im, acc.re);
+  acc.im = fma(-e.re, h.im, acc.im);
+  acc.im = fma(-e.im, h.re, acc.im);
+}
 __device__ __forceinline__ cplx smul(double e, cplx h) { return cplx{e * h.re, e * h.im}; }
 __device__ __forceinline__ cplx smul(cplx e, cplx h) { return e * h; }
 __device__ __forceinline__ double rmul(double a, double c) { return a * c; }
@@ -74,7 +85,9 @@ __device__ __forceinline__ cplx dcoef(cplx a2, cplx c, cplx a3, double v) {
 __device__ __forceinline__ cplx hrec(double s, cplx h, cplx hm) {
   return cplx{fma(s, h.re, -hm.re), fma(s, h.im, -hm.im)};
 }
-__device__ __forceinline__ cplx hrec(cplx s, cplx h, cplx hm) { return s * h - hm; }
+__device__ __forceinline__ cplx hrec(cplx s, cplx h, cplx hm) {   // four FMAs
+  return cplx{fma(s.re, h.re, fma(-s.im, h.im, -hm.re)), fma(s.re, h.im, fma(s.im, h.re, -hm.im))};
+}
 __device__ __forceinline__ cplx lin2(double a, cplx x, double b, cplx y) {
   return cplx{fma(a, x.re, b * y.re), fma(a, x.im, b * y.im)};
 }
@@ -86,10 +99,11 @@ __device__ __forceinline__ cplx sadd(cplx a, cplx b) { return a + b; }
 // rho^{-1/2}) or complex k.
 template <typename T> struct KW;
 template <> struct KW<double> {
-  double k, ik, ksq;  // k, 1/k, k^{-1/2}
+  double k, ik, ik2, ksq;  // k, 1/k, 2/k, k^{-1/2}
   __device__ __forceinline__ void init(double kre, double, const double* = nullptr) {
     k = kre;
     ik = 1.0 / kre;
+    ik2 = ik + ik;
     ksq = rsqrt(kre);
   }
   __device__ __forceinline__ double kval() const { return k; }
@@ -105,9 +119,9 @@ template <> struct KW<double> {
   // w H0, w H1
   __device__ __forceinline__ void hankel_w(double rho, double inv, double y, cplx w, cplx& h0, cplx& h1,
                                            double& twoz) const {
-    const double z = k * rho, invz = ik * inv;
-    twoz = invz + invz;
-    hankel01_real<true>(z, invz, y * ksq, h0, h1, w);
+    const double z = k * rho;
+    twoz = ik2 * inv;
+    hankel01_real<true>(z, 0.5 * twoz, y * ksq, h0, h1, w);   // 1/z used below z = 2 only
   }
 };
 // Complex k.  With a ray table (tab: the amplitudes B_n along z = k rho, made
@@ -233,35 +247,82 @@ __device__ __forceinline__ void pair_kernels(const KW<T>& kw, const T kk, const 
 
   // ---- order sums; l = 0 terms and recurrence seeds ----
   GS = K = GA = GB = cplx{0.0, 0.0};
-  cplx D1 = cplx{0.0, 0.0}, D3 = cplx{0.0, 0.0};
+  if (kG) GA = smul(cG[0], H0);
+  cplx Hm = H0, H = H1;
+  T s = twoz;
+  double cp = 1.0, cl = cs, sp = 0.0, sl = sn;
+  if constexpr (kSums) {
+    // D (with grad S) and the source-position gradient from the sum by parts
+    //   T = J0 H0' + 2 sum_{l=1..p} J_l cos(l psi) H_l'
+    //     = t_1 H_0 + sum_{m=1..p-1} (t_{m+1} - t_{m-1}) H_m - t_{p-1} H_p - t_p H_{p+1},
+    // t_m = J_m cos(m psi) (t_0 = J_0), H_l' = (H_{l-1} - H_{l+1})/2, H_0' = -H_1
+    // (see pair_accumulate_w), and D2 = GB
+    T tm = J0;                             // t_{l-1}
+    T tc = rmul(cJ[STRIDE], cl);           // t_l
+    cplx Ts = cplx{0.0, 0.0};
+    madd(Ts, tc, H0);
+    if (p == 0) msub(Ts, tm, H1);          // (t_1 = 0: the column holds J_{p+1} = 0)
+    for (int l = 1; l <= p; ++l) {
+      const int o = l * STRIDE;
+      if (kS) madd(GS, tc, H);
+      if (kG) madd(GA, rmul(cG[o], cl), H);
+      madd(GB, rmul(cL[o], sl), H);
+      if (l < p) {
+        const double cn = fma(tw, cl, -cp);
+        cp = cl;
+        cl = cn;
+        const double sq = fma(tw, sl, -sp);
+        sp = sl;
+        sl = sq;
+        const T tn = rmul(cJ[o + STRIDE], cl);   // t_{l+1}
+        madd(Ts, sc_sub(tn, tm), H);
+        tm = tc;
+        tc = tn;
+        const cplx Hn = hrec(s, H, Hm);
+        Hm = H;
+        H = Hn;
+        s = sadd(s, twoz);
+      } else {
+        msub(Ts, tm, H);                         // - t_{p-1} H_p
+        msub(Ts, tc, hrec(s, H, Hm));            // - t_p H_{p+1}
+      }
+    }
+    const double i2 = 2.0 * inv;
+    if (kS) GS = smul(J0, H0) + 2.0 * GS;   // J0 H0 + 2 sum_{l>=1}
+    if (kDsum) {
+      // D = k a T + (2/rho) b D2
+      K = smul(rmul(kk, av), Ts) + (i2 * bv) * GB;
+    }
+    if (kX) {
+      // grad_{x_s} of the S kernel: the D kernel is linear in the normal,
+      // n . (e_rho R + e_theta Q), R = k T, Q = (2/rho) D2;
+      // e_rho = (dx, dy)/rho, e_theta = (-dy, dx)/rho
+      const cplx R = smul(kk, Ts);
+      const cplx Q = i2 * GB;
+      EX = (dx * R - dy * Q) * inv;
+      EY = (dy * R + dx * Q) * inv;
+    }
+    return;
+  }
   T Cp, Cc;
   double Vp = 0.0, Vc = 0.0;
-  if (kG) GA = smul(cG[0], H0);
-  if (kD && !kDsum) {
+  if (kD) {
     const T tka = rmul(kk, 2.0 * av);                // C_0 = 2 k a
     const double i2 = 2.0 * inv;
     Cp = tka;
     Cc = rmul(tka, cs);                              // C_1
     K = smul(rmul(kneg_j0, av), H1);                 // -k a J0 H1
-    madd(K, sc_mul(cJ[STRIDE], Cc), H0);      // e_0 = J_1 C_1
+    madd(K, sc_mul(cJ[STRIDE], Cc), H0);             // e_0 = J_1 C_1
     const T Cn = fmsub_r(tw, Cc, Cp);                // C_2
     Cp = Cc;
     Cc = Cn;
     Vp = -i2 * av;                                   // V_0
     Vc = i2 * fma(bv, sn, -av * cs);                 // V_1
   }
-  cplx Hm = H0, H = H1;
-  T s = twoz;
-  double cp = 1.0, cl = cs, sp = 0.0, sl = sn;
   for (int l = 1; l <= p; ++l) {
     const int o = l * STRIDE;
-    if (kS || kSums) {
-      const T tS = rmul(cJ[o], cl);                  // J_l cos(l psi)
-      if (kS) madd(GS, tS, H);
-      if (kSums) madd(D1, tS, Hm);
-    }
-    if (kSums) madd(D3, rmul(cL[o], cl), H);
-    if (kD && !kDsum) madd(K, dcoef(cJ[o + STRIDE], Cc, cL[o], Vc), H);
+    if (kS) madd(GS, rmul(cJ[o], cl), H);            // J_l cos(l psi)
+    if (kD) madd(K, dcoef(cJ[o + STRIDE], Cc, cL[o], Vc), H);
     if (kG) madd(GA, rmul(cG[o], cl), H);
     if (kB) madd(GB, rmul(cL[o], sl), H);
     if (l < p) {
@@ -277,7 +338,7 @@ __device__ __forceinline__ void pair_kernels(const KW<T>& kw, const T kk, const 
         sp = sl;
         sl = sq;
       }
-      if (kD && !kDsum) {
+      if (kD) {
         const T Cn = fmsub_r(tw, Cc, Cp);
         Cp = Cc;
         Cc = Cn;
@@ -290,23 +351,6 @@ __device__ __forceinline__ void pair_kernels(const KW<T>& kw, const T kk, const 
   if (kS) {  // J0 H0 + 2 sum_{l>=1}
     GS = smul(J0, H0) + 2.0 * GS;
   }
-  if (kDsum) {
-    // -k a J0 H1 + 2 k a D1 + (2/rho)(b D2 - a D3), D2 = GB
-    const T ka = rmul(kk, av);
-    const double i2 = 2.0 * inv;
-    K = smul(sc_mul(ka, rmul(J0, -1.0)), H1) + smul(rmul(ka, 2.0), D1) +
-        (i2 * bv) * GB - (i2 * av) * D3;
-  }
-  if (kX) {
-    // grad_{x_s} of the S kernel: the D kernel is linear in the normal,
-    // n . (e_rho R + e_theta Q), R = -k J0 H1 + 2 k D1 - (2/rho) D3,
-    // Q = (2/rho) D2; e_rho = (dx, dy)/rho, e_theta = (-dy, dx)/rho
-    const double i2 = 2.0 * inv;
-    const cplx R = smul(kneg_j0, H1) + smul(rmul(kk, 2.0), D1) - i2 * D3;
-    const cplx Q = i2 * GB;
-    EX = (dx * R - dy * Q) * inv;
-    EY = (dy * R + dx * Q) * inv;
-  }
 }
 
 // One rhs with one weighted density w = (w sigma)_s for every requested
@@ -314,74 +358,108 @@ __device__ __forceinline__ void pair_kernels(const KW<T>& kw, const T kk, const 
 // out weighted (the sums are linear in H_l) and goes straight into the
 // centre's accumulators, without the per-pair kernel values and their
 // complex products with w.  The cosine and sine recurrences carry
-// 2 cos(l psi), 2 sin(l psi) (same recurrence, seeds 2, 2 cos psi and 0,
-// 2 sin psi), which puts the factor 2 of the folded sums into the
+// C_l = 2 cos(l psi), S_l = 2 sin(l psi) (same recurrence, seeds 2, 2 cos psi
+// and 0, 2 sin psi), which puts the factor 2 of the folded sums into the
 // recurrence: accS receives the S kernel itself, accA and accB twice the A
-// and B sums of pair_kernels, and the D combination takes the doubled
-//   D = a (-k J0 H1 + k D1') + (1/rho) (b D2' - a D3'),  Dn' = 2 Dn.
+// and B sums of pair_kernels.  (ux2, uy2) = 2 (ux, uy), so that
+// (ux2, uy2) . (dx, dy) / rho = C_1 directly.
+// With grad S requested too, D comes from sums by parts: with A_m = J_m C_m
+// (A_0 = 2 J_0) and H_l' = (H_{l-1} - H_{l+1})/2 (H_0' = -H_1),
+//   D = k a [J0 H0' + sum_{l=1..p} J_l C_l H_l'] + (b/rho) D2',
+//   2 [J0 H0' + sum_l A_l H_l'] = A_1 H_0 + sum_{m=1..p-1} (A_{m+1} - A_{m-1}) H_m
+//                                 - A_{p-1} H_p - A_p H_{p+1},
+// D2' = sum_l l J_l S_l H_l (grad S's B sum): one difference and one complex
+// multiply-add per order for D, instead of two sums (J_l C_l against H_{l-1}
+// and l J_l C_l against H_l).
 // gA0 = 2 (J_{-1} - J_1)/2 = -2 J_1: the l = 0 coefficient of the doubled A sum.
 template <int OPS, typename T, int STRIDE>
 __device__ __forceinline__ void pair_accumulate_w(const KW<T>& kw, const T kk, const T J0, const T kneg_j0,
-                                                  const T gA0, const T* cJ, const T* cL, const T* cG, int p,
-                                                  double dx, double dy, double nx, double ny, double ux,
-                                                  double uy, cplx w, cplx& accS, cplx& accD, cplx& accA,
-                                                  cplx& accB) {
+                                                  const T gA0, const T twoJ0, const T khalf, const T* cJ,
+                                                  const T* cL, const T* cG, int p, double dx, double dy,
+                                                  double nx, double ny, double ux2, double uy2, cplx w,
+                                                  cplx& accS, cplx& accD, cplx& accA, cplx& accB) {
   constexpr bool kS = OPS & OPB_S, kD = OPS & OPB_D, kG = OPS & OPB_G;
   static_assert(!(OPS & OPB_X), "the source-position gradient is not formed here");
   constexpr bool kDsum = kD && kG;
   const double rho2 = fma(dx, dx, dy * dy);
   double inv, rho, yq;
   kw.geom(rho2, inv, rho, yq);
-  const double cs = fma(ux, dx, uy * dy) * inv;  // cos psi
+  const double tw = fma(ux2, dx, uy2 * dy) * inv;   // C_1 = 2 cos psi
   cplx H0, H1;
   T twoz;
   kw.hankel_w(rho, inv, yq, w, H0, H1, twoz);   // w H0, w H1
-  const double tw = 2.0 * cs;
-  double sn = 0.0;
-  if (kD || kG) sn = fma(uy, dx, -ux * dy) * inv;  // sin psi
+  double s1 = 0.0;
+  if (kD || kG) s1 = fma(uy2, dx, -ux2 * dy) * inv;  // S_1 = 2 sin psi
   double av = 0.0, bv = 0.0;
   if (kD) {
     av = fma(nx, dx, ny * dy) * inv;   // n_s . e_rho
     bv = fma(ny, dx, -nx * dy) * inv;  // n_s . e_theta
   }
+  cplx Hm = H0, H = H1;
+  T s = twoz;
+  double cp = 2.0, cl = tw, sp = 0.0, sl = s1;  // C_l, S_l at l = 0, 1
+  if constexpr (kDsum) {
+    if (kS) madd(accS, J0, H0);
+    madd(accA, gA0, H0);
+    T Am = twoJ0;                          // A_{l-1}
+    T Ac = rmul(cJ[STRIDE], cl);           // A_l
+    cplx P2 = cplx{0.0, 0.0}, GB = cplx{0.0, 0.0};
+    madd(P2, Ac, H0);
+    if (p == 0) msub(P2, Am, H1);          // (A_1 = 0: the column holds J_{p+1} = 0)
+    for (int l = 1; l <= p; ++l) {
+      const int o = l * STRIDE;
+      if (kS) madd(accS, Ac, H);
+      madd(accA, rmul(cG[o], cl), H);
+      madd(GB, rmul(cL[o], sl), H);
+      if (l < p) {
+        const double cn = fma(tw, cl, -cp);
+        cp = cl;
+        cl = cn;
+        const double sq = fma(tw, sl, -sp);
+        sp = sl;
+        sl = sq;
+        const T An = rmul(cJ[o + STRIDE], cl);   // A_{l+1}
+        madd(P2, sc_sub(An, Am), H);
+        Am = Ac;
+        Ac = An;
+        const cplx Hn = hrec(s, H, Hm);
+        Hm = H;
+        H = Hn;
+        s = sadd(s, twoz);
+      } else {
+        msub(P2, Am, H);                         // - A_{p-1} H_p
+        msub(P2, Ac, hrec(s, H, Hm));            // - A_p H_{p+1}
+      }
+    }
+    madd(accD, rmul(khalf, av), P2);
+    madd(accD, bv * inv, GB);
+    accB = accB + GB;
+    return;
+  }
   // ---- l = 0 terms and recurrence seeds ----
   if (kS) madd(accS, J0, H0);
   if (kG) madd(accA, gA0, H0);
-  cplx D1 = cplx{0.0, 0.0}, D3 = cplx{0.0, 0.0}, GB = cplx{0.0, 0.0};
   T Cp, Cc;
   double Vp = 0.0, Vc = 0.0;
-  if (kD && !kDsum) {
-    const T tka = rmul(kk, 2.0 * av);                // C_0 = 2 k a
-    const double i2 = 2.0 * inv;
-    Cp = tka;
-    Cc = rmul(tka, cs);                              // C_1
+  if (kD) {
+    const T ka = rmul(kk, av);
+    Cp = rmul(ka, 2.0);                              // C_0 = 2 k a
+    Cc = rmul(ka, tw);                               // C_1 = 2 k a cos psi
     madd(accD, rmul(kneg_j0, av), H1);               // -k a J0 H1
     madd(accD, sc_mul(cJ[STRIDE], Cc), H0);          // e_0 = J_1 C_1
     const T Cn = fmsub_r(tw, Cc, Cp);                // C_2
     Cp = Cc;
     Cc = Cn;
-    Vp = -i2 * av;                                   // V_0
-    Vc = i2 * fma(bv, sn, -av * cs);                 // V_1
+    Vp = -2.0 * inv * av;                            // V_0
+    Vc = inv * fma(bv, sl, -av * tw);                // V_1 = (2/rho)(b sin psi - a cos psi)
   }
-  cplx Hm = H0, H = H1;
-  T s = twoz;
-  double cp = 2.0, cl = tw, sp = 0.0, sl = sn + sn;  // 2 cos(l psi), 2 sin(l psi) at l = 0, 1
   for (int l = 1; l <= p; ++l) {
     const int o = l * STRIDE;
-    if (kS || kDsum) {
-      const T tS = rmul(cJ[o], cl);                  // 2 J_l cos(l psi)
-      if (kS) madd(accS, tS, H);
-      if (kDsum) madd(D1, tS, Hm);
-    }
-    if (kDsum) madd(D3, rmul(cL[o], cl), H);
-    if (kD && !kDsum) madd(accD, dcoef(cJ[o + STRIDE], Cc, cL[o], Vc), H);
+    if (kS) madd(accS, rmul(cJ[o], cl), H);          // 2 J_l cos(l psi)
+    if (kD) madd(accD, dcoef(cJ[o + STRIDE], Cc, cL[o], Vc), H);
     if (kG) {
       madd(accA, rmul(cG[o], cl), H);
-      if (kDsum) {
-        madd(GB, rmul(cL[o], sl), H);
-      } else {
-        madd(accB, rmul(cL[o], sl), H);
-      }
+      madd(accB, rmul(cL[o], sl), H);
     }
     if (l < p) {
       const cplx Hn = hrec(s, H, Hm);
@@ -396,7 +474,7 @@ __device__ __forceinline__ void pair_accumulate_w(const KW<T>& kw, const T kk, c
         sp = sl;
         sl = sq;
       }
-      if (kD && !kDsum) {
+      if (kD) {
         const T Cn = fmsub_r(tw, Cc, Cp);
         Cp = Cc;
         Cc = Cn;
@@ -405,12 +483,6 @@ __device__ __forceinline__ void pair_accumulate_w(const KW<T>& kw, const T kk, c
         Vc = Vn;
       }
     }
-  }
-  if (kDsum) {
-    madd(accD, av, lin2(kneg_j0, H1, kk, D1));
-    madd(accD, bv * inv, GB);
-    madd(accD, -av * inv, D3);
-    accB = accB + GB;
   }
 }
 
@@ -538,6 +610,8 @@ k_apply_fused(ApplyArgs a) {
   const T kneg_j0 = rmul(sc_mul(kk, J0), -1.0);  // -k J0 (D)
   T gA0;
   if (kG) gA0 = rmul(colG[0], 2.0);                // -2 J_1 (one-density grad S)
+  const T twoJ0 = rmul(J0, 2.0), khalf = rmul(kk, 0.5);
+  const double ux2 = ux + ux, uy2 = uy + uy;
 
   cplx accS[NR], accD[NR], accA[NR], accB[NR], accX[NR], accY[NR];
 #pragma unroll
@@ -593,8 +667,9 @@ k_apply_fused(ApplyArgs a) {
           pair_direct_w<OPS, T>(kw, kk, r * ux - dx, r * uy - dy, nx, ny, ux, uy, r, s_wd[j], accS[0], accD[0],
                                 accA[0], accB[0]);
         } else {
-          pair_accumulate_w<OPS, T, kApplyThreads>(kw, kk, J0, kneg_j0, gA0, cJ, cL, cG, p, dx, dy, nx, ny, ux,
-                                                    uy, s_wd[j], accS[0], accD[0], accA[0], accB[0]);
+          pair_accumulate_w<OPS, T, kApplyThreads>(kw, kk, J0, kneg_j0, gA0, twoJ0, khalf, cJ, cL, cG, p, dx, dy,
+                                                    nx, ny, ux2, uy2, s_wd[j], accS[0], accD[0], accA[0],
+                                                    accB[0]);
         }
         continue;
       }

@@ -112,10 +112,14 @@ def test_batch_reads_current_densities(cuda):
             assert torch.allclose(second[i][o], first[i][o] * (2.0 - 1.0j), rtol=1e-12, atol=1e-14)
 
 
-def test_batch_full_size_sampled(cuda):
+def test_batch_full_size_every_curve(cuda):
     """The 64-curve workload (16..512 panels, k in (1, 40), p = 10, 32 rhs, S
-    and D) in the benchmark's launch configuration: every curve against the
-    per-curve apply, and three curves against the oracle on sampled targets."""
+    and D, interior) in the benchmark's launch configuration (tuned): every
+    curve against the per-curve apply at every target, and every curve against
+    the oracle at 48 targets (both ends and 46 seeded ones), all 32 rhs, per
+    output array.  Every interior centre of these curves is admissible
+    (closest source at distance >= r), the condition under which the Graf
+    sums' rounding stays at the 1e-11 level."""
     bw = W.cfg3()
     insts = bw.instances()
     Mmax = max(M for _, M, _ in insts)
@@ -127,19 +131,22 @@ def test_batch_full_size_sampled(cuda):
     out = batch.apply()
     batch.status()
     for i, g in enumerate(geoms):
+        assert g["ctr_ratio"][:g.n_tgt].min().item() >= 1.0, i
         ref = qbx.qbx_apply_ops(plan, g, (0, 1), qbx.SIDE_INT, 0, insts[i][2], bw.p, dens[i])
         for o in (0, 1):
             assert (torch.abs(out[i][o] - ref[o]).max() / torch.abs(ref[o]).max()).item() < 1e-12
-    order = np.argsort([M for _, M, _ in insts])
     rng = np.random.default_rng(9)
-    for i in (order[0], order[len(order) // 2], order[-1]):
-        c, M, k = insts[i]
+    worst = 0.0
+    for i, (c, M, k) in enumerate(insts):
         go = oracle.geometry(c, c.edges(M), 16, 64)
-        sel = np.unique(np.concatenate([[0, go["n_tgt"] - 1], rng.integers(0, go["n_tgt"], 2)]))
+        sel = np.unique(np.concatenate([[0, go["n_tgt"] - 1], rng.integers(0, go["n_tgt"], 46)]))
         d = bw.dens(i, go["n_tgt"])
         for o in (0, 1):
             ref = oracle.apply(go, o, oracle.SIDE_INT, 0, k, bw.p, d, sel=sel)
-            assert rel(out[i][o].cpu().numpy()[sel], ref) < TOL, (i, o)
+            e = rel(out[i][o].cpu().numpy()[sel], ref)
+            worst = max(worst, e)
+            assert e < TOL, (i, M, k, o, e)
+    print(f"batch of 64 curves: largest relative difference from the oracle {worst:.2e}")
 
 
 @pytest.mark.parametrize("nrhs", [12, 3])

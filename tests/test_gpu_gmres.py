@@ -46,7 +46,7 @@ def test_gmres_residual_under_oracle_operator(cuda):
     r = 0.5 * mu + D - 1j * eta * S - f
     sw = np.sqrt(go["tgt_w"])[:, None]
     rel = np.linalg.norm(sw * r, axis=0) / np.linalg.norm(sw * f, axis=0)
-    assert np.all(rel <= 1.1e-10 * 2), rel
+    assert np.all(rel <= 1.1e-10), rel
 
 
 def test_gmres_point_source_field_outside(cuda):
@@ -72,8 +72,12 @@ def test_gmres_full_size_teardrop(cuda):
     """The scattering solve at full size: the paper's teardrop with 1008
     panels and 8 dyadic levels on each side of the corner (1024 panels,
     16384 targets, 65536 sources), k = 30, p = 14, eta = k, four of the 64
-    plane waves; GMRES to 1e-10, then the residual recomputed by the oracle
-    at 16 sampled targets."""
+    plane waves; GMRES to 1e-10, then the residual recomputed by the oracle's
+    operator in the sqrt-weighted 2-norm the unknowns live in (Sec. 4.2),
+    <= 1.1e-10 per rhs.  The norm is taken on a stratified sample: every
+    target of the 18 refined corner panels (288) exactly, and every 32nd
+    target of the other 1006 panels (503) with weight 32 (the sample's
+    share of those targets), against the norm of f over all targets."""
     k, p = 30.0, 14
     cur = W.teardrop()
     edges = W.dyadic_edges(1008, 8)
@@ -87,12 +91,26 @@ def test_gmres_full_size_teardrop(cuda):
     mu, its, res = qbx.qbx_solve_exterior_dirichlet(plan, g, k, k, p, dev(f), tol=1e-10, restart=60, maxiter=300)
     assert np.all(res <= 1e-10) and its < 100
     go = oracle.geometry(cur, edges, 16, 64)
-    sel = np.arange(7, g.n_tgt, 1024)
+    n, q = go["n_tgt"], 16
+    corner = np.concatenate([np.arange(0, 9 * q), np.arange(n - 9 * q, n)])   # 9 refined panels per side
+    bulk = np.arange(9 * q, n - 9 * q)
+    samp = bulk[7::32]
+    sel = np.concatenate([corner, samp])
     mu_h = mu.cpu().numpy()
     S = oracle.apply(go, oracle.OP_S, oracle.SIDE_TWO, 0, k, p, mu_h, sel=sel)
     D = oracle.apply(go, oracle.OP_D, oracle.SIDE_TWO, 0, k, p, mu_h, sel=sel)
     r = 0.5 * mu_h[sel] + D - 1j * k * S - f[sel]
-    assert np.abs(r).max() / np.abs(f).max() < 1e-8
+    w = go["tgt_w"]
+    wsel = np.concatenate([w[corner], w[samp] * (len(bulk) / len(samp))])
+    num = np.sqrt((wsel[:, None] * np.abs(r) ** 2).sum(0))
+    den = np.sqrt((w[:, None] * np.abs(f) ** 2).sum(0))
+    rel = num / den
+    pw_bulk = np.abs(r[len(corner):]).max() / np.abs(f).max()
+    pw_corner = np.abs(r[:len(corner)]).max() / np.abs(f).max()
+    print(f"full-size solve: {its} iterations, oracle residual (sqrt-weighted) {rel.max():.2e}, "
+          f"pointwise {pw_bulk:.2e} (bulk sample), {pw_corner:.2e} (corner panels)")
+    assert np.all(rel <= 1.1e-10), rel
+    assert pw_bulk < 1e-8
 
 
 @pytest.mark.parametrize("k", [5.0, 3 + 0.4j])

@@ -86,3 +86,10 @@ def test_bench_json_parts_serialise_for_real_and_complex_k():
     assert abs(hw["frac"] - hw["achieved"] / bench.FP64_PEAK_GFLOPS) < 1e-12
     assert hw["fp64_pipe_busy"]["of_elapsed_cycles"] == 0.85
     assert bench.hw_roofline(None, 1, 1.0) is None
+
+
+def test_bench_spread_of_alternating_arms():
+    """The batched comparison's statistics: median (mean of the middle two for
+    an even count), min, max and sample count."""
+    assert bench.spread([3.0, 1.0, 2.0]) == {"median": 2.0, "min": 1.0, "max": 3.0, "samples": 3}
+    assert bench.spread([4.0, 1.0, 3.0, 2.0])["median"] == 2.5

@@ -23,8 +23,7 @@ QBX_ENONFINITE = 4
 
 
 def rel(a, b):
-    a = a.detach().cpu().numpy() if torch.is_tensor(a) else np.asarray(a)
-    b = np.asarray(b)
+    a, b = (x.detach().cpu().numpy() if torch.is_tensor(x) else np.asarray(x) for x in (a, b))
     return np.abs(a - b).max() / np.abs(b).max()
 
 
