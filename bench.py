@@ -659,6 +659,7 @@ def run_solve(args):
         asm_ms_calls.append(e0.elapsed_time(e1))
     asm_solve_ms = asm_ms_calls[-1]
     mu_diff = (torch.abs(mu_a - mu).max() / torch.abs(mu).max()).item()
+    prod_ms = time_matmul(torch, qbx, A, f, 3)["own_ms"]
     del A
     # the residual recomputed by one more apply of both operators to mu: in
     # GMRES's norm (sqrt-weighted 2-norm per rhs, relative to f) and pointwise
@@ -684,8 +685,68 @@ def run_solve(args):
                           "first_solve_call_s": asm_ms_calls[0] * 1e-3, "matvecs": its_a,
                           "max_resid": float(np.max(res_a)), "max_rel_diff_vs_matrix_free": mu_diff,
                           "matrix_bytes": 16 * g.n_tgt * g.n_tgt,
-                          "call": "qbx_assemble_cfie + qbx_solve_exterior_dirichlet_assembled (cuBLAS ZGEMM3M)"},
+                          "product_ms": prod_ms,
+                          "outside_products_s": asm_solve_ms * 1e-3 - (its_a + 2) * prod_ms * 1e-3,
+                          "outside_products_note": "solve time less (matvecs + restart residuals) x one product: "
+                                                   "Arnoldi kernels, launches and the one host wait per cycle",
+                          "call": "qbx_assemble_cfie + qbx_solve_exterior_dirichlet_assembled (qbx_matmul_cm "
+                                  "products; one Arnoldi step as a CUDA graph, Givens and residual tests on the "
+                                  "device)"},
             "clocks": clk}
+    print(json.dumps(line))
+    return 0
+
+
+def time_matmul(torch, qbx, A, x, reps, library=False):
+    """qbx_matmul_cm on the column-major matrix A ([n][n] tensor, A(i, j) at
+    [j][i]) and x [n][nrhs]: mean time of `reps` calls after a warm-up call
+    (CUDA events); with library=True also torch's complex matmul of the same
+    product (cuBLAS ZGEMM), as the library reference."""
+    n = A.shape[0]
+    work = torch.empty(max(qbx.lib().qbx_matmul_cm_work_bytes(n, x.shape[1]), 16), dtype=torch.uint8, device="cuda")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    y = qbx.qbx_matmul_cm(A, x, work)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        y = qbx.qbx_matmul_cm(A, x, work)
+    e1.record()
+    e1.synchronize()
+    out = {"own_ms": e0.elapsed_time(e1) / reps}
+    if library:
+        ref = A.T @ x
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            ref = A.T @ x
+        e1.record()
+        e1.synchronize()
+        out["library_ms"] = e0.elapsed_time(e1) / reps
+        out["max_rel_diff_vs_library"] = ((y - ref).abs().max() / ref.abs().max()).item()
+    return out
+
+
+def run_matmul(args):
+    """The assembled solve's product alone: y = A x, A a seeded random complex
+    n x n matrix (column-major), x n x 64, by qbx_matmul_cm (FP64, three real
+    products per complex multiply-add) and by torch's matmul (cuBLAS ZGEMM)
+    for reference.  Prints one JSON line (not the benchmark metric)."""
+    import torch
+    import paper_1207_4461_gb300 as qbx
+    torch.cuda.set_device(0)
+    n, nrhs = args.matmul_n, 64
+    g = torch.Generator(device="cuda").manual_seed(7)
+    A = torch.randn((n, n), dtype=torch.complex128, device="cuda", generator=g)
+    x = torch.randn((n, nrhs), dtype=torch.complex128, device="cuda", generator=g)
+    clocks = ClockSampler(0)
+    clocks.start()
+    t = time_matmul(torch, qbx, A, x, args.steps, library=True)
+    clk = clocks.stop()
+    flops = 3 * 2 * n * n * nrhs   # three real products per complex multiply-add
+    line = {"matmul": f"y = A x, A {n} x {n} complex (column-major), x {n} x {nrhs}, FP64", "n": n, "nrhs": nrhs,
+            "steps": args.steps, **t, "own_gflops": flops / (t["own_ms"] * 1e-3) / 1e9,
+            "own_frac_of_fp64_peak": flops / (t["own_ms"] * 1e-3) / 1e9 / FP64_PEAK_GFLOPS,
+            "flops_model": "3 real products x 2 flops per complex multiply-add", "clocks": clk}
     print(json.dumps(line))
     return 0
 
@@ -936,9 +997,13 @@ def main():
                     help="panels equispaced in t before the 2 x 8 corner bisections (profiling: smaller)")
     ap.add_argument("--assemble-only", action="store_true",
                     help="profiling only: with --solve, time the matrix assembly alone")
+    ap.add_argument("--matmul", action="store_true", help="the assembled solve's matrix product alone")
+    ap.add_argument("--matmul-n", type=int, default=16384)
     ap.add_argument("--solve-restart", type=int, default=60)
     ap.add_argument("--solve-maxiter", type=int, default=400)
     args = ap.parse_args()
+    if args.matmul:
+        return run_matmul(args)
     if args.solve:
         return run_solve(args)
     if args.adjoint:

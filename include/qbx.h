@@ -313,8 +313,10 @@ size_t qbx_shape_adjoint_workspace_bytes(int M, int q_tgt, int q_src, int p, int
  * clusters at zero), unknowns scaled by sqrt(w) (Sec. 4.2), by restarted
  * GMRES(restart) for nrhs right-hand sides f [n_tgt][nrhs] at once (every
  * system its own Krylov space; one S+D apply per iteration serves all).
- * Arnoldi by classical Gram-Schmidt with re-orthogonalisation on the device;
- * Givens rotations on the host.  mu [n_tgt][nrhs]: initial guess in,
+ * Arnoldi by classical Gram-Schmidt with re-orthogonalisation, the Givens
+ * rotations, the residual estimates, the convergence test and the
+ * back-substitution all run on the device; the host waits once per restart
+ * cycle (and, matrix-free, once per iteration, each a full QBX apply).  mu [n_tgt][nrhs]: initial guess in,
  * solution out.  Stops when every relative residual ||f - A mu||/||f|| (in
  * the sqrt-weighted norm, GMRES estimate) is below tol, or after maxiter
  * matvecs (QBX_ENOCONV).  iters (host, may be NULL) receives the matvec
@@ -354,15 +356,30 @@ int qbx_vec_combine(int n, int nrhs, int nv, const qbx_c64 *V, const qbx_c64 *y,
  * the truncated Graf sums against every source node carried back to the
  * target grid by the per-panel interpolation.  q_tgt <= 16.  Async on
  * stream.  qbx_solve_exterior_dirichlet_assembled then runs the same GMRES
- * with one complex GEMM (cuBLAS ZGEMM3M) per iteration for all right-hand
- * sides; k, eta and p are those the matrix was assembled with.  Its first
- * call on a plan creates the plan's cuBLAS handle (freed by
- * qbx_plan_destroy). */
+ * with one complex matrix product (qbx_matmul_cm) per iteration for all
+ * right-hand sides, one Arnoldi step captured as a CUDA graph and launched
+ * up to `restart` times per cycle without a host wait (steps after
+ * convergence do nothing); k, eta and p are those the matrix was assembled
+ * with. */
 int qbx_assemble_cfie(qbx_plan *plan, const qbx_geom *g, qbx_c64 k, qbx_c64 eta, int p, qbx_c64 *A,
                       void *stream);
 int qbx_solve_exterior_dirichlet_assembled(qbx_plan *plan, const qbx_geom *g, const qbx_c64 *A,
                                            const qbx_c64 *f, int nrhs, double tol, int restart, int maxiter,
                                            qbx_c64 *mu, int *iters, double *resid, void *stream);
+
+/* y = A x for a column-major n x n complex matrix A (entry (i, j) at
+ * A[j n + i]; the layout qbx_assemble_cfie writes) and nrhs vectors x, y
+ * [n][nrhs] (device, caller-owned; y must not overlap A or x), in FP64 with
+ * three real products per complex multiply-add (Re A Re x, Im A Im x and
+ * (Re A + Im A)(Re x + Im x)).  The paper's Sec. 3.3 notes that the discrete
+ * operator may be stored; this applies it.  work: device array of at least
+ * qbx_matmul_cm_work_bytes(n, nrhs) bytes (split partial sums, added in a
+ * fixed order: the result does not depend on timing).  Async on stream;
+ * QBX_EINVAL on bad sizes or NULL pointers, QBX_ENOMEM when work is too
+ * small.  qbx_matmul_cm_work_bytes queries the current device (host call). */
+int qbx_matmul_cm(int n, int nrhs, const qbx_c64 *A, const qbx_c64 *x, qbx_c64 *y, void *work,
+                  size_t work_bytes, void *stream);
+size_t qbx_matmul_cm_work_bytes(int n, int nrhs);
 
 /* Batched apply: many curves, each with its own panels, wavenumber and nrhs
  * densities, in one persistent launch run as a CUDA graph (the paper's cost

@@ -18,7 +18,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libqbx_gb300.so")
 SOURCES = ["qbx_apply_real.cu", "qbx_apply_cplx.cu", "qbx_apply_local.cu", "qbx_far.cu", "qbx_misc.cu", "qbx_capi.cu", "qbx_batch.cu",
            "qbx_adjoint.cu", "qbx_gmres.cu", "qbx_shape.cu", "qbx_assemble.cu",
-           "qbx_static.cu", "qbx_grad_d.cu", "qbx_hk_table.cu"]
+           "qbx_static.cu", "qbx_grad_d.cu", "qbx_hk_table.cu", "qbx_zgemm.cu"]
 HEADERS = ["qbx_device.cuh", "qbx_internal.h", "special_tables.h", "qbx_apply_impl.cuh",
            "qbx_group_impl.cuh", "qbx_adjoint_impl.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -68,7 +68,7 @@ def build(force: bool = False, verbose_ptx: bool = False, quiet: bool = True) ->
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nv] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart", "-lcublas"]
+    cmd = [nv] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

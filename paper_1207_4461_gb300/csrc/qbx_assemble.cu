@@ -16,7 +16,6 @@
 // matrix is stored column-major
 // (entry (t, t') at t' n + t), so a warp writes 32 consecutive rows of one
 // column at a time.
-#include <cublas_v2.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdio.h>

@@ -1,7 +1,6 @@
 // qbx_capi.cu -- host side of the C ABI declared in include/qbx.h: plans,
 // the Gauss-Legendre rule, the per-panel interpolation matrix, argument
 // checks and the launch sequence of each call.
-#include <cublas_v2.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdarg.h>
@@ -32,7 +31,6 @@ struct qbx_plan {
   // waves of resident CTAs the split choice aims for (qbx_plan_set_min_waves)
   int min_waves = 1;
   // cuBLAS handle of the assembled-matrix solve, created on first use
-  cublasHandle_t blas = nullptr;
   // H0/H1 amplitude table of the ray z = k rho for the last complex k
   // (tab_kim = 0: none made yet)
   double* d_hk_tab;
@@ -223,15 +221,6 @@ void host_plan_info(const qbx_plan* plan, int* device, int* q_tgt, int* q_src, c
   *interp = plan->d_interp;
 }
 
-void* host_plan_blas(qbx_plan* plan) {
-  if (!plan->blas) {
-    if (cudaSetDevice(plan->device) != cudaSuccess) return nullptr;
-    cublasHandle_t h = nullptr;
-    if (cublasCreate(&h) != CUBLAS_STATUS_SUCCESS) return nullptr;
-    plan->blas = h;
-  }
-  return plan->blas;
-}
 
 // The plan's amplitude table for complex k (made on `st` when k changes;
 // later calls on the plan's streams see it in stream order), or null for real k.
@@ -362,7 +351,6 @@ int qbx_plan_destroy(qbx_plan* p) {
   cudaSetDevice(p->device);
   if (p->ev0) cudaEventDestroy(p->ev0);
   if (p->ev1) cudaEventDestroy(p->ev1);
-  if (p->blas) cublasDestroy(p->blas);
   cudaFree(p->d_interp);
   cudaFree(p->d_wgl_tgt);
   cudaFree(p->d_wgl_src);

@@ -154,8 +154,10 @@ int host_choose_split_waves(int num_sms, int occ, int n_units, int n_src, size_t
 int host_split_len(int n_src, int ns);
 int host_fail(int code, const char* msg);   // sets qbx_last_error(), returns code
 void host_plan_info(const qbx_plan* plan, int* device, int* q_tgt, int* q_src, const double** interp);
-// The plan's cuBLAS handle (a cublasHandle_t), created on first use; NULL on failure.
-void* host_plan_blas(qbx_plan* plan);
+// y = A x for a column-major n x n matrix (qbx_matmul_cm); with gate, every
+// kernel returns at once while *gate (device) is 0.
+int matmul_cm_gated(int n, int nrhs, const qbx_c64* A, const qbx_c64* x, qbx_c64* y, void* work,
+                    size_t work_bytes, const int* gate, void* stream);
 
 }  // namespace qbx
 

@@ -121,6 +121,10 @@ def lib():
             L.qbx_shape_adjoint_workspace_bytes.restype = ctypes.c_size_t
             L.qbx_apply_static.argtypes = [G, I, I, I, c64, I, _P, I, _P, _P]
             L.qbx_apply_static.restype = I
+            L.qbx_matmul_cm.argtypes = [I, I, _P, _P, _P, _P, ctypes.c_size_t, _P]
+            L.qbx_matmul_cm.restype = I
+            L.qbx_matmul_cm_work_bytes.argtypes = [I, I]
+            L.qbx_matmul_cm_work_bytes.restype = ctypes.c_size_t
             L.qbx_apply_static_status.argtypes = [_P]
             L.qbx_apply_static_status.restype = I
             L.qbx_vec_dots.argtypes = [I, I, I, _P, _P, _P, _P, _P]
@@ -469,7 +473,8 @@ def qbx_solve_exterior_dirichlet(plan: Plan, g: Geometry, k, eta, p, f, tol=1e-1
                                  mu0=None, raise_on_noconv=True, A=None):
     """GMRES for (1/2 + D - i eta S) mu = f (two-sided D and S, sqrt-weight
     unknowns).  Returns (mu, matvecs, relative residuals).  With A (from
-    qbx_assemble_cfie with the same k, eta, p) every matvec is one ZGEMM."""
+    qbx_assemble_cfie with the same k, eta, p) every matvec is one complex
+    matrix product (qbx_matmul_cm)."""
     ff = _dens2d(f, g.n_tgt)
     nrhs = ff.shape[1]
     mu = torch.zeros_like(ff) if mu0 is None else _dens2d(mu0, g.n_tgt).clone()
@@ -488,6 +493,22 @@ def qbx_solve_exterior_dirichlet(plan: Plan, g: Geometry, k, eta, p, f, tol=1e-1
 
 
 OPS_S, OPS_D, OPS_GRAD_S = 1, 2, 4
+
+
+def qbx_matmul_cm(A, x, work=None):
+    """y = A x for the column-major n x n matrix A (a tensor [n][n] holding
+    A(i, j) at [j][i], the layout of qbx_assemble_cfie) and x [n][nrhs]
+    (complex128 on the device), by the library's FP64 kernel."""
+    n = A.shape[0]
+    xx = _dens2d(x, n)
+    nrhs = xx.shape[1]
+    wb = lib().qbx_matmul_cm_work_bytes(n, nrhs)
+    if work is None:
+        work = torch.empty(max(wb, 16), dtype=torch.uint8, device=xx.device)
+    y = torch.empty_like(xx)
+    _check(lib().qbx_matmul_cm(n, nrhs, _ptr(A.contiguous()), _ptr(xx), _ptr(y), _ptr(work), work.numel(),
+                               _stream()))
+    return y
 
 
 def qbx_vec_dots(V, w):

@@ -135,7 +135,7 @@ def test_assembled_matrix_matches_oracle(cuda, k):
 
 
 def test_assembled_solve_matches_matrix_free(cuda):
-    """GMRES with ZGEMM matvecs on the assembled matrix reaches the same
+    """GMRES with the library's matrix products on the assembled matrix reaches the same
     solution as the matrix-free solve and the oracle's residual bound."""
     cur, edges, plan, g, go, k, p = setup()
     eta = k
@@ -174,3 +174,22 @@ def test_krylov_vector_kernels(cuda, n, nrhs, nv):
     assert (w2 - (w - torch.einsum("jir,jr->ir", V, h))).abs().max().item() <= 1e-12 * w.abs().max().item() * nv
     x = qbx.qbx_vec_combine(V, h, w.clone())
     assert (x - (w + torch.einsum("jir,jr->ir", V, h))).abs().max().item() <= 1e-12 * w.abs().max().item() * nv
+
+
+@pytest.mark.parametrize("n,nrhs", [(1000, 3), (777, 64), (2048, 17), (64, 1), (130, 100), (16, 16)])
+def test_matmul_cm_matches_torch(cuda, n, nrhs):
+    """qbx_matmul_cm (the assembled solve's product, three real products per
+    complex multiply-add, split partial sums in a fixed order) against
+    torch's complex matmul at ragged sizes: below, at and above a tile of 64
+    rows and of 16 / 64 rhs; two calls agree bit for bit."""
+    g = torch.Generator(device="cpu").manual_seed(n * 131 + nrhs)
+    Mt = torch.randn((n, n), dtype=torch.complex128, generator=g).cuda()   # Mt[j][i] = A(i, j)
+    x = torch.randn((n, nrhs), dtype=torch.complex128, generator=g).cuda()
+    y = qbx.qbx_matmul_cm(Mt, x)
+    ref = Mt.T @ x
+    assert ((y - ref).abs().max() / ref.abs().max()).item() < 1e-14 * max(1.0, n ** 0.5)
+    assert torch.equal(y, qbx.qbx_matmul_cm(Mt, x))
+    small = torch.empty(16, dtype=torch.uint8, device="cuda")
+    if qbx.lib().qbx_matmul_cm_work_bytes(n, nrhs) > 16:
+        with pytest.raises(qbx.QBXError):
+            qbx.qbx_matmul_cm(Mt, x, work=small)

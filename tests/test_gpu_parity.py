@@ -274,7 +274,8 @@ def test_apply_full_size_complex_k(cuda):
         ref = oracle.apply(go, op, oracle.SIDE_TWO, 0, k, wl.p, dens, sel=sel)
         assert rel(together[op].cpu().numpy()[sel], ref) < TOL, op
         alone = qbx.qbx_apply(plan, g, op, qbx.SIDE_TWO, 0, k, wl.p, dev(dens))
-        assert rel(together[op], alone.cpu().numpy()) < 1e-13
+        # (complex J_l and recurrences: the two kernels' rounding differs more than at real k)
+        assert rel(together[op], alone.cpu().numpy()) < 1e-12
     qbx.qbx_sync_status(plan)
 
 
