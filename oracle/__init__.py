@@ -136,13 +136,15 @@ def panel_nodes(t_edges, q):
     return (0.5 * (a + b)[:, None] + 0.5 * (b - a)[:, None] * x[None, :]).reshape(-1)
 
 
-RADIUS_H, RADIUS_SQRT_H = 0, 1
+RADIUS_H, RADIUS_SQRT_H, RADIUS_ADMISSIBLE = 0, 1, 2
 
 
 def geometry(curve, t_edges, q_tgt: int, q_src: int, r_factor: float = 0.5, rule: int = RADIUS_H):
     """Discretise `curve` (callable t -> (gamma [n,2], dgamma [n,2])) on panels
     with edges t_edges; Sec. 3.3 step 4a geometry and centres, with
-    r = r_factor h (rule 0) or r = r_factor sqrt(h) (rule 1, Sec. 3.1)."""
+    r = r_factor h (rule 0), r = r_factor sqrt(h) (rule 1, Sec. 3.1), or
+    r = r_factor h lowered per centre to the largest radius whose disk holds
+    no source node (rule 2, a departure from step 4a for sharp corners)."""
     t_edges = _f64(t_edges)
     M = t_edges.size - 1
     tt = panel_nodes(t_edges, q_tgt)

@@ -293,6 +293,12 @@ void orc_besselj_seq_array(int n, const double *zin, int nmax, double *jout)
 /*   r_m = r_factor sqrt(h_m): r refined more slowly than h, the classically    */
 /*   convergent choice of the remarks after eq. error_anal (Sec. 3.1)           */
 /*   c   = x - r_m n (interior side), x + r_m n (exterior side)  (step 4a)    */
+/*   rule 2 (a departure from step 4a, for corners of 90 degrees or less):   */
+/*   each centre's radius r_m is lowered to the largest r whose disk holds   */
+/*   no source node, |x_s - c| >= r for all s.  With d = x_s - x, the        */
+/*   interior condition |d + r n|^2 >= r^2 reads |d|^2 + 2 r (d.n) >= 0, a   */
+/*   bound r <= |d|^2 / (-2 d.n) for every source with d.n < 0 (exterior:   */
+/*   r <= |d|^2 / (2 d.n) where d.n > 0).                                    */
 /*   ratio = min_s |x_s - c| / r_m  (Graf validity, eq. x-c-closest)          */
 /* Centre arrays have length 2*n_tgt: interior centres first, then exterior.  */
 /* ------------------------------------------------------------------------- */
@@ -341,6 +347,25 @@ int orc_geometry(int M, int q_tgt, int q_src, const double *t_edges,
             ctr_x[n_tgt + t] = tgt_x[t] + r * tgt_nx[t];
             ctr_y[n_tgt + t] = tgt_y[t] + r * tgt_ny[t];
             ctr_r[n_tgt + t] = r;
+        }
+    }
+    if (rule == 2) {
+        #pragma omp parallel for schedule(static)
+        for (int c = 0; c < 2 * n_tgt; ++c) {
+            int t = c % n_tgt;
+            double sg = c < n_tgt ? -1.0 : 1.0;      /* c = x + sg r n */
+            double r = ctr_r[c];
+            for (int s = 0; s < n_src; ++s) {
+                double dx = src_x[s] - tgt_x[t], dy = src_y[s] - tgt_y[t];
+                double a = sg * (dx * tgt_nx[t] + dy * tgt_ny[t]);   /* -d.n interior, d.n exterior */
+                if (a > 0.0) {
+                    double bound = (dx * dx + dy * dy) / (2.0 * a);
+                    if (bound < r) r = bound;
+                }
+            }
+            ctr_r[c] = r;
+            ctr_x[c] = tgt_x[t] + sg * r * tgt_nx[t];
+            ctr_y[c] = tgt_y[t] + sg * r * tgt_ny[t];
         }
     }
     #pragma omp parallel for schedule(static)
