@@ -69,24 +69,24 @@ def flops_per_pair_ops(ops, p, nrhs=1):
 # on the full-size starfish workload, from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum); valid only for the kernel
 # sources it was taken with, identified by their hash.
-TRAFFIC = {"7e064da1b8dcfcd2": 1.61e6}   # profiles/k_apply_fused_S_D_gradS_starfish_M256_dram.md
+TRAFFIC = {"9192ae8281d1a5d2": 1.648e6}   # profiles/k_apply_fused_S_D_gradS_starfish_M256_dram.md
 KERNEL_SOURCES = ["qbx_apply_impl.cuh", "qbx_device.cuh", "special_tables.h", "qbx_apply_real.cu"]
 GROUP_SOURCES = ["qbx_group_impl.cuh", "qbx_apply_impl.cuh", "qbx_device.cuh", "special_tables.h"]
 # Hardware-counted FP64 operations per (centre, source) pair, 2 DFMA + DMUL +
 # DADD from ncu's smsp__sass_thread_inst_executed_op_{dfma,dmul,dadd}_pred_on
 # counters divided by the pairs of the captured launch, for the kernel
 # sources with the given hash (profiles/*_fp64_counts.md).
-HW_FP64_PER_PAIR = {"7e064da1b8dcfcd2": 543.7}         # fused S + D + grad S, p = 12, one rhs
+HW_FP64_PER_PAIR = {"9192ae8281d1a5d2": 495.7}         # fused S + D + grad S, p = 12, one rhs
 HW_FP64_PER_PAIR_GROUP = {"58788bd53b242af9": 756.0}   # group kernel, S + D, p = 10, 32 rhs
 # sm__pipe_fp64_cycles_active (of peak) over the active and the elapsed
 # cycles, from the same captures (fused: 128-panel starfish, one wave;
 # group: the first 4 curves of the batch)
-HW_FP64_PIPE = {"7e064da1b8dcfcd2": (0.922, 0.891)}
+HW_FP64_PIPE = {"9192ae8281d1a5d2": (0.924, 0.870)}
 HW_FP64_PIPE_GROUP = {"58788bd53b242af9": (0.949, 0.925)}
 # the fused S + D + grad S apply at the complex wavenumber 20 + 1i (same
 # capture set-up: 128-panel starfish, p = 12, one rhs)
-HW_FP64_PER_PAIR_CPLX = {}
-HW_FP64_PIPE_CPLX = {}
+HW_FP64_PER_PAIR_CPLX = {"9192ae8281d1a5d2": 855.8}
+HW_FP64_PIPE_CPLX = {"9192ae8281d1a5d2": (0.928, 0.810)}
 
 
 def source_hash(names=KERNEL_SOURCES):
@@ -595,11 +595,14 @@ def run_solve(args):
     import paper_1207_4461_gb300 as qbx
     torch.cuda.set_device(0)
     k, p, nrhs, m_base, levels = 30.0, 14, 64, args.solve_base, 8
-    cur = W.teardrop()
+    # the paper's teardrop (about 115 degrees), or the right-angle one with the
+    # admissible radius (r = h/2 lowered where a source enters the disk)
+    cur = W.teardrop(args.corner90)
     edges = W.dyadic_edges(m_base, levels)
     M = len(edges) - 1
     plan = qbx.Plan(16, 64, n_src=64 * M, n_ctr=32 * M, ncoef=2, nrhs=nrhs)
-    g = qbx.qbx_geometry(plan, cur, edges)
+    rule = qbx.RADIUS_ADMISSIBLE if args.corner90 else qbx.RADIUS_H
+    g = qbx.qbx_geometry(plan, cur, edges, rule=rule)
     if args.assemble_only:   # the assembly kernel alone (profiling), after one warm-up call
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         A = qbx.qbx_assemble_cfie(plan, g, k, k, p)
@@ -672,7 +675,9 @@ def run_solve(args):
     resid_w = (torch.linalg.norm(sw * r, dim=0) / torch.linalg.norm(sw * f, dim=0)).max().item()
     resid_apply = (torch.abs(r).max() / torch.abs(f).max()).item()
     pairs = 2 * g.n_tgt * g.n_src
-    line = {"solve": f"exterior sound-soft, paper's teardrop, {m_base}+16 panels (dyadic toward the corner), "
+    curve_name = ("teardrop with a 90-degree corner, admissible radius (r = h/2 lowered to the largest "
+                  "source-free disk)" if args.corner90 else "paper's teardrop (2 atan(pi/2), about 115 degrees)")
+    line = {"solve": f"exterior sound-soft, {curve_name}, {m_base}+16 panels (dyadic toward the corner), "
                      "k=30, p=14, eta=k, 64 plane waves, two-sided D and S, GMRES on the device",
             "n_tgt": g.n_tgt, "n_src": g.n_src, "n_ctr": 2 * g.n_tgt, "nrhs": nrhs,
             "restart": args.solve_restart, "tol": 1e-10, "matvecs": its,
@@ -997,6 +1002,8 @@ def main():
                     help="panels equispaced in t before the 2 x 8 corner bisections (profiling: smaller)")
     ap.add_argument("--assemble-only", action="store_true",
                     help="profiling only: with --solve, time the matrix assembly alone")
+    ap.add_argument("--corner90", action="store_true",
+                    help="with --solve: the teardrop with a 90-degree corner and the admissible radius rule")
     ap.add_argument("--matmul", action="store_true", help="the assembled solve's matrix product alone")
     ap.add_argument("--matmul-n", type=int, default=16384)
     ap.add_argument("--solve-restart", type=int, default=60)

@@ -165,8 +165,15 @@ int qbx_geometry(qbx_plan *plan, qbx_geom *g, const double *t_edges,
  * r = r_factor * panel_h (as qbx_geometry), QBX_RADIUS_SQRT_H gives
  * r = r_factor * sqrt(panel_h): r refined more slowly than h, which makes
  * QBX classically convergent without source oversampling (the remarks after
- * eq. error_anal, Sec. 3.1).  QBX_EINVAL for another rule. */
-enum { QBX_RADIUS_H = 0, QBX_RADIUS_SQRT_H = 1 };
+ * eq. error_anal, Sec. 3.1).  QBX_RADIUS_ADMISSIBLE starts from
+ * r = r_factor * panel_h and lowers each centre's radius to the largest one
+ * whose disk holds no source node (|x_s - c| >= r for every s; closed form
+ * r <= |d|^2 / (2 |d.n|) per source, d = x_s - x, on the centre's side of
+ * the tangent): a departure from Sec. 3.3 step 4a for corners of 90 degrees
+ * or less, where the r = h/2 centres of the targets next to the corner lie
+ * on the opposite arm whatever the refinement; the radius then varies within
+ * a panel (ctr_r holds it per centre).  QBX_EINVAL for another rule. */
+enum { QBX_RADIUS_H = 0, QBX_RADIUS_SQRT_H = 1, QBX_RADIUS_ADMISSIBLE = 2 };
 int qbx_geometry_rule(qbx_plan *plan, qbx_geom *g, const double *t_edges,
                       const double *gam_tgt, const double *dgam_tgt,
                       const double *gam_src, const double *dgam_src,

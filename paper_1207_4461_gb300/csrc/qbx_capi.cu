@@ -413,7 +413,8 @@ int qbx_geometry_rule(qbx_plan* p, qbx_geom* g, const double* t_edges, const dou
   if (!g->panel_h || !g->ctr_ratio || !g->src_w || !g->tgt_w) return fail(QBX_EINVAL, "geometry: NULL output");
   if (!t_edges || !gam_tgt || !dgam_tgt || !gam_src || !dgam_src) return fail(QBX_EINVAL, "NULL curve samples");
   if (!(r_factor > 0.0) || !isfinite(r_factor)) return fail(QBX_EINVAL, "r_factor must be > 0");
-  if (rule != QBX_RADIUS_H && rule != QBX_RADIUS_SQRT_H) return fail(QBX_EINVAL, "bad radius rule %d", rule);
+  if (rule != QBX_RADIUS_H && rule != QBX_RADIUS_SQRT_H && rule != QBX_RADIUS_ADMISSIBLE)
+    return fail(QBX_EINVAL, "bad radius rule %d", rule);
   CK(cudaSetDevice(p->device), "cudaSetDevice");
   CK(launch_geometry(g->M, g->q_tgt, g->q_src, t_edges, gam_tgt, dgam_tgt, gam_src, dgam_src,
                      p->d_wgl_tgt, p->d_wgl_src, r_factor, rule, *g, (cudaStream_t)stream),

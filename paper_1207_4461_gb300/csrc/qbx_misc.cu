@@ -53,6 +53,41 @@ __global__ void k_centres(int n_tgt, int q_tgt, double r_factor, int rule, const
   cr[n_tgt + t] = r;
 }
 
+// Radius rule QBX_RADIUS_ADMISSIBLE (a departure from Sec. 3.3 step 4a for
+// corners of 90 degrees or less): each centre's radius lowered to the largest
+// r whose disk holds no source node.  With d = x_s - x and c = x + sg r n,
+// |d - sg r n|^2 >= r^2 reads |d|^2 - 2 sg r (d.n) >= 0: a bound
+// r <= |d|^2 / (2 sg d.n) for every source with sg d.n > 0.
+__global__ void k_cap_radius(int n_tgt, const double* tx, const double* ty, const double* tnx, const double* tny,
+                             int n_src, const double* sx, const double* sy, double* cx, double* cy, double* cr) {
+  __shared__ double bx[256], by[256];
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int cc = c < 2 * n_tgt ? c : 2 * n_tgt - 1;
+  const int t = cc % n_tgt;
+  const double sg = cc < n_tgt ? -1.0 : 1.0;
+  const double x = tx[t], y = ty[t], nx = sg * tnx[t], ny = sg * tny[t];
+  double r = cr[cc];
+  for (int base = 0; base < n_src; base += 256) {
+    const int nt = min(256, n_src - base);
+    __syncthreads();
+    for (int i = threadIdx.x; i < nt; i += blockDim.x) {
+      bx[i] = sx[base + i];
+      by[i] = sy[base + i];
+    }
+    __syncthreads();
+    for (int j = 0; j < nt; ++j) {
+      const double dx = bx[j] - x, dy = by[j] - y;
+      const double a = fma(dx, nx, dy * ny);
+      if (a > 0.0) r = fmin(r, fma(dx, dx, dy * dy) / (2.0 * a));
+    }
+  }
+  if (c < 2 * n_tgt) {
+    cr[c] = r;
+    cx[c] = fma(r, nx, x);
+    cy[c] = fma(r, ny, y);
+  }
+}
+
 // ratio = min_s |x_s - c| / r  (eq. x-c-closest)
 __global__ void k_ratio(int n_ctr, const double* cx, const double* cy, const double* cr, int n_src,
                         const double* sx, const double* sy, double* ratio) {
@@ -90,6 +125,9 @@ cudaError_t launch_geometry(int M, int q_tgt, int q_src, const double* t_edges,
   k_panel_h<<<(M + 127) / 128, 128, 0, st>>>(M, q_src, g.src_w, g.panel_h);
   k_centres<<<(n_t + 255) / 256, 256, 0, st>>>(n_t, q_tgt, r_factor, rule, g.panel_h, g.tgt_x, g.tgt_y,
                                               g.tgt_nx, g.tgt_ny, g.ctr_x, g.ctr_y, g.ctr_r);
+  if (rule == QBX_RADIUS_ADMISSIBLE)
+    k_cap_radius<<<(2 * n_t + 255) / 256, 256, 0, st>>>(n_t, g.tgt_x, g.tgt_y, g.tgt_nx, g.tgt_ny, n_s, g.src_x,
+                                                       g.src_y, g.ctr_x, g.ctr_y, g.ctr_r);
   k_ratio<<<(2 * n_t + 255) / 256, 256, 0, st>>>(2 * n_t, g.ctr_x, g.ctr_y, g.ctr_r, n_s, g.src_x,
                                                 g.src_y, g.ctr_ratio);
   return cudaGetLastError();

@@ -274,7 +274,7 @@ def panel_nodes(t_edges, q):
     return (0.5 * (a + b)[:, None] + 0.5 * (b - a)[:, None] * x[None, :]).reshape(-1)
 
 
-RADIUS_H, RADIUS_SQRT_H = 0, 1
+RADIUS_H, RADIUS_SQRT_H, RADIUS_ADMISSIBLE = 0, 1, 2
 
 
 def qbx_geometry(plan: Plan, curve, t_edges, r_factor=0.5, rule=RADIUS_H) -> Geometry:

@@ -113,6 +113,107 @@ def test_gmres_full_size_teardrop(cuda):
     assert pw_bulk < 1e-8
 
 
+def test_geometry_admissible_radius_matches_oracle(cuda):
+    """Radius rule QBX_RADIUS_ADMISSIBLE on the right-angle teardrop (12
+    panels + 3 dyadic levels), where it lowers the interior radii next to the
+    corner: radii element by element, centres and ratios against the oracle."""
+    cur, edges = W.teardrop(True), W.dyadic_edges(12, 3)
+    M = len(edges) - 1
+    plan = qbx.Plan(16, 64, n_src=M * 64, n_ctr=2 * M * 16)
+    g = qbx.qbx_geometry(plan, cur, edges, rule=qbx.RADIUS_ADMISSIBLE)
+    go = oracle.geometry(cur, edges, 16, 64, rule=oracle.RADIUS_ADMISSIBLE)
+    r = g["ctr_r"].cpu().numpy()
+    assert go["ctr_r"].min() < 0.01 * go["ctr_r"].max()
+    assert (np.abs(r - go["ctr_r"]) / go["ctr_r"]).max() < 1e-12
+    for name in ("ctr_x", "ctr_y", "ctr_ratio"):
+        a = g[name].cpu().numpy()
+        assert np.abs(a - go[name]).max() / np.abs(go[name]).max() < 1e-13, name
+
+
+def _right_angle_solve(m_base, levels, k, p, f_of, restart=60, maxiter=300):
+    cur = W.teardrop(True)
+    edges = W.dyadic_edges(m_base, levels)
+    M = len(edges) - 1
+    plan = qbx.Plan(16, 64, n_src=M * 64, n_ctr=2 * M * 16, ncoef=2, nrhs=4)
+    g = qbx.qbx_geometry(plan, cur, edges, rule=qbx.RADIUS_ADMISSIBLE)
+    tx, ty = g["tgt_x"].cpu().numpy(), g["tgt_y"].cpu().numpy()
+    f = f_of(tx, ty)
+    mu, its, res = qbx.qbx_solve_exterior_dirichlet(plan, g, k, k, p, dev(f), tol=1e-10, restart=restart,
+                                                     maxiter=maxiter)
+    go = oracle.geometry(cur, edges, 16, 64, rule=oracle.RADIUS_ADMISSIBLE)
+    return plan, g, go, f, mu, its, res
+
+
+def _point_source_field_error(plan, g, mu, k, x0):
+    th = np.linspace(0, 2 * np.pi, 41)[:-1]
+    xy = np.stack([3 * np.cos(th), 3 * np.sin(th)], 1)
+    wd = qbx.qbx_upsample(plan, g, mu.contiguous())
+    u = (qbx.qbx_far(plan, g, qbx.OP_D, k, wd, dev(xy)) - 1j * k * qbx.qbx_far(plan, g, qbx.OP_S, k, wd, dev(xy)))
+    u = u.cpu().numpy()[:, 0]
+    ref = 0.25j * sp.hankel1(0, k * np.hypot(xy[:, 0] - x0[0], xy[:, 1] - x0[1]))
+    return np.abs(u - ref).max() / np.abs(ref).max()
+
+
+def test_gmres_right_angle_corner(cuda):
+    """The solve on the right-angle teardrop (20 panels + 3 dyadic levels,
+    k = 5, p = 8) with the admissible radius: GMRES on the device converges,
+    the oracle's operator gives the residual in the sqrt-weighted norm, and
+    the field of a point source inside is reproduced outside to the accuracy
+    the oracle's own dense solve reaches with this radius (its pin: 4e-4 at
+    12 + 3 panels)."""
+    k, p = 5.0, 8
+    x0 = np.array([0.15, -0.05])
+    fo = lambda tx, ty: np.stack([-np.exp(1j * k * tx),
+                                  0.25j * sp.hankel1(0, k * np.hypot(tx - x0[0], ty - x0[1]))], 1)
+    plan, g, go, f, mu, its, res = _right_angle_solve(20, 3, k, p, fo)
+    assert np.all(res <= 1e-10) and its < 60
+    mu_h = mu.cpu().numpy()
+    S = oracle.apply(go, oracle.OP_S, oracle.SIDE_TWO, 0, k, p, mu_h)
+    D = oracle.apply(go, oracle.OP_D, oracle.SIDE_TWO, 0, k, p, mu_h)
+    r = 0.5 * mu_h + D - 1j * k * S - f
+    sw = np.sqrt(go["tgt_w"])[:, None]
+    rel = np.linalg.norm(sw * r, axis=0) / np.linalg.norm(sw * f, axis=0)
+    assert np.all(rel <= 1.1e-10), rel
+    assert _point_source_field_error(plan, g, mu[:, 1:2], k, x0) < 1e-3
+
+
+def test_gmres_full_size_right_angle_teardrop(cuda):
+    """The solve configuration on its own curve: the teardrop with a
+    90-degree corner, 1008 panels + 8 dyadic levels on each side (1024
+    panels), k = 30, p = 14, eta = k, with the admissible radius (the r = h/2
+    centres next to the corner lie on the opposite arm); three plane waves and
+    a point source inside: GMRES to 1e-10, the oracle's residual in the
+    sqrt-weighted norm on the stratified sample of the 115-degree test, and
+    the point source's field outside."""
+    k, p = 30.0, 14
+    x0 = np.array([0.15, -0.05])
+    ang = 2 * np.pi * np.array([0, 16, 33]) / 64
+
+    def fo(tx, ty):
+        pw = -np.exp(1j * k * (tx[:, None] * np.cos(ang)[None, :] + ty[:, None] * np.sin(ang)[None, :]))
+        ps = 0.25j * sp.hankel1(0, k * np.hypot(tx - x0[0], ty - x0[1]))
+        return np.concatenate([pw, ps[:, None]], 1)
+    plan, g, go, f, mu, its, res = _right_angle_solve(1008, 8, k, p, fo)
+    assert np.all(res <= 1e-10) and its < 150
+    n, q = go["n_tgt"], 16
+    corner = np.concatenate([np.arange(0, 9 * q), np.arange(n - 9 * q, n)])
+    bulk = np.arange(9 * q, n - 9 * q)
+    samp = bulk[7::32]
+    sel = np.concatenate([corner, samp])
+    mu_h = mu.cpu().numpy()
+    S = oracle.apply(go, oracle.OP_S, oracle.SIDE_TWO, 0, k, p, mu_h, sel=sel)
+    D = oracle.apply(go, oracle.OP_D, oracle.SIDE_TWO, 0, k, p, mu_h, sel=sel)
+    r = 0.5 * mu_h[sel] + D - 1j * k * S - f[sel]
+    w = go["tgt_w"]
+    wsel = np.concatenate([w[corner], w[samp] * (len(bulk) / len(samp))])
+    rel = np.sqrt((wsel[:, None] * np.abs(r) ** 2).sum(0)) / np.sqrt((w[:, None] * np.abs(f) ** 2).sum(0))
+    err = _point_source_field_error(plan, g, mu[:, 3:4], k, x0)
+    print(f"right-angle teardrop, full size: {its} iterations, oracle residual (sqrt-weighted) {rel.max():.2e}, "
+          f"point-source field error {err:.2e}")
+    assert np.all(rel <= 1.1e-10), rel
+    assert err < 1e-4
+
+
 @pytest.mark.parametrize("k", [5.0, 3 + 0.4j])
 def test_assembled_matrix_matches_oracle(cuda, k):
     """qbx_assemble_cfie: the sqrt-weighted matrix of 1/2 + D - i eta S
