@@ -309,8 +309,20 @@ int qbx_apply_shape_adjoint(qbx_plan *plan, const qbx_geom *g, int side, qbx_c64
                             const double *dgam_tgt, const double *dgam_src, double *g_gam_tgt,
                             double *g_dgam_tgt, double *g_gam_src, double *g_dgam_src, void *stream);
 
-/* Workspace for qbx_apply_shape_adjoint with up to 64 splits of each sweep
- * (any side).  Host, pure function; 0 on bad arguments. */
+/* The same gradient for the D apply, L = Re sum conj(gout) (D mu) (any
+ * limit: the PV jump term does not depend on the curve), Sec. 3.2's double
+ * layer n_s . grad_{x_s} G differentiated through the source positions (the
+ * second source derivatives of the Graf sum), the source normals, the
+ * weights and the centres.  Same arguments, layouts, workspace and errors as
+ * qbx_apply_shape_adjoint (dens_tgt is mu). */
+int qbx_apply_shape_adjoint_d(qbx_plan *plan, const qbx_geom *g, int side, qbx_c64 k, int p,
+                              const qbx_c64 *dens_tgt, const qbx_c64 *gout, int nrhs,
+                              const double *dgam_tgt, const double *dgam_src, double *g_gam_tgt,
+                              double *g_dgam_tgt, double *g_gam_src, double *g_dgam_src, void *stream);
+
+/* Workspace for qbx_apply_shape_adjoint and qbx_apply_shape_adjoint_d with up
+ * to 64 splits of each sweep (any side).  Host, pure function; 0 on bad
+ * arguments. */
 size_t qbx_shape_adjoint_workspace_bytes(int M, int q_tgt, int q_src, int p, int nrhs);
 
 /* Second-kind exterior Dirichlet (sound-soft) solve, Sec. 4.2 eq.

@@ -95,6 +95,8 @@ def lib():
             L.qbx_apply_adjoint.restype = I
             L.qbx_apply_shape_adjoint.argtypes = [_P, G, I, c64, I, _P, _P, I, _P, _P, _P, _P, _P, _P, _P]
             L.qbx_apply_shape_adjoint.restype = I
+            L.qbx_apply_shape_adjoint_d.argtypes = [_P, G, I, c64, I, _P, _P, I, _P, _P, _P, _P, _P, _P, _P]
+            L.qbx_apply_shape_adjoint_d.restype = I
             L.qbx_shape_adjoint_workspace_bytes.argtypes = [I, I, I, I, I]
             L.qbx_batch_tune.argtypes = [_P, _P, ctypes.POINTER(I), ctypes.POINTER(I)]
             L.qbx_batch_tune.restype = I
@@ -410,10 +412,13 @@ def qbx_shape_adjoint_workspace_bytes(M, q_tgt, q_src, p, nrhs):
     return int(lib().qbx_shape_adjoint_workspace_bytes(M, q_tgt, q_src, p, nrhs))
 
 
-def qbx_apply_shape_adjoint(plan: Plan, g: Geometry, side, k, p, dens, gout):
-    """Gradient of L = Re sum conj(gout) (S dens) with respect to the curve
-    samples given to qbx_geometry: returns (d gamma_tgt, d gamma'_tgt,
-    d gamma_src, d gamma'_src), [n, 2] float64 each."""
+def qbx_apply_shape_adjoint(plan: Plan, g: Geometry, side, k, p, dens, gout, op=OP_S):
+    """Gradient of L = Re sum conj(gout) (S dens) (op = OP_S) or of
+    Re sum conj(gout) (D dens) (op = OP_D) with respect to the curve samples
+    given to qbx_geometry: returns (d gamma_tgt, d gamma'_tgt, d gamma_src,
+    d gamma'_src), [n, 2] float64 each."""
+    if op not in (OP_S, OP_D):
+        raise ValueError("the shape adjoint covers S and D")
     if getattr(g, "rule", RADIUS_H) != RADIUS_H:
         raise ValueError("the shape adjoint needs r = r_factor * h (RADIUS_H)")
     d = _dens2d(dens, g.n_tgt)
@@ -424,8 +429,9 @@ def qbx_apply_shape_adjoint(plan: Plan, g: Geometry, side, k, p, dens, gout):
     outs = [torch.empty((g.n_tgt, 2), **f64), torch.empty((g.n_tgt, 2), **f64),
             torch.empty((g.n_src, 2), **f64), torch.empty((g.n_src, 2), **f64)]
     dgt, dgs = g.inputs[2], g.inputs[4]
-    _check(lib().qbx_apply_shape_adjoint(plan.handle, g.ref(), side, _k(k), p, _ptr(d), _ptr(go), d.shape[1],
-                                         _ptr(dgt), _ptr(dgs), *[_ptr(o) for o in outs], _stream()))
+    fn = lib().qbx_apply_shape_adjoint if op == OP_S else lib().qbx_apply_shape_adjoint_d
+    _check(fn(plan.handle, g.ref(), side, _k(k), p, _ptr(d), _ptr(go), d.shape[1], _ptr(dgt), _ptr(dgs),
+              *[_ptr(o) for o in outs], _stream()))
     return tuple(outs)
 
 
@@ -450,6 +456,36 @@ class QBXShapeS(torch.autograd.Function):
         if gd is not None and gd.shape != grad_u.shape:
             gd = gd.reshape(grad_u.shape)
         return (gd,) + tuple(shp) + (None,) * 6
+
+
+class QBXShapeD(torch.autograd.Function):
+    """u = D mu (one-sided limit or PV) on the curve given by its samples:
+    forward = qbx_geometry + qbx_apply; backward = qbx_apply_adjoint for mu
+    and qbx_apply_shape_adjoint_d for the samples."""
+
+    @staticmethod
+    def forward(ctx, dens, gam_tgt, dgam_tgt, gam_src, dgam_src, plan, t_edges, side, limit, k, p, r_factor):
+        g = qbx_geometry_samples(plan, t_edges, gam_tgt, dgam_tgt, gam_src, dgam_src, r_factor)
+        d = dens.detach().contiguous()
+        ctx.args = (plan, g, side, limit, k, p, d)
+        return qbx_apply(plan, g, OP_D, side, limit, k, p, d)
+
+    @staticmethod
+    def backward(ctx, grad_u):
+        plan, g, side, limit, k, p, d = ctx.args
+        go = grad_u.contiguous()
+        gd = qbx_apply_adjoint(plan, g, OP_D, side, limit, k, p, go) if ctx.needs_input_grad[0] else None
+        shp = (qbx_apply_shape_adjoint(plan, g, side, k, p, d, go, op=OP_D) if any(ctx.needs_input_grad[1:5])
+               else (None,) * 4)
+        if gd is not None and gd.shape != grad_u.shape:
+            gd = gd.reshape(grad_u.shape)
+        return (gd,) + tuple(shp) + (None,) * 7
+
+
+def apply_d_shape_autograd(plan: Plan, t_edges, gam_tgt, dgam_tgt, gam_src, dgam_src, dens, side, limit, k, p,
+                           r_factor=0.5):
+    """Differentiable D mu with respect to the density and to the curve samples."""
+    return QBXShapeD.apply(dens, gam_tgt, dgam_tgt, gam_src, dgam_src, plan, t_edges, side, limit, k, p, r_factor)
 
 
 def apply_s_shape_autograd(plan: Plan, t_edges, gam_tgt, dgam_tgt, gam_src, dgam_src, dens, side, k, p,
