@@ -830,6 +830,23 @@ def run_adjoint(args):
         return coef.grad, s.grad
 
     t_step = timed(loss_and_grad)
+    # D: forward, shape adjoint and a loss-and-gradient step of ||D mu - g||^2
+    ud = qbx.qbx_apply(plan, g, qbx.OP_D, side, 0, k, p, sig)
+    goutd = (2 * (ud - target)).contiguous()
+    t_fwd_d = timed(lambda: qbx.qbx_apply(plan, g, qbx.OP_D, side, 0, k, p, sig))
+    t_shape_d = timed(lambda: qbx.qbx_apply_shape_adjoint(plan, g, side, k, p, sig, goutd, op=qbx.OP_D))
+
+    def loss_and_grad_d():
+        coef = c0.clone().requires_grad_(True)
+        s = sig.clone().requires_grad_(True)
+        a, da = fourier_curve_samples(torch, coef, tt)
+        b, db = fourier_curve_samples(torch, coef, ts)
+        v = qbx.apply_d_shape_autograd(plan, edges, a, da, b, db, s, side, 0, k, p)
+        L = (torch.abs(v - torch.exp(1j * k * a[:, 0]).reshape(-1, 1)) ** 2).sum()
+        L.backward()
+        return coef.grad, s.grad
+
+    t_step_d = timed(loss_and_grad_d)
     clk = clocks.stop()
     qbx.qbx_sync_status(plan)
     # the adjoint identity Re <S sigma, y> = Re <sigma, S^H y> for a random y
@@ -850,6 +867,10 @@ def run_adjoint(args):
         "density_adjoint_terms_per_s": terms / (t_adj * 1e-3),
         "density_adjoint_over_forward": t_adj / t_fwd, "shape_adjoint_over_forward": t_shape / t_fwd,
         "adjoint_identity_relerr": ident,
+        "d": {"loss": "||D mu - g||^2, interior limit, same curve and density", "forward_ms": t_fwd_d,
+              "shape_adjoint_ms": t_shape_d, "shape_adjoint_over_forward": t_shape_d / t_fwd_d,
+              "loss_and_gradient_step_ms": t_step_d,
+              "calls": "qbx_apply (D), qbx_apply_shape_adjoint_d, QBXShapeD through autograd"},
         "calls": "qbx_apply (S), qbx_apply_adjoint (S), qbx_apply_shape_adjoint; step: qbx_geometry_samples + "
                  "qbx_apply forward, qbx_apply_adjoint + qbx_apply_shape_adjoint backward, torch for r(t)",
         "clocks": clk}))

@@ -48,8 +48,10 @@ __global__ void __launch_bounds__(kAsmLanes * kAsmWarps) k_assemble_cfie(AsmArgs
   double* sP = reinterpret_cast<double*>(smem_raw);                  // [q_src][q_tgt]
   T* slot = reinterpret_cast<T*>(sP + a.q_src * a.q_tgt + (a.q_src * a.q_tgt & 1));
   const int p = a.p, P2 = (p + 2) * kAsmLanes;
-  T* sJ = slot;        // J_l(k r), [p+2][32]
-  T* sL = slot + P2;   // l J_l
+  T* sJ = slot;             // J_l(k r) of the interior centre, [p+2][32]
+  T* sL = slot + P2;        // l J_l
+  T* sJe = slot + 2 * P2;   // the same for the exterior centre (its radius may differ:
+  T* sLe = slot + 3 * P2;   // QBX_RADIUS_ADMISSIBLE lowers each centre's radius separately)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int t = blockIdx.x * kAsmLanes + lane;
   const bool active = t < a.n_tgt;
@@ -61,21 +63,26 @@ __global__ void __launch_bounds__(kAsmLanes * kAsmWarps) k_assemble_cfie(AsmArgs
   const double r = hypot(ux, uy);
   ux /= r;
   uy /= r;
+  const double re = hypot(a.tx[tt] - cxe, a.ty[tt] - cye);
   KW<T> kw;
   kw.init(a.kre, a.kim, a.hk_tab);
   const T kk = kw.kval();
-  if (warp == 0) {
-    besselj_seq<T>(rmul(kk, r), p + 1, sJ + lane, kAsmLanes);
-    for (int l = 0; l <= p; ++l) sL[l * kAsmLanes + lane] = rmul(sJ[l * kAsmLanes + lane], (double)l);
+  if (warp < 2) {
+    T* J = warp == 0 ? sJ : sJe;
+    T* Lc = warp == 0 ? sL : sLe;
+    besselj_seq<T>(rmul(kk, warp == 0 ? r : re), p + 1, J + lane, kAsmLanes);
+    for (int l = 0; l <= p; ++l) Lc[l * kAsmLanes + lane] = rmul(J[l * kAsmLanes + lane], (double)l);
     T z0;
     sc_zero(z0);
-    sJ[(p + 1) * kAsmLanes + lane] = z0;
+    J[(p + 1) * kAsmLanes + lane] = z0;
   }
   __syncthreads();
   const T* cJ = sJ + lane;
   const T* cL = sL + lane;
-  const T J0 = cJ[0];
-  const T kneg_j0 = rmul(sc_mul(kk, J0), -1.0);
+  const T* cJe = sJe + lane;
+  const T* cLe = sLe + lane;
+  const T J0 = cJ[0], J0e = cJe[0];
+  const T kneg_j0 = rmul(sc_mul(kk, J0), -1.0), kneg_j0e = rmul(sc_mul(kk, J0e), -1.0);
   const cplx ieta = cplx{-a.eta_im, a.eta_re};   // i eta
   const double swt = sqrt(a.tw[tt]);
   for (int m = (int)blockIdx.y * kAsmWarps + warp; m < a.M; m += kAsmWarps * (int)gridDim.y) {
@@ -89,8 +96,8 @@ __global__ void __launch_bounds__(kAsmLanes * kAsmWarps) k_assemble_cfie(AsmArgs
       pair_kernels<OPB_S | OPB_D, T, kAsmLanes>(kw, kk, J0, kneg_j0, cJ, cL, cJ, p, sx - cxi, sy - cyi, nx, ny, ux,
                                                uy, GS, K, GA, GB, EX, EY);
       v = K - ieta * GS;
-      pair_kernels<OPB_S | OPB_D, T, kAsmLanes>(kw, kk, J0, kneg_j0, cJ, cL, cJ, p, sx - cxe, sy - cye, nx, ny, -ux,
-                                               -uy, GS, K, GA, GB, EX, EY);
+      pair_kernels<OPB_S | OPB_D, T, kAsmLanes>(kw, kk, J0e, kneg_j0e, cJe, cLe, cJe, p, sx - cxe, sy - cye, nx, ny,
+                                               -ux, -uy, GS, K, GA, GB, EX, EY);
       v = v + K - ieta * GS;
       v = a.sw[s] * v;
       const double* Pj = sP + j * a.q_tgt;
@@ -118,7 +125,7 @@ __global__ void __launch_bounds__(kAsmLanes * kAsmWarps) k_assemble_cfie(AsmArgs
 
 template <typename T>
 size_t asm_smem(int p, int q_src, int q_tgt) {
-  return ((size_t)q_src * q_tgt + 1) * 8 + 2 * (size_t)(p + 2) * kAsmLanes * sizeof(T) + 16;
+  return ((size_t)q_src * q_tgt + 1) * 8 + 4 * (size_t)(p + 2) * kAsmLanes * sizeof(T) + 16;
 }
 
 int afail(int code, const char* what) {

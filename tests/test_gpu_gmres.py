@@ -214,19 +214,25 @@ def test_gmres_full_size_right_angle_teardrop(cuda):
     assert err < 1e-4
 
 
-@pytest.mark.parametrize("k", [5.0, 3 + 0.4j])
-def test_assembled_matrix_matches_oracle(cuda, k):
+@pytest.mark.parametrize("k,right_angle", [(5.0, False), (3 + 0.4j, False), (5.0, True)])
+def test_assembled_matrix_matches_oracle(cuda, k, right_angle):
     """qbx_assemble_cfie: the sqrt-weighted matrix of 1/2 + D - i eta S
     (two-sided) against the oracle's operator matrices, entry by entry (the
-    paper's teardrop, 12 panels + 2 dyadic levels, p = 8, eta = k)."""
+    paper's teardrop, 12 panels + 2 dyadic levels, p = 8, eta = k; and the
+    right-angle teardrop with the admissible radius, whose interior and
+    exterior radii differ next to the corner)."""
     p, eta = 8, k
-    cur = W.teardrop()
+    cur = W.teardrop(right_angle)
+    rule = qbx.RADIUS_ADMISSIBLE if right_angle else qbx.RADIUS_H
     edges = W.dyadic_edges(12, 2)
     M = len(edges) - 1
     plan = qbx.Plan(16, 64, n_src=M * 64, n_ctr=2 * M * 16, ncoef=2, nrhs=1)
-    g = qbx.qbx_geometry(plan, cur, edges)
+    g = qbx.qbx_geometry(plan, cur, edges, rule=rule)
     A = qbx.qbx_assemble_cfie(plan, g, k, eta, p).cpu().numpy().T   # row-major A~[t, t']
-    go = oracle.geometry(cur, edges, 16, 64)
+    go = oracle.geometry(cur, edges, 16, 64, rule=rule)
+    if right_angle:
+        n = go["n_tgt"]
+        assert np.abs(go["ctr_r"][:n] - go["ctr_r"][n:]).max() > 0.1 * go["ctr_r"].max()
     n = go["n_tgt"]
     S = oracle.matrix(go, oracle.OP_S, oracle.SIDE_TWO, 0, k, p)
     D = oracle.matrix(go, oracle.OP_D, oracle.SIDE_TWO, 0, k, p)
