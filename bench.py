@@ -77,12 +77,12 @@ GROUP_SOURCES = ["qbx_group_impl.cuh", "qbx_apply_impl.cuh", "qbx_device.cuh", "
 # counters divided by the pairs of the captured launch, for the kernel
 # sources with the given hash (profiles/*_fp64_counts.md).
 HW_FP64_PER_PAIR = {"9192ae8281d1a5d2": 495.7}         # fused S + D + grad S, p = 12, one rhs
-HW_FP64_PER_PAIR_GROUP = {"58788bd53b242af9": 756.0}   # group kernel, S + D, p = 10, 32 rhs
+HW_FP64_PER_PAIR_GROUP = {"4e7d8da75a49300f": 755.9}   # group kernel, S + D, p = 10, 32 rhs
 # sm__pipe_fp64_cycles_active (of peak) over the active and the elapsed
 # cycles, from the same captures (fused: 128-panel starfish, one wave;
 # group: the first 4 curves of the batch)
 HW_FP64_PIPE = {"9192ae8281d1a5d2": (0.924, 0.870)}
-HW_FP64_PIPE_GROUP = {"58788bd53b242af9": (0.949, 0.925)}
+HW_FP64_PIPE_GROUP = {"4e7d8da75a49300f": (0.949, 0.926)}
 # the fused S + D + grad S apply at the complex wavenumber 20 + 1i (same
 # capture set-up: 128-panel starfish, p = 12, one rhs)
 HW_FP64_PER_PAIR_CPLX = {"9192ae8281d1a5d2": 855.8}
@@ -644,13 +644,13 @@ def run_solve(args):
     clk = clocks.stop()
     solve_ms = e0.elapsed_time(e1)
     qbx.qbx_sync_status(plan)
-    # the same solve on the assembled matrix (one ZGEMM per matvec)
+    # the same solve on the assembled matrix (one qbx_matmul_cm product per matvec)
     e0.record()
     A = qbx.qbx_assemble_cfie(plan, g, k, k, p)
     e1.record()
     e1.synchronize()
     asm_ms = e0.elapsed_time(e1)
-    # twice: the first call also creates the plan's cuBLAS handle
+    # twice (the first call also queries the product's split)
     asm_ms_calls = []
     for _ in range(2):
         e0.record()

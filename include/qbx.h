@@ -24,8 +24,9 @@
  *  - Every compute call is asynchronous on `stream` (a cudaStream_t passed as
  *    void*, NULL = legacy default stream) and allocates nothing; only
  *    qbx_plan_create (its workspace), qbx_batch_create (the batch's arrays)
- *    and the GMRES solves (their Krylov bases; the assembled solve also
- *    creates the plan's cuBLAS handle on first use) allocate.
+ *    and the GMRES solves (their Krylov bases, and for the assembled solve
+ *    the product's split partial sums and one instantiated CUDA graph, freed
+ *    before they return) allocate.
  *  - A plan is not thread-safe: calls on one plan from several host threads,
  *    or on several streams at once, must be serialised by the caller (they
  *    share the plan's workspace and its complex-k amplitude table).
