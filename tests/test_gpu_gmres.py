@@ -49,6 +49,39 @@ def test_gmres_residual_under_oracle_operator(cuda):
     assert np.all(rel <= 1.1e-10), rel
 
 
+@pytest.mark.parametrize("assembled", [False, True])
+def test_gmres_restart_cycles_and_maxiter(cuda, assembled):
+    """Restarted GMRES(6) (several cycles: the device-side back-substitution,
+    update and restart residual) reaches the same solution as one long cycle
+    and the oracle's residual bound, matrix-free and on the assembled matrix
+    (one CUDA-graph Arnoldi step launched per inner iteration); a maxiter too
+    small returns QBX_ENOCONV after exactly maxiter matvecs."""
+    cur, edges, plan, g, go, k, p = setup()
+    eta = k
+    tx, ty = go["tgt_x"], go["tgt_y"]
+    f = np.stack([-np.exp(1j * k * tx), -np.exp(1j * k * (0.6 * tx + 0.8 * ty)), -np.exp(-1j * k * ty)], 1)
+    A = qbx.qbx_assemble_cfie(plan, g, k, eta, p) if assembled else None
+    mu6, its6, res6 = qbx.qbx_solve_exterior_dirichlet(plan, g, k, eta, p, dev(f), tol=1e-10, restart=6,
+                                                       maxiter=400, A=A)
+    mu1, its1, res1 = qbx.qbx_solve_exterior_dirichlet(plan, g, k, eta, p, dev(f), tol=1e-10, restart=80,
+                                                       maxiter=400, A=A)
+    assert np.all(res6 <= 1e-10) and np.all(res1 <= 1e-10)
+    assert its6 > 6 and its6 >= its1
+    mu6 = mu6.cpu().numpy()
+    assert np.abs(mu6 - mu1.cpu().numpy()).max() / np.abs(mu6).max() < 1e-8
+    S = oracle.apply(go, oracle.OP_S, oracle.SIDE_TWO, 0, k, p, mu6)
+    D = oracle.apply(go, oracle.OP_D, oracle.SIDE_TWO, 0, k, p, mu6)
+    r = 0.5 * mu6 + D - 1j * eta * S - f
+    sw = np.sqrt(go["tgt_w"])[:, None]
+    assert np.all(np.linalg.norm(sw * r, axis=0) / np.linalg.norm(sw * f, axis=0) <= 1.1e-10)
+    mu_x, its_x, res_x = qbx.qbx_solve_exterior_dirichlet(plan, g, k, eta, p, dev(f), tol=1e-10, restart=6,
+                                                          maxiter=9, A=A, raise_on_noconv=False)
+    assert its_x == 9 and np.any(res_x > 1e-10)
+    with pytest.raises(qbx.QBXError) as e:
+        qbx.qbx_solve_exterior_dirichlet(plan, g, k, eta, p, dev(f), tol=1e-10, restart=6, maxiter=9, A=A)
+    assert e.value.code == 5
+
+
 def test_gmres_point_source_field_outside(cuda):
     """f = G(., x0) on Gamma with x0 inside: u = (D - i eta S) mu equals
     G(x, x0) everywhere outside (evaluated by plain quadrature far away)."""

@@ -16,15 +16,18 @@ from test_gpu_shape import dev, fourier_pert, fourier_samples, node_pert
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("side,limit,k,nrhs", [(qbx.SIDE_INT, qbx.LIMIT_ONE_SIDED, 5.0, 1),
-                                               (qbx.SIDE_EXT, qbx.LIMIT_PV, 3 + 0.5j, 2),
-                                               (qbx.SIDE_TWO, qbx.LIMIT_ONE_SIDED, 7.0, 5)])
-def test_shape_adjoint_d_vs_oracle_tangent(cuda, side, limit, k, nrhs):
+@pytest.mark.parametrize("side,limit,k,nrhs,p", [(qbx.SIDE_INT, qbx.LIMIT_ONE_SIDED, 5.0, 1, 8),
+                                                 (qbx.SIDE_EXT, qbx.LIMIT_PV, 3 + 0.5j, 2, 8),
+                                                 (qbx.SIDE_TWO, qbx.LIMIT_ONE_SIDED, 7.0, 5, 8),
+                                                 (qbx.SIDE_INT, qbx.LIMIT_PV, 4.0, 1, 0),
+                                                 (qbx.SIDE_TWO, qbx.LIMIT_ONE_SIDED, 2 + 0.3j, 2, 1)])
+def test_shape_adjoint_d_vs_oracle_tangent(cuda, side, limit, k, nrhs, p):
     """<grad, direction> from the reverse-mode GPU gradient of
     Re sum conj(gout) D mu equals the oracle's forward-mode derivative along
     random per-sample directions and Fourier directions: starfish, 12 panels
-    (192 targets, 768 sources), p = 8; 5 rhs take two passes of 4."""
-    cur, M, p = W.starfish(), 12, 8
+    (192 targets, 768 sources), p = 8, and the edge orders p = 0, 1 (where the
+    sums by parts reduce to their end terms); 5 rhs take two passes of 4."""
+    cur, M = W.starfish(), 12
     edges = cur.edges(M)
     n_t, n_s = M * 16, M * 64
     plan = qbx.Plan(16, 64, workspace_bytes=qbx.qbx_shape_adjoint_workspace_bytes(M, 16, 64, p, nrhs))
