@@ -336,6 +336,23 @@ def test_single_panel_and_order_zero(cuda):
         assert rel(got, ref) < TOL
 
 
+@pytest.mark.parametrize("k", [3.0, 2 + 0.4j])
+@pytest.mark.parametrize("nrhs", [1, 3, 17])
+def test_all_operators_low_orders(cuda, k, nrhs):
+    """S, D and grad S in one pass at the orders where D's sum by parts
+    reduces to its end terms (p = 0, 1, 2): one density with weighted seeds
+    (1 rhs), per-pair kernel values (3 rhs) and the group kernel (17 rhs),
+    both sides, against the oracle."""
+    plan, g, go = make(W.ellipse(2.0), 9, nrhs=nrhs)   # every centre admissible
+    dens = W.complex_gaussian(40 + nrhs, g.n_tgt * nrhs).reshape(g.n_tgt, nrhs)
+    ops = (qbx.OP_S, qbx.OP_D, qbx.OP_GRAD_S)
+    for p in (0, 1, 2):
+        got = qbx.qbx_apply_ops(plan, g, ops, qbx.SIDE_TWO, 0, k, p, dev(dens))
+        for op in ops:
+            ref = oracle.apply(go, op, oracle.SIDE_TWO, 0, k, p, dens)
+            assert rel(got[op], ref) < TOL, (p, op)
+
+
 def test_other_grid_sizes(cuda):
     plan, g, go = make(W.starfish(), 7, q_tgt=10, q_src=30)
     dens = W.density_cfg1(g.t_tgt)

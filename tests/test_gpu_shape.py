@@ -41,14 +41,15 @@ def fourier_pert(m, kind):
     return fn
 
 
-@pytest.mark.parametrize("side,k,nrhs", [(qbx.SIDE_INT, 5.0, 1), (qbx.SIDE_EXT, 3 + 0.5j, 2),
-                                         (qbx.SIDE_TWO, 7.0, 3)])
-def test_shape_adjoint_vs_oracle_tangent(cuda, side, k, nrhs):
+@pytest.mark.parametrize("side,k,nrhs,p", [(qbx.SIDE_INT, 5.0, 1, 8), (qbx.SIDE_EXT, 3 + 0.5j, 2, 8),
+                                           (qbx.SIDE_TWO, 7.0, 3, 8), (qbx.SIDE_INT, 4.0, 1, 1),
+                                           (qbx.SIDE_TWO, 2 + 0.3j, 2, 0)])
+def test_shape_adjoint_vs_oracle_tangent(cuda, side, k, nrhs, p):
     """<grad, direction> from the reverse-mode GPU gradient equals the
     oracle's forward-mode Re sum conj(gout) du along random per-sample
     directions and Fourier directions: starfish, 12 panels (192 targets,
-    768 sources), p = 8."""
-    cur, M, p = W.starfish(), 12, 8
+    768 sources), p = 8 and the edge orders p = 0, 1."""
+    cur, M = W.starfish(), 12
     edges = cur.edges(M)
     n_t, n_s = M * 16, M * 64
     plan = qbx.Plan(16, 64, workspace_bytes=qbx.qbx_shape_adjoint_workspace_bytes(M, 16, 64, p, nrhs))
