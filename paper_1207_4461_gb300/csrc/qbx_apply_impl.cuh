@@ -304,6 +304,46 @@ __device__ __forceinline__ void pair_kernels(const KW<T>& kw, const T kk, const 
     }
     return;
   }
+  if constexpr (kS && kD) {
+    // S with D: J_{m+1} C_{m+1} = 2 k a J_{m+1} cos((m+1) psi) is 2 k a times
+    // the next order's S product t_{m+1} = J_{m+1} cos((m+1) psi), so
+    // e_m = 2 k a t_{m+1} + m J_m V_m needs no C_m recurrence (the column's
+    // J_{p+1} = 0 gives t_{p+1} = 0)
+    const T tka = rmul(kk, 2.0 * av);                // 2 k a
+    const double i2 = 2.0 * inv;
+    T tc = rmul(cJ[STRIDE], cl);                     // t_1
+    K = smul(rmul(kneg_j0, av), H1);                 // -k a J0 H1
+    madd(K, sc_mul(tka, tc), H0);                    // e_0 = 2 k a t_1
+    double Vp = -i2 * av;                            // V_0
+    double Vc = i2 * fma(bv, sn, -av * cs);          // V_1
+    for (int l = 1; l <= p; ++l) {
+      const int o = l * STRIDE;
+      madd(GS, tc, H);
+      T tn;
+      double cn = 0.0;
+      if (l < p) {
+        cn = fma(tw, cl, -cp);
+        tn = rmul(cJ[o + STRIDE], cn);               // t_{l+1}
+      } else {
+        sc_zero(tn);
+      }
+      madd(K, dcoef(tka, tn, cL[o], Vc), H);         // e_l = 2 k a t_{l+1} + l J_l V_l
+      if (l < p) {
+        const cplx Hn = hrec(s, H, Hm);
+        Hm = H;
+        H = Hn;
+        s = sadd(s, twoz);
+        cp = cl;
+        cl = cn;
+        tc = tn;
+        const double Vn = fma(tw, Vc, -Vp);
+        Vp = Vc;
+        Vc = Vn;
+      }
+    }
+    GS = smul(J0, H0) + 2.0 * GS;   // J0 H0 + 2 sum_{l>=1}
+    return;
+  }
   T Cp, Cc;
   double Vp = 0.0, Vc = 0.0;
   if (kD) {

@@ -282,8 +282,8 @@ struct DsArgs {
   const double *sx, *sy, *snx, *sny;
   const cplx* wd;     // [n_src][nrhs] (forward)
   const cplx* gc;     // [n_ctr][nrhs] (transposed)
-  const void* coef;   // [n_ctr][p+2] J_0..J_{p+1}
-  const double* cgeo; // [n_ctr][4] ux, uy, r, unused
+  void* coef;         // [n_ctr][p+2] J_0..J_{p+1} (written by k_dshape_columns)
+  double* cgeo;       // [n_ctr][4] ux, uy, r, unused (written by k_dshape_columns)
   int nsplit, per_split;
   cplx* part;
 };
@@ -297,9 +297,8 @@ __global__ void k_dshape_columns(DsArgs a) {
   const double cx = a.cx[c], cy = a.cy[c];
   const int t = c % a.n_tgt;
   const double ux = a.tx[t] - cx, uy = a.ty[t] - cy, r = hypot(ux, uy);
-  besselj_seq<T>(rmul(kw.kval(), r), a.p + 1, reinterpret_cast<T*>(const_cast<void*>(a.coef)) + (size_t)c * (a.p + 2),
-                 1);
-  double* geo = const_cast<double*>(a.cgeo) + 4 * (size_t)c;
+  besselj_seq<T>(rmul(kw.kval(), r), a.p + 1, reinterpret_cast<T*>(a.coef) + (size_t)c * (a.p + 2), 1);
+  double* geo = a.cgeo + 4 * (size_t)c;
   geo[0] = ux / r;
   geo[1] = uy / r;
   geo[2] = r;
@@ -619,7 +618,7 @@ static int shape_impl(int op, qbx_plan* plan, const qbx_geom* g, int side, qbx_c
     d.wd = (const cplx*)wd;
     d.gc = (const cplx*)(base + L.gc);
     d.coef = base + L.coef;
-    d.cgeo = (const double*)(base + L.cgeo);
+    d.cgeo = (double*)(base + L.cgeo);
     // per-centre J_0..J_{p+1} and target direction
     if (ck) k_dshape_columns<cplx><<<(nc + 127) / 128, 128, 0, st>>>(d);
     else k_dshape_columns<double><<<(nc + 127) / 128, 128, 0, st>>>(d);
