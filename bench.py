@@ -634,6 +634,10 @@ def run_solve(args):
     mv_ms = e0.elapsed_time(e1)
     mv_kernel_ms = qbx.qbx_plan_kernel_ms(plan)
     qbx.qbx_plan_set_timing(plan, False)
+    if args.solve_matvec_only:   # profiling: the matvec alone
+        print(json.dumps({"matvec": "S + D two-sided, 64 rhs (the solve's matvec)", "n_tgt": g.n_tgt,
+                          "n_src": g.n_src, "matvec_ms": mv_ms, "matvec_kernel_ms": mv_kernel_ms}))
+        return 0
     clocks = ClockSampler(0)
     clocks.start()
     e0.record()
@@ -1027,6 +1031,7 @@ def main():
                     help="with --solve: the teardrop with a 90-degree corner and the admissible radius rule")
     ap.add_argument("--matmul", action="store_true", help="the assembled solve's matrix product alone")
     ap.add_argument("--matmul-n", type=int, default=16384)
+    ap.add_argument("--solve-matvec-only", action="store_true", help="profiling only: with --solve, time one matvec")
     ap.add_argument("--solve-restart", type=int, default=60)
     ap.add_argument("--solve-maxiter", type=int, default=400)
     args = ap.parse_args()

@@ -642,7 +642,9 @@ static int apply_impl(qbx_plan* p, const qbx_geom* g, int ops, int side, int lim
   // formed once per pair for all rhs); otherwise the fused kernel
   const bool ck = k.im != 0.0;
   const bool group = nrhs >= 16 && nd == 1 && (ops == 1 || ops == 2 || ops == 3 || ops == 7);
-  const int rg = 8;
+  // more than 32 rhs (global apply): eight warps of 8 rhs, so that the kernel
+  // values of a pair are formed once per 64 rhs instead of once per 32
+  const int rg = (nrhs > 32 && !(eta > 0.0)) ? kGrpRhsWide : 8;
   const int units = group ? (nc + kGrpCentres - 1) / kGrpCentres : (nc + kApplyThreads - 1) / kApplyThreads;
   const bool local = eta > 0.0;
   const int chunk = local ? std::min(4, apply_chunk(ops)) : apply_chunk(ops);

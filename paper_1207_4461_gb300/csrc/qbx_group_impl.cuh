@@ -24,7 +24,7 @@ namespace qbx {
 // T2 = sum b d, T3 = sum (a + b)(c + d)), the sums a + b and c + d formed
 // once per stored value; kernel values and densities then sit in shared
 // memory as three real planes.  Otherwise four FMAs per complex product.
-template <int OPS, typename T, int RG>
+template <int OPS, typename T, int RG, int W = kGrpWarps>
 struct GroupSmem {
   static constexpr int kNc = ops_ncomp(OPS);   // raw components: S 1, D 1, grad S 2
   static constexpr bool kD = OPS & OPB_D, kG = OPS & OPB_G;
@@ -33,7 +33,7 @@ struct GroupSmem {
   static __host__ __device__ int nslots() { return 1 + ((kD || kG) ? 1 : 0) + (kG ? 1 : 0); }
   static __host__ __device__ size_t bytes(int p) {
     return 4 * kGrpTile * 8 +                                  // x, y, nx, ny
-           (size_t)kGrpTile * kGrpWarps * RG * kVal +           // densities [tile][4 RG]
+           (size_t)kGrpTile * W * RG * kVal +                   // densities [tile][W RG]
            (size_t)kNc * kGrpTile * kGrpCentres * kVal +        // kernel values [comp][tile][centre]
            (size_t)nslots() * (p + 2) * kGrpCentres * sizeof(T) +  // coefficient columns
            16;                                                  // item index
@@ -41,14 +41,16 @@ struct GroupSmem {
 };
 
 // LOCAL: near-only QBX (sources at |x_s - c| >= eta r by the smooth rule at
-// the target, pair_direct), a separate instance.
-template <int OPS, typename T, int RG, bool LOCAL = false>
-__global__ void __launch_bounds__(kGrpCentres * kGrpWarps)
+// the target, pair_direct), a separate instance.  W warps per CTA: W RG rhs
+// per pass (kernel values are formed once per pass; W = 8 serves 64 rhs in
+// one pass, the GMRES matvec's count).
+template <int OPS, typename T, int RG, bool LOCAL = false, int W = kGrpWarps>
+__global__ void __launch_bounds__(kGrpCentres * W)
 k_apply_group(GroupArgs a) {
-  using L = GroupSmem<OPS, T, RG>;
+  using L = GroupSmem<OPS, T, RG, W>;
   constexpr bool kS = OPS & OPB_S, kD = OPS & OPB_D, kG = OPS & OPB_G;
   constexpr int kNc = L::kNc;
-  constexpr int kRP = kGrpWarps * RG;   // rhs per pass
+  constexpr int kRP = W * RG;   // rhs per pass
   constexpr bool k3M = L::k3M;
   constexpr int kNW = kGrpTile * kRP, kNK = kNc * kGrpTile * kGrpCentres;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -179,7 +181,7 @@ k_apply_group(GroupArgs a) {
         }
         __syncthreads();
         // ---- phase 1: kernel values of this warp's sources ----
-        for (int j = warp; j < nt; j += kGrpWarps) {
+        for (int j = warp; j < nt; j += W) {
           const double dx = s_x[j] - cx, dy = s_y[j] - cy;
           double nx = 0.0, ny = 0.0;
           if (kD) {
@@ -277,13 +279,13 @@ k_apply_group(GroupArgs a) {
   }
 }
 
-template <int OPS, typename T, int RG, bool LOCAL = false>
+template <int OPS, typename T, int RG, bool LOCAL = false, int W = kGrpWarps>
 static cudaError_t launch_group_t(const GroupArgs& a, int grid, cudaStream_t st) {
-  const size_t smem = GroupSmem<OPS, T, RG>::bytes(a.p);
-  auto kern = k_apply_group<OPS, T, RG, LOCAL>;
+  const size_t smem = GroupSmem<OPS, T, RG, W>::bytes(a.p);
+  auto kern = k_apply_group<OPS, T, RG, LOCAL, W>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  kern<<<grid, kGrpCentres * kGrpWarps, smem, st>>>(a);
+  kern<<<grid, kGrpCentres * W, smem, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -296,9 +298,19 @@ static cudaError_t launch_group_t(const GroupArgs& a, int grid, cudaStream_t st)
     default: break;                                                      \
   }
 
+// rg: rhs per warp 2 or 8 with four warps per CTA, or kGrpRhsWide (64 rhs
+// per pass: eight warps of 8; single curves, global apply)
 template <typename T, bool LOCAL = false>
 static cudaError_t launch_group_any(const GroupArgs& a, int rg, int grid, cudaStream_t st) {
   const int ops = a.ops;
+  if constexpr (!LOCAL) {
+    if (rg == kGrpRhsWide) {
+#define X(O, TT, R) return launch_group_t<O, TT, R, false, 8>(a, grid, st)
+      QBX_GROUP_OPS(X, T, 8)
+#undef X
+      return cudaErrorInvalidValue;
+    }
+  }
 #define X(O, TT, R) return launch_group_t<O, TT, R, LOCAL>(a, grid, st)
   if (rg == 8) {
     QBX_GROUP_OPS(X, T, 8)
@@ -312,6 +324,19 @@ static cudaError_t launch_group_any(const GroupArgs& a, int rg, int grid, cudaSt
 template <typename T, bool LOCAL = false>
 static int group_occupancy_any(int ops, int p, int rg) {
   int n = 0;
+  if constexpr (!LOCAL) {
+    if (rg == kGrpRhsWide) {
+#define X(O, TT, R)                                                                                               \
+  cudaFuncSetAttribute(k_apply_group<O, TT, R, false, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,           \
+                       (int)GroupSmem<O, TT, R, 8>::bytes(p));                                                   \
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_apply_group<O, TT, R, false, 8>, kGrpCentres * 8,          \
+                                                GroupSmem<O, TT, R, 8>::bytes(p));                               \
+  return n
+      QBX_GROUP_OPS(X, T, 8)
+#undef X
+      return 0;
+    }
+  }
 #define X(O, TT, R)                                                                                         \
   cudaFuncSetAttribute(k_apply_group<O, TT, R, LOCAL>, cudaFuncAttributeMaxDynamicSharedMemorySize,        \
                        (int)GroupSmem<O, TT, R>::bytes(p));                                                 \
@@ -341,6 +366,12 @@ static const void* group_ptr_any(int ops, int rg) {
 
 template <typename T>
 static size_t group_smem_any(int ops, int p, int rg) {
+  if (rg == kGrpRhsWide) {
+#define X(O, TT, R) return GroupSmem<O, TT, R, 8>::bytes(p)
+    QBX_GROUP_OPS(X, T, 8)
+#undef X
+    return 0;
+  }
 #define X(O, TT, R) return GroupSmem<O, TT, R>::bytes(p)
   if (rg == 8) {
     QBX_GROUP_OPS(X, T, 8)

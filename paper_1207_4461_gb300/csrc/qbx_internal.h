@@ -166,6 +166,7 @@ namespace qbx {
 // ---- many right-hand sides and batches: the group kernel ------------------
 constexpr int kGrpCentres = 32;   // centres per CTA (one per lane)
 constexpr int kGrpWarps = 4;      // warps per CTA: rhs groups in phase 2
+constexpr int kGrpRhsWide = 64;   // the rg code of the eight-warp instances (64 rhs per pass)
 constexpr int kGrpTile = 32;      // sources per shared-memory tile
 
 // One curve of a batch (or the single curve of a many-rhs apply).

@@ -23,11 +23,12 @@ def dev(a):
 
 @pytest.mark.parametrize("ops", [(0,), (1,), (0, 1), (0, 1, 2)])
 @pytest.mark.parametrize("side,limit,k,nrhs", [(qbx.SIDE_TWO, 0, 9.0, 20), (qbx.SIDE_INT, 1, 3 + 0.5j, 37),
-                                               (qbx.SIDE_EXT, 1, 14.0, 16)])
+                                               (qbx.SIDE_EXT, 1, 14.0, 16), (qbx.SIDE_TWO, 0, 6.0, 70)])
 def test_group_kernel_many_rhs(cuda, ops, side, limit, k, nrhs):
     """qbx_apply_ops with >= 16 rhs of one density takes the group kernel:
     9 panels (144 targets -> 4.5 tiles of 32 centres), 576 sources
-    (18 tiles of 32); 37 rhs = 2 passes of 32."""
+    (18 tiles of 32); up to 32 rhs four warps of 8 per pass, above that
+    eight warps of 8 (64 rhs per pass): 37 rhs in one pass, 70 in two."""
     p = 8
     cur = W.starfish(0.2, 3)
     M = 9
