@@ -77,12 +77,12 @@ GROUP_SOURCES = ["qbx_group_impl.cuh", "qbx_apply_impl.cuh", "qbx_device.cuh", "
 # counters divided by the pairs of the captured launch, for the kernel
 # sources with the given hash (profiles/*_fp64_counts.md).
 HW_FP64_PER_PAIR = {"2591a2f21dc35b9e": 495.7}         # fused S + D + grad S, p = 12, one rhs
-HW_FP64_PER_PAIR_GROUP = {"2eecf0ced570d2a7": 734.9}   # group kernel, S + D, p = 10, 32 rhs
+HW_FP64_PER_PAIR_GROUP = {"14472de5c9ab429b": 734.9}   # group kernel, S + D, p = 10, 32 rhs
 # sm__pipe_fp64_cycles_active (of peak) over the active and the elapsed
 # cycles, from the same captures (fused: 128-panel starfish, one wave;
 # group: the first 4 curves of the batch)
 HW_FP64_PIPE = {"2591a2f21dc35b9e": (0.924, 0.870)}
-HW_FP64_PIPE_GROUP = {"2eecf0ced570d2a7": (0.948, 0.930)}
+HW_FP64_PIPE_GROUP = {"14472de5c9ab429b": (0.948, 0.929)}
 # the fused S + D + grad S apply at the complex wavenumber 20 + 1i (same
 # capture set-up: 128-panel starfish, p = 12, one rhs)
 HW_FP64_PER_PAIR_CPLX = {"2591a2f21dc35b9e": 855.8}
