@@ -3,8 +3,8 @@
 // a matrix, Sec. 3.3): A = 1/2 I + D - i eta S with D and S two-sided
 // averages, in the sqrt-weight unknowns of Sec. 4.2,
 //   At[t][t'] = sqrt(w_t) A[t][t'] / sqrt(w_t'),
-// and the GMRES solve whose matvecs are then one complex GEMM (cuBLAS ZGEMM3M)
-// for all right-hand sides.
+// and the GMRES solve whose matvecs are then one complex GEMM (qbx_zgemm.cu, three
+// real products per complex multiply-add) for all right-hand sides.
 //
 // Row t of A collects, for both centres of target t (interior, exterior;
 // weight 1/2 each), the truncated Graf sums of D and S against every source

@@ -30,7 +30,6 @@ struct qbx_plan {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   // waves of resident CTAs the split choice aims for (qbx_plan_set_min_waves)
   int min_waves = 1;
-  // cuBLAS handle of the assembled-matrix solve, created on first use
   // H0/H1 amplitude table of the ray z = k rho for the last complex k
   // (tab_kim = 0: none made yet)
   double* d_hk_tab;
