@@ -42,9 +42,11 @@ __global__ void k_coef_columns(AdjArgs a) {
       col[2 * P2 + l] = (l == 0) ? rmul(jn, -1.0) : sc_sub(jp, jn);
     }
   }
-  T z0;
-  sc_zero(z0);
-  col[a.p + 1] = z0;
+  if (!keeps_jp1(OPS)) {
+    T z0;
+    sc_zero(z0);
+    col[a.p + 1] = z0;
+  }
   double* geo = a.cgeo + 3 * (size_t)c;
   geo[0] = ux / r;
   geo[1] = uy / r;
@@ -139,7 +141,7 @@ k_adjoint(AdjArgs a) {
         const T kneg_j0 = rmul(sc_mul(kk, J0), -1.0);
         cplx GS, K, GA, GB, EX, EY;
         pair_kernels<OPS, T, kGrpTile>(kw, kk, J0, kneg_j0, cJ, cL, cG, p, dx, dy, snx, sny, s_ux[j], s_uy[j],
-                                       GS, K, GA, GB, EX, EY);
+                                       s_ir[j], GS, K, GA, GB, EX, EY);
         int q = 0;
         if (kS) s_kv[(q++ * kGrpTile + j) * kGrpCentres + lane] = GS;
         if (kD) s_kv[(q++ * kGrpTile + j) * kGrpCentres + lane] = K;

@@ -94,6 +94,9 @@ __device__ __forceinline__ cplx lin2(double a, cplx x, double b, cplx y) {
 __device__ __forceinline__ cplx lin2(cplx a, cplx x, cplx b, cplx y) { return a * x + b * y; }
 __device__ __forceinline__ double sadd(double a, double b) { return a + b; }
 __device__ __forceinline__ cplx sadd(cplx a, cplx b) { return a + b; }
+// complex k: J_l(k r) and the other coefficient columns are complex
+template <typename T> struct IsCplx { static constexpr bool value = false; };
+template <> struct IsCplx<cplx> { static constexpr bool value = true; };
 
 // Per-pair distance powers and H0, H1 for real k (fitted path, needs
 // rho^{-1/2}) or complex k.
@@ -192,10 +195,16 @@ __host__ __device__ constexpr bool multi_op(int m) { return popc3(m) > 1 || (m &
 __host__ __device__ constexpr int ops_ncomp(int m) {
   return (m & 1) + ((m >> 1) & 1) + 2 * ((m >> 2) & 1) + 2 * ((m >> 3) & 1);
 }
+// D (or the source-position gradient) taken from grad S's A and B sums (the
+// operator sets with grad S and one of them) reads the true J_{p+1} in the
+// J column's last row; every other operator set wants 0 there (orders
+// |l| <= p, no J_{p+1} term).
+__host__ __device__ constexpr bool keeps_jp1(int m) { return (m & OPB_G) && (m & (OPB_D | OPB_X)); }
 
 // Shared memory layout (bytes): source tile x, y [, nx, ny] ; densities
 // [nops][tile][NR] (one slot for the one-density instances) ; per-centre
-// coefficient columns of type T, kApplyThreads wide: J (J_l, l = 0..p+1),
+// coefficient columns of type T, kApplyThreads wide: J (J_l, l = 0..p+1;
+// J_{p+1} = 0 unless keeps_jp1),
 // then with D or grad S  L (l J_l, l = 0..p), then with grad S
 // G (J_{l-1} - J_{l+1}, l = 0..p).
 template <int OPS, typename T, int NR, bool ONEW = false>
@@ -216,12 +225,13 @@ struct ApplySmem {
 // without the factor i/4: GS (S), K (D), GA and GB (grad S: the e_r and
 // e_theta sums before scaling), EX and EY (X: the gradient of the S kernel
 // with respect to the source position).  (dx, dy) = x_s - c, (nx, ny) = n_s,
-// (ux, uy) = unit vector from c to its target; cJ, cL, cG: the centre's
-// coefficient columns (J_l, l J_l, J_{l-1} - J_{l+1}) with stride STRIDE.
+// (ux, uy) = unit vector from c to its target, ir = 1/r; cJ, cL, cG: the
+// centre's coefficient columns (J_l, l J_l, J_{l-1} - J_{l+1}) with stride
+// STRIDE.
 template <int OPS, typename T, int STRIDE>
 __device__ __forceinline__ void pair_kernels(const KW<T>& kw, const T kk, const T J0, const T kneg_j0,
                                              const T* cJ, const T* cL, const T* cG, int p, double dx,
-                                             double dy, double nx, double ny, double ux, double uy,
+                                             double dy, double nx, double ny, double ux, double uy, double ir,
                                              cplx& GS, cplx& K, cplx& GA, cplx& GB, cplx& EX, cplx& EY) {
   constexpr bool kS = OPS & OPB_S, kD = OPS & OPB_D, kG = OPS & OPB_G, kX = OPS & OPB_X;
   static_assert(!(kX && kD), "the source-position gradient is not combined with D");
@@ -232,18 +242,22 @@ __device__ __forceinline__ void pair_kernels(const KW<T>& kw, const T kk, const 
   const double rho2 = fma(dx, dx, dy * dy);
   double inv, rho, yq;
   kw.geom(rho2, inv, rho, yq);
-  const double cs = fma(ux, dx, uy * dy) * inv;  // cos psi
+  double cs, sn = 0.0, av = 0.0, bv = 0.0;
+  if constexpr (kD) {
+    // four projections: onto the unit vector e_rho first
+    const double ex = dx * inv, ey = dy * inv;
+    cs = fma(ux, ex, uy * ey);    // cos psi
+    sn = fma(uy, ex, -ux * ey);   // sin psi
+    av = fma(nx, ex, ny * ey);    // n_s . e_rho
+    bv = fma(ny, ex, -nx * ey);   // n_s . e_theta
+  } else {
+    cs = fma(ux, dx, uy * dy) * inv;
+    if (kB) sn = fma(uy, dx, -ux * dy) * inv;
+  }
   cplx H0, H1;
   T twoz;
   kw.hankel(rho, inv, yq, H0, H1, twoz);
   const double tw = 2.0 * cs;
-  double sn = 0.0;
-  if (kD || kB) sn = fma(uy, dx, -ux * dy) * inv;  // sin psi
-  double av = 0.0, bv = 0.0;
-  if (kD) {
-    av = fma(nx, dx, ny * dy) * inv;   // n_s . e_rho
-    bv = fma(ny, dx, -nx * dy) * inv;  // n_s . e_theta
-  }
 
   // ---- order sums; l = 0 terms and recurrence seeds ----
   GS = K = GA = GB = cplx{0.0, 0.0};
@@ -251,12 +265,81 @@ __device__ __forceinline__ void pair_kernels(const KW<T>& kw, const T kk, const 
   cplx Hm = H0, H = H1;
   T s = twoz;
   double cp = 1.0, cl = cs, sp = 0.0, sl = sn;
-  if constexpr (kSums) {
-    // D (with grad S) and the source-position gradient from the sum by parts
+  if constexpr (kSums && kG) {
+    // D and the source-position gradient from grad S's sums: with
+    //   T = J0 H0' + 2 sum_{l=1..p} J_l cos(l psi) H_l',  H_l' = (H_{l-1} - H_{l+1})/2,
+    // the sum by parts (below) regroups T by H_m with the coefficients
+    // t_{m+1} - t_{m-1}, t_m = J_m cos(m psi); writing cos((m +- 1) psi) =
+    // cos(m psi) cos psi -+ sin(m psi) sin psi and J_{m+1} -+ J_{m-1} by the
+    // Bessel recurrences (-2 J_m', (2m/kr) J_m) gives
+    //   T = -cos psi GA - (2 sin psi/(k r)) GB - E,
+    //   E = J_{p+1} cos((p+1) psi) H_p + J_p cos(p psi) H_{p+1},
+    // GA = sum_{l>=0} G_l cos(l psi) H_l and GB = sum l J_l sin(l psi) H_l
+    // the A and B sums of grad S, E what the truncation at order p leaves
+    // (the column holds the true J_{p+1}).  So the orders carry only S, GA
+    // and GB, and D = k a T + (2/rho) b GB and R = k T take per-pair factors.
+    T tc = rmul(cJ[STRIDE], cl);           // t_1
+    for (int l = 1; l <= p; ++l) {
+      const int o = l * STRIDE;
+      if constexpr (IsCplx<T>::value) {
+        const cplx Y = cl * H;                   // cos(l psi) H_l once for S and A
+        if (kS) madd(GS, cJ[o], Y);
+        madd(GA, cG[o], Y);
+      } else {
+        if (kS) madd(GS, tc, H);
+        madd(GA, rmul(cG[o], cl), H);
+      }
+      madd(GB, rmul(cL[o], sl), H);
+      if (l < p) {
+        const double cn = fma(tw, cl, -cp);
+        cp = cl;
+        cl = cn;
+        const double sq = fma(tw, sl, -sp);
+        sp = sl;
+        sl = sq;
+        if constexpr (!IsCplx<T>::value) tc = rmul(cJ[o + STRIDE], cl);   // t_{l+1}
+        const cplx Hn = hrec(s, H, Hm);
+        Hm = H;
+        H = Hn;
+        s = sadd(s, twoz);
+      }
+    }
+    // E: at p = 0, J_1 cos psi H_0 + J_0 H_1; else (H, Hm) = (H_p, H_{p-1}), tc = t_p
+    cplx E;
+    if (p == 0) {
+      E = smul(tc, Hm);
+      madd(E, J0, H);
+    } else {
+      if constexpr (IsCplx<T>::value) tc = rmul(cJ[p * STRIDE], cl);
+      E = smul(rmul(cJ[(p + 1) * STRIDE], fma(tw, cl, -cp)), H);
+      madd(E, tc, hrec(s, H, Hm));
+    }
+    if (kS) GS = smul(J0, H0) + 2.0 * GS;   // J0 H0 + 2 sum_{l>=1}
+    const double sr = 2.0 * sn * ir;        // k (2 sin psi/(k r))
+    if (kD) {
+      // D = -k a cos psi GA + 2 (b/rho - a sin psi/r) GB - k a E
+      const T ka = rmul(kk, av);
+      K = smul(rmul(ka, -cs), GA) + (2.0 * bv * inv - av * sr) * GB;
+      msub(K, ka, E);
+    }
+    if (kX) {
+      // grad_{x_s} of the S kernel: the D kernel is linear in the normal,
+      // n . (e_rho R + e_theta Q), R = k T, Q = (2/rho) D2;
+      // e_rho = (dx, dy)/rho, e_theta = (-dy, dx)/rho
+      cplx R = smul(rmul(kk, -cs), GA) - sr * GB;
+      msub(R, kk, E);
+      const cplx Q = (2.0 * inv) * GB;
+      EX = (dx * R - dy * Q) * inv;
+      EY = (dy * R + dx * Q) * inv;
+    }
+    return;
+  }
+  if constexpr (kSums && !kG) {
+    // the source-position gradient (without grad S) from the sum by parts
     //   T = J0 H0' + 2 sum_{l=1..p} J_l cos(l psi) H_l'
     //     = t_1 H_0 + sum_{m=1..p-1} (t_{m+1} - t_{m-1}) H_m - t_{p-1} H_p - t_p H_{p+1},
     // t_m = J_m cos(m psi) (t_0 = J_0), H_l' = (H_{l-1} - H_{l+1})/2, H_0' = -H_1
-    // (see pair_accumulate_w), and D2 = GB
+    // and D2 = GB
     T tm = J0;                             // t_{l-1}
     T tc = rmul(cJ[STRIDE], cl);           // t_l
     cplx Ts = cplx{0.0, 0.0};
@@ -265,7 +348,6 @@ __device__ __forceinline__ void pair_kernels(const KW<T>& kw, const T kk, const 
     for (int l = 1; l <= p; ++l) {
       const int o = l * STRIDE;
       if (kS) madd(GS, tc, H);
-      if (kG) madd(GA, rmul(cG[o], cl), H);
       madd(GB, rmul(cL[o], sl), H);
       if (l < p) {
         const double cn = fma(tw, cl, -cp);
@@ -287,21 +369,14 @@ __device__ __forceinline__ void pair_kernels(const KW<T>& kw, const T kk, const 
         msub(Ts, tc, hrec(s, H, Hm));            // - t_p H_{p+1}
       }
     }
-    const double i2 = 2.0 * inv;
     if (kS) GS = smul(J0, H0) + 2.0 * GS;   // J0 H0 + 2 sum_{l>=1}
-    if (kDsum) {
-      // D = k a T + (2/rho) b D2
-      K = smul(rmul(kk, av), Ts) + (i2 * bv) * GB;
-    }
-    if (kX) {
-      // grad_{x_s} of the S kernel: the D kernel is linear in the normal,
-      // n . (e_rho R + e_theta Q), R = k T, Q = (2/rho) D2;
-      // e_rho = (dx, dy)/rho, e_theta = (-dy, dx)/rho
-      const cplx R = smul(kk, Ts);
-      const cplx Q = i2 * GB;
-      EX = (dx * R - dy * Q) * inv;
-      EY = (dy * R + dx * Q) * inv;
-    }
+    // grad_{x_s} of the S kernel: the D kernel is linear in the normal,
+    // n . (e_rho R + e_theta Q), R = k T, Q = (2/rho) D2;
+    // e_rho = (dx, dy)/rho, e_theta = (-dy, dx)/rho
+    const cplx R = smul(kk, Ts);
+    const cplx Q = (2.0 * inv) * GB;
+    EX = (dx * R - dy * Q) * inv;
+    EY = (dy * R + dx * Q) * inv;
     return;
   }
   if constexpr (kS && kD) {
@@ -403,79 +478,139 @@ __device__ __forceinline__ void pair_kernels(const KW<T>& kw, const T kk, const 
 // recurrence: accS receives the S kernel itself, accA and accB twice the A
 // and B sums of pair_kernels.  (ux2, uy2) = 2 (ux, uy), so that
 // (ux2, uy2) . (dx, dy) / rho = C_1 directly.
-// With grad S requested too, D comes from sums by parts: with A_m = J_m C_m
-// (A_0 = 2 J_0) and H_l' = (H_{l-1} - H_{l+1})/2 (H_0' = -H_1),
-//   D = k a [J0 H0' + sum_{l=1..p} J_l C_l H_l'] + (b/rho) D2',
-//   2 [J0 H0' + sum_l A_l H_l'] = A_1 H_0 + sum_{m=1..p-1} (A_{m+1} - A_{m-1}) H_m
-//                                 - A_{p-1} H_p - A_p H_{p+1},
-// D2' = sum_l l J_l S_l H_l (grad S's B sum): one difference and one complex
-// multiply-add per order for D, instead of two sums (J_l C_l against H_{l-1}
-// and l J_l C_l against H_l).
-// gA0 = 2 (J_{-1} - J_1)/2 = -2 J_1: the l = 0 coefficient of the doubled A sum.
+// With grad S requested too, D comes from grad S's A and B sums (the
+// identity in pair_kernels, here in the doubled C_l, S_l): with A_m = J_m C_m
+// (A_0 = 2 J_0), H_l' = (H_{l-1} - H_{l+1})/2 (H_0' = -H_1) and this pair's
+//   PA = gA0 H0 + sum_{l=1..p} G_l C_l H_l,  GB = sum_{l=1..p} l J_l S_l H_l,
+//   2 [J0 H0' + sum_{l=1..p} A_l H_l'] = -(C_1/2) PA - (S_1/(k r)) GB - E,
+//   E = J_{p+1} C_{p+1} H_p + A_p H_{p+1},
+//   D = k a [J0 H0' + sum A_l H_l'] + (b/rho) GB
+//     = -(k/2) a [(C_1/2) PA + E] + (b/rho - a S_1/(2 r)) GB,
+// so the orders carry S, PA and GB only; the J column holds the true J_{p+1}.
+// gA0 = 2 (J_{-1} - J_1)/2 = -2 J_1: the l = 0 coefficient of the doubled A
+// sum; khalf = k/2, hir = 1/(2 r).
+// D with grad S (and S) for NP sources at once (NP = 1 or 2): the identity
+// above, with the pairs' recurrences interleaved order by order so that a
+// warp holds NP independent dependency chains and the pairs share the
+// column loads of each order.
+template <int OPS, typename T, int STRIDE, int NP>
+__device__ __forceinline__ void pair_dsum_w(const KW<T>& kw, const T J0, const T gA0, const T khalf, double hir,
+                                            const T* cJ, const T* cL, const T* cG, int p, const double* dx,
+                                            const double* dy, const double* nx, const double* ny, double ux2,
+                                            double uy2, const cplx* w, cplx& accS, cplx& accD, cplx& accA,
+                                            cplx& accB) {
+  constexpr bool kS = OPS & OPB_S;
+  double inv[NP], tw[NP], s1[NP], av[NP], bv[NP], cp[NP], cl[NP], sp[NP], sl[NP];
+  cplx H[NP], Hm[NP], PA[NP], GB[NP];
+  T s[NP], twoz[NP], Ac[NP];
+#pragma unroll
+  for (int q = 0; q < NP; ++q) {
+    const double rho2 = fma(dx[q], dx[q], dy[q] * dy[q]);
+    double rho, yq;
+    kw.geom(rho2, inv[q], rho, yq);
+    const double ex = dx[q] * inv[q], ey = dy[q] * inv[q];   // e_rho
+    tw[q] = fma(ux2, ex, uy2 * ey);                           // C_1 = 2 cos psi
+    s1[q] = fma(uy2, ex, -ux2 * ey);                          // S_1 = 2 sin psi
+    av[q] = fma(nx[q], ex, ny[q] * ey);                       // n_s . e_rho
+    bv[q] = fma(ny[q], ex, -nx[q] * ey);                      // n_s . e_theta
+    kw.hankel_w(rho, inv[q], yq, w[q], Hm[q], H[q], twoz[q]);   // w H0, w H1
+    s[q] = twoz[q];
+    cp[q] = 2.0;
+    cl[q] = tw[q];
+    sp[q] = 0.0;
+    sl[q] = s1[q];
+    if (kS) madd(accS, J0, Hm[q]);
+    PA[q] = smul(gA0, Hm[q]);
+    GB[q] = cplx{0.0, 0.0};
+    Ac[q] = rmul(cJ[STRIDE], cl[q]);   // A_1
+  }
+  for (int l = 1; l <= p; ++l) {
+    const int o = l * STRIDE;
+    const T Jl = cJ[o], Gl = cG[o], Ll = cL[o];
+    T Jn;
+    if (!IsCplx<T>::value && l < p) Jn = cJ[o + STRIDE];
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+      if constexpr (IsCplx<T>::value) {
+        // complex columns: C_l H_l once for S and A (2 + 4 + 4 against 2 x (2 + 4))
+        const cplx Y = cl[q] * H[q];
+        if (kS) madd(accS, Jl, Y);
+        madd(PA[q], Gl, Y);
+      } else {
+        if (kS) madd(accS, Ac[q], H[q]);
+        madd(PA[q], rmul(Gl, cl[q]), H[q]);
+      }
+      madd(GB[q], rmul(Ll, sl[q]), H[q]);
+      if (l < p) {
+        const double cn = fma(tw[q], cl[q], -cp[q]);
+        cp[q] = cl[q];
+        cl[q] = cn;
+        const double sq = fma(tw[q], sl[q], -sp[q]);
+        sp[q] = sl[q];
+        sl[q] = sq;
+        if constexpr (!IsCplx<T>::value) Ac[q] = rmul(Jn, cn);   // A_{l+1}
+        const cplx Hn = hrec(s[q], H[q], Hm[q]);
+        Hm[q] = H[q];
+        H[q] = Hn;
+        s[q] = sadd(s[q], twoz[q]);
+      }
+    }
+  }
+  const T Jp = cJ[p * STRIDE], Jp1 = cJ[(p + 1) * STRIDE];
+#pragma unroll
+  for (int q = 0; q < NP; ++q) {
+    // E: at p = 0, A_1 H_0 + 2 J_0 H_1; else (H, Hm) = (H_p, H_{p-1}), A_p = J_p C_p
+    cplx E;
+    if (p == 0) {
+      E = smul(Ac[q], Hm[q]);
+      madd(E, rmul(J0, 2.0), H[q]);
+    } else {
+      const T Ap = IsCplx<T>::value ? rmul(Jp, cl[q]) : Ac[q];
+      E = smul(rmul(Jp1, fma(tw[q], cl[q], -cp[q])), H[q]);
+      madd(E, Ap, hrec(s[q], H[q], Hm[q]));
+    }
+    madd(E, 0.5 * tw[q], PA[q]);
+    msub(accD, rmul(khalf, av[q]), E);
+    madd(accD, fma(-av[q] * s1[q], hir, bv[q] * inv[q]), GB[q]);
+    accA = accA + PA[q];
+    accB = accB + GB[q];
+  }
+}
+
 template <int OPS, typename T, int STRIDE>
 __device__ __forceinline__ void pair_accumulate_w(const KW<T>& kw, const T kk, const T J0, const T kneg_j0,
-                                                  const T gA0, const T twoJ0, const T khalf, const T* cJ,
+                                                  const T gA0, const T khalf, double hir, const T* cJ,
                                                   const T* cL, const T* cG, int p, double dx, double dy,
                                                   double nx, double ny, double ux2, double uy2, cplx w,
                                                   cplx& accS, cplx& accD, cplx& accA, cplx& accB) {
   constexpr bool kS = OPS & OPB_S, kD = OPS & OPB_D, kG = OPS & OPB_G;
   static_assert(!(OPS & OPB_X), "the source-position gradient is not formed here");
-  constexpr bool kDsum = kD && kG;
+  if constexpr (kD && kG) {
+    pair_dsum_w<OPS, T, STRIDE, 1>(kw, J0, gA0, khalf, hir, cJ, cL, cG, p, &dx, &dy, &nx, &ny, ux2, uy2, &w, accS,
+                                   accD, accA, accB);
+    return;
+  }
   const double rho2 = fma(dx, dx, dy * dy);
   double inv, rho, yq;
   kw.geom(rho2, inv, rho, yq);
-  const double tw = fma(ux2, dx, uy2 * dy) * inv;   // C_1 = 2 cos psi
+  double tw, s1 = 0.0, av = 0.0, bv = 0.0;   // C_1 = 2 cos psi, S_1 = 2 sin psi
+  if constexpr (kD) {
+    // four projections: onto the unit vector e_rho first
+    const double ex = dx * inv, ey = dy * inv;
+    tw = fma(ux2, ex, uy2 * ey);
+    s1 = fma(uy2, ex, -ux2 * ey);
+    av = fma(nx, ex, ny * ey);    // n_s . e_rho
+    bv = fma(ny, ex, -nx * ey);   // n_s . e_theta
+  } else {
+    tw = fma(ux2, dx, uy2 * dy) * inv;
+    if (kG) s1 = fma(uy2, dx, -ux2 * dy) * inv;
+  }
   cplx H0, H1;
   T twoz;
   kw.hankel_w(rho, inv, yq, w, H0, H1, twoz);   // w H0, w H1
-  double s1 = 0.0;
-  if (kD || kG) s1 = fma(uy2, dx, -ux2 * dy) * inv;  // S_1 = 2 sin psi
-  double av = 0.0, bv = 0.0;
-  if (kD) {
-    av = fma(nx, dx, ny * dy) * inv;   // n_s . e_rho
-    bv = fma(ny, dx, -nx * dy) * inv;  // n_s . e_theta
-  }
   cplx Hm = H0, H = H1;
   T s = twoz;
   double cp = 2.0, cl = tw, sp = 0.0, sl = s1;  // C_l, S_l at l = 0, 1
-  if constexpr (kDsum) {
-    if (kS) madd(accS, J0, H0);
-    madd(accA, gA0, H0);
-    T Am = twoJ0;                          // A_{l-1}
-    T Ac = rmul(cJ[STRIDE], cl);           // A_l
-    cplx P2 = cplx{0.0, 0.0}, GB = cplx{0.0, 0.0};
-    madd(P2, Ac, H0);
-    if (p == 0) msub(P2, Am, H1);          // (A_1 = 0: the column holds J_{p+1} = 0)
-    for (int l = 1; l <= p; ++l) {
-      const int o = l * STRIDE;
-      if (kS) madd(accS, Ac, H);
-      madd(accA, rmul(cG[o], cl), H);
-      madd(GB, rmul(cL[o], sl), H);
-      if (l < p) {
-        const double cn = fma(tw, cl, -cp);
-        cp = cl;
-        cl = cn;
-        const double sq = fma(tw, sl, -sp);
-        sp = sl;
-        sl = sq;
-        const T An = rmul(cJ[o + STRIDE], cl);   // A_{l+1}
-        madd(P2, sc_sub(An, Am), H);
-        Am = Ac;
-        Ac = An;
-        const cplx Hn = hrec(s, H, Hm);
-        Hm = H;
-        H = Hn;
-        s = sadd(s, twoz);
-      } else {
-        msub(P2, Am, H);                         // - A_{p-1} H_p
-        msub(P2, Ac, hrec(s, H, Hm));            // - A_p H_{p+1}
-      }
-    }
-    madd(accD, rmul(khalf, av), P2);
-    madd(accD, bv * inv, GB);
-    accB = accB + GB;
-    return;
-  }
   // ---- l = 0 terms and recurrence seeds ----
   if (kS) madd(accS, J0, H0);
   if (kG) madd(accA, gA0, H0);
@@ -584,8 +719,15 @@ __device__ __forceinline__ void pair_direct_w(const KW<T>& kw, const T kk, doubl
 // apply carries no per-pair test).  ONEW: one rhs and one density for all
 // operators, accumulated through weighted seeds (pair_accumulate_w,
 // pair_direct_w).
+// Register budget: the two-source D-with-grad-S instances keep three CTAs
+// per SM (up to 168 registers), the other one-density instances four.
+template <int OPS, bool LOCAL, bool ONEW>
+__host__ __device__ constexpr int fused_min_ctas() {
+  return !ONEW ? 1 : ((OPS & OPB_D) && (OPS & OPB_G) && !LOCAL) ? 3 : 4;
+}
+
 template <int OPS, typename T, int NR, bool LOCAL = false, bool ONEW = false>
-__global__ void __launch_bounds__(kApplyThreads)
+__global__ void __launch_bounds__(kApplyThreads, (fused_min_ctas<OPS, LOCAL, ONEW>()))
 k_apply_fused(ApplyArgs a) {
   using L = ApplySmem<OPS, T, NR, ONEW>;
   constexpr bool kS = L::kS, kD = L::kD, kG = L::kG, kX = OPS & OPB_X;
@@ -642,7 +784,7 @@ k_apply_fused(ApplyArgs a) {
       colG[l * kApplyThreads] = (l == 0) ? rmul(jn, -1.0) : sc_sub(jp, jn);
     }
   }
-  {
+  if (!keeps_jp1(OPS)) {
     T z0;
     sc_zero(z0);
     colJ[(p + 1) * kApplyThreads] = z0;  // e_p has no J_{p+1} term (orders |l| <= p)
@@ -650,7 +792,7 @@ k_apply_fused(ApplyArgs a) {
   const T kneg_j0 = rmul(sc_mul(kk, J0), -1.0);  // -k J0 (D)
   T gA0;
   if (kG) gA0 = rmul(colG[0], 2.0);                // -2 J_1 (one-density grad S)
-  const T twoJ0 = rmul(J0, 2.0), khalf = rmul(kk, 0.5);
+  const T khalf = rmul(kk, 0.5);
   const double ux2 = ux + ux, uy2 = uy + uy;
 
   cplx accS[NR], accD[NR], accA[NR], accB[NR], accX[NR], accY[NR];
@@ -695,7 +837,25 @@ k_apply_fused(ApplyArgs a) {
     const T* cL = colL;
     const T* cG = colG;
 
-    for (int j = 0; j < nt; ++j) {
+    int j0 = 0;
+    if constexpr (ONEW && kD && kG && !LOCAL) {
+      // two sources per step: two independent recurrence chains per thread
+      for (; j0 + 2 <= nt; j0 += 2) {
+        double dx2[2], dy2[2], nx2[2], ny2[2];
+        cplx w2[2];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          dx2[q] = s_x[j0 + q] - cx;
+          dy2[q] = s_y[j0 + q] - cy;
+          nx2[q] = s_nx[j0 + q];
+          ny2[q] = s_ny[j0 + q];
+          w2[q] = s_wd[j0 + q];
+        }
+        pair_dsum_w<OPS, T, kApplyThreads, 2>(kw, J0, gA0, khalf, 0.5 * ir, cJ, cL, cG, p, dx2, dy2, nx2, ny2,
+                                              ux2, uy2, w2, accS[0], accD[0], accA[0], accB[0]);
+      }
+    }
+    for (int j = j0; j < nt; ++j) {
       const double dx = s_x[j] - cx, dy = s_y[j] - cy;
       double nx = 0.0, ny = 0.0;
       if (kD) {
@@ -707,7 +867,7 @@ k_apply_fused(ApplyArgs a) {
           pair_direct_w<OPS, T>(kw, kk, r * ux - dx, r * uy - dy, nx, ny, ux, uy, r, s_wd[j], accS[0], accD[0],
                                 accA[0], accB[0]);
         } else {
-          pair_accumulate_w<OPS, T, kApplyThreads>(kw, kk, J0, kneg_j0, gA0, twoJ0, khalf, cJ, cL, cG, p, dx, dy,
+          pair_accumulate_w<OPS, T, kApplyThreads>(kw, kk, J0, kneg_j0, gA0, khalf, 0.5 * ir, cJ, cL, cG, p, dx, dy,
                                                     nx, ny, ux2, uy2, s_wd[j], accS[0], accD[0], accA[0],
                                                     accB[0]);
         }
@@ -717,7 +877,7 @@ k_apply_fused(ApplyArgs a) {
       if (LOCAL && fma(dx, dx, dy * dy) >= lim2) {   // near-only QBX: a distant source
         pair_direct<OPS, T>(kw, kk, r * ux - dx, r * uy - dy, nx, ny, ux, uy, r, GS, K, GA, GB);
       } else {
-        pair_kernels<OPS, T, kApplyThreads>(kw, kk, J0, kneg_j0, cJ, cL, cG, p, dx, dy, nx, ny, ux, uy, GS,
+        pair_kernels<OPS, T, kApplyThreads>(kw, kk, J0, kneg_j0, cJ, cL, cG, p, dx, dy, nx, ny, ux, uy, ir, GS,
                                              K, GA, GB, EX, EY);
       }
       // ---- weighted densities ----

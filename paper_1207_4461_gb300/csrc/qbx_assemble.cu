@@ -94,10 +94,10 @@ __global__ void __launch_bounds__(kAsmLanes * kAsmWarps) k_assemble_cfie(AsmArgs
       const double sx = a.sx[s], sy = a.sy[s], nx = a.snx[s], ny = a.sny[s];
       cplx GS, K, GA, GB, EX, EY, v{0.0, 0.0};
       pair_kernels<OPB_S | OPB_D, T, kAsmLanes>(kw, kk, J0, kneg_j0, cJ, cL, cJ, p, sx - cxi, sy - cyi, nx, ny, ux,
-                                               uy, GS, K, GA, GB, EX, EY);
+                                               uy, 1.0 / r, GS, K, GA, GB, EX, EY);
       v = K - ieta * GS;
       pair_kernels<OPB_S | OPB_D, T, kAsmLanes>(kw, kk, J0e, kneg_j0e, cJe, cLe, cJe, p, sx - cxe, sy - cye, nx, ny,
-                                               -ux, -uy, GS, K, GA, GB, EX, EY);
+                                               -ux, -uy, 1.0 / re, GS, K, GA, GB, EX, EY);
       v = v + K - ieta * GS;
       v = a.sw[s] * v;
       const double* Pj = sP + j * a.q_tgt;

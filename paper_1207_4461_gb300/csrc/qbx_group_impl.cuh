@@ -136,9 +136,11 @@ k_apply_group(GroupArgs a) {
           colG[l * kGrpCentres] = (l == 0) ? rmul(jn, -1.0) : sc_sub(jp, jn);
         }
       }
-      T z0;
-      sc_zero(z0);
-      colJ[(p + 1) * kGrpCentres] = z0;
+      if (!keeps_jp1(OPS)) {
+        T z0;
+        sc_zero(z0);
+        colJ[(p + 1) * kGrpCentres] = z0;
+      }
     }
     __syncthreads();
     const T J0 = colJ[0];
@@ -193,7 +195,7 @@ k_apply_group(GroupArgs a) {
             pair_direct<OPS, T>(kw, kk, r * ux - dx, r * uy - dy, nx, ny, ux, uy, r, GS, K, GA, GB);
           } else {
             pair_kernels<OPS, T, kGrpCentres>(kw, kk, J0, kneg_j0, colJ, colL, colG, p, dx, dy, nx, ny, ux,
-                                              uy, GS, K, GA, GB, EX, EY);
+                                              uy, ir, GS, K, GA, GB, EX, EY);
           }
           auto put = [&](int q, cplx v) {
             const int idx = (q * kGrpTile + j) * kGrpCentres + lane;
