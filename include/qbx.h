@@ -132,8 +132,11 @@ int qbx_plan_kernel_ms(qbx_plan *plan, float *ms);
 
 /* Work decomposition of the plan's applies (no counterpart in the paper):
  * the source-split choice aims for at least `waves` waves of the kernel's
- * resident CTAs (1..64; default set at plan creation), so that the block
- * scheduler can even out CTAs of unequal duration.  Host call. */
+ * resident CTAs (1..64; 1 at plan creation), so that the block scheduler
+ * can even out CTAs of unequal duration.  The near-only applies and the
+ * applies of one rhs of one density take at least 4 whatever the setting
+ * (one density at complex k: 8).
+ * Host call. */
 int qbx_plan_set_min_waves(qbx_plan *plan, int waves);
 
 /* Workspace a call needs: for qbx_apply / qbx_far / qbx_form_locals with the

@@ -710,11 +710,13 @@ __device__ __forceinline__ void pair_direct_w(const KW<T>& kw, const T kk, doubl
   }
 }
 
-// D through sums shared with grad S when both are requested:
-//   D = -k a J0 H1 + 2 k a D1 + (2/rho)(b D2 - a D3),
-//   D1 = sum_{l>=1} J_l cos(l psi) H_{l-1},  D2 = sum l J_l sin(l psi) H_l (= grad S's B / 2),
-//   D3 = sum l J_l cos(l psi) H_l,
-// otherwise by the coefficients e_m with the C_m, V_m recurrences.
+// The storage-free apply (a2-a6 fused): one thread per centre, a CTA of
+// kApplyThreads centres against one split of the sources, staged through
+// shared memory in tiles of kSrcTile; each pair's order sums go straight
+// into the centre's accumulators (split partial sums, finished by
+// k_apply_finish).  D with grad S comes from grad S's own sums and two end
+// terms (pair_kernels, pair_dsum_w), otherwise from the coefficients e_m
+// with the C_m, V_m recurrences (or S's next product, with S).
 // LOCAL: the near-only variant (a separate instance, so that the global
 // apply carries no per-pair test).  ONEW: one rhs and one density for all
 // operators, accumulated through weighted seeds (pair_accumulate_w,

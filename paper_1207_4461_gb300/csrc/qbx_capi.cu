@@ -657,8 +657,15 @@ static int apply_impl(qbx_plan* p, const qbx_geom* g, int ops, int side, int lim
   else occ = ck ? apply_occupancy_cplx(ops, pp, std::min(chunk, nrhs), one_w)
                 : apply_occupancy_real(ops, pp, std::min(chunk, nrhs), one_w);
   // the near-only variant's items differ more in cost (distant pairs take the
-  // short direct path): four waves let the near-field items spread out
-  const int waves = local ? std::max(p->min_waves, 4) : p->min_waves;
+  // short direct path), and the one-density items (the near-field ones take
+  // the slower small-argument Hankel branch) end unevenly: four waves (eight
+  // at complex k) let the near-field items spread out (one density,
+  // full-size starfish, real k: 63.9 ms with one wave of 3 CTAs per SM, 63.1
+  // with four, 64.0 with six or eight; k = 20 + 1i, 2 CTAs per SM: 106.0,
+  // 105.1, 103.9 ms with four, six, eight)
+  const int waves = local   ? std::max(p->min_waves, 4)
+                    : one_w ? std::max(p->min_waves, ck ? 8 : 4)
+                            : p->min_waves;
   const int ns = host_choose_split_waves(p->num_sms, occ, units, g->n_src, per_split, avail, waves);
   if (ns < 1) return fail(QBX_ENOMEM, "workspace too small for the apply partial sums");
   if (group ? (ck ? group_smem_cplx(ops, pp, rg) : group_smem_real(ops, pp, rg)) > 220 * 1024
