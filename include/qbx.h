@@ -248,6 +248,18 @@ int qbx_apply(qbx_plan *plan, const qbx_geom *g, int op, int side, int limit, qb
 int qbx_apply_ops(qbx_plan *plan, const qbx_geom *g, int ops, int side, int limit, qbx_c64 k, int p,
                   const qbx_c64 *const dens[3], int nrhs, qbx_c64 *const out[3], void *stream);
 
+/* The combined-field operator of the exterior Dirichlet problem without its
+ * identity term (Sec. 4.2, the integral equation (1/2 I + D - i eta S) mu =
+ * f): out = (D - i eta S) mu, both operators as two-sided QBX averages
+ * (qbx_apply_ops with side QBX_SIDE_TWO and dens[S] = dens[D] = mu, then
+ * out[D] - i eta out[S]), with the two kernel values of each (centre, source)
+ * pair combined before they multiply the right-hand sides: one complex
+ * multiply-add per pair and rhs instead of two.  dens, out: [n_tgt][nrhs]
+ * interleaved complex, device.  eta finite, else QBX_EINVAL.  Needs
+ * qbx_workspace_bytes(n_src, n_ctr, 1, nrhs). */
+int qbx_apply_cfie(qbx_plan *plan, const qbx_geom *g, qbx_c64 k, qbx_c64 eta, int p, const qbx_c64 *dens,
+                   int nrhs, qbx_c64 *out, void *stream);
+
 /* Near-only QBX (the optimisation remarked in Sec. 5: direct evaluation for
  * distant interactions, QBX for near ones): as qbx_apply_ops, except that a
  * source node with |x_s - c| >= eta r_c goes through the smooth rule at the
@@ -335,7 +347,8 @@ size_t qbx_shape_adjoint_workspace_bytes(int M, int q_tgt, int q_src, int p, int
  * two-sided averages (Sec. 3.5: two-sided averaging gives a spectrum that
  * clusters at zero), unknowns scaled by sqrt(w) (Sec. 4.2), by restarted
  * GMRES(restart) for nrhs right-hand sides f [n_tgt][nrhs] at once (every
- * system its own Krylov space; one S+D apply per iteration serves all).
+ * system its own Krylov space; one combined-field apply per iteration,
+ * qbx_apply_cfie, serves all).
  * Arnoldi by classical Gram-Schmidt with re-orthogonalisation, the Givens
  * rotations, the residual estimates, the convergence test and the
  * back-substitution all run on the device; the host waits once per restart
@@ -353,7 +366,8 @@ int qbx_solve_exterior_dirichlet(qbx_plan *plan, const qbx_geom *g, qbx_c64 k, q
 /* Vector kernels of the solve, also usable on their own.  Vectors are
  * [n][nrhs] complex device arrays; bases [nv][n][nrhs].
  *   qbx_vec_scale_sqrtw: out = in * sqrt(w) (inverse = 0) or in / sqrt(w).
- *   qbx_cfie_combine: y = sqrt(w) (xden/2 + dmu - i eta smu).
+ *   qbx_cfie_combine: y = sqrt(w) (xden/2 + dmu - i eta smu); smu may be NULL,
+ *     dmu then holding (D - i eta S) mu (qbx_apply_cfie).
  *   qbx_vec_dots: out[j][r] = sum_i conj(V_j[i][r]) w[i][r], j < nv <= 65535
  *     (fixed reduction order); work needs qbx_vec_dots_work_bytes(nrhs, nv) bytes.
  *   qbx_vec_orth_update: w -= sum_j V_j h[j][r].

@@ -31,7 +31,9 @@
 
 namespace qbx {
 
-enum { OPB_S = 1, OPB_D = 2, OPB_G = 4, OPB_X = 8 };
+// OPB_C: the combined field D - i eta S of one density (Sec. 4.2), one
+// component; formed per pair in the group kernel only
+enum { OPB_S = 1, OPB_D = 2, OPB_G = 4, OPB_X = 8, OPB_C = kOpsCombined };
 
 // Near-field-first work order: rank r of a launch takes, for the centre
 // block whose middle target is tmid, the source split at offset 0, +1, -1,
@@ -191,9 +193,10 @@ template <> struct KW<cplx> {
 __host__ __device__ constexpr int popc3(int m) { return (m & 1) + ((m >> 1) & 1) + ((m >> 2) & 1); }
 // several accumulator sets per rhs: at most 4 rhs per launch
 __host__ __device__ constexpr bool multi_op(int m) { return popc3(m) > 1 || (m & 8) != 0; }
-// partial-sum components: S -> 1, D -> 1, grad S -> 2, grad_{x_s} S -> 2 (in this order)
+// partial-sum components: S -> 1, D -> 1, grad S -> 2, grad_{x_s} S -> 2 (in this order),
+// D - i eta S -> 1
 __host__ __device__ constexpr int ops_ncomp(int m) {
-  return (m & 1) + ((m >> 1) & 1) + 2 * ((m >> 2) & 1) + 2 * ((m >> 3) & 1);
+  return (m & 1) + ((m >> 1) & 1) + 2 * ((m >> 2) & 1) + 2 * ((m >> 3) & 1) + ((m >> 4) & 1);
 }
 // D (or the source-position gradient) taken from grad S's A and B sums (the
 // operator sets with grad S and one of them) reads the true J_{p+1} in the

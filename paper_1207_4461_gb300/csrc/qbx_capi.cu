@@ -598,10 +598,12 @@ int qbx_far(qbx_plan* p, const qbx_geom* g, int op, qbx_c64 k, const qbx_c64* wd
 // all of them), plus far targets when a single operator is requested.
 // tangent: the R operator (Sec. 3.2, eq. riesz-def): the D sums with the
 // source tangents in place of the normals, and no jump (ops must be D alone).
+// cf_eta: the combined field (D - i eta S) mu of one density on both sides
+// (Sec. 4.2), formed per pair (group kernel, one component) into out[1].
 static int apply_impl(qbx_plan* p, const qbx_geom* g, int ops, int side, int limit, qbx_c64 k, int pp,
                       const qbx_c64* const dens[3], int nrhs, qbx_c64* const out[3], int n_far,
                       const double* x_far, qbx_c64* out_far, void* stream, bool tangent = false,
-                      double eta = 0.0) {
+                      double eta = 0.0, const qbx_c64* cf_eta = nullptr) {
   if (int rc = check_plan(p)) return rc;
   if (int rc = check_geom(p, g, true)) return rc;
   if (ops < 1 || ops > 7) return fail(QBX_EINVAL, "operator set %d is not a non-empty subset of {S, D, grad S}", ops);
@@ -609,17 +611,30 @@ static int apply_impl(qbx_plan* p, const qbx_geom* g, int ops, int side, int lim
   if (int rc = check_k(k)) return rc;
   if (int rc = check_p(pp)) return rc;
   if (nrhs < 1) return fail(QBX_EINVAL, "nrhs = %d < 1", nrhs);
-  for (int o = 0; o < 3; ++o)
-    if ((ops >> o & 1) && (!dens[o] || !out[o])) return fail(QBX_EINVAL, "NULL density or output of operator %d", o);
+  const bool cf = cf_eta != nullptr;
+  if (cf) {
+    if (ops != (QBX_OPS_S | QBX_OPS_D) || side != QBX_SIDE_TWO || dens[0] != dens[1] || n_far != 0 || tangent ||
+        eta > 0.0)
+      return fail(QBX_EINVAL, "combined field: S and D of one density, both sides, no far targets");
+    if (!isfinite(cf_eta->re) || !isfinite(cf_eta->im)) return fail(QBX_EINVAL, "eta is not finite");
+    if (!dens[0] || !out[1]) return fail(QBX_EINVAL, "NULL density or output");
+  } else {
+    for (int o = 0; o < 3; ++o)
+      if ((ops >> o & 1) && (!dens[o] || !out[o])) return fail(QBX_EINVAL, "NULL density or output of operator %d", o);
+  }
   if (n_far < 0) return fail(QBX_EINVAL, "n_far < 0");
   if (n_far > 0 && (!x_far || !out_far)) return fail(QBX_EINVAL, "n_far > 0 needs x_far and out_far");
   int c0, nc;
   if (int rc = side_range(side, g->n_tgt, &c0, &nc)) return rc;
-  // components of a partial-sum row: S 1, D 1, grad S 2
+  // components of a partial-sum row: S 1, D 1, grad S 2 (the combined field 1)
   int comp0[3], ncomp = 0;
   for (int o = 0; o < 3; ++o) {
     comp0[o] = ncomp;
     if (ops >> o & 1) ncomp += (o == QBX_OP_GRAD_S) ? 2 : 1;
+  }
+  if (cf) {
+    comp0[0] = comp0[1] = 0;
+    ncomp = 1;
   }
   // one oversampled density per distinct input array
   const qbx_c64* distinct[3];
@@ -640,7 +655,8 @@ static int apply_impl(qbx_plan* p, const qbx_geom* g, int ops, int side, int lim
   // many right-hand sides of one density: the group kernel (kernel values
   // formed once per pair for all rhs); otherwise the fused kernel
   const bool ck = k.im != 0.0;
-  const bool group = nrhs >= 16 && nd == 1 && (ops == 1 || ops == 2 || ops == 3 || ops == 7);
+  const bool group = cf || (nrhs >= 16 && nd == 1 && (ops == 1 || ops == 2 || ops == 3 || ops == 7));
+  const int gops = cf ? kOpsCombined : ops;   // the group kernel's operator set
   // more than 32 rhs (global apply): eight warps of 8 rhs, so that the kernel
   // values of a pair are formed once per 64 rhs instead of once per 32
   const int rg = (nrhs > 32 && !(eta > 0.0)) ? kGrpRhsWide : 8;
@@ -652,7 +668,7 @@ static int apply_impl(qbx_plan* p, const qbx_geom* g, int ops, int side, int lim
   CK(cudaSetDevice(p->device), "cudaSetDevice");
   int occ;
   if (group && local) occ = group_occupancy_local(ops, ck, pp, rg);
-  else if (group) occ = ck ? group_occupancy_cplx(ops, pp, rg) : group_occupancy_real(ops, pp, rg);
+  else if (group) occ = ck ? group_occupancy_cplx(gops, pp, rg) : group_occupancy_real(gops, pp, rg);
   else if (local) occ = apply_occupancy_local(ops, ck, pp, std::min(chunk, nrhs), one_w);
   else occ = ck ? apply_occupancy_cplx(ops, pp, std::min(chunk, nrhs), one_w)
                 : apply_occupancy_real(ops, pp, std::min(chunk, nrhs), one_w);
@@ -668,7 +684,7 @@ static int apply_impl(qbx_plan* p, const qbx_geom* g, int ops, int side, int lim
                             : p->min_waves;
   const int ns = host_choose_split_waves(p->num_sms, occ, units, g->n_src, per_split, avail, waves);
   if (ns < 1) return fail(QBX_ENOMEM, "workspace too small for the apply partial sums");
-  if (group ? (ck ? group_smem_cplx(ops, pp, rg) : group_smem_real(ops, pp, rg)) > 220 * 1024
+  if (group ? (ck ? group_smem_cplx(gops, pp, rg) : group_smem_real(gops, pp, rg)) > 220 * 1024
             : apply_smem_bytes(ops, ck, pp, chunk) > 220 * 1024)
     return fail(QBX_EINVAL, "p = %d too large", pp);
   cudaStream_t st = (cudaStream_t)stream;
@@ -719,9 +735,13 @@ static int apply_impl(qbx_plan* p, const qbx_geom* g, int ops, int side, int lim
   }
   if (group) {
     GroupArgs ga{};
-    ga.ops = ops;
+    ga.ops = gops;
     ga.p = pp;
     ga.nrhs = nrhs;
+    if (cf) {
+      ga.cf_re = cf_eta->re;
+      ga.cf_im = cf_eta->im;
+    }
     GroupInst& in = ga.inst0;
     in.kre = k.re;
     in.kim = k.im;
@@ -761,7 +781,14 @@ static int apply_impl(qbx_plan* p, const qbx_geom* g, int ops, int side, int lim
     }
   }
   if (p->timing) CK(cudaEventRecord(p->ev1, st), "timing event");
-  // a7: reduce, i/4, jumps / two-sided average, per operator
+  // a7: reduce, i/4, jumps / two-sided average, per operator (the combined
+  // field: one finish, the two-sided average as for S and D)
+  if (cf) {
+    CK(launch_apply_finish(QBX_OP_S, side, limit, g->n_tgt, ns, nc, nrhs, 0, 1, part, dens[0], g->tgt_nx,
+                           g->tgt_ny, out[1], p->d_status, st),
+       "apply finish");
+    return QBX_OK;
+  }
   for (int o = 0; o < 3; ++o) {
     if (!(ops >> o & 1)) continue;
     CK(launch_apply_finish(tangent ? QBX_OP_S : o, side, limit, g->n_tgt, ns, nc, nrhs, comp0[o], ncomp, part,
@@ -947,6 +974,14 @@ int qbx_apply_ops(qbx_plan* p, const qbx_geom* g, int ops, int side, int limit, 
                   const qbx_c64* const dens[3], int nrhs, qbx_c64* const out[3], void* stream) {
   if (!dens || !out) return fail(QBX_EINVAL, "NULL density or output table");
   return apply_impl(p, g, ops, side, limit, k, pp, dens, nrhs, out, 0, nullptr, nullptr, stream);
+}
+
+int qbx_apply_cfie(qbx_plan* p, const qbx_geom* g, qbx_c64 k, qbx_c64 eta, int pp, const qbx_c64* dens, int nrhs,
+                   qbx_c64* out, void* stream) {
+  const qbx_c64* const d3[3] = {dens, dens, nullptr};
+  qbx_c64* const o3[3] = {nullptr, out, nullptr};
+  return apply_impl(p, g, QBX_OPS_S | QBX_OPS_D, QBX_SIDE_TWO, QBX_LIMIT_ONE_SIDED, k, pp, d3, nrhs, o3, 0,
+                    nullptr, nullptr, stream, false, 0.0, &eta);
 }
 
 int qbx_assign_centres(qbx_plan* p, const qbx_geom* g, int side, int n, const double* xy, int* out,

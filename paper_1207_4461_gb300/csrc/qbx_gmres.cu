@@ -29,14 +29,16 @@ __global__ void k_scale_sqrtw(int n, int nrhs, const double* w, const cplx* in, 
   out[idx] = (inverse ? 1.0 / s : s) * in[idx];
 }
 
-// y = sqrt(w) * (x_density / 2 + D - i eta S), x_density = x / sqrt(w)
+// y = sqrt(w) * (x_density / 2 + D - i eta S), x_density = x / sqrt(w);
+// s == NULL: d holds (D - i eta S) x_density
 __global__ void k_cfie_combine(int n, int nrhs, const double* w, const cplx* xden, const cplx* d, const cplx* s,
                                double eta_re, double eta_im, cplx* y) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= n * nrhs) return;
   const double sw = sqrt(w[idx / nrhs]);
   const cplx ie = cplx{-eta_im, eta_re};   // i eta
-  const cplx v = 0.5 * xden[idx] + d[idx] - ie * s[idx];
+  cplx v = 0.5 * xden[idx] + d[idx];
+  if (s) v = v - ie * s[idx];
   y[idx] = sw * v;
 }
 
@@ -138,7 +140,7 @@ int qbx_vec_scale_sqrtw(int n, int nrhs, const double* w, const qbx_c64* in, qbx
 
 int qbx_cfie_combine(int n, int nrhs, const double* w, const qbx_c64* xden, const qbx_c64* dmu,
                      const qbx_c64* smu, qbx_c64 eta, qbx_c64* y, void* stream) {
-  if (n < 0 || nrhs < 1 || !w || !xden || !dmu || !smu || !y) return gfail(QBX_EINVAL, "bad arguments to qbx_cfie_combine");
+  if (n < 0 || nrhs < 1 || !w || !xden || !dmu || !y) return gfail(QBX_EINVAL, "bad arguments to qbx_cfie_combine");
   if (n == 0) return QBX_OK;
   k_cfie_combine<<<blocks((long)n * nrhs), 256, 0, (cudaStream_t)stream>>>(
       n, nrhs, w, (const cplx*)xden, (const cplx*)dmu, (const cplx*)smu, eta.re, eta.im, (cplx*)y);
@@ -412,7 +414,7 @@ __global__ void k_sub(long nel, const cplx* f, const cplx* w, cplx* out) {
 }  // namespace
 
 // Adense: the sqrt-weighted matrix from qbx_assemble_cfie (column-major), or
-// NULL for matrix-free matvecs through qbx_apply_ops.
+// NULL for matrix-free matvecs through qbx_apply_cfie.
 static int solve_impl(qbx_plan* plan, const qbx_geom* g, qbx_c64 k, qbx_c64 eta, int p, const qbx_c64* Adense,
                       const qbx_c64* f, int nrhs, double tol, int restart, int maxiter, qbx_c64* mu, int* iters,
                       double* resid, void* stream) {
@@ -424,7 +426,7 @@ static int solve_impl(qbx_plan* plan, const qbx_geom* g, qbx_c64 k, qbx_c64 eta,
   const int m = restart;
   const size_t zw = Adense ? qbx_matmul_cm_work_bytes(n, nrhs) : 0;
   if (Adense && zw == 0) return gfail(QBX_ECUDA, "matrix product set-up failed");
-  Dev V, W, X, F, DEN, SM, DM, WORK, ST, ZW, CTL;
+  Dev V, W, X, F, DEN, DM, WORK, ST, ZW, CTL;
   // small state: h1, h2 [(m+1)][nrhs], hn [nrhs], Hm [(m+1)][m][nrhs], cs, sn [m][nrhs],
   // gv [(m+1)][nrhs], y [m][nrhs] (complex); fnorm, rel, scl [nrhs] (real)
   const size_t nst = (size_t)nrhs * (2 * (m + 1) + 1 + (size_t)(m + 1) * m + 2 * m + (m + 1) + m);
@@ -433,8 +435,7 @@ static int solve_impl(qbx_plan* plan, const qbx_geom* g, qbx_c64 k, qbx_c64 eta,
   if (e == cudaSuccess) e = cudaMalloc(&X.p, vec * 16);
   if (e == cudaSuccess) e = cudaMalloc(&F.p, vec * 16);
   if (e == cudaSuccess) e = cudaMalloc(&DEN.p, vec * 16);
-  if (e == cudaSuccess && !Adense) e = cudaMalloc(&SM.p, vec * 16);   // (S and D outputs of the apply)
-  if (e == cudaSuccess && !Adense) e = cudaMalloc(&DM.p, vec * 16);
+  if (e == cudaSuccess && !Adense) e = cudaMalloc(&DM.p, vec * 16);   // (D - i eta S) of the density
   if (e == cudaSuccess) e = cudaMalloc(&WORK.p, qbx_vec_dots_work_bytes(nrhs, m + 1));
   if (e == cudaSuccess) e = cudaMalloc(&ST.p, nst * 16 + 3 * (size_t)nrhs * 8);
   if (e == cudaSuccess && Adense) e = cudaMalloc(&ZW.p, zw);
@@ -464,17 +465,15 @@ static int solve_impl(qbx_plan* plan, const qbx_geom* g, qbx_c64 k, qbx_c64 eta,
   // scaled right-hand side and initial guess: f~ = sqrt(w) f, x~ = sqrt(w) mu
   if ((rc = qbx_vec_scale_sqrtw(n, nrhs, g->tgt_w, f, (qbx_c64*)F.p, 0, stream))) return rc;
   if ((rc = qbx_vec_scale_sqrtw(n, nrhs, g->tgt_w, mu, (qbx_c64*)X.p, 0, stream))) return rc;
-  const int ops = QBX_OPS_S | QBX_OPS_D;
-  // y = A~ x~ : density x~/sqrt(w), S and D two-sided in one pass, combine;
-  // or one complex matrix product with the assembled A~ (qbx_matmul_cm)
+  // y = A~ x~ : density x~/sqrt(w), (D - i eta S) two-sided with the two
+  // kernel values of each pair combined (qbx_apply_cfie), plus x/2; or one
+  // complex matrix product with the assembled A~ (qbx_matmul_cm)
   auto matvec = [&](const qbx_c64* xs, qbx_c64* y, cudaStream_t s) -> int {
     int r;
     if (Adense) return qbx_matmul_cm(n, nrhs, Adense, xs, y, ZW.p, zw, s);
     if ((r = qbx_vec_scale_sqrtw(n, nrhs, g->tgt_w, xs, (qbx_c64*)DEN.p, 1, s))) return r;
-    const qbx_c64* dens[3] = {(qbx_c64*)DEN.p, (qbx_c64*)DEN.p, nullptr};
-    qbx_c64* outs[3] = {(qbx_c64*)SM.p, (qbx_c64*)DM.p, nullptr};
-    if ((r = qbx_apply_ops(plan, g, ops, QBX_SIDE_TWO, QBX_LIMIT_ONE_SIDED, k, p, dens, nrhs, outs, s))) return r;
-    return qbx_cfie_combine(n, nrhs, g->tgt_w, (qbx_c64*)DEN.p, (qbx_c64*)DM.p, (qbx_c64*)SM.p, eta, y, s);
+    if ((r = qbx_apply_cfie(plan, g, k, eta, p, (qbx_c64*)DEN.p, nrhs, (qbx_c64*)DM.p, s))) return r;
+    return qbx_cfie_combine(n, nrhs, g->tgt_w, (qbx_c64*)DEN.p, (qbx_c64*)DM.p, nullptr, eta, y, s);
   };
   // one Arnoldi step on stream s, every kernel gated by the control block:
   // V_j -> W, W = A~ W, W -> V_{j+1}, CGS2 against V_0..V_j, the norm, the

@@ -26,8 +26,8 @@ namespace qbx {
 // memory as three real planes.  Otherwise four FMAs per complex product.
 template <int OPS, typename T, int RG, int W = kGrpWarps>
 struct GroupSmem {
-  static constexpr int kNc = ops_ncomp(OPS);   // raw components: S 1, D 1, grad S 2
-  static constexpr bool kD = OPS & OPB_D, kG = OPS & OPB_G;
+  static constexpr int kNc = ops_ncomp(OPS);   // raw components: S 1, D 1, grad S 2; D - i eta S 1
+  static constexpr bool kD = (OPS & OPB_D) || (OPS & OPB_C), kG = OPS & OPB_G;
   static constexpr bool k3M = kNc <= 2;
   static constexpr int kVal = k3M ? 24 : 16;   // bytes per stored complex value
   static __host__ __device__ int nslots() { return 1 + ((kD || kG) ? 1 : 0) + (kG ? 1 : 0); }
@@ -43,12 +43,16 @@ struct GroupSmem {
 // LOCAL: near-only QBX (sources at |x_s - c| >= eta r by the smooth rule at
 // the target, pair_direct), a separate instance.  W warps per CTA: W RG rhs
 // per pass (kernel values are formed once per pass; W = 8 serves 64 rhs in
-// one pass, the GMRES matvec's count).
+// one pass, the GMRES matvec's count).  OPS = OPB_C: the S and D kernel
+// values of a pair are combined into D - i eta S before phase 2, so the
+// rhs products are one complex multiply-add per rhs instead of two.
 template <int OPS, typename T, int RG, bool LOCAL = false, int W = kGrpWarps>
 __global__ void __launch_bounds__(kGrpCentres * W)
 k_apply_group(GroupArgs a) {
   using L = GroupSmem<OPS, T, RG, W>;
-  constexpr bool kS = OPS & OPB_S, kD = OPS & OPB_D, kG = OPS & OPB_G;
+  constexpr bool kC = OPS & OPB_C;
+  constexpr int PK = kC ? (OPB_S | OPB_D) : OPS;   // the pair kernels formed
+  constexpr bool kS = PK & OPB_S, kD = PK & OPB_D, kG = PK & OPB_G;
   constexpr int kNc = L::kNc;
   constexpr int kRP = W * RG;   // rhs per pass
   constexpr bool k3M = L::k3M;
@@ -136,7 +140,7 @@ k_apply_group(GroupArgs a) {
           colG[l * kGrpCentres] = (l == 0) ? rmul(jn, -1.0) : sc_sub(jp, jn);
         }
       }
-      if (!keeps_jp1(OPS)) {
+      if (!keeps_jp1(PK)) {
         T z0;
         sc_zero(z0);
         colJ[(p + 1) * kGrpCentres] = z0;
@@ -192,10 +196,10 @@ k_apply_group(GroupArgs a) {
           }
           cplx GS, K, GA, GB, EX, EY;
           if (LOCAL && fma(dx, dx, dy * dy) >= lim2) {   // near-only QBX: a distant source
-            pair_direct<OPS, T>(kw, kk, r * ux - dx, r * uy - dy, nx, ny, ux, uy, r, GS, K, GA, GB);
+            pair_direct<PK, T>(kw, kk, r * ux - dx, r * uy - dy, nx, ny, ux, uy, r, GS, K, GA, GB);
           } else {
-            pair_kernels<OPS, T, kGrpCentres>(kw, kk, J0, kneg_j0, colJ, colL, colG, p, dx, dy, nx, ny, ux,
-                                              uy, ir, GS, K, GA, GB, EX, EY);
+            pair_kernels<PK, T, kGrpCentres>(kw, kk, J0, kneg_j0, colJ, colL, colG, p, dx, dy, nx, ny, ux,
+                                             uy, ir, GS, K, GA, GB, EX, EY);
           }
           auto put = [&](int q, cplx v) {
             const int idx = (q * kGrpTile + j) * kGrpCentres + lane;
@@ -207,12 +211,18 @@ k_apply_group(GroupArgs a) {
               s_kv[idx] = v;
             }
           };
-          int q = 0;
-          if (kS) put(q++, GS);
-          if (kD) put(q++, K);
-          if (kG) {
-            put(q++, GA);
-            put(q++, GB);
+          if constexpr (kC) {
+            // K - (i eta) GS, i eta = (-eta_im, eta_re)
+            put(0, cplx{fma(a.cf_im, GS.re, fma(a.cf_re, GS.im, K.re)),
+                        fma(a.cf_im, GS.im, fma(-a.cf_re, GS.re, K.im))});
+          } else {
+            int q = 0;
+            if (kS) put(q++, GS);
+            if (kD) put(q++, K);
+            if (kG) {
+              put(q++, GA);
+              put(q++, GB);
+            }
           }
         }
         __syncthreads();
@@ -260,6 +270,10 @@ k_apply_group(GroupArgs a) {
           const int rr = r0 + warp * RG + g;
           if (rr >= a.nrhs) break;
           int q = 0;
+          if (kC) {
+            part[row * a.nrhs + rr] = acc[0][g];
+            continue;
+          }
           if (kS) {
             part[(row + q) * a.nrhs + rr] = acc[q][g];
             ++q;
@@ -297,6 +311,7 @@ static cudaError_t launch_group_t(const GroupArgs& a, int grid, cudaStream_t st)
     case OPB_D: X(OPB_D, T, RG);                                         \
     case OPB_S | OPB_D: X(OPB_S | OPB_D, T, RG);                         \
     case OPB_S | OPB_D | OPB_G: X(OPB_S | OPB_D | OPB_G, T, RG);         \
+    case OPB_C: X(OPB_C, T, RG);                                         \
     default: break;                                                      \
   }
 

@@ -167,6 +167,8 @@ namespace qbx {
 constexpr int kGrpCentres = 32;   // centres per CTA (one per lane)
 constexpr int kGrpWarps = 4;      // warps per CTA: rhs groups in phase 2
 constexpr int kGrpRhsWide = 64;   // the rg code of the eight-warp instances (64 rhs per pass)
+// the group kernel's operator set of the combined field D - i eta S (OPB_C)
+constexpr int kOpsCombined = 16;
 constexpr int kGrpTile = 32;      // sources per shared-memory tile
 
 // One curve of a batch (or the single curve of a many-rhs apply).
@@ -198,6 +200,7 @@ struct GroupArgs {
   int st_units, st_nsplit, st_split_len;   // static mode (items == nullptr): one instance
   double eta2;                    // near-only QBX (> 0): sources with |x_s - c|^2 >= eta2 r^2 by the
                                   // smooth rule at the target; 0: all through the expansion
+  double cf_re, cf_im;            // ops == OPB_C: eta of the combined field D - i eta S
 };
 cudaError_t launch_group_real(const GroupArgs& a, int rg, int grid, cudaStream_t st);
 cudaError_t launch_group_cplx(const GroupArgs& a, int rg, int grid, cudaStream_t st);

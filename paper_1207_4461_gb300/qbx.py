@@ -81,6 +81,8 @@ def lib():
             L.qbx_assign_centres.argtypes = [_P, G, I, I, _P, _P, _P]
             L.qbx_apply_ops.argtypes = [_P, G, I, I, I, c64, I, ctypes.POINTER(_P), I, ctypes.POINTER(_P), _P]
             L.qbx_apply_ops.restype = I
+            L.qbx_apply_cfie.argtypes = [_P, G, c64, c64, I, _P, I, _P, _P]
+            L.qbx_apply_cfie.restype = I
             L.qbx_batch_create.argtypes = [PP, _P, I, G, ctypes.POINTER(c64), I, I, I, I, I,
                                            ctypes.POINTER(_P), ctypes.POINTER(_P)]
             L.qbx_batch_apply.argtypes = [_P, _P]
@@ -601,6 +603,20 @@ def qbx_apply_ops(plan: Plan, g: Geometry, ops, side, limit, k, p, dens, out=Non
         _check(lib().qbx_apply_local(plan.handle, g.ref(), mask, side, limit, _k(k), p, float(eta), dp, nrhs, op_,
                                      _stream()))
     return {o: out[o] for o in ops}
+
+
+def qbx_apply_cfie(plan: Plan, g: Geometry, k, eta, p, dens, out=None):
+    """(D - i eta S) dens on both sides, the two kernel values of each pair
+    combined before the rhs products (qbx_apply_cfie).  dens: [n_tgt] or
+    [n_tgt][nrhs] complex128 device tensor; returns [n_tgt][nrhs]."""
+    d = _dens2d(dens, g.n_tgt)
+    nrhs = d.shape[1]
+    if out is None:
+        out = torch.empty((g.n_tgt, nrhs), dtype=torch.complex128, device=d.device)
+    e = complex(eta)
+    _check(lib().qbx_apply_cfie(plan.handle, g.ref(), _k(k), c64(e.real, e.imag), p, _ptr(d), nrhs, _ptr(out),
+                                _stream()))
+    return out
 
 
 class Batch:

@@ -247,6 +247,33 @@ def test_gmres_full_size_right_angle_teardrop(cuda):
     assert err < 1e-4
 
 
+@pytest.mark.parametrize("k,eta,nrhs", [(5.0, 5.0, 1), (5.0, 2 - 1j, 5), (3 + 0.4j, 3.0, 40), (6.0, 6.0, 70)])
+def test_apply_cfie_matches_oracle(cuda, k, eta, nrhs):
+    """qbx_apply_cfie, the GMRES matvec's operator: (D - i eta S) mu on both
+    sides with the two kernel values of each pair combined before the rhs
+    products, against the oracle's two-sided D and S, and against
+    qbx_apply_ops' separate S and D outputs combined afterwards; 1, 5, 40
+    and 70 rhs (passes of 32 and of 64 rhs), complex k and complex eta."""
+    cur = W.teardrop()
+    edges = W.dyadic_edges(12, 2)
+    M = len(edges) - 1
+    p = 8
+    plan = qbx.Plan(16, 64, n_src=M * 64, n_ctr=2 * M * 16, ncoef=4, nrhs=nrhs)
+    g = qbx.qbx_geometry(plan, cur, edges)
+    go = oracle.geometry(cur, edges, 16, 64)
+    dens = W.complex_gaussian(41, g.n_tgt * nrhs).reshape(g.n_tgt, nrhs)
+    got = qbx.qbx_apply_cfie(plan, g, k, eta, p, dev(dens))
+    sep = qbx.qbx_apply_ops(plan, g, (qbx.OP_S, qbx.OP_D), qbx.SIDE_TWO, 0, k, p, dev(dens))
+    qbx.qbx_sync_status(plan)
+    got = got.cpu().numpy()
+    comb = (sep[qbx.OP_D] - 1j * eta * sep[qbx.OP_S]).cpu().numpy()
+    assert np.abs(got - comb).max() / np.abs(comb).max() < 1e-13
+    S = oracle.apply(go, oracle.OP_S, oracle.SIDE_TWO, 0, k, p, dens)
+    D = oracle.apply(go, oracle.OP_D, oracle.SIDE_TWO, 0, k, p, dens)
+    ref = D - 1j * eta * S
+    assert np.abs(got - ref).max() / np.abs(ref).max() < 1e-11
+
+
 @pytest.mark.parametrize("k,right_angle", [(5.0, False), (3 + 0.4j, False), (5.0, True)])
 def test_assembled_matrix_matches_oracle(cuda, k, right_angle):
     """qbx_assemble_cfie: the sqrt-weighted matrix of 1/2 + D - i eta S

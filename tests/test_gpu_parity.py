@@ -327,6 +327,28 @@ def test_deterministic_and_stream_ordered(cuda):
     assert torch.equal(a, b)
 
 
+@pytest.mark.parametrize("k", [14.0, 6 + 0.8j])
+def test_source_split_count_leaves_the_result(cuda, k):
+    """The source splits (more waves of CTAs, each over fewer sources) change
+    only the order of the sums: one density, S + D + grad S in one pass, the
+    same values for 1, 8, 16 and 64 requested waves (the one-density apply
+    takes at least 4, 8 at complex k) and against the oracle."""
+    p = 10
+    plan, g, go = make(W.starfish(), 48, p=p)
+    dens = W.complex_gaussian(5, g.n_tgt).reshape(g.n_tgt, 1)
+    ops = (qbx.OP_S, qbx.OP_D, qbx.OP_GRAD_S)
+    outs = []
+    for waves in (1, 8, 16, 64):
+        qbx.qbx_plan_set_min_waves(plan, waves)
+        outs.append(qbx.qbx_apply_ops(plan, g, ops, qbx.SIDE_TWO, 0, k, p, dev(dens)))
+    qbx.qbx_sync_status(plan)
+    for op in ops:
+        ref = oracle.apply(go, op, oracle.SIDE_TWO, 0, k, p, dens)
+        for out in outs:
+            assert rel(out[op], ref) < TOL, op
+            assert rel(out[op], outs[0][op].cpu().numpy()) < 1e-13, op
+
+
 def test_single_panel_and_order_zero(cuda):
     plan, g, go = make(W.circle(1.0), 1, q_tgt=16, q_src=64)
     dens = W.density_cfg1(g.t_tgt)
