@@ -69,24 +69,24 @@ def flops_per_pair_ops(ops, p, nrhs=1):
 # on the full-size starfish workload, from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum); valid only for the kernel
 # sources it was taken with, identified by their hash.
-TRAFFIC = {"b3debfcd29007c92": 1.438e6}   # profiles/k_apply_fused_S_D_gradS_starfish_M256_dram.md
+TRAFFIC = {"27706399748d3043": 1.667e6}   # profiles/k_apply_fused_S_D_gradS_starfish_M256_dram.md
 KERNEL_SOURCES = ["qbx_apply_impl.cuh", "qbx_device.cuh", "special_tables.h", "qbx_apply_real.cu"]
 GROUP_SOURCES = ["qbx_group_impl.cuh", "qbx_apply_impl.cuh", "qbx_device.cuh", "special_tables.h"]
 # Hardware-counted FP64 operations per (centre, source) pair, 2 DFMA + DMUL +
 # DADD from ncu's smsp__sass_thread_inst_executed_op_{dfma,dmul,dadd}_pred_on
 # counters divided by the pairs of the captured launch, for the kernel
 # sources with the given hash (profiles/fp64_counts_fused_M128_and_group_batch4.md).
-HW_FP64_PER_PAIR = {"b3debfcd29007c92": 431.5}         # fused S + D + grad S, p = 12, one rhs
-HW_FP64_PER_PAIR_GROUP = {"616ccf9755323a4f": 732.9}   # group kernel, S + D, p = 10, 32 rhs
+HW_FP64_PER_PAIR = {"27706399748d3043": 434.9}         # fused S + D + grad S, p = 12, one rhs
+HW_FP64_PER_PAIR_GROUP = {"5b690bb633cedf23": 732.9}   # group kernel, S + D, p = 10, 32 rhs
 # sm__pipe_fp64_cycles_active (of peak) over the active and the elapsed
 # cycles, from the same captures (fused: 128-panel starfish, one wave;
 # group: the first 4 curves of the batch)
-HW_FP64_PIPE = {"b3debfcd29007c92": (0.922, 0.853)}
-HW_FP64_PIPE_GROUP = {"616ccf9755323a4f": (0.949, 0.927)}
+HW_FP64_PIPE = {"27706399748d3043": (0.922, 0.880)}
+HW_FP64_PIPE_GROUP = {"5b690bb633cedf23": (0.949, 0.926)}
 # the fused S + D + grad S apply at the complex wavenumber 20 + 1i (same
 # capture set-up: 128-panel starfish, p = 12, one rhs)
-HW_FP64_PER_PAIR_CPLX = {"b3debfcd29007c92": 718.3}
-HW_FP64_PIPE_CPLX = {"b3debfcd29007c92": (0.922, 0.789)}
+HW_FP64_PER_PAIR_CPLX = {"27706399748d3043": 726.4}
+HW_FP64_PIPE_CPLX = {"27706399748d3043": (0.923, 0.878)}
 
 
 def source_hash(names=KERNEL_SOURCES):

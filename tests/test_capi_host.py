@@ -56,6 +56,8 @@ def test_host_argument_errors_need_no_device():
     assert b"q_tgt" in L.qbx_last_error()
     assert L.qbx_apply(None, None, 0, 0, 0, qbx.c64(1.0, 0.0), 4, None, 1, 0, None, None, None, None) == 1
     assert b"plan" in L.qbx_last_error()
+    assert L.qbx_apply_cfie(None, None, qbx.c64(1.0, 0.0), qbx.c64(1.0, 0.0), 4, None, 1, None, None) == 1
+    assert b"plan" in L.qbx_last_error()
 
 
 def test_workspace_bytes_formula():
