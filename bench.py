@@ -391,7 +391,7 @@ def run_gpu(args, wl):
             "gpu_launches": args.steps * launches,
             "targets_per_s": world * len(wl.ops) * wl.n_tgt * wl.nrhs / (step_ms * 1e-3),
             "pairs_per_s": world * len(wl.ops) * pairs / (step_ms * 1e-3)}
-    if rank == 0 and not args.panels and not args.separate:
+    if rank == 0 and not args.separate:
         line["near_only"] = run_local_compare(args, qbx, torch, plan, g, codes, wl, dens, outs, flush, stream,
                                               step_ms)
     if rank == 0 and not args.panels and not args.separate and not args.k and not args.ops:
