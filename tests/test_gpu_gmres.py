@@ -324,6 +324,52 @@ def test_assembled_solve_matches_matrix_free(cuda):
     assert np.all(np.linalg.norm(sw * r, axis=0) / np.linalg.norm(sw * f, axis=0) <= 5e-11)
 
 
+@pytest.mark.parametrize("k,eta", [(3 + 0.4j, 3.0), (5.0, 2 + 1j)])
+def test_matrix_free_solve_complex_k_and_eta(cuda, k, eta):
+    """The matrix-free solve (every matvec one combined-field apply,
+    qbx_apply_cfie) at a complex wavenumber and at a complex coupling eta:
+    the same solution as the assembled solve and the oracle's residual
+    bound."""
+    cur, edges, plan, g, go, _, p = setup()
+    tx, ty = go["tgt_x"], go["tgt_y"]
+    f = np.stack([-np.exp(1j * k * tx), -np.exp(1j * k * (0.6 * tx + 0.8 * ty))], 1)
+    A = qbx.qbx_assemble_cfie(plan, g, k, eta, p)
+    mu_a, its_a, res_a = qbx.qbx_solve_exterior_dirichlet(plan, g, k, eta, p, dev(f), tol=1e-11, restart=40,
+                                                         maxiter=200, A=A)
+    mu_f, its_f, res_f = qbx.qbx_solve_exterior_dirichlet(plan, g, k, eta, p, dev(f), tol=1e-11, restart=40,
+                                                         maxiter=200)
+    assert np.all(res_a <= 1e-11) and np.all(res_f <= 1e-11)
+    assert abs(its_a - its_f) <= 2
+    mu_f = mu_f.cpu().numpy()
+    assert np.abs(mu_a.cpu().numpy() - mu_f).max() / np.abs(mu_f).max() < 1e-8
+    S = oracle.apply(go, oracle.OP_S, oracle.SIDE_TWO, 0, k, p, mu_f)
+    D = oracle.apply(go, oracle.OP_D, oracle.SIDE_TWO, 0, k, p, mu_f)
+    r = 0.5 * mu_f + D - 1j * eta * S - f
+    sw = np.sqrt(go["tgt_w"])[:, None]
+    assert np.all(np.linalg.norm(sw * r, axis=0) / np.linalg.norm(sw * f, axis=0) <= 5e-11)
+
+
+def test_apply_cfie_rejects_bad_arguments(cuda):
+    """Non-finite eta, a NULL array or too many rhs for the plan's workspace:
+    an error code and message, nothing launched."""
+    import ctypes
+    cur, edges, plan, g, go, k, p = setup()
+    L = qbx.lib()
+    d = torch.zeros((g.n_tgt, 1), dtype=torch.complex128, device="cuda")
+    o = torch.zeros_like(d)
+    st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    ptr = lambda t: ctypes.c_void_p(t.data_ptr())
+    assert L.qbx_apply_cfie(plan.handle, g.ref(), qbx.c64(k, 0.0), qbx.c64(float("nan"), 0.0), p, ptr(d), 1,
+                            ptr(o), st) == 1
+    assert b"eta" in L.qbx_last_error()
+    assert L.qbx_apply_cfie(plan.handle, g.ref(), qbx.c64(k, 0.0), qbx.c64(k, 0.0), p, None, 1, ptr(o), st) == 1
+    # 2^20 rhs need far more workspace than the plan holds: refused before any launch
+    assert L.qbx_apply_cfie(plan.handle, g.ref(), qbx.c64(k, 0.0), qbx.c64(k, 0.0), p, ptr(d), 1 << 20, ptr(o),
+                            st) == 7
+    assert b"workspace" in L.qbx_last_error()
+    qbx.qbx_sync_status(plan)
+
+
 @pytest.mark.parametrize("n,nrhs,nv", [(1000, 1, 3), (16391, 64, 41), (777, 3, 1), (300, 300, 2), (5, 100, 4)])
 def test_krylov_vector_kernels(cuda, n, nrhs, nv):
     """The GMRES vector kernels against torch: the inner products of every
