@@ -247,17 +247,18 @@ def test_gmres_full_size_right_angle_teardrop(cuda):
     assert err < 1e-4
 
 
-@pytest.mark.parametrize("k,eta,nrhs", [(5.0, 5.0, 1), (5.0, 2 - 1j, 5), (3 + 0.4j, 3.0, 40), (6.0, 6.0, 70)])
-def test_apply_cfie_matches_oracle(cuda, k, eta, nrhs):
+@pytest.mark.parametrize("k,eta,nrhs,p", [(5.0, 5.0, 1, 8), (5.0, 2 - 1j, 5, 8), (3 + 0.4j, 3.0, 40, 8),
+                                          (6.0, 6.0, 70, 8), (4.0, 4.0, 3, 0), (2 + 0.3j, 1.0, 33, 1)])
+def test_apply_cfie_matches_oracle(cuda, k, eta, nrhs, p):
     """qbx_apply_cfie, the GMRES matvec's operator: (D - i eta S) mu on both
     sides with the two kernel values of each pair combined before the rhs
     products, against the oracle's two-sided D and S, and against
-    qbx_apply_ops' separate S and D outputs combined afterwards; 1, 5, 40
-    and 70 rhs (passes of 32 and of 64 rhs), complex k and complex eta."""
+    qbx_apply_ops' separate S and D outputs combined afterwards; 1, 3, 5,
+    33, 40 and 70 rhs (passes of 32 and of 64 rhs), complex k and complex eta,
+    orders p = 0 and 1 (the D coefficients' end terms)."""
     cur = W.teardrop()
     edges = W.dyadic_edges(12, 2)
     M = len(edges) - 1
-    p = 8
     plan = qbx.Plan(16, 64, n_src=M * 64, n_ctr=2 * M * 16, ncoef=4, nrhs=nrhs)
     g = qbx.qbx_geometry(plan, cur, edges)
     go = oracle.geometry(cur, edges, 16, 64)

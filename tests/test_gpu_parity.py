@@ -342,6 +342,9 @@ def test_source_split_count_leaves_the_result(cuda, k):
         qbx.qbx_plan_set_min_waves(plan, waves)
         outs.append(qbx.qbx_apply_ops(plan, g, ops, qbx.SIDE_TWO, 0, k, p, dev(dens)))
     qbx.qbx_sync_status(plan)
+    for bad in (0, 65):
+        with pytest.raises(qbx.QBXError):
+            qbx.qbx_plan_set_min_waves(plan, bad)
     for op in ops:
         ref = oracle.apply(go, op, oracle.SIDE_TWO, 0, k, p, dens)
         for out in outs:
